@@ -1,0 +1,312 @@
+"""Benchmark: forward + adjoint cone-beam projector pair throughput (Gsamples/s).
+
+One step = forward projection P x of a clinical-size phantom followed by the
+backprojection P* of that projection (256x256x192 at 2 mm, 400 angles over 360
+deg, 512x384 panel at 0.8 mm, +160 mm lateral offset), inputs resident in HBM.
+A sample is one (ray, plane) pair of the Joseph sum; a step processes
+S_fwd + S_adj = 2 S_fwd samples.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank projects its own volume (the
+path shards by volume with no data-path collective: weak scaling); the max
+over ranks of the timed region is reported.
+--impl reference times the FP64 CPU checker (the only reference that exists:
+the paper ships no code) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "clinical"
+WORKLOAD_DESC = ("projector pair, 256x256x192 FP32 volume at 2 mm (40 seeded ellipsoids with bone/air inserts), "
+                 "400 angles over 360 deg, 512x384 panel at 0.8 mm, +160 mm offset, SID 1000 / SDD 1536 mm")
+METRIC = "fwd+adjoint projector Gsamples/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_reference(steps: int, warmup: int, sample_angles: int):
+    """FP64 CPU checker on a bounded sample: the clinical geometry restricted to
+    `sample_angles` evenly spaced angles (same volume, panel and ray count per
+    angle); throughput in Gsamples/s of forward + adjoint."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2512_21180_gb300 import inputs as I
+
+    g = I.geometry(WORKLOAD)
+    ang = 2 * np.pi * np.arange(0, g["n_angles"], g["n_angles"] // sample_angles)[:sample_angles] / g["n_angles"]
+    gs = dict(g)
+    gs["n_angles"] = len(ang)
+    G = O.Geom(gs, angles=ang)
+    vol = O.phantom(G, I.phantom_params(WORKLOAD, 2))
+    _, ns = O.forward(G, vol, return_count=True)
+    times = []
+    for it in range(warmup + steps):
+        t0 = time.perf_counter()
+        p = O.forward(G, vol)
+        O.adjoint(G, p)
+        dt = time.perf_counter() - t0
+        if it >= warmup:
+            times.append(dt)
+    mean = sum(times) / len(times)
+    return {"value": 2 * ns / mean / 1e9, "sec_per_step": mean, "samples_per_step": 2 * ns,
+            "cores": O.num_threads(), "angles": len(ang)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    r = cpu_reference(max(1, args.steps), args.warmup, args.ref_angles)
+    sample = (f"{r['angles']} of 400 evenly spaced angles of the clinical workload "
+              f"({r['samples_per_step'] / 1e9:.3f} G samples per forward+adjoint step)")
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": "Gsamples/s", "impl": "reference",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r["sec_per_step"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "sample": sample},
+        "cpu_baseline": {"value": r["value"], "unit": "Gsamples/s", "cores": r["cores"], "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": r["value"], "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--ref-angles", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2512_21180_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_2512_21180_gb300 import inputs as I
+    from paper_2512_21180_gb300 import projector as P
+    from paper_2512_21180_gb300 import ops
+
+    g = I.geometry(WORKLOAD)
+    geom = P.Geometry(g)
+    S_fwd = geom.count_samples()
+    samples_step = 2 * S_fwd
+    ell = I.phantom_params(WORKLOAD, 2 + rank)
+    vol = ops.phantom(geom, ell).unsqueeze(0)
+    proj = torch.empty((1,) + geom.proj_shape, device="cuda")
+    back = torch.empty((1,) + geom.vol_shape, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        P.forward_project(geom, vol, out=proj)
+        P.back_project(geom, proj, out=back)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # per-kernel timing on the launching stream, L2 flushed between steps (not timed)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for e0, e1, e2 in ev:
+        flush.fill_(1.0)
+        e0.record(stream)
+        P.forward_project(geom, vol, out=proj)
+        e1.record(stream)
+        P.back_project(geom, proj, out=back)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    t_fwd = [a.elapsed_time(b) for a, b, _ in ev]
+    t_adj = [b.elapsed_time(c) for _, b, c in ev]
+    ms = sum(f + a for f, a in zip(t_fwd, t_adj)) / args.steps
+    ms_fwd, ms_adj = sum(t_fwd) / args.steps, sum(t_adj) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms, ms_fwd, ms_adj], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_fwd, ms_adj = t.tolist()
+    value = samples_step * world / (ms * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers: pinned host volume in,
+    # backprojected volume out, copies inside the timed region
+    host_in = vol.cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    dvol = torch.empty_like(vol)
+    for _ in range(2):
+        dvol.copy_(host_in, non_blocking=True)
+        step()
+        host_out.copy_(back, non_blocking=True)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dvol.copy_(host_in, non_blocking=True)
+        P.forward_project(geom, dvol, out=proj)
+        P.back_project(geom, proj, out=back)
+        host_out.copy_(back, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = t.item()
+    e2e = samples_step * world / (ms_e2e * 1e-3) / 1e9
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    pk, pk_kind = peaks()
+    nvox = int(np.prod(geom.vol_shape))
+    nray = int(np.prod(geom.proj_shape))
+    # dominant kernel: the slower of the pair
+    dom = "back_project" if ms_adj >= ms_fwd else "forward_project"
+    ms_dom = max(ms_adj, ms_fwd)
+    roof = roofline(dom, ms_dom, S_fwd, nvox, nray, pk, pk_kind, clk)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "samples_per_step": samples_step,
+                   "l2": "flushed between timed steps (256 MiB write, untimed)",
+                   "ms_forward": ms_fwd, "ms_adjoint": ms_adj,
+                   "gsamples_s_forward": S_fwd / (ms_fwd * 1e-3) / 1e9,
+                   "gsamples_s_adjoint": S_fwd / (ms_adj * 1e-3) / 1e9},
+        "roofline": roof,
+        "e2e": {"value": e2e, "unit": "Gsamples/s", "h2d_bytes_per_step": nvox * 4, "d2h_bytes_per_step": nvox * 4},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        r = cpu_reference(1, 0, args.ref_angles)
+        line["cpu_baseline"] = {"value": r["value"], "unit": "Gsamples/s", "cores": r["cores"], "kind": "oracle",
+                                "sample": f"{r['angles']} of 400 evenly spaced angles of the same workload, "
+                                          f"forward + adjoint, FP64, one step"}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def roofline(kernel, ms, S_fwd, nvox, nray, pk, pk_kind, clk):
+    """Roofline of the dominant kernel. The projector is a gather: its algorithmic
+    on-chip traffic is 16 B per sample (the four FP32 bilinear neighbours). The
+    binding unit is the SM's L1/shared-memory datapath (128 B/clk/SM); its peak is
+    derived from the unit count and clock: 152 SMs x 128 B x max SM clock."""
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    peak = 152 * 128 * sm_mhz * 1e6 / 1e9   # GB/s
+    achieved = 16.0 * S_fwd / (ms * 1e-3) / 1e9
+    return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_kind": f"derived: L1/SMEM datapath 152 SM x 128 B/clk x {sm_mhz:.0f} MHz",
+            "hbm": {"compulsory_bytes": 4 * (nvox + nray), "peak_gbs": pk.get("hbm_gbs"), "peak_kind": pk_kind}}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

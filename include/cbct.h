@@ -1,0 +1,174 @@
+/*
+ * cbct.h — C ABI of the GB300 (sm_103a) cone-beam CT library.
+ *
+ * The library computes the discretised cone-beam transform P and its exact
+ * adjoint P* (paper: "Equivariant Multiscale Learned Invertible Reconstruction
+ * for Cone Beam CT", arXiv 2512.21180, Sec. 2.1, projection-operator equation:
+ * P(mu)(t,u) is the integral of mu along the line from the source to detector
+ * element u at time t, and P* is its adjoint, the backprojection), the
+ * field-of-view tensor V and redundancy weight w used by the reconstruction
+ * (Sec. 2.4), FDK with redundancy weighting, PDHG-TV (Sec. 2.3 baselines), the
+ * primary-signal simulation (Sec. 2.1 primary model with Poisson noise, Sec. 2.3
+ * log normalisation) and the learned primal-dual reconstruction (Sec. 2.4,
+ * Algorithm 1).
+ *
+ * Conventions for every call
+ *  - Pointers named vol/proj/... are DEVICE pointers on the device that was current
+ *    when the geometry was created; the caller owns them. They must be contiguous
+ *    and 16-byte aligned, in these layouts (fastest index last):
+ *        volume      [batch][nz][ny][nx]       (x fastest)
+ *        projection  [batch][n_angles][nv][nu] (u fastest)
+ *  - The library owns geometry tables, weights and workspaces behind opaque
+ *    handles. Scratch memory is taken from the CUDA stream-ordered pool on the
+ *    caller's stream (cudaMallocAsync) and returned on the same stream.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; 0 = legacy default) and
+ *    never synchronise the device.
+ *  - Return value: 0 on success, negative on error; cbct_last_error() returns a
+ *    thread-local message for the last failing call on this thread.
+ *        CBCT_EINVAL  -1  invalid argument (nothing was launched)
+ *        CBCT_ECUDA   -2  CUDA runtime error (launch or allocation)
+ *        CBCT_ENOMEM  -3  out of device memory
+ *        CBCT_EDEVICE -4  a kernel reported an error through its status word
+ *
+ * Geometry (the paper's scanner, Sec. 2.1: circular orbit, offset flat panel):
+ * isocentre at the origin, rotation axis z. At angle theta the source sits at
+ * sid (cos theta, sin theta, 0), the panel centre at sid - sdd along that
+ * direction, the panel axes are e_u = (-sin theta, cos theta, 0) (the direction
+ * of rotation) and e_v = z. Pixel (iu, iv) is at ((iu - (nu-1)/2) du + u_offset)
+ * e_u + ((iv - (nv-1)/2) dv + v_offset) e_v from the panel centre; voxel
+ * (ix, iy, iz) is centred at ((ix - (nx-1)/2) vox_x + center_x, ...). A positive
+ * u_offset moves the panel in the direction of rotation.
+ *
+ * Discretisation (the paper defines only the continuous P): Joseph-style ray
+ * sums. For the ray from the source to a pixel centre the principal axis a is x
+ * if |r_x| >= |r_y| else y, decided on the FP32 ray direction
+ * r = fmaf(iv, EV, fmaf(iu, EU, D0S)) of the FP32 geometry table; every
+ * voxel-centre plane i of axis a between source and pixel contributes
+ * (step length) x (bilinear interpolation of the volume on that plane, zero
+ * outside the grid). Rays whose principal axis would be z are not supported and
+ * such geometries are rejected at creation.
+ */
+#ifndef CBCT_H
+#define CBCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CBCT_EINVAL (-1)
+#define CBCT_ECUDA (-2)
+#define CBCT_ENOMEM (-3)
+#define CBCT_EDEVICE (-4)
+
+typedef struct cbct_geom cbct_geom; /* opaque: geometry tables on one device */
+
+typedef struct {
+    int nx, ny, nz;          /* volume grid */
+    double vox[3];           /* voxel pitch, mm */
+    double center[3];        /* volume centre relative to the isocentre, mm */
+    int nu, nv;              /* panel columns (along e_u) and rows (along z) */
+    double du, dv;           /* pixel pitch, mm */
+    double u_offset, v_offset; /* panel offset, mm; +u = direction of rotation */
+    double sid, sdd;         /* source-isocentre and source-detector distances, mm */
+    int n_angles;            /* projections over the orbit */
+    const double *angles;    /* host array of n_angles radians, or NULL for 2 pi k / n_angles */
+    int normalize;           /* 1: scale P and P* by 1/||P|| (Sec. 2.4, "normalized
+                                operators"); ||P|| from 30 FP64-accumulated power
+                                iterations at creation. 0: unscaled. */
+} cbct_geom_desc;
+
+/* Last error message of this thread (static storage, never NULL). */
+const char *cbct_last_error(void);
+
+/* Build the per-angle ray tables on the current device (a1). The descriptor and
+ * its angle array are copied. Synchronises the current device once (table
+ * upload; with normalize = 1 also the power iteration). Errors: CBCT_EINVAL for
+ * non-positive sizes/pitches/distances, sizes whose index products exceed 2^31,
+ * or a geometry with z-principal rays; CBCT_ECUDA/ENOMEM on CUDA failures. */
+int geometry_create(const cbct_geom_desc *desc, cbct_geom **out);
+
+/* Free the device tables (synchronises with the device). NULL is a no-op. */
+void geometry_destroy(cbct_geom *g);
+
+/* Operator scale applied by forward_project/back_project (1/||P|| when the
+ * geometry was created with normalize = 1, else 1). */
+double geometry_scale(const cbct_geom *g);
+
+/* Forward projection (a2, Sec. 2.1): proj[b] (+)= P vol[b] for b < batch.
+ * accumulate = 0 overwrites proj, 1 adds to it. FP32 in, FP32 accumulation.
+ * batch >= 1; batch * n_angles <= 65535. Scratch: none. */
+int forward_project(const cbct_geom *g, const float *vol, float *proj, int batch, int accumulate,
+                    void *stream);
+
+/* Backprojection (a3, Sec. 2.1): vol[b] (+)= P* proj[b], the exact transpose of
+ * forward_project (same rays, planes and bilinear weights), computed as an
+ * atomic-free voxel-driven gather. Scratch: batch * n_angles * nv * nu floats
+ * (the ray-weighted projections), from the stream-ordered pool. */
+int back_project(const cbct_geom *g, const float *proj, float *vol, int batch, int accumulate,
+                 void *stream);
+
+/* FP64 instantiations of the same operators (tests and finite-difference checks;
+ * the principal-axis decision stays the FP32 one). */
+int forward_project_f64(const cbct_geom *g, const double *vol, double *proj, int batch,
+                        int accumulate, void *stream);
+int back_project_f64(const cbct_geom *g, const double *proj, double *vol, int batch,
+                     int accumulate, void *stream);
+
+/* Number of samples of one forward projection: (ray, plane) pairs with the
+ * source-to-pixel parameter in (0, 1) and the in-plane point inside the
+ * (-1, n) x (-1, n) extended grid. The throughput unit. Writes one int64 to the
+ * host pointer *out; synchronises `stream`. */
+int cbct_count_samples(const cbct_geom *g, long long *out, void *stream);
+
+
+/* ---- simulation and per-geometry tensors (a5, a6) ---- */
+
+/* Ellipsoid phantom on the geometry's voxel grid. ell_host: n_ell rows of 17
+ * doubles in host memory: centre (3, mm), semi-axes (3, mm), rotation (9,
+ * row-major; rows are the ellipsoid axes in world coordinates), value (1/mm),
+ * mode (0: add the value inside, 1: overwrite with it). Rows apply in order. A
+ * point P is inside when sum_i ((R (P - c))_i / a_i)^2 <= 1 (FP64). With
+ * supersample = s in [1, 8] each voxel is the mean over s^3 sub-points at offsets
+ * ((j + 1/2)/s - 1/2) vox. Writes one volume [nz][ny][nx]. Synchronises `stream`
+ * before returning (the host rows may be reused at once). Stand-in for the
+ * paper's CT volumes (Sec. 2.3). */
+int cbct_phantom(const cbct_geom *g, const double *ell_host, int n_ell, int supersample, float *vol,
+                 void *stream);
+
+/* Photon counts (Sec. 2.1, primary model, one energy): counts[e] ~
+ * Poisson(I0 exp(-line_integrals[e])) for e < n, device arrays. Random words come
+ * from Philox4x32-10 (Salmon et al., SC'11) with key (seed lo, seed hi) and counter
+ * (e lo, e hi, block, 0x50303031); means below 10 are sampled by inversion, others
+ * by Hoermann's PTRS (1993); decisions in FP64. Deterministic for a given seed. */
+int cbct_poisson(const float *line_integrals, long long n, double I0, unsigned long long seed, int32_t *counts,
+                 void *stream);
+
+/* Normalised log transform (Sec. 2.3): y[e] = -log(min(max(counts[e], 1) / I0, 1)). */
+int cbct_neglog(const int32_t *counts, long long n, double I0, float *y, void *stream);
+
+/* Simulated measurement of `batch` volumes: line_integrals = P vol (forward_project),
+ * then y = -log(min(max(N, 1)/I0, 1)) with N ~ Poisson(I0 exp(-line_integrals)),
+ * the counter e running over the whole [batch][n_angles][nv][nu] array. */
+int cbct_simulate(const cbct_geom *g, const float *vol, int batch, double I0, unsigned long long seed,
+                  float *line_integrals, float *y, void *stream);
+
+/* Offset-detector redundancy weight w[nu] (device), Sec. 2.4 (the paper names no
+ * scheme; this is Wang's): u' = (iu - (nu-1)/2) du + u_offset, D = nu du/2 -
+ * |u_offset|; for u_offset > 0 w = 0 below -D, sin^2(pi/4 (u' + D)/D) on [-D, D],
+ * 1 above D (mirrored for u_offset < 0); w = 1/2 for a centred panel, so that
+ * conjugate rays sum to one. */
+int cbct_redundancy_weight(const cbct_geom *g, float *w, void *stream);
+
+/* Field-of-view tensor V[nz][ny][nx] (device), Sec. 2.4: the fraction of angles at
+ * which the voxel centre projects onto the panel (continuous pixel coordinates in
+ * [-1/2, n - 1/2]), FP64. Synchronises `stream`. */
+int cbct_fov(const cbct_geom *g, float *V, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CBCT_H */

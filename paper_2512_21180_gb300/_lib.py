@@ -1,0 +1,81 @@
+"""ctypes loader for libcbct.so: argument marshalling only.
+
+The library is built in-tree by `build.py`. There is no fallback: if the shared
+library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcbct.so")
+_lock = threading.Lock()
+_lib = None
+
+P = ctypes.c_void_p
+I32 = ctypes.c_int
+I64 = ctypes.c_longlong
+F32 = ctypes.c_float
+F64 = ctypes.c_double
+U64 = ctypes.c_uint64
+
+
+class GeomDesc(ctypes.Structure):
+    _fields_ = [
+        ("nx", I32), ("ny", I32), ("nz", I32),
+        ("vox", F64 * 3), ("center", F64 * 3),
+        ("nu", I32), ("nv", I32),
+        ("du", F64), ("dv", F64), ("u_offset", F64), ("v_offset", F64),
+        ("sid", F64), ("sdd", F64),
+        ("n_angles", I32), ("angles", P), ("normalize", I32),
+    ]
+
+
+# name -> (restype, argtypes); kept beside the declarations in include/cbct.h
+SIGNATURES = {
+    "cbct_last_error": (ctypes.c_char_p, []),
+    "geometry_create": (I32, [ctypes.POINTER(GeomDesc), ctypes.POINTER(P)]),
+    "geometry_destroy": (None, [P]),
+    "geometry_scale": (F64, [P]),
+    "forward_project": (I32, [P, P, P, I32, I32, P]),
+    "back_project": (I32, [P, P, P, I32, I32, P]),
+    "forward_project_f64": (I32, [P, P, P, I32, I32, P]),
+    "back_project_f64": (I32, [P, P, P, I32, I32, P]),
+    "cbct_count_samples": (I32, [P, ctypes.POINTER(I64), P]),
+    "cbct_phantom": (I32, [P, P, I32, I32, P, P]),
+    "cbct_poisson": (I32, [P, I64, F64, U64, P, P]),
+    "cbct_neglog": (I32, [P, I64, F64, P, P]),
+    "cbct_simulate": (I32, [P, P, I32, F64, U64, P, P, P]),
+    "cbct_redundancy_weight": (I32, [P, P, P]),
+    "cbct_fov": (I32, [P, P, P]),
+}
+
+EXTRA_SIGNATURES: dict = {}
+
+
+class CbctError(RuntimeError):
+    pass
+
+
+def load():
+    """Load libcbct.so (raises if it is absent: there is no CPU fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise CbctError(f"CUDA library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in {**SIGNATURES, **EXTRA_SIGNATURES}.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def check(rc: int, what: str = ""):
+    if rc != 0:
+        msg = load().cbct_last_error().decode(errors="replace")
+        raise CbctError(f"{what} failed ({rc}): {msg}")

@@ -1,0 +1,369 @@
+// Cone-beam projector pair (a2, a3): Joseph-style forward projection P and its
+// exact transpose P* as an atomic-free voxel-driven gather (paper Sec. 2.1,
+// projection operator and its adjoint, the backprojection).
+//
+// Forward (k_forward): one thread per ray; the ray visits every voxel-centre plane
+// of its principal axis between source and pixel and accumulates the bilinear
+// sample of that plane (zero outside the grid) times the step length.
+//
+// Backward (k_backproject): one thread per voxel run along z. For each angle and
+// each principal axis it finds the detector columns whose rays cross the voxel's
+// own plane within one voxel of it (a closed-form interval), then the rows, and
+// gathers step * bilinear weight * projection over exactly the (ray, plane,
+// neighbour) triples the forward visits. The per-ray step is folded into the
+// projection beforehand (k_weight_rays) so the gather needs no square root.
+#include <cmath>
+
+#include "common.cuh"
+#include "geom_impl.h"
+
+namespace cbct {
+
+// Conservative plane interval for q0 + i dq in (L, H); intersects [lo, hi].
+template <typename T>
+__device__ __forceinline__ void lin_range(T q0, T dq, T L, T H, T &lo, T &hi) {
+    if (dq == T(0)) {
+        if (!(q0 > L && q0 < H)) { lo = T(1); hi = T(0); }
+        return;
+    }
+    T i1 = (L - q0) / dq, i2 = (H - q0) / dq;
+    lo = fmax(lo, fmin(i1, i2));
+    hi = fmin(hi, fmax(i1, i2));
+}
+
+// ---- forward projection -------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_forward(GeomDev g, const T *__restrict__ vol, T *__restrict__ proj,
+                                                 int accumulate) {
+    const int iu = blockIdx.x * 32 + threadIdx.x;
+    const int iv = blockIdx.y * 8 + threadIdx.y;
+    const int k = blockIdx.z % g.na, b = blockIdx.z / g.na;
+    if (iu >= g.nu || iv >= g.nv) return;
+    const int a = principal_axis(g.f32[k], iu);
+    const ColT<T> c = col_of<T>(g, k, iu);
+    const T rz = rz_of<T>(g, iv);
+    T dqz, qcz;
+    ray_row(g, c, rz, dqz, qcz);
+    const int na = g.n[a], nb = g.n[1 - a], nz = g.n[2];
+    const T ca = T(0.5) * T(na - 1);
+    const long long nx = g.n[0], nxy = (long long)g.n[0] * g.n[1];
+    const long long sa = a == 0 ? 1 : nx, sb = a == 0 ? nx : 1;
+    const T *V = vol + (long long)b * nxy * nz;
+
+    // planes with t in (0, 1) and the in-plane point in (-1, n): conservative range
+    // in di = i - ca, the exact tests are repeated per sample
+    T lo = -ca, hi = ca;
+    lin_range(c.tc, c.inv, T(0), T(1), lo, hi);
+    lin_range(c.qcb, c.dqb, T(-1), T(nb), lo, hi);
+    lin_range(qcz, dqz, T(-1), T(nz), lo, hi);
+    const int ilo = max(0, (int)floor(lo + ca) - 1), ihi = min(na - 1, (int)ceil(hi + ca) + 1);
+
+    T acc = T(0);
+    for (int i = ilo; i <= ihi; ++i) {
+        const T di = T(i) - ca;
+        const T t = fma_rn(di, c.inv, c.tc);
+        if (!(t > T(0) && t < T(1))) continue;
+        const T qb = fma_rn(di, c.dqb, c.qcb);
+        const T qz = fma_rn(di, dqz, qcz);
+        if (!(qb > T(-1) && qb < T(nb) && qz > T(-1) && qz < T(nz))) continue;
+        const T fb0 = floor(qb), fz0 = floor(qz);
+        const int jb = (int)fb0, jz = (int)fz0;
+        const T fb = qb - fb0, fz = qz - fz0;
+        const T *P = V + i * sa;
+        const bool b0 = jb >= 0, b1 = jb + 1 < nb, z0 = jz >= 0, z1 = jz + 1 < nz;
+        const long long o = (long long)jb * sb + (long long)jz * nxy;
+        const T v00 = (b0 && z0) ? __ldg(P + o) : T(0);
+        const T v10 = (b1 && z0) ? __ldg(P + o + sb) : T(0);
+        const T v01 = (b0 && z1) ? __ldg(P + o + nxy) : T(0);
+        const T v11 = (b1 && z1) ? __ldg(P + o + sb + nxy) : T(0);
+        acc += (T(1) - fz) * ((T(1) - fb) * v00 + fb * v10) + fz * ((T(1) - fb) * v01 + fb * v11);
+    }
+    T scale;
+    if constexpr (sizeof(T) == 4) scale = g.scale; else scale = g.scaled;
+    acc *= ray_step<T>(g, a, c.dqb, dqz) * scale;
+    T *out = proj + (((long long)b * g.na + k) * g.nv + iv) * g.nu + iu;
+    *out = accumulate ? *out + acc : acc;
+}
+
+// ---- backprojection -------------------------------------------------------------
+
+// pw = proj * step(ray) * scale
+template <typename T>
+__global__ void k_weight_rays(GeomDev g, const T *__restrict__ proj, T *__restrict__ pw) {
+    const int iu = blockIdx.x * 32 + threadIdx.x;
+    const int iv = blockIdx.y * 8 + threadIdx.y;
+    const int k = blockIdx.z % g.na, b = blockIdx.z / g.na;
+    if (iu >= g.nu || iv >= g.nv) return;
+    const int a = principal_axis(g.f32[k], iu);
+    const ColT<T> c = col_of<T>(g, k, iu);
+    T dqz, qcz;
+    ray_row(g, c, rz_of<T>(g, iv), dqz, qcz);
+    T scale;
+    if constexpr (sizeof(T) == 4) scale = g.scale; else scale = g.scaled;
+    const long long o = (((long long)b * g.na + k) * g.nv + iv) * g.nu + iu;
+    pw[o] = proj[o] * ray_step<T>(g, a, c.dqb, dqz) * scale;
+}
+
+// Detector column (continuous) hit by the ray from the source through the xy
+// index-space point (px, py): D0S + u EU parallel to P - S.
+__device__ __forceinline__ float column_of(const Frame32 &F, float px, float py) {
+    const float dx = px - F.S[0], dy = py - F.S[1];
+    const float num = F.D0S[0] * dy - F.D0S[1] * dx;
+    const float den = F.EU[0] * dy - F.EU[1] * dx;
+    return -num / den;
+}
+
+template <typename T, int ZS>
+__global__ void __launch_bounds__(256) k_backproject(GeomDev g, const T *__restrict__ pw, T *__restrict__ vol,
+                                                     int accumulate) {
+    const int ix = blockIdx.x * 32 + threadIdx.x;
+    const int iy = blockIdx.y * 8 + threadIdx.y;
+    const int nzs = (g.n[2] + ZS - 1) / ZS;
+    const int z0 = (blockIdx.z % nzs) * ZS, b = blockIdx.z / nzs;
+    if (ix >= g.n[0] || iy >= g.n[1]) return;
+    const int nz = g.n[2];
+    T acc[ZS];
+#pragma unroll
+    for (int j = 0; j < ZS; ++j) acc[j] = T(0);
+    const T *PB = pw + (long long)b * g.na * g.nv * g.nu;
+    const T Sz = sz_of<T>(g);
+    // rows: q_z = Sz + t rz(v) and rz(v) = rz0 + v drz
+    const float rz0 = g.rz32[0], drz = g.nv > 1 ? g.rz32[1] - g.rz32[0] : 1.0f;
+
+    for (int k = 0; k < g.na; ++k) {
+        const Frame32 &F = g.f32[k];
+        const T *Pk = PB + (long long)k * g.nv * g.nu;
+        for (int a = 0; a < 2; ++a) {
+            const int alo = a == 0 ? F.ux_lo : F.uy_lo, ahi = a == 0 ? F.ux_hi : F.uy_hi;
+            if (alo > ahi) continue;
+            const int i = a == 0 ? ix : iy;   // the voxel's plane on axis a
+            const int j = a == 0 ? iy : ix;   // its in-plane coordinate along b
+            const T di = T(i) - T(0.5) * T(g.n[a] - 1);
+            // columns whose rays meet plane i inside (j - 1, j + 1)
+            float u1, u2;
+            if (a == 0) { u1 = column_of(F, (float)ix, (float)(iy - 1)); u2 = column_of(F, (float)ix, (float)(iy + 1)); }
+            else { u1 = column_of(F, (float)(ix - 1), (float)iy); u2 = column_of(F, (float)(ix + 1), (float)iy); }
+            int ulo = alo, uhi = ahi;
+            if (isfinite(u1) && isfinite(u2)) {
+                const float lo_f = fmaxf(fminf(u1, u2), -1.0e6f), hi_f = fminf(fmaxf(u1, u2), 1.0e6f);
+                ulo = max(ulo, (int)floorf(lo_f) - 1);
+                uhi = min(uhi, (int)ceilf(hi_f) + 1);
+            }
+            for (int u = ulo; u <= uhi; ++u) {
+                if (principal_axis(F, u) != a) continue;
+                const ColT<T> c = col_of<T>(g, k, u);
+                const T t = fma_rn(di, c.inv, c.tc);
+                if (!(t > T(0) && t < T(1))) continue;
+                const T qb = fma_rn(di, c.dqb, c.qcb);
+                const T wb = T(1) - fabs(qb - T(j));
+                if (!(wb > T(0))) continue;
+                // rows whose sample on plane i lies within one voxel of [z0, z0+ZS-1]
+                const float tf = (float)t;
+                float v1 = ((float)(z0 - 1) - (float)Sz) / tf, v2 = ((float)(z0 + ZS) - (float)Sz) / tf;
+                v1 = (v1 - rz0) / drz;
+                v2 = (v2 - rz0) / drz;
+                if (!(v1 == v1) || !(v2 == v2)) continue;
+                const float vmin = fmaxf(fminf(v1, v2), -1.0e6f), vmax = fminf(fmaxf(v1, v2), 1.0e6f);
+                const int vlo = max(0, (int)floorf(vmin) - 1);
+                const int vhi = min(g.nv - 1, (int)ceilf(vmax) + 1);
+                for (int v = vlo; v <= vhi; ++v) {
+                    T dqz, qcz;
+                    ray_row(g, c, rz_of<T>(g, v), dqz, qcz);
+                    const T qz = fma_rn(di, dqz, qcz);
+                    const T p = wb * __ldg(Pk + (long long)v * g.nu + u);
+#pragma unroll
+                    for (int jj = 0; jj < ZS; ++jj) {
+                        const T wz = T(1) - fabs(qz - T(z0 + jj));
+                        if (wz > T(0)) acc[jj] += wz * p;
+                    }
+                }
+            }
+        }
+    }
+    const long long nxy = (long long)g.n[0] * g.n[1];
+    T *out = vol + (long long)b * nxy * nz + ((long long)z0 * g.n[1] + iy) * g.n[0] + ix;
+#pragma unroll
+    for (int jj = 0; jj < ZS; ++jj) {
+        if (z0 + jj < nz) {
+            T *o = out + (long long)jj * nxy;
+            *o = accumulate ? *o + acc[jj] : acc[jj];
+        }
+    }
+}
+
+// ---- sample count -----------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_count(GeomDev g, unsigned long long *total) {
+    const int iu = blockIdx.x * 32 + threadIdx.x;
+    const int iv = blockIdx.y * 8 + threadIdx.y;
+    const int k = blockIdx.z;
+    unsigned long long cnt = 0;
+    if (iu < g.nu && iv < g.nv) {
+        const int a = principal_axis(g.f32[k], iu);
+        const ColT<float> c = col_of<float>(g, k, iu);
+        float dqz, qcz;
+        ray_row(g, c, rz_of<float>(g, iv), dqz, qcz);
+        const int na = g.n[a], nb = g.n[1 - a], nz = g.n[2];
+        const float ca = 0.5f * (float)(na - 1);
+        for (int i = 0; i < na; ++i) {
+            const float di = (float)i - ca;
+            const float t = fma_rn(di, c.inv, c.tc);
+            if (!(t > 0.0f && t < 1.0f)) continue;
+            const float qb = fma_rn(di, c.dqb, c.qcb);
+            const float qz = fma_rn(di, dqz, qcz);
+            if (qb > -1.0f && qb < float(nb) && qz > -1.0f && qz < float(nz)) cnt++;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(total, cnt);
+}
+
+// ---- FP64 norms for the power iteration ------------------------------------------
+
+__global__ void k_sumsq(const float *__restrict__ x, long long n, double *out) {
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double v = x[i];
+        s += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+__global__ void k_scale_by(float *x, long long n, const double *sumsq) {
+    const float s = (float)(1.0 / sqrt(*sumsq));
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] *= s;
+}
+
+__global__ void k_fill(float *x, long long n, float v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+// ---- launchers ------------------------------------------------------------------------
+
+static int check_common(const cbct_geom *g, const void *a, const void *b, int batch, int accumulate) {
+    if (!g || !a || !b) return fail(CBCT_EINVAL, "NULL geometry or buffer");
+    if (batch < 1) return fail(CBCT_EINVAL, "batch must be >= 1");
+    if (accumulate != 0 && accumulate != 1) return fail(CBCT_EINVAL, "accumulate must be 0 or 1");
+    if ((long long)batch * g->dev.na > 65535) return fail(CBCT_EINVAL, "batch * n_angles must be <= 65535");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != g->device) return fail(CBCT_EINVAL, "current device differs from the geometry's device");
+    return 0;
+}
+
+template <typename T>
+static int forward_impl(const cbct_geom *g, const T *vol, T *proj, int batch, int accumulate, cudaStream_t st) {
+    int rc = check_common(g, vol, proj, batch, accumulate);
+    if (rc) return rc;
+    const GeomDev &d = g->dev;
+    dim3 blk(32, 8), grd((d.nu + 31) / 32, (d.nv + 7) / 8, d.na * batch);
+    k_forward<T><<<grd, blk, 0, st>>>(d, vol, proj, accumulate);
+    CBCT_LAUNCH_CHECK("forward_project launch");
+    return 0;
+}
+
+constexpr int kZS = 4;
+
+template <typename T>
+static int backward_impl(const cbct_geom *g, const T *proj, T *vol, int batch, int accumulate, cudaStream_t st) {
+    int rc = check_common(g, proj, vol, batch, accumulate);
+    if (rc) return rc;
+    const GeomDev &d = g->dev;
+    const long long nproj = (long long)batch * d.na * d.nv * d.nu;
+    const int nzs = (d.n[2] + kZS - 1) / kZS;
+    if ((long long)nzs * batch > 65535) return fail(CBCT_EINVAL, "back_project: batch too large");
+    T *pw = nullptr;
+    CBCT_CUDA_TRY(cudaMallocAsync((void **)&pw, sizeof(T) * nproj, st));
+    dim3 blk(32, 8), gw((d.nu + 31) / 32, (d.nv + 7) / 8, d.na * batch);
+    k_weight_rays<T><<<gw, blk, 0, st>>>(d, proj, pw);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        dim3 gb((d.n[0] + 31) / 32, (d.n[1] + 7) / 8, nzs * batch);
+        k_backproject<T, kZS><<<gb, blk, 0, st>>>(d, pw, vol, accumulate);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(pw, st);
+    if (e != cudaSuccess) return cuda_fail(e, "back_project launch");
+    return 0;
+}
+
+int operator_norm(cbct_geom *g, int iters, double *out) {
+    const GeomDev &d = g->dev;
+    const long long nvox = (long long)d.n[0] * d.n[1] * d.n[2], nproj = (long long)d.na * d.nv * d.nu;
+    float *x = nullptr, *p = nullptr;
+    double *acc = nullptr;
+    cudaError_t e = cudaMalloc(&x, sizeof(float) * nvox);
+    if (e == cudaSuccess) e = cudaMalloc(&p, sizeof(float) * nproj);
+    if (e == cudaSuccess) e = cudaMalloc(&acc, sizeof(double));
+    double nrm2 = 0.0;
+    int rc = 0;
+    if (e == cudaSuccess) {
+        k_fill<<<1024, 256>>>(x, nvox, 1.0f);
+        for (int it = 0; it < iters && rc == 0; ++it) {
+            cudaMemset(acc, 0, sizeof(double));
+            k_sumsq<<<1024, 256>>>(x, nvox, acc);
+            k_scale_by<<<1024, 256>>>(x, nvox, acc);
+            rc = forward_impl<float>(g, x, p, 1, 0, 0);
+            if (rc == 0) rc = backward_impl<float>(g, p, x, 1, 0, 0);
+        }
+        if (rc == 0) {
+            cudaMemset(acc, 0, sizeof(double));
+            k_sumsq<<<1024, 256>>>(x, nvox, acc);
+            e = cudaMemcpy(&nrm2, acc, sizeof(double), cudaMemcpyDeviceToHost);
+        }
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(x);
+    cudaFree(p);
+    cudaFree(acc);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "operator norm");
+    *out = sqrt(sqrt(nrm2));  // ||P^T P x|| with ||x|| = 1 -> ||P||^2
+    return 0;
+}
+
+}  // namespace cbct
+
+using namespace cbct;
+
+extern "C" int forward_project(const cbct_geom *g, const float *vol, float *proj, int batch, int accumulate,
+                               void *stream) {
+    return forward_impl<float>(g, vol, proj, batch, accumulate, (cudaStream_t)stream);
+}
+
+extern "C" int back_project(const cbct_geom *g, const float *proj, float *vol, int batch, int accumulate,
+                            void *stream) {
+    return backward_impl<float>(g, proj, vol, batch, accumulate, (cudaStream_t)stream);
+}
+
+extern "C" int forward_project_f64(const cbct_geom *g, const double *vol, double *proj, int batch, int accumulate,
+                                   void *stream) {
+    return forward_impl<double>(g, vol, proj, batch, accumulate, (cudaStream_t)stream);
+}
+
+extern "C" int back_project_f64(const cbct_geom *g, const double *proj, double *vol, int batch, int accumulate,
+                                void *stream) {
+    return backward_impl<double>(g, proj, vol, batch, accumulate, (cudaStream_t)stream);
+}
+
+extern "C" int cbct_count_samples(const cbct_geom *g, long long *out, void *stream) {
+    if (!g || !out) return fail(CBCT_EINVAL, "cbct_count_samples: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long *d = nullptr, h = 0;
+    CBCT_CUDA_TRY(cudaMallocAsync((void **)&d, sizeof(unsigned long long), st));
+    cudaMemsetAsync(d, 0, sizeof(unsigned long long), st);
+    const GeomDev &v = g->dev;
+    dim3 blk(32, 8), grd((v.nu + 31) / 32, (v.nv + 7) / 8, v.na);
+    k_count<<<grd, blk, 0, st>>>(v, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(d, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cbct_count_samples");
+    *out = (long long)h;
+    return 0;
+}

@@ -1,0 +1,73 @@
+"""Python binding of the simulation and per-geometry calls (argument marshalling
+only; the arithmetic runs in libcbct.so)."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+from .projector import Geometry
+
+
+def _st(t: torch.Tensor) -> int:
+    return torch.cuda.current_stream(t.device).cuda_stream
+
+
+def phantom(geom: Geometry, ell: np.ndarray, supersample: int = 1, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Voxelised ellipsoid phantom [nz, ny, nx] (float32, on the geometry's device)."""
+    e = np.ascontiguousarray(ell, dtype=np.float64).reshape(-1, 17)
+    if out is None:
+        out = torch.empty(geom.vol_shape, device=geom.device, dtype=torch.float32)
+    assert out.is_contiguous() and out.dtype == torch.float32 and out.numel() == int(np.prod(geom.vol_shape))
+    with torch.cuda.device(geom.device):
+        check(_lib.load().cbct_phantom(geom.handle, e.ctypes.data, e.shape[0], supersample, out.data_ptr(), _st(out)),
+              "cbct_phantom")
+    return out
+
+
+def poisson(line_integrals: torch.Tensor, I0: float, seed: int) -> torch.Tensor:
+    p = line_integrals.contiguous()
+    assert p.dtype == torch.float32 and p.is_cuda
+    out = torch.empty(p.shape, dtype=torch.int32, device=p.device)
+    with torch.cuda.device(p.device):
+        check(_lib.load().cbct_poisson(p.data_ptr(), p.numel(), float(I0), int(seed), out.data_ptr(), _st(p)),
+              "cbct_poisson")
+    return out
+
+
+def neglog(counts: torch.Tensor, I0: float) -> torch.Tensor:
+    c = counts.contiguous()
+    assert c.dtype == torch.int32 and c.is_cuda
+    out = torch.empty(c.shape, dtype=torch.float32, device=c.device)
+    with torch.cuda.device(c.device):
+        check(_lib.load().cbct_neglog(c.data_ptr(), c.numel(), float(I0), out.data_ptr(), _st(c)), "cbct_neglog")
+    return out
+
+
+def simulate(geom: Geometry, vol: torch.Tensor, I0: float, seed: int):
+    """(line integrals P vol, noisy log data y) for a batch of volumes."""
+    v = vol.contiguous()
+    if v.dim() == 3:
+        v = v.unsqueeze(0)
+    B = v.shape[0]
+    p = torch.empty((B,) + geom.proj_shape, device=v.device, dtype=torch.float32)
+    y = torch.empty_like(p)
+    with torch.cuda.device(v.device):
+        check(_lib.load().cbct_simulate(geom.handle, v.data_ptr(), B, float(I0), int(seed), p.data_ptr(),
+                                        y.data_ptr(), _st(v)), "cbct_simulate")
+    return p, y
+
+
+def redundancy_weight(geom: Geometry) -> torch.Tensor:
+    w = torch.empty(geom.nu, device=geom.device, dtype=torch.float32)
+    with torch.cuda.device(geom.device):
+        check(_lib.load().cbct_redundancy_weight(geom.handle, w.data_ptr(), _st(w)), "cbct_redundancy_weight")
+    return w
+
+
+def fov(geom: Geometry) -> torch.Tensor:
+    V = torch.empty(geom.vol_shape, device=geom.device, dtype=torch.float32)
+    with torch.cuda.device(geom.device):
+        check(_lib.load().cbct_fov(geom.handle, V.data_ptr(), _st(V)), "cbct_fov")
+    return V

@@ -155,6 +155,9 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--ref-angles", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="geometry name from paper_2512_21180_gb300.inputs (profiling runs use smaller ones)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -180,11 +183,11 @@ def main():
     from paper_2512_21180_gb300 import projector as P
     from paper_2512_21180_gb300 import ops
 
-    g = I.geometry(WORKLOAD)
+    g = I.geometry(args.workload)
     geom = P.Geometry(g)
     S_fwd = geom.count_samples()
     samples_step = 2 * S_fwd
-    ell = I.phantom_params(WORKLOAD, 2 + rank)
+    ell = I.phantom_params(args.workload, 2 + rank)
     vol = ops.phantom(geom, ell).unsqueeze(0)
     proj = torch.empty((1,) + geom.proj_shape, device="cuda")
     back = torch.empty((1,) + geom.vol_shape, device="cuda")
@@ -231,6 +234,28 @@ def main():
 
     # end to end through the public API with host buffers: pinned host volume in,
     # backprojected volume out, copies inside the timed region
+    if args.no_e2e:
+        ms_e2e = float("nan")
+    else:
+        ms_e2e = e2e_leg(args, geom, vol, proj, back, stream, dist)
+    e2e = samples_step * world / (ms_e2e * 1e-3) / 1e9
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    return report(args, geom, world, S_fwd, samples_step, value, ms, ms_fwd, ms_adj, e2e, clk, g, dist)
+
+
+def e2e_leg(args, geom, vol, proj, back, stream, dist):
+    import torch
+
+    from paper_2512_21180_gb300 import projector as P
+
+    def step():
+        P.forward_project(geom, vol, out=proj)
+        P.back_project(geom, proj, out=back)
+
     host_in = vol.cpu().pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     dvol = torch.empty_like(vol)
@@ -255,12 +280,11 @@ def main():
         t = torch.tensor([ms_e2e], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_e2e = t.item()
-    e2e = samples_step * world / (ms_e2e * 1e-3) / 1e9
+    return ms_e2e
 
-    if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
-        return 0
+
+def report(args, geom, world, S_fwd, samples_step, value, ms, ms_fwd, ms_adj, e2e, clk, g, dist):
+    import numpy as np
 
     pk, pk_kind = peaks()
     nvox = int(np.prod(geom.vol_shape))
@@ -273,7 +297,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "samples_per_step": samples_step,
+        "config": {"workload": WORKLOAD_DESC if args.workload == WORKLOAD else args.workload,
+                   "samples_per_step": samples_step,
                    "l2": "flushed between timed steps (256 MiB write, untimed)",
                    "ms_forward": ms_fwd, "ms_adjoint": ms_adj,
                    "gsamples_s_forward": S_fwd / (ms_fwd * 1e-3) / 1e9,
@@ -283,7 +308,7 @@ def main():
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
     }
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and args.workload == WORKLOAD:
         r = cpu_reference(1, 0, args.ref_angles)
         line["cpu_baseline"] = {"value": r["value"], "unit": "Gsamples/s", "cores": r["cores"], "kind": "oracle",
                                 "sample": f"{r['angles']} of 400 evenly spaced angles of the same workload, "

@@ -117,6 +117,22 @@ int forward_project_f64(const cbct_geom *g, const double *vol, double *proj, int
 int back_project_f64(const cbct_geom *g, const double *proj, double *vol, int batch,
                      int accumulate, void *stream);
 
+/* back_project without any device allocation (the paper has no counterpart; this
+ * serves callers that cannot allocate device memory during the call, e.g. a host
+ * framework that owns the whole device memory budget through its own allocator,
+ * or a latency-critical loop that must not enter the CUDA allocator). Same
+ * arguments and result as back_project, up to FP32 summation order. Its scratch
+ * is a fixed 8 Mi-float (32 MiB) device array inside the library, which every GPU
+ * that loads the library holds until the process exits; the angles are processed
+ * in chunks that fit it. Limit: nu * nv <= 8388608 (one projection must fit),
+ * else CBCT_EINVAL before any launch. The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) and should come before any stream
+ * capture on that device. All calls share the one array: calls whose executions
+ * overlap on the GPU (different streams, or different host threads) race and give
+ * wrong results. Nothing in the array needs to start at zero. */
+int back_project_noalloc(const cbct_geom *g, const float *proj, float *vol, int batch, int accumulate,
+                         void *stream);
+
 /* Number of samples of one forward projection: (ray, plane) pairs with the
  * source-to-pixel parameter in (0, 1) and the in-plane point inside the
  * (-1, n) x (-1, n) extended grid. The throughput unit. Writes one int64 to the

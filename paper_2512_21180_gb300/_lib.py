@@ -43,6 +43,7 @@ SIGNATURES = {
     "back_project": (I32, [P, P, P, I32, I32, P]),
     "forward_project_f64": (I32, [P, P, P, I32, I32, P]),
     "back_project_f64": (I32, [P, P, P, I32, I32, P]),
+    "back_project_noalloc": (I32, [P, P, P, I32, I32, P]),
     "cbct_count_samples": (I32, [P, ctypes.POINTER(I64), P]),
     "cbct_phantom": (I32, [P, P, I32, I32, P, P]),
     "cbct_poisson": (I32, [P, I64, F64, U64, P, P]),

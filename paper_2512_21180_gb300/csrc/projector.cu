@@ -12,7 +12,10 @@
 // gathers step * bilinear weight * projection over exactly the (ray, plane,
 // neighbour) triples the forward visits. The per-ray step is folded into the
 // projection beforehand (k_weight_rays) so the gather needs no square root.
+#include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <string>
 
 #include "common.cuh"
 #include "geom_impl.h"
@@ -365,5 +368,82 @@ extern "C" int cbct_count_samples(const cbct_geom *g, long long *out, void *stre
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "cbct_count_samples");
     *out = (long long)h;
+    return 0;
+}
+
+// ---- backprojection without allocation --------------------------------------------
+//
+// back_project needs a scratch copy of the projections with the per-ray step
+// length folded in, which it takes from the stream-ordered pool. Some callers
+// cannot allocate device memory at call time: a host framework that owns the
+// whole device memory budget through its own allocator, or a latency-critical
+// loop that must not enter the CUDA allocator (which may take locks or wait on
+// the device). back_project_noalloc serves them: its scratch is the fixed
+// device array below, and it processes the angles in chunks that fit it.
+
+namespace cbct {
+
+// 8 Mi floats (32 MiB). The CUDA runtime places it on every GPU that loads this
+// library, for the lifetime of the process.
+constexpr long long kNoAllocScratchFloats = 8ll * 1024 * 1024;
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
+
+static std::mutex g_noalloc_mu;
+constexpr int kMaxDevices = 256;
+static float *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on `dev` (the current device). Looked up
+// once per device: in host code the array's name is only a host-side stand-in.
+static int noalloc_scratch(int dev, float **out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (dev < 0 || dev >= kMaxDevices) return fail(CBCT_EINVAL, "back_project_noalloc: device index out of range");
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "back_project_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = static_cast<float *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return 0;
+}
+
+}  // namespace cbct
+
+extern "C" int back_project_noalloc(const cbct_geom *g, const float *proj, float *vol, int batch, int accumulate,
+                                    void *stream) {
+    int rc = check_common(g, proj, vol, batch, accumulate);
+    if (rc) return rc;
+    const GeomDev &d = g->dev;
+    const long long per_angle = (long long)d.nv * d.nu;
+    if (per_angle > kNoAllocScratchFloats)
+        return fail(CBCT_EINVAL, "back_project_noalloc: one projection (nu * nv = " + std::to_string(per_angle) +
+                                     " floats) exceeds the fixed scratch of " +
+                                     std::to_string(kNoAllocScratchFloats) + " floats");
+    float *scratch = nullptr;
+    rc = noalloc_scratch(g->device, &scratch);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int chunk = (int)std::min<long long>(d.na, kNoAllocScratchFloats / per_angle);
+    const int nzs = (d.n[2] + kZS - 1) / kZS;
+    const long long nvox = (long long)d.n[0] * d.n[1] * d.n[2];
+    dim3 blk(32, 8);
+    for (int b = 0; b < batch; ++b) {
+        for (int k0 = 0; k0 < d.na; k0 += chunk) {
+            const int kc = std::min(chunk, d.na - k0);
+            // the same kernels on the angle sub-range [k0, k0 + kc)
+            GeomDev v = d;
+            v.na = kc;
+            v.f32 = d.f32 + k0;
+            v.f64 = d.f64 + k0;
+            v.col32 = d.col32 + (long long)k0 * d.nu;
+            v.col64 = d.col64 + (long long)k0 * d.nu;
+            const float *pb = proj + ((long long)b * d.na + k0) * per_angle;
+            dim3 gw((d.nu + 31) / 32, (d.nv + 7) / 8, kc);
+            k_weight_rays<float><<<gw, blk, 0, st>>>(v, pb, scratch);
+            dim3 gb((d.n[0] + 31) / 32, (d.n[1] + 7) / 8, nzs);
+            k_backproject<float, kZS><<<gb, blk, 0, st>>>(v, scratch, vol + b * nvox, k0 == 0 ? accumulate : 1);
+            CBCT_LAUNCH_CHECK("back_project_noalloc launch");
+        }
+    }
     return 0;
 }

@@ -97,9 +97,22 @@ void geometry_destroy(cbct_geom *g);
  * geometry was created with normalize = 1, else 1). */
 double geometry_scale(const cbct_geom *g);
 
+/* Read (and with clear = 1 reset) the geometry's device status word: 0 = ok,
+ * 1 = a kernel gave up waiting on a shared-memory barrier (it then left its
+ * outputs unwritten). Synchronises the device. */
+int cbct_device_status(const cbct_geom *g, int *out, int clear);
+
+/* Staged-forward configuration chosen for this geometry: *cfg = index of the
+ * shared-memory box (0..3) or -1 for the direct kernel; *need_b / *need_z = host
+ * bounds of a 32 x 8 ray tile's footprint over 8 planes (voxels). Any pointer may
+ * be NULL. */
+int cbct_forward_config(const cbct_geom *g, int *cfg, double *need_b, double *need_z);
+
 /* Forward projection (a2, Sec. 2.1): proj[b] (+)= P vol[b] for b < batch.
  * accumulate = 0 overwrites proj, 1 adds to it. FP32 in, FP32 accumulation.
- * batch >= 1; batch * n_angles <= 65535. Scratch: none. */
+ * batch >= 1; batch * n_angles <= 65535. Scratch: two plane-major copies of the
+ * volumes (2 * batch * nx * ny * nz floats, rows padded to 4), from the
+ * stream-ordered pool. */
 int forward_project(const cbct_geom *g, const float *vol, float *proj, int batch, int accumulate,
                     void *stream);
 

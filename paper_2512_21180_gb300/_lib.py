@@ -45,6 +45,8 @@ SIGNATURES = {
     "back_project_f64": (I32, [P, P, P, I32, I32, P]),
     "back_project_noalloc": (I32, [P, P, P, I32, I32, P]),
     "cbct_count_samples": (I32, [P, ctypes.POINTER(I64), P]),
+    "cbct_device_status": (I32, [P, ctypes.POINTER(I32), I32]),
+    "cbct_forward_config": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(F64), ctypes.POINTER(F64)]),
     "cbct_phantom": (I32, [P, P, I32, I32, P, P]),
     "cbct_poisson": (I32, [P, I64, F64, U64, P, P]),
     "cbct_neglog": (I32, [P, I64, F64, P, P]),

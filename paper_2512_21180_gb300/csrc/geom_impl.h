@@ -17,10 +17,17 @@ struct cbct_geom {
     float *rz32 = nullptr;                 // [nv]
     double *rz64 = nullptr;
     cbct::GeomDev dev{};                   // kernel view
+    int *status = nullptr;                 // device status word of this geometry's kernels
+    int fwd_cfg = -1;                      // staged forward box configuration, -1: direct kernel
+    double fwd_need_b = 0.0, fwd_need_z = 0.0;  // host bounds of a tile's chunk footprint
+    bool axis_contiguous = true;           // x- and y-principal columns form intervals at every angle
 };
 
 namespace cbct {
 // ||P|| by power iteration on P^T P (FP32 operators, FP64 norms), used for the
 // normalised operators. Synchronises the current device.
 int operator_norm(cbct_geom *g, int iters, double *out);
+// Staged (TMA) forward: returns 1 if it ran, 0 if the direct kernel must be used.
+int forward_staged(const cbct_geom *g, const float *vol, float *proj, int batch, int accumulate, cudaStream_t st);
+int choose_forward_cfg(double need_b, double need_z);
 }  // namespace cbct

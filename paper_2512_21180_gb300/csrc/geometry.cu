@@ -8,6 +8,7 @@
 //   EU  = (-du sin/vx, du cos/vy, 0),  EV = (0, 0, dv/vz)
 // with a = -(nu-1)/2 du + u_offset and b = -(nv-1)/2 dv + v_offset, evaluated in
 // FP64 on the host in this order and rounded once to FP32 for the kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -121,6 +122,44 @@ static void build_columns(const cbct_geom_desc &d, const std::vector<Frame32> &f
     }
 }
 
+// Bounds on the footprint of a 32 x 8 ray tile over one 8-plane chunk (the staged
+// forward's TMA box must hold it): per-column changes of the central-plane
+// parameters times the tile width, plane slopes times the chunk depth, plus
+// neighbour, floor and alignment margins. Also checks that at every angle the
+// x- and y-principal columns form intervals.
+static void forward_bounds(const cbct_geom_desc &d, const std::vector<Frame32> &f32, const std::vector<Col64> &c64,
+                           const std::vector<double> &rz64, double &need_b, double &need_z, bool &contiguous) {
+    const int TU = 32, TV = 8, P = 8;
+    const int n[2] = {d.nx, d.ny};
+    double rzmax = 0.0;
+    for (double r : rz64) rzmax = std::max(rzmax, std::fabs(r));
+    const double drz = d.nv > 1 ? std::fabs(rz64[1] - rz64[0]) : 0.0;
+    double Mb = 0, Mzu = 0, Dq = 0, Dz = 0, tmax = 0;
+    contiguous = true;
+    for (int k = 0; k < d.n_angles; ++k) {
+        const Frame32 &F = f32[k];
+        for (int u = F.ux_lo; u <= F.ux_hi; ++u)
+            if (principal_axis(F, u) != 0) contiguous = false;
+        for (int u = F.uy_lo; u <= F.uy_hi; ++u)
+            if (principal_axis(F, u) != 1) contiguous = false;
+        for (int u = 0; u < d.nu; ++u) {
+            const int a = principal_axis(F, u);
+            const double ca = 0.5 * (n[a] - 1);
+            const Col64 &c = c64[(size_t)k * d.nu + u];
+            Dq = std::max(Dq, std::fabs(c.dqb));
+            Dz = std::max(Dz, rzmax * std::fabs(c.inv));
+            tmax = std::max(tmax, std::fabs(c.tc) + ca * std::fabs(c.inv));
+            if (u + 1 < d.nu && principal_axis(F, u + 1) == a) {
+                const Col64 &e = c64[(size_t)k * d.nu + u + 1];
+                Mb = std::max(Mb, std::fabs(e.qcb - c.qcb) + ca * std::fabs(e.dqb - c.dqb));
+                Mzu = std::max(Mzu, rzmax * (std::fabs(e.tc - c.tc) + ca * std::fabs(e.inv - c.inv)));
+            }
+        }
+    }
+    need_b = (TU - 1) * Mb + (P - 1) * Dq + 8.0;
+    need_z = (TV - 1) * tmax * drz + (TU - 1) * Mzu + (P - 1) * Dz + 5.0;
+}
+
 // No ray may have z as its principal axis: at every angle the smallest
 // max(|r_x|, |r_y|) over columns must exceed the largest |r_z| over rows (r_x, r_y
 // depend on the column only and r_z on the row only), on the FP32 directions.
@@ -174,7 +213,11 @@ extern "C" int geometry_create(const cbct_geom_desc *desc, cbct_geom **out) {
     std::vector<double> rz64;
     build_columns(d, f32, f64, c32, c64, rz32, rz64);
     const size_t ncol = (size_t)d.n_angles * d.nu;
-    e = cudaMalloc(&g->f32, sizeof(Frame32) * d.n_angles);
+    forward_bounds(d, f32, c64, rz64, g->fwd_need_b, g->fwd_need_z, g->axis_contiguous);
+    g->fwd_cfg = g->axis_contiguous ? choose_forward_cfg(g->fwd_need_b, g->fwd_need_z) : -1;
+    e = cudaMalloc(&g->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(g->status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&g->f32, sizeof(Frame32) * d.n_angles);
     if (e == cudaSuccess) e = cudaMalloc(&g->f64, sizeof(Frame64) * d.n_angles);
     if (e == cudaSuccess) e = cudaMalloc(&g->col32, sizeof(Col32) * ncol);
     if (e == cudaSuccess) e = cudaMalloc(&g->col64, sizeof(Col64) * ncol);
@@ -228,8 +271,26 @@ extern "C" void geometry_destroy(cbct_geom *g) {
     if (g->col64) cudaFree(g->col64);
     if (g->rz32) cudaFree(g->rz32);
     if (g->rz64) cudaFree(g->rz64);
+    if (g->status) cudaFree(g->status);
     cudaSetDevice(cur);
     delete g;
 }
 
 extern "C" double geometry_scale(const cbct_geom *g) { return g ? g->dev.scaled : 0.0; }
+
+extern "C" int cbct_device_status(const cbct_geom *g, int *out, int clear) {
+    if (!g || !out) return fail(CBCT_EINVAL, "cbct_device_status: NULL argument");
+    int v = 0;
+    CBCT_CUDA_TRY(cudaMemcpy(&v, g->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (clear && v) CBCT_CUDA_TRY(cudaMemset(g->status, 0, sizeof(int)));
+    *out = v;
+    return 0;
+}
+
+extern "C" int cbct_forward_config(const cbct_geom *g, int *cfg, double *need_b, double *need_z) {
+    if (!g) return fail(CBCT_EINVAL, "cbct_forward_config: NULL geometry");
+    if (cfg) *cfg = g->fwd_cfg;
+    if (need_b) *need_b = g->fwd_need_b;
+    if (need_z) *need_z = g->fwd_need_z;
+    return 0;
+}

@@ -262,6 +262,11 @@ template <typename T>
 static int forward_impl(const cbct_geom *g, const T *vol, T *proj, int batch, int accumulate, cudaStream_t st) {
     int rc = check_common(g, vol, proj, batch, accumulate);
     if (rc) return rc;
+    if constexpr (sizeof(T) == 4) {
+        rc = forward_staged(g, vol, proj, batch, accumulate, st);
+        if (rc < 0) return rc;
+        if (rc == 1) return 0;
+    }
     const GeomDev &d = g->dev;
     dim3 blk(32, 8), grd((d.nu + 31) / 32, (d.nv + 7) / 8, d.na * batch);
     k_forward<T><<<grd, blk, 0, st>>>(d, vol, proj, accumulate);

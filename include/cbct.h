@@ -196,6 +196,44 @@ int cbct_redundancy_weight(const cbct_geom *g, float *w, void *stream);
  * [-1/2, n - 1/2]), FP64. Synchronises `stream`. */
 int cbct_fov(const cbct_geom *g, float *V, void *stream);
 
+/* ---- classical reconstructions (a5 FDK_w, a10 PDHG-TV and Landweber) ---- */
+
+/* Columns of zero padding FDK adds on the short side of an offset panel:
+ * ceil(2 |u_offset| / du). */
+int cbct_fdk_pad(const cbct_geom *g);
+
+/* FDK with redundancy weighting (Algorithm 1 initialisation, Sec. 2.4; Feldkamp
+ * 1984): rows weighted by w(u') sdd / sqrt(sdd^2 + u'^2 + v'^2), zero-padded on the
+ * short side (cbct_fdk_pad), filtered by the Ram-Lak kernel at the isocentre pitch
+ * tau = du sid / sdd (tau h(0) = 1/(4 tau), tau h(odd j) = -1/(pi^2 j^2 tau)), then
+ * vol(P) (+)= (2 pi / n_angles) sum_k (sid / U_k)^2 q_k(u_k(P), v_k(P)) with bilinear
+ * sampling (zero off the extended panel), U_k the depth of P along the central ray.
+ * Scratch: 2 batch n_angles nv (nu + pad) floats. Synchronises `stream`. */
+int cbct_fdk(const cbct_geom *g, const float *proj, float *vol, int batch, int accumulate, void *stream);
+
+/* ||K|| for K = [P; gamma grad] by `iters` power iterations on K^T K from the
+ * all-ones volume (FP32 operators, FP64 norms); gamma = 0 gives ||P||.
+ * Synchronises `stream`. */
+int cbct_opnorm(const cbct_geom *g, double gamma, int iters, double *out, void *stream);
+
+/* PDHG (Chambolle-Pock 2011) for min_x 1/2 ||P x - y||^2 + lam ||grad x||_{2,1}
+ * (+ x >= 0 when nonneg), the paper's TV baseline (Sec. 2.3), on K = [P; gamma grad]
+ * with F2 = (lam/gamma) ||.||_{2,1}: per iteration
+ *   z1 <- (z1 + sigma (P xbar - y)) / (1 + sigma)
+ *   z2 <- project_{|.| <= lam/gamma}(z2 + sigma gamma grad xbar)
+ *   x+ <- max(0, x - tau (P^T z1 - gamma div z2)); xbar <- 2 x+ - x; x <- x+
+ * grad = forward differences in voxel units, zero on the last index (Neumann),
+ * div = -grad^T. Convergence needs sigma tau ||K||^2 < 1 (cbct_opnorm). y, x0 and x
+ * are device arrays of `batch` items; x0 and x may alias. Scratch: 5 volumes and 2
+ * projections per item. */
+int cbct_pdhg(const cbct_geom *g, const float *y, const float *x0, float *x, int batch, int niter, double lam,
+              double gamma, double sigma, double tau, int nonneg, void *stream);
+
+/* Landweber iterations x <- x - tau P^T (P x - y) (clamped at 0 when nonneg), in place
+ * on x. Scratch: one volume and one projection per item. */
+int cbct_landweber(const cbct_geom *g, const float *y, float *x, int batch, int niter, double tau, int nonneg,
+                   void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -53,6 +53,11 @@ SIGNATURES = {
     "cbct_simulate": (I32, [P, P, I32, F64, U64, P, P, P]),
     "cbct_redundancy_weight": (I32, [P, P, P]),
     "cbct_fov": (I32, [P, P, P]),
+    "cbct_fdk_pad": (I32, [P]),
+    "cbct_fdk": (I32, [P, P, P, I32, I32, P]),
+    "cbct_opnorm": (I32, [P, F64, I32, ctypes.POINTER(F64), P]),
+    "cbct_pdhg": (I32, [P, P, P, P, I32, I32, F64, F64, F64, F64, I32, P]),
+    "cbct_landweber": (I32, [P, P, P, I32, I32, F64, I32, P]),
 }
 
 EXTRA_SIGNATURES: dict = {}

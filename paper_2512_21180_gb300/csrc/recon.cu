@@ -1,0 +1,363 @@
+// Classical reconstructions used by the learned method and as its judge:
+//  - FDK with redundancy weighting (paper Algorithm 1 initialisation "FDK_w",
+//    Sec. 2.4; Feldkamp, Davis, Kress 1984): cosine and redundancy weights, Ram-Lak
+//    ramp filter along detector rows at the isocentre pitch, distance-weighted
+//    voxel backprojection. An offset panel's rows are zero-padded on the short side
+//    to the mirror image of the long edge before filtering.
+//  - PDHG (Chambolle-Pock 2011) for 1/2 ||P x - y||^2 + lam TV(x), x >= 0, isotropic
+//    TV by forward differences (the paper's TV baseline, Sec. 2.3), on K = [P; gamma grad]
+//    with the TV ball radius lam / gamma.
+//  - Landweber iterations x <- x - tau P^T (P x - y) (the gradient term of Algorithm 1).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "geom_impl.h"
+
+namespace cbct {
+
+static int grid1(long long n) {
+    long long b = (n + 255) / 256;
+    return (int)std::max<long long>(1, std::min<long long>(b, 152LL * 32));
+}
+
+// ---- FDK ---------------------------------------------------------------------------
+
+// q0[b][k][v][e] = proj * w(u) * sdd / sqrt(sdd^2 + u^2 + v^2) on the extended row
+// (e = iu + lo), zero in the padding.
+__global__ void k_fdk_weight(const float *__restrict__ proj, const float *__restrict__ w, float *__restrict__ q0,
+                             int nu, int nv, int nue, int lo, long long rows, double du, double dv, double uoff,
+                             double voff, double sdd) {
+    const long long n = rows * nue;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const long long row = e / nue;
+        const int ie = (int)(e - row * nue), iu = ie - lo;
+        const int iv = (int)(row % nv);
+        float val = 0.f;
+        if (iu >= 0 && iu < nu) {
+            const float u = (float)((iu - 0.5 * (nu - 1)) * du + uoff);
+            const float v = (float)((iv - 0.5 * (nv - 1)) * dv + voff);
+            const float s = (float)sdd;
+            val = proj[row * nu + iu] * w[iu] * s * rsqrtf(s * s + u * u + v * v);
+        }
+        q0[e] = val;
+    }
+}
+
+// q[row][e] = tau * sum_m h(e - m) q0[row][m], Ram-Lak at pitch tau (h(0) = 1/(4 tau^2),
+// h(odd j) = -1/(pi^2 j^2 tau^2), 0 for even j != 0); one CTA per row, the row and
+// the kernel table (tau h(|j|)) staged in shared memory.
+__global__ void k_fdk_ramp(const float *__restrict__ q0, float *__restrict__ q, int nue, float tau) {
+    extern __shared__ float sm[];
+    float *row = sm, *hk = sm + nue;
+    const long long r = blockIdx.x;
+    const float *src = q0 + r * nue;
+    const float c1 = -1.0f / (3.14159265358979f * 3.14159265358979f * tau);
+    for (int i = threadIdx.x; i < nue; i += blockDim.x) {
+        row[i] = src[i];
+        hk[i] = i == 0 ? 1.0f / (4.0f * tau) : ((i & 1) ? c1 / ((float)i * (float)i) : 0.0f);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nue; e += blockDim.x) {
+        float acc = hk[0] * row[e];
+        // odd offsets only: m of the other parity than e
+        for (int m = (e & 1) ? 0 : 1; m < nue; m += 2) acc = fmaf(hk[abs(e - m)], row[m], acc);
+        q[r * nue + e] = acc;
+    }
+}
+
+// vol(P) (+)= (2 pi / n_angles) sum_k (sid / U)^2 bilinear(q_k, u(P), v(P))
+__global__ void k_fdk_backproject(const float *__restrict__ q, const double2 *__restrict__ cs, float *__restrict__ vol,
+                                  int nx, int ny, int nz, int na, int nue, int nv, int lo, int nu, float vx, float vy,
+                                  float vz, float cx, float cy, float cz, float sid, float sdd, float du, float dv,
+                                  float uoff, float voff, int accumulate) {
+    const int ix = blockIdx.x * 32 + threadIdx.x, iy = blockIdx.y * 8 + threadIdx.y;
+    const int iz = blockIdx.z % nz, b = blockIdx.z / nz;
+    if (ix >= nx || iy >= ny) return;
+    const float px = (ix - 0.5f * (nx - 1)) * vx + cx;
+    const float py = (iy - 0.5f * (ny - 1)) * vy + cy;
+    const float pz = (iz - 0.5f * (nz - 1)) * vz + cz;
+    const float hu = 0.5f * (nu - 1) + lo, hv = 0.5f * (nv - 1);
+    const float *qb = q + (long long)b * na * nv * nue;
+    float acc = 0.f;
+    for (int k = 0; k < na; ++k) {
+        const double2 t = cs[k];
+        const float c = (float)t.x, s = (float)t.y;
+        const float U = sid - (px * c + py * s);
+        if (!(U > 0.f)) continue;
+        const float m = sdd / U;
+        const float fu = (m * (-px * s + py * c) - uoff) / du + hu;
+        const float fv = (m * pz - voff) / dv + hv;
+        const float u0 = floorf(fu), v0 = floorf(fv);
+        const float au = fu - u0, av = fv - v0;
+        const int ju = (int)u0, jv = (int)v0;
+        if (ju < -1 || ju >= nue || jv < -1 || jv >= nv) continue;
+        const float *qk = qb + (long long)k * nv * nue;
+        const bool u0k = ju >= 0, u1k = ju + 1 < nue, v0k = jv >= 0, v1k = jv + 1 < nv;
+        const float q00 = (u0k && v0k) ? __ldg(qk + (long long)jv * nue + ju) : 0.f;
+        const float q10 = (u1k && v0k) ? __ldg(qk + (long long)jv * nue + ju + 1) : 0.f;
+        const float q01 = (u0k && v1k) ? __ldg(qk + (long long)(jv + 1) * nue + ju) : 0.f;
+        const float q11 = (u1k && v1k) ? __ldg(qk + (long long)(jv + 1) * nue + ju + 1) : 0.f;
+        const float a0 = fmaf(au, q10 - q00, q00), a1 = fmaf(au, q11 - q01, q01);
+        const float r = sid / U;
+        acc = fmaf(r * r, fmaf(av, a1 - a0, a0), acc);
+    }
+    acc *= 6.28318530717958647f / na;
+    float *o = vol + (((long long)b * nz + iz) * ny + iy) * nx + ix;
+    *o = accumulate ? *o + acc : acc;
+}
+
+// ---- PDHG-TV pieces -------------------------------------------------------------------
+
+// z1 <- (z1 + sigma (p - y)) / (1 + sigma)
+__global__ void k_pdhg_dual1(float *__restrict__ z1, const float *__restrict__ p, const float *__restrict__ y,
+                             long long n, float sigma) {
+    const float inv = 1.0f / (1.0f + sigma);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        z1[e] = (z1[e] + sigma * (p[e] - y[e])) * inv;
+}
+
+// z2 <- project_{|.| <= rad}(z2 + sigma gamma grad xbar), grad = forward differences
+// (zero on the last index of each axis); z2 layout [3][B][nz][ny][nx]
+__global__ void k_pdhg_dual2(float *__restrict__ z2, const float *__restrict__ xb, int nx, int ny, int nz, int batch,
+                             float sg, float rad) {
+    const long long N = (long long)batch * nx * ny * nz;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(e % nx), iy = (int)((e / nx) % ny), iz = (int)((e / ((long long)nx * ny)) % nz);
+        const float x = xb[e];
+        const float gx = ix < nx - 1 ? xb[e + 1] - x : 0.f;
+        const float gy = iy < ny - 1 ? xb[e + nx] - x : 0.f;
+        const float gz = iz < nz - 1 ? xb[e + (long long)nx * ny] - x : 0.f;
+        const float a0 = z2[e] + sg * gx, a1 = z2[N + e] + sg * gy, a2 = z2[2 * N + e] + sg * gz;
+        const float nrm = sqrtf(a0 * a0 + a1 * a1 + a2 * a2);
+        const float sc = nrm > rad ? rad / nrm : 1.0f;
+        z2[e] = a0 * sc;
+        z2[N + e] = a1 * sc;
+        z2[2 * N + e] = a2 * sc;
+    }
+}
+
+// x+ = max(0, x - tau (bt - gamma div z2)); xbar = 2 x+ - x; x = x+
+__global__ void k_pdhg_primal(float *__restrict__ x, float *__restrict__ xb, const float *__restrict__ bt,
+                              const float *__restrict__ z2, int nx, int ny, int nz, int batch, float tau, float gamma,
+                              int nonneg) {
+    const long long N = (long long)batch * nx * ny * nz;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(e % nx), iy = (int)((e / nx) % ny), iz = (int)((e / ((long long)nx * ny)) % nz);
+        const long long sxy = (long long)nx * ny;
+        float dv = 0.f;
+        dv += (ix < nx - 1 ? z2[e] : 0.f) - (ix > 0 ? z2[e - 1] : 0.f);
+        dv += (iy < ny - 1 ? z2[N + e] : 0.f) - (iy > 0 ? z2[N + e - nx] : 0.f);
+        dv += (iz < nz - 1 ? z2[2 * N + e] : 0.f) - (iz > 0 ? z2[2 * N + e - sxy] : 0.f);
+        const float xo = x[e];
+        float xn = xo - tau * (bt[e] - gamma * dv);
+        if (nonneg && xn < 0.f) xn = 0.f;
+        xb[e] = 2.f * xn - xo;
+        x[e] = xn;
+    }
+}
+
+// r = p - y
+__global__ void k_sub(const float *__restrict__ p, const float *__restrict__ y, float *__restrict__ r, long long n) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        r[e] = p[e] - y[e];
+}
+
+// x <- x - tau g  (optionally clamped at 0)
+__global__ void k_axpy_clamp(float *__restrict__ x, const float *__restrict__ gr, long long n, float tau, int nonneg) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        float v = x[e] - tau * gr[e];
+        if (nonneg && v < 0.f) v = 0.f;
+        x[e] = v;
+    }
+}
+
+// out = P^T P x - gamma^2 div grad x  (operator of the power iteration for ||K||)
+__global__ void k_tv_normal(const float *__restrict__ x, float *__restrict__ out, int nx, int ny, int nz, int batch,
+                            float g2) {
+    const long long N = (long long)batch * nx * ny * nz, sxy = (long long)nx * ny;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(e % nx), iy = (int)((e / nx) % ny), iz = (int)((e / sxy) % nz);
+        const float c = x[e];
+        // -div grad x = sum over axes of (x - x_prev) contributions, Neumann
+        float l = 0.f;
+        if (ix < nx - 1) l += c - x[e + 1];
+        if (ix > 0) l += c - x[e - 1];
+        if (iy < ny - 1) l += c - x[e + nx];
+        if (iy > 0) l += c - x[e - nx];
+        if (iz < nz - 1) l += c - x[e + sxy];
+        if (iz > 0) l += c - x[e - sxy];
+        out[e] += g2 * l;
+    }
+}
+
+__global__ void k_sumsq_d(const float *__restrict__ x, long long n, double *out) {
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        s += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+__global__ void k_scale_inv_sqrt(float *x, long long n, const double *sumsq) {
+    const float s = (float)(1.0 / sqrt(*sumsq));
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] *= s;
+}
+
+__global__ void k_fill1(float *x, long long n, float v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+}  // namespace cbct
+
+using namespace cbct;
+
+extern "C" int cbct_fdk_pad(const cbct_geom *g) {
+    if (!g) return fail(CBCT_EINVAL, "cbct_fdk_pad: NULL geometry");
+    return (int)ceil(2.0 * fabs(g->desc.u_offset) / g->desc.du - 1e-9);
+}
+
+extern "C" int cbct_fdk(const cbct_geom *g, const float *proj, float *vol, int batch, int accumulate, void *stream) {
+    if (!g || !proj || !vol || batch < 1 || (accumulate != 0 && accumulate != 1))
+        return fail(CBCT_EINVAL, "cbct_fdk: invalid argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const cbct_geom_desc &d = g->desc;
+    const int npad = cbct_fdk_pad(g), nue = d.nu + npad, lo = d.u_offset > 0 ? npad : 0;
+    const long long rows = (long long)batch * d.n_angles * d.nv;
+    const size_t smem = 2 * sizeof(float) * nue;
+    if (smem > 200 * 1024) return fail(CBCT_EINVAL, "cbct_fdk: extended detector row too long");
+    const double PI = 3.14159265358979323846;
+    std::vector<double2> cs(d.n_angles);
+    for (int k = 0; k < d.n_angles; ++k) {
+        const double th = g->angles.empty() ? 2.0 * PI * k / d.n_angles : g->angles[k];
+        cs[k] = make_double2(cos(th), sin(th));
+    }
+    float *q0 = nullptr, *q = nullptr, *w = nullptr;
+    double2 *dcs = nullptr;
+    CBCT_CUDA_TRY(cudaMallocAsync((void **)&q0, sizeof(float) * rows * nue * 2 + sizeof(float) * d.nu, st));
+    q = q0 + rows * nue;
+    w = q + rows * nue;
+    cudaError_t e = cudaMallocAsync((void **)&dcs, sizeof(double2) * d.n_angles, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dcs, cs.data(), sizeof(double2) * d.n_angles, cudaMemcpyHostToDevice, st);
+    int rc = 0;
+    if (e == cudaSuccess) rc = cbct_redundancy_weight(g, w, stream);
+    if (e == cudaSuccess && rc == 0) {
+        k_fdk_weight<<<grid1(rows * nue), 256, 0, st>>>(proj, w, q0, d.nu, d.nv, nue, lo, rows, d.du, d.dv, d.u_offset,
+                                                        d.v_offset, d.sdd);
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k_fdk_ramp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_fdk_ramp<<<(unsigned)rows, 256, smem, st>>>(q0, q, nue, (float)(d.du * d.sid / d.sdd));
+        dim3 grd((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz * batch);
+        k_fdk_backproject<<<grd, dim3(32, 8), 0, st>>>(
+            q, dcs, vol, d.nx, d.ny, d.nz, d.n_angles, nue, d.nv, lo, d.nu, (float)d.vox[0], (float)d.vox[1],
+            (float)d.vox[2], (float)d.center[0], (float)d.center[1], (float)d.center[2], (float)d.sid, (float)d.sdd,
+            (float)d.du, (float)d.dv, (float)d.u_offset, (float)d.v_offset, accumulate);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host angle table must outlive the upload
+    cudaFreeAsync(q0, st);
+    if (dcs) cudaFreeAsync(dcs, st);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "cbct_fdk");
+    return 0;
+}
+
+extern "C" int cbct_opnorm(const cbct_geom *g, double gamma, int iters, double *out, void *stream) {
+    if (!g || !out || iters < 1) return fail(CBCT_EINVAL, "cbct_opnorm: invalid argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const GeomDev &d = g->dev;
+    const long long nvox = (long long)d.n[0] * d.n[1] * d.n[2], nproj = (long long)d.na * d.nv * d.nu;
+    float *x = nullptr, *p = nullptr, *y = nullptr;
+    double *acc = nullptr;
+    CBCT_CUDA_TRY(cudaMallocAsync((void **)&x, sizeof(float) * (2 * nvox + nproj) + 16, st));
+    y = x + nvox;
+    p = y + nvox;
+    acc = reinterpret_cast<double *>(p + nproj + (nproj & 1));
+    int rc = 0;
+    k_fill1<<<grid1(nvox), 256, 0, st>>>(x, nvox, 1.0f);
+    double nrm2 = 0.0;
+    for (int it = 0; it < iters && rc == 0; ++it) {
+        cudaMemsetAsync(acc, 0, sizeof(double), st);
+        k_sumsq_d<<<grid1(nvox), 256, 0, st>>>(x, nvox, acc);
+        k_scale_inv_sqrt<<<grid1(nvox), 256, 0, st>>>(x, nvox, acc);
+        rc = forward_project(g, x, p, 1, 0, stream);
+        if (rc == 0) rc = back_project(g, p, y, 1, 0, stream);
+        if (rc == 0 && gamma != 0.0)
+            k_tv_normal<<<grid1(nvox), 256, 0, st>>>(x, y, d.n[0], d.n[1], d.n[2], 1, (float)(gamma * gamma));
+        std::swap(x, y);
+    }
+    cudaError_t e = cudaSuccess;
+    if (rc == 0) {
+        cudaMemsetAsync(acc, 0, sizeof(double), st);
+        k_sumsq_d<<<grid1(nvox), 256, 0, st>>>(x, nvox, acc);
+        e = cudaMemcpyAsync(&nrm2, acc, sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    cudaFreeAsync(std::min(x, y), st);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "cbct_opnorm");
+    *out = sqrt(sqrt(nrm2));
+    return 0;
+}
+
+extern "C" int cbct_pdhg(const cbct_geom *g, const float *y, const float *x0, float *x, int batch, int niter,
+                         double lam, double gamma, double sigma, double tau, int nonneg, void *stream) {
+    if (!g || !y || !x0 || !x || batch < 1 || niter < 0 || !(gamma > 0) || !(sigma > 0) || !(tau > 0) || lam < 0)
+        return fail(CBCT_EINVAL, "cbct_pdhg: invalid argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const GeomDev &d = g->dev;
+    const long long N = (long long)batch * d.n[0] * d.n[1] * d.n[2], M = (long long)batch * d.na * d.nv * d.nu;
+    float *buf = nullptr;
+    // xbar, bt (N each), z2 (3N), z1, p (M each)
+    CBCT_CUDA_TRY(cudaMallocAsync((void **)&buf, sizeof(float) * (5 * N + 2 * M), st));
+    float *xb = buf, *bt = xb + N, *z2 = bt + N, *z1 = z2 + 3 * N, *p = z1 + M;
+    if (x != x0) cudaMemcpyAsync(x, x0, sizeof(float) * N, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(xb, x0, sizeof(float) * N, cudaMemcpyDeviceToDevice, st);
+    cudaMemsetAsync(z2, 0, sizeof(float) * (3 * N + M), st);
+    int rc = 0;
+    const float rad = (float)(lam / gamma);
+    for (int it = 0; it < niter && rc == 0; ++it) {
+        rc = forward_project(g, xb, p, batch, 0, stream);
+        if (rc) break;
+        k_pdhg_dual1<<<grid1(M), 256, 0, st>>>(z1, p, y, M, (float)sigma);
+        k_pdhg_dual2<<<grid1(N), 256, 0, st>>>(z2, xb, d.n[0], d.n[1], d.n[2], batch, (float)(sigma * gamma), rad);
+        rc = back_project(g, z1, bt, batch, 0, stream);
+        if (rc) break;
+        k_pdhg_primal<<<grid1(N), 256, 0, st>>>(x, xb, bt, z2, d.n[0], d.n[1], d.n[2], batch, (float)tau,
+                                                 (float)gamma, nonneg);
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(buf, st);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "cbct_pdhg");
+    return 0;
+}
+
+extern "C" int cbct_landweber(const cbct_geom *g, const float *y, float *x, int batch, int niter, double tau,
+                              int nonneg, void *stream) {
+    if (!g || !y || !x || batch < 1 || niter < 0) return fail(CBCT_EINVAL, "cbct_landweber: invalid argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const GeomDev &d = g->dev;
+    const long long N = (long long)batch * d.n[0] * d.n[1] * d.n[2], M = (long long)batch * d.na * d.nv * d.nu;
+    float *buf = nullptr;
+    CBCT_CUDA_TRY(cudaMallocAsync((void **)&buf, sizeof(float) * (N + M), st));
+    float *gr = buf, *r = buf + N;
+    int rc = 0;
+    for (int it = 0; it < niter && rc == 0; ++it) {
+        rc = forward_project(g, x, r, batch, 0, stream);
+        if (rc) break;
+        k_sub<<<grid1(M), 256, 0, st>>>(r, y, r, M);
+        rc = back_project(g, r, gr, batch, 0, stream);
+        if (rc) break;
+        k_axpy_clamp<<<grid1(N), 256, 0, st>>>(x, gr, N, (float)tau, nonneg);
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(buf, st);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "cbct_landweber");
+    return 0;
+}

@@ -71,3 +71,51 @@ def fov(geom: Geometry) -> torch.Tensor:
     with torch.cuda.device(geom.device):
         check(_lib.load().cbct_fov(geom.handle, V.data_ptr(), _st(V)), "cbct_fov")
     return V
+
+
+def _b(t: torch.Tensor, shape):
+    t = t.contiguous()
+    if t.dim() == len(shape):
+        t = t.unsqueeze(0)
+    assert tuple(t.shape[1:]) == tuple(shape) and t.dtype == torch.float32 and t.is_cuda
+    return t
+
+
+def fdk(geom: Geometry, proj: torch.Tensor) -> torch.Tensor:
+    """FDK_w reconstruction of [B, na, nv, nu] projections -> [B, nz, ny, nx]."""
+    p = _b(proj, geom.proj_shape)
+    out = torch.empty((p.shape[0],) + geom.vol_shape, device=p.device, dtype=torch.float32)
+    with torch.cuda.device(p.device):
+        check(_lib.load().cbct_fdk(geom.handle, p.data_ptr(), out.data_ptr(), p.shape[0], 0, _st(p)), "cbct_fdk")
+    return out
+
+
+def opnorm(geom: Geometry, gamma: float = 0.0, iters: int = 30) -> float:
+    import ctypes
+    out = ctypes.c_double(0.0)
+    with torch.cuda.device(geom.device):
+        check(_lib.load().cbct_opnorm(geom.handle, float(gamma), int(iters), ctypes.byref(out),
+                                      torch.cuda.current_stream().cuda_stream), "cbct_opnorm")
+    return out.value
+
+
+def pdhg(geom: Geometry, y: torch.Tensor, x0: torch.Tensor, niter: int, lam: float, gamma: float, sigma: float,
+         tau: float, nonneg: bool = True) -> torch.Tensor:
+    yy = _b(y, geom.proj_shape)
+    xx = _b(x0, geom.vol_shape)
+    out = torch.empty_like(xx)
+    with torch.cuda.device(yy.device):
+        check(_lib.load().cbct_pdhg(geom.handle, yy.data_ptr(), xx.data_ptr(), out.data_ptr(), yy.shape[0], int(niter),
+                                    float(lam), float(gamma), float(sigma), float(tau), int(nonneg), _st(yy)),
+              "cbct_pdhg")
+    return out
+
+
+def landweber(geom: Geometry, y: torch.Tensor, x: torch.Tensor, niter: int, tau: float,
+              nonneg: bool = False) -> torch.Tensor:
+    yy = _b(y, geom.proj_shape)
+    xx = _b(x, geom.vol_shape).clone()
+    with torch.cuda.device(yy.device):
+        check(_lib.load().cbct_landweber(geom.handle, yy.data_ptr(), xx.data_ptr(), yy.shape[0], int(niter),
+                                         float(tau), int(nonneg), _st(yy)), "cbct_landweber")
+    return xx

@@ -1,0 +1,103 @@
+"""FP64 reference of the learned primal-dual blocks (test infrastructure only).
+
+Plain PyTorch CPU in float64. The convolution blocks of the paper's dual and primal
+updates (Sec. 2.4, Algorithm 1: Gamma and Lambda; here 3-layer width-32 blocks
+with LeakyReLU between layers, 2D over the detector plane for the dual block, 3D
+over the volume for the primal block) and one unrolled iteration pair, with the
+projector pair taken from the FP64 C oracle through autograd functions.
+
+BF16 operands are emulated by rounding the inputs and weights to bfloat16 before
+the FP64 arithmetic, exactly where the GPU path rounds them.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+import torch.nn.functional as F
+
+from . import adjoint as _adjoint
+from . import forward as _forward
+
+SLOPE = 0.2
+
+
+def bf16(t: torch.Tensor) -> torch.Tensor:
+    """Round to bfloat16 (round to nearest even) and back to float64."""
+    return t.to(torch.bfloat16).to(torch.float64)
+
+
+def conv(x: torch.Tensor, w: torch.Tensor, b: torch.Tensor | None) -> torch.Tensor:
+    """'Same' zero-padded 3x3 (2D, x [N, C, H, W]) or 3x3x3 (3D, x [N, C, D, H, W])
+    cross-correlation: y[o, p] = b[o] + sum_{c, t} w[o, c, t] x[c, p + t - 1]."""
+    if x.dim() == 4:
+        return F.conv2d(x, w, b, padding=1)
+    return F.conv3d(x, w, b, padding=1)
+
+
+def lrelu(x: torch.Tensor) -> torch.Tensor:
+    return torch.where(x > 0, x, SLOPE * x)
+
+
+def block(x: torch.Tensor, params, round_bf16: bool = True) -> torch.Tensor:
+    """conv -> LReLU -> conv -> LReLU -> conv; params = [(w1, b1), (w2, b2), (w3, b3)].
+    With round_bf16 the conv inputs and weights are rounded to bfloat16 first (the
+    GPU's operand precision); accumulation stays FP64."""
+    r = bf16 if round_bf16 else (lambda t: t)
+    h = x
+    for i, (w, b) in enumerate(params):
+        h = conv(r(h), r(w), b)
+        if i < len(params) - 1:
+            h = lrelu(h)
+    return h
+
+
+class _Proj(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, G, x):
+        ctx.G = G
+        return torch.from_numpy(_forward(G, x.detach().numpy()))
+
+    @staticmethod
+    def backward(ctx, g):
+        return None, torch.from_numpy(_adjoint(ctx.G, g.detach().numpy()))
+
+
+class _Back(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, G, y):
+        ctx.G = G
+        return torch.from_numpy(_adjoint(G, y.detach().numpy()))
+
+    @staticmethod
+    def backward(ctx, g):
+        return None, torch.from_numpy(_forward(ctx.G, g.detach().numpy()))
+
+
+def project(G, x):
+    return _Proj.apply(G, x)
+
+
+def backproject(G, y):
+    return _Back.apply(G, y)
+
+
+def lpd(G, y: torch.Tensor, x0: torch.Tensor, w_red: torch.Tensor, dual_params, primal_params,
+        n_mem: int = 5, round_bf16: bool = True, scale: float = 1.0):
+    """Learned primal-dual (Adler-style memory of n_mem channels, the reading of the
+    paper's primal/dual latents for this workload):
+        h <- h + Gamma_n([h, P f_1, y])          (per projection image, 2D block)
+        f <- f + Lambda_n([f, P^T (w h_1)])      (3D block)
+    f starts as x0 repeated, h as zeros; the output is f_0. Projections use the
+    operators scaled by `scale` (normalised operators). y: [na, nv, nu];
+    x0: [nz, ny, nx]; w_red: [nu] redundancy weight."""
+    na, nv, nu = y.shape
+    f = x0.unsqueeze(0).repeat(n_mem, 1, 1, 1)
+    h = torch.zeros((n_mem, na, nv, nu), dtype=torch.float64)
+    for dp, pp in zip(dual_params, primal_params):
+        pf = scale * project(G, f[1])
+        inp = torch.cat([h, pf.unsqueeze(0), y.unsqueeze(0)], 0)         # [n_mem + 2, na, nv, nu]
+        h = h + block(inp.permute(1, 0, 2, 3), dp, round_bf16).permute(1, 0, 2, 3)
+        bp = scale * backproject(G, w_red.view(1, 1, -1) * h[1])
+        inp = torch.cat([f, bp.unsqueeze(0)], 0).unsqueeze(0)             # [1, n_mem + 1, nz, ny, nx]
+        f = f + block(inp, pp, round_bf16)[0]
+    return f[0]

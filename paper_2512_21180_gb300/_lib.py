@@ -58,6 +58,8 @@ SIGNATURES = {
     "cbct_opnorm": (I32, [P, F64, I32, ctypes.POINTER(F64), P]),
     "cbct_pdhg": (I32, [P, P, P, P, I32, I32, F64, F64, F64, F64, I32, P]),
     "cbct_landweber": (I32, [P, P, P, I32, I32, F64, I32, P]),
+    "cbct_conv": (I32, [P, I32, I32, I32, I32, I32, I32, P, P, I32, I32, I32, I32, F32, P, I32, P, P, I64, P, P]),
+    "cbct_conv_wgrad": (I32, [P, I32, I32, P, I32, I32, I32, I32, I32, I32, I32, P, P, I32, P]),
 }
 
 EXTRA_SIGNATURES: dict = {}

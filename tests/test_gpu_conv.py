@@ -1,0 +1,125 @@
+"""Tensor-core convolutions (tcgen05) and their gradients against the FP64
+reference on BF16-rounded operands."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+SLOPE = 0.2
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2512_21180_gb300 import build
+    build.build()
+    from paper_2512_21180_gb300 import _lib
+    return _lib
+
+
+def to_cl(x, cp):
+    """[N, C, *S] float64 -> BF16 channels-last [N, *S, cp] on the GPU (zero padded)."""
+    n, c = x.shape[:2]
+    y = torch.zeros((n,) + tuple(x.shape[2:]) + (cp,), dtype=torch.float64)
+    y[..., :c] = x.movedim(1, -1)
+    return y.to(torch.bfloat16).cuda().contiguous()
+
+
+def from_cl(y, c):
+    return y[..., :c].double().movedim(-1, 1).cpu()
+
+
+def run_conv(L, x_cl, dims, taps3d, w, b, cin, cout, flip, epi, cpout, mask=None, state=None):
+    nimg = x_cl.shape[0]
+    D, H, W = dims if taps3d else (1,) + dims
+    n_out = cin if flip else cout
+    y = torch.zeros((nimg,) + tuple(x_cl.shape[1:-1]) + (cpout,), dtype=torch.bfloat16, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sp = state.data_ptr() if state is not None else None
+    ss = state[0].numel() if state is not None else 0
+    rc = L.load().cbct_conv(x_cl.data_ptr(), nimg, D, H, W, x_cl.shape[-1], taps3d, w.data_ptr(),
+                            b.data_ptr() if b is not None else None, cin, cout, flip, epi, SLOPE,
+                            y.data_ptr(), cpout, mask.data_ptr() if mask is not None else None, sp, ss,
+                            status.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    L.check(rc, "cbct_conv")
+    torch.cuda.synchronize()
+    assert status.item() == 0
+    return y
+
+
+def rel(a, b):
+    return float((a - b).norm() / b.norm())
+
+
+CASES = [
+    ("2d_7to32", (19, 37), 0, 7, 32, 3),
+    ("2d_32to32", (16, 40), 0, 32, 32, 2),
+    ("3d_6to32", (9, 10, 21), 1, 6, 32, 2),
+    ("3d_32to32", (8, 12, 17), 1, 32, 32, 1),
+]
+
+
+@pytest.mark.parametrize("name,dims,taps3d,cin,cout,nimg", CASES)
+def test_conv_forward_act(L, name, dims, taps3d, cin, cout, nimg):
+    from oracle import lpd_ref as R
+    rng = np.random.default_rng(hash(name) % 1000)
+    x = torch.tensor(rng.standard_normal((nimg, cin) + dims))
+    w = torch.tensor(rng.standard_normal((cout, cin) + (3,) * len(dims)) * 0.2)
+    b = torch.tensor(rng.standard_normal(cout) * 0.1)
+    cp = (cin + 7) // 8 * 8
+    wg = w.reshape(cout, cin, -1).permute(0, 2, 1).contiguous().float().cuda()   # [cout][taps][cin]
+    y = run_conv(L, to_cl(x, cp), dims, taps3d, wg, b.float().cuda(), cin, cout, 0, 0, 32)
+    ref = R.lrelu(R.conv(R.bf16(x), R.bf16(w), b.float().double()))
+    got = from_cl(y, cout)
+    assert rel(got, ref) <= 1e-2, rel(got, ref)
+    assert rel(got, R.bf16(ref)) <= 4e-3
+
+
+@pytest.mark.parametrize("taps3d,dims", [(0, (21, 33)), (1, (7, 11, 13))])
+def test_conv_residual_into_state(L, taps3d, dims):
+    from oracle import lpd_ref as R
+    rng = np.random.default_rng(7)
+    cin, cout, nimg = 32, 5, 2
+    x = torch.tensor(rng.standard_normal((nimg, cin) + dims))
+    w = torch.tensor(rng.standard_normal((cout, cin) + (3,) * len(dims)) * 0.1)
+    b = torch.tensor(rng.standard_normal(cout) * 0.1)
+    state0 = torch.tensor(rng.standard_normal((cout, nimg) + dims))
+    state = state0.float().cuda().contiguous()
+    wg = w.reshape(cout, cin, -1).permute(0, 2, 1).contiguous().float().cuda()
+    run_conv(L, to_cl(x, 32), dims, taps3d, wg, b.float().cuda(), cin, cout, 0, 1, 8, state=state)
+    ref = state0 + R.conv(R.bf16(x), R.bf16(w), b.float().double()).movedim(1, 0)
+    assert rel(state.double().cpu(), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("taps3d,dims", [(0, (17, 26)), (1, (6, 9, 11))])
+def test_conv_input_gradient_and_weight_gradient(L, taps3d, dims):
+    """flip = 1 computes dL/dx of conv for upstream dL/dy, masked by the LeakyReLU
+    derivative of a forward activation; wgrad matches autograd."""
+    from oracle import lpd_ref as R
+    rng = np.random.default_rng(11)
+    cin, cout, nimg = 32, 32, 2
+    x = R.bf16(torch.tensor(rng.standard_normal((nimg, cin) + dims)))
+    w = R.bf16(torch.tensor(rng.standard_normal((cout, cin) + (3,) * len(dims)) * 0.1))
+    dy = R.bf16(torch.tensor(rng.standard_normal((nimg, cout) + dims)))
+    act = torch.tensor(rng.standard_normal((nimg, cin) + dims))        # sign pattern of a forward activation
+    xr = x.clone().requires_grad_(True)
+    wr = w.clone().requires_grad_(True)
+    br = torch.zeros(cout, dtype=torch.float64, requires_grad=True)
+    (R.conv(xr, wr, br) * dy).sum().backward()
+    ref_dx = xr.grad * torch.where(R.bf16(act) > 0, 1.0, SLOPE)
+    wg = w.reshape(cout, cin, -1).permute(0, 2, 1).contiguous().float().cuda()
+    y = run_conv(L, to_cl(dy, 32), dims, taps3d, wg, None, cin, cout, 1, 2, 32, mask=to_cl(act, 32))
+    got = from_cl(y, cin)
+    assert rel(got, ref_dx) <= 1e-2, rel(got, ref_dx)
+    # weight / bias gradient
+    D, H, W = dims if taps3d else (1,) + dims
+    dw = torch.zeros((cout, 27 if taps3d else 9, cin), device="cuda")
+    db = torch.zeros(cout, device="cuda")
+    x_cl, dy_cl = to_cl(x, 32), to_cl(dy, 32)   # keep both alive until the kernel has run
+    L.check(L.load().cbct_conv_wgrad(x_cl.data_ptr(), 32, cin, dy_cl.data_ptr(), 32, cout, nimg, D,
+                                     H, W, taps3d, dw.data_ptr(), db.data_ptr(), 0,
+                                     torch.cuda.current_stream().cuda_stream), "wgrad")
+    torch.cuda.synchronize()
+    ref_dw = wr.grad.reshape(cout, cin, -1).permute(0, 2, 1)
+    assert rel(dw.double().cpu(), ref_dw) <= 1e-5
+    assert rel(db.double().cpu(), br.grad) <= 1e-5

@@ -260,6 +260,64 @@ int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d
 int cbct_conv_wgrad(const void *x, int cpin, int cin, const void *dy, int cpout, int cout, int nimg, int D, int H,
                     int W, int taps3d, float *dw, float *db, int accumulate, void *stream);
 
+/* ---- learned primal-dual reconstruction (a7-a9, a12; Sec. 2.4, Algorithm 1) ---- */
+
+typedef struct cbct_lpd cbct_lpd; /* opaque: weights (FP32 master), gradients, Adam moments, workspaces */
+
+typedef struct {
+    int n_iter;                  /* unrolled iterations (8 in the learned workload) */
+    int n_mem;                   /* primal / dual memory channels, 2..6 (5) */
+    int width;                   /* hidden channels of every block; must be 32 */
+    float slope;                 /* LeakyReLU slope (0.2) */
+    float mu_ref;                /* volume unit (1/mm): f' = f / mu_ref internally (0.02) */
+    float bp_scale;              /* scale of P^T (w h_1) in the primal input; <= 0: 1 / max P^T(w 1) */
+    unsigned long long seed;     /* initial weights (He normal; last layer of a block x 0.1; zero bias) */
+} cbct_lpd_desc;
+
+/* Network on geometry g (which must outlive it): per iteration n a dual block
+ * Gamma_n (3x3 convs over each projection image: n_mem + 2 -> width -> width -> n_mem)
+ * and a primal block Lambda_n (3x3x3: n_mem + 1 -> width -> width -> n_mem), LeakyReLU
+ * between convs; parameters flat FP32 per iteration [dual w1 b1 w2 b2 w3 b3, primal
+ * ...], w as [cout][taps][cin]. Memory: (n_iter + 1) iterates of n_mem volumes and
+ * n_mem projections plus ~4 x 32-channel BF16 activations per block. Synchronises. */
+int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lpd **out);
+void lpd_destroy(cbct_lpd *m);
+
+/* Parameter count and device pointers to the parameters and the gradient buffer. */
+int lpd_info(const cbct_lpd *m, long long *nparams, float **params, float **grads, float *bp_scale);
+
+/* x_out = LPD(y, x0): f <- x0 / mu_ref repeated, h <- 0; for n < n_iter:
+ *   h <- h + Gamma_n([h, mu_ref P f_1, y]);  f <- f + Lambda_n([f, bp_scale P^T(w h_1)])
+ * (w = the redundancy weight per detector column), x_out = mu_ref f_0. batch must be 1
+ * (gradient accumulation covers larger effective batches). save_for_backward = 1 keeps
+ * the iterates for lpd_backward. */
+int lpd_forward(cbct_lpd *m, const float *y, const float *x0, float *x_out, int batch, int save_for_backward,
+                void *stream);
+
+/* Reverse sweep for dL/dx_out = grad_x: recomputes each block's activations from the
+ * saved iterate, ADDS the parameter gradients to the model's gradient buffer, writes
+ * dL/dy and dL/dx0 when those pointers are not NULL. */
+int lpd_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float *grad_x0, void *stream);
+
+int lpd_zero_grad(cbct_lpd *m, void *stream);
+
+/* Adam (Kingma & Ba) on the gradient buffer times grad_scale, bias-corrected for step
+ * number `step` (>= 1). */
+int lpd_adam_step(cbct_lpd *m, float lr, float beta1, float beta2, float eps, int step, float grad_scale,
+                  void *stream);
+
+/* Copy the n FP32 parameters to / from host memory (checkpoints). Synchronous. */
+int lpd_set_params(cbct_lpd *m, const float *host, long long n);
+int lpd_get_params(const cbct_lpd *m, float *host, long long n);
+/* Copy the n accumulated parameter gradients to host memory. Synchronous. */
+int lpd_get_grads(const cbct_lpd *m, float *host, long long n);
+
+/* Masked mean squared error on the device: over elements with V[i] >= thr (all if V is
+ * NULL), *loss = mean (x - ref)^2 and grad = 2 (x - ref) / count there, 0 elsewhere
+ * (grad may be NULL). loss is a device float. Deterministic (fixed-order reduction). */
+int cbct_masked_mse(const float *x, const float *ref, const float *V, float thr, long long n, float *loss,
+                    float *grad, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,22 +82,22 @@ def backproject(G, y):
 
 
 def lpd(G, y: torch.Tensor, x0: torch.Tensor, w_red: torch.Tensor, dual_params, primal_params,
-        n_mem: int = 5, round_bf16: bool = True, scale: float = 1.0):
+        n_mem: int = 5, round_bf16: bool = True, mu_ref: float = 1.0, bp_scale: float = 1.0):
     """Learned primal-dual (Adler-style memory of n_mem channels, the reading of the
-    paper's primal/dual latents for this workload):
-        h <- h + Gamma_n([h, P f_1, y])          (per projection image, 2D block)
-        f <- f + Lambda_n([f, P^T (w h_1)])      (3D block)
-    f starts as x0 repeated, h as zeros; the output is f_0. Projections use the
-    operators scaled by `scale` (normalised operators). y: [na, nv, nu];
-    x0: [nz, ny, nx]; w_red: [nu] redundancy weight."""
+    paper's primal/dual latents for this workload), in units of mu_ref:
+        f <- x0 / mu_ref repeated, h <- 0
+        h <- h + Gamma_n([h, mu_ref P f_1, y])                  (per projection image, 2D)
+        f <- f + Lambda_n([f, bp_scale P^T (w h_1)])            (3D)
+        output mu_ref f_0.
+    y: [na, nv, nu]; x0: [nz, ny, nx]; w_red: [nu] redundancy weight."""
     na, nv, nu = y.shape
-    f = x0.unsqueeze(0).repeat(n_mem, 1, 1, 1)
+    f = (x0 / mu_ref).unsqueeze(0).repeat(n_mem, 1, 1, 1)
     h = torch.zeros((n_mem, na, nv, nu), dtype=torch.float64)
     for dp, pp in zip(dual_params, primal_params):
-        pf = scale * project(G, f[1])
+        pf = mu_ref * project(G, f[1])
         inp = torch.cat([h, pf.unsqueeze(0), y.unsqueeze(0)], 0)         # [n_mem + 2, na, nv, nu]
         h = h + block(inp.permute(1, 0, 2, 3), dp, round_bf16).permute(1, 0, 2, 3)
-        bp = scale * backproject(G, w_red.view(1, 1, -1) * h[1])
+        bp = bp_scale * backproject(G, w_red.view(1, 1, -1) * h[1])
         inp = torch.cat([f, bp.unsqueeze(0)], 0).unsqueeze(0)             # [1, n_mem + 1, nz, ny, nx]
         f = f + block(inp, pp, round_bf16)[0]
-    return f[0]
+    return mu_ref * f[0]

@@ -22,6 +22,11 @@ F64 = ctypes.c_double
 U64 = ctypes.c_uint64
 
 
+class LpdDesc(ctypes.Structure):
+    _fields_ = [("n_iter", I32), ("n_mem", I32), ("width", I32), ("slope", F32), ("mu_ref", F32),
+                ("bp_scale", F32), ("seed", U64)]
+
+
 class GeomDesc(ctypes.Structure):
     _fields_ = [
         ("nx", I32), ("ny", I32), ("nz", I32),
@@ -60,6 +65,17 @@ SIGNATURES = {
     "cbct_landweber": (I32, [P, P, P, I32, I32, F64, I32, P]),
     "cbct_conv": (I32, [P, I32, I32, I32, I32, I32, I32, P, P, I32, I32, I32, I32, F32, P, I32, P, P, I64, P, P]),
     "cbct_conv_wgrad": (I32, [P, I32, I32, P, I32, I32, I32, I32, I32, I32, I32, P, P, I32, P]),
+    "lpd_create": (I32, [P, ctypes.POINTER(LpdDesc), ctypes.POINTER(P)]),
+    "lpd_destroy": (None, [P]),
+    "lpd_info": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(F32)]),
+    "lpd_forward": (I32, [P, P, P, P, I32, I32, P]),
+    "lpd_backward": (I32, [P, P, P, P, P]),
+    "lpd_zero_grad": (I32, [P, P]),
+    "lpd_adam_step": (I32, [P, F32, F32, F32, F32, I32, F32, P]),
+    "lpd_set_params": (I32, [P, P, I64]),
+    "lpd_get_params": (I32, [P, P, I64]),
+    "lpd_get_grads": (I32, [P, P, I64]),
+    "cbct_masked_mse": (I32, [P, P, P, F32, I64, P, P, P]),
 }
 
 EXTRA_SIGNATURES: dict = {}

@@ -397,8 +397,9 @@ using namespace cbct;
 extern "C" int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d, const float *w,
                          const float *bias, int cin, int cout, int flip, int epi, float slope, void *y, int cpout,
                          const void *mask, float *state, long long sstride, int *status, void *stream) {
-    if (!x || !w || nimg < 1 || D < 1 || H < 1 || W < 1 || cin < 1 || cout < 1 || cpin < cin || cpin % 8)
-        return fail(CBCT_EINVAL, "cbct_conv: invalid argument");
+    if (!x || !w || nimg < 1 || D < 1 || H < 1 || W < 1 || cin < 1 || cout < 1 || cpin % 8 ||
+        cpin < (flip ? cout : cin))
+        return fail(CBCT_EINVAL, "cbct_conv: invalid argument (sizes, or cpin below the input channels)");
     const int n_out = flip ? cin : cout;
     if (n_out > 32) return fail(CBCT_EINVAL, "cbct_conv: at most 32 output channels");
     if (epi < 0 || epi > 2) return fail(CBCT_EINVAL, "cbct_conv: bad epilogue");

@@ -1,0 +1,547 @@
+// Learned primal-dual reconstruction (paper Sec. 2.4, Algorithm 1; the unrolled
+// primal-dual network with additive primal and dual updates), in the form of the
+// learned-primal-dual workload: n_iter iterations of
+//     h <- h + Gamma_n([h, P f_1, y])            dual block, 2D convs per projection
+//     f <- f + Lambda_n([f, P^T (w h_1)])        primal block, 3D convs
+// with n_mem-channel primal/dual memories, f starting from the FDK-style initial
+// volume repeated, h from zero, output f_0. Every block is conv3x3(x3) -> LReLU ->
+// conv -> LReLU -> conv at width `width`, BF16 operands on the tensor cores, FP32
+// states. Internally volumes are in units of mu_ref (f' = f / mu_ref, so mu_ref P f'
+// is in the units of y) and the backprojection is scaled by bp_scale.
+//
+// Backward: the iterates (f_n, h_n) are the only saved tensors; each block's
+// activations are recomputed from its saved input during the reverse sweep
+// (activation recomputation), and the projector's adjoint carries gradients through
+// P and P^T.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "geom_impl.h"
+
+namespace cbct {
+
+// from conv.cu
+struct ConvArgs;
+int conv_packed_bytes(int n_out, int ntaps, int cp_in);
+int conv_pack(const float *w, int cout, int ntaps, int cin, int cp_in, int flip, uint8_t *out, cudaStream_t st);
+int conv_wgrad(const __nv_bfloat16 *x, int cpin, int cin, const __nv_bfloat16 *dy, int cpout, int cout, int nimg,
+               int D, int H, int W, int taps3d, float *dw, float *db, int accumulate, cudaStream_t st);
+
+}  // namespace cbct
+
+extern "C" int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d, const float *w,
+                         const float *bias, int cin, int cout, int flip, int epi, float slope, void *y, int cpout,
+                         const void *mask, float *state, long long sstride, int *status, void *stream);
+
+using namespace cbct;
+
+struct LayerSpec {
+    int cin, cout, taps3d;
+    long long w_off, b_off;  // offsets into the flat parameter array
+};
+
+struct cbct_lpd {
+    const cbct_geom *g = nullptr;
+    cbct_lpd_desc d{};
+    std::vector<LayerSpec> layers;  // per iteration: 3 dual then 3 primal
+    long long nparams = 0;
+    float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+    float *wred = nullptr;  // redundancy weight [nu]
+    float bp_scale = 1.f;
+    // saved iterates: f[n_iter + 1][n_mem][nvox], h[n_iter + 1][n_mem][nproj]
+    float *f = nullptr, *h = nullptr;
+    float *y = nullptr;  // the data of the last forward (copied)
+    int saved = 0;
+    // workspaces
+    float *tproj = nullptr, *tproj2 = nullptr, *tvol = nullptr;
+    __nv_bfloat16 *din = nullptr, *a1 = nullptr, *a2 = nullptr, *pin = nullptr, *b1 = nullptr, *b2 = nullptr;
+    __nv_bfloat16 *g32a = nullptr, *g32b = nullptr, *gsmall = nullptr;  // gradient buffers
+    float *gf = nullptr, *gh = nullptr;  // [n_mem + 1][nvox], [n_mem + 2][nproj]
+    int *status = nullptr;
+    long long nvox = 0, nproj = 0;
+};
+
+namespace {
+
+// SplitMix64 + Box-Muller: deterministic initial weights on every platform.
+struct InitRng {
+    uint64_t s;
+    uint64_t next() {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    double uniform() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+    double normal() {
+        const double u1 = uniform(), u2 = uniform();
+        return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+    }
+};
+
+__global__ void k_fill_f(float *x, long long n, float v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+// f[c][i] = x0[i] * s for c < n_mem
+__global__ void k_init_f(const float *__restrict__ x0, float *__restrict__ f, long long n, int n_mem, float s) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float v = x0[i] * s;
+        for (int c = 0; c < n_mem; ++c) f[c * n + i] = v;
+    }
+}
+
+// channels-last BF16 [n][8] from up to 8 FP32 channel-first planes (null = zero)
+struct Planes {
+    const float *p[8];
+    float s[8];
+};
+__global__ void k_pack8(Planes pl, long long n, __nv_bfloat16 *__restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = __float2bfloat16_rn(pl.p[c] ? pl.p[c][i] * pl.s[c] : 0.f);
+        *reinterpret_cast<uint4 *>(out + i * 8) = *reinterpret_cast<const uint4 *>(v);
+    }
+}
+
+// out[k][v][u] = w[u] * in[k][v][u] * s
+__global__ void k_scale_cols(const float *__restrict__ in, const float *__restrict__ w, long long n, int nu, float s,
+                             float *__restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = in[i] * w[i % nu] * s;
+}
+
+// acc[i] += s * src[i]
+__global__ void k_axpy(float *__restrict__ acc, const float *__restrict__ src, long long n, float s) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc[i] += s * src[i];
+}
+
+// out[i] = s * sum_c g[c][i]
+__global__ void k_sum_channels(const float *__restrict__ g, int nc, long long n, float s, float *__restrict__ out,
+                               int accumulate) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        for (int c = 0; c < nc; ++c) v += g[c * n + i];
+        out[i] = accumulate ? out[i] + s * v : s * v;
+    }
+}
+
+__global__ void k_max_reduce(const float *__restrict__ x, long long n, float *out) {
+    float m = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, x[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(out), __float_as_int(m));  // m >= 0
+}
+
+// Adam (Kingma & Ba 2014) with bias correction.
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
+                       long long n, float lr, float b1, float b2, float eps, float c1, float c2, float gs) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i] * gs;
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// masked mean squared error: loss = sum_{mask} (x - r)^2 / count, grad = 2 (x - r) / count on
+// the mask (mask: voxels with V >= thr). Deterministic: per-block partials, fixed-order sum.
+__global__ void k_mse_partial(const float *__restrict__ x, const float *__restrict__ r, const float *__restrict__ V,
+                              float thr, long long n, double *part, double *pcount) {
+    double s = 0.0, c = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (V && V[i] < thr) continue;
+        const double d = (double)x[i] - (double)r[i];
+        s += d * d;
+        c += 1.0;
+    }
+    __shared__ double ss[256], sc[256];
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            ss[threadIdx.x] += ss[threadIdx.x + o];
+            sc[threadIdx.x] += sc[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = ss[0];
+        pcount[blockIdx.x] = sc[0];
+    }
+}
+
+__global__ void k_mse_final(const double *part, const double *pcount, int nb, float *loss, float *count) {
+    double s = 0.0, c = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        s += part[b];
+        c += pcount[b];
+    }
+    *loss = (float)(c > 0 ? s / c : 0.0);
+    *count = (float)c;
+}
+
+__global__ void k_mse_grad(const float *__restrict__ x, const float *__restrict__ r, const float *__restrict__ V,
+                           float thr, long long n, const float *count, float *__restrict__ g) {
+    const float inv = *count > 0.f ? 2.f / *count : 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        g[i] = (V && V[i] < thr) ? 0.f : inv * (x[i] - r[i]);
+}
+
+int grid_n(long long n) {
+    long long b = (n + 255) / 256;
+    return (int)std::max<long long>(1, std::min<long long>(b, 152LL * 32));
+}
+
+}  // namespace
+
+static int conv_fwd(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *x, int cpin, int nimg, int D, int H, int W,
+                    int epi, __nv_bfloat16 *y, float *state, long long sstride, cudaStream_t st) {
+    return cbct_conv(x, nimg, D, H, W, cpin, L.taps3d, m->params + L.w_off, m->params + L.b_off, L.cin, L.cout, 0, epi,
+                     m->d.slope, y, 32, nullptr, state, sstride, m->status, st);
+}
+
+// input-gradient conv of layer L: dy (BF16 [..][cp_dy], L.cout channels) -> L.cin outputs
+static int conv_dx(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *dy, int cp_dy, int nimg, int D, int H, int W,
+                   int epi, __nv_bfloat16 *y, const __nv_bfloat16 *mask, float *state, long long sstride,
+                   cudaStream_t st) {
+    return cbct_conv(dy, nimg, D, H, W, cp_dy, L.taps3d, m->params + L.w_off, nullptr, L.cin, L.cout, 1, epi,
+                     m->d.slope, y, 32, mask, state, sstride, m->status, st);
+}
+
+// geometry of the two blocks' tensors: dual = na images of nv x nu (2D), primal = nz x ny x nx (3D)
+#define DUAL_DIMS m->g->dev.na, 1, m->g->dev.nv, m->g->dev.nu
+#define PRIM_DIMS 1, m->g->dev.n[2], m->g->dev.n[1], m->g->dev.n[0]
+
+// One forward iteration n: (f_in, h_in) -> (f_out, h_out); activations left in the
+// workspaces (a1, a2, b1, b2, din, pin).
+static int lpd_iter_fwd(cbct_lpd *m, int n, const float *f_in, const float *h_in, float *f_out, float *h_out,
+                        cudaStream_t st) {
+    const long long NV = m->nvox, NP = m->nproj;
+    const int M = m->d.n_mem;
+    const LayerSpec *Ld = &m->layers[6 * n], *Lp = &m->layers[6 * n + 3];
+    void *sv = (void *)st;
+    // dual block input [h (M), mu_ref P f_1, y]
+    int rc = forward_project(m->g, f_in + 1 * NV, m->tproj, 1, 0, sv);
+    if (rc) return rc;
+    Planes pl{};
+    for (int c = 0; c < M; ++c) { pl.p[c] = h_in + c * NP; pl.s[c] = 1.f; }
+    pl.p[M] = m->tproj; pl.s[M] = m->d.mu_ref;
+    pl.p[M + 1] = m->y; pl.s[M + 1] = 1.f;
+    k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
+    if (h_out != h_in) cudaMemcpyAsync(h_out, h_in, sizeof(float) * M * NP, cudaMemcpyDeviceToDevice, st);
+    if ((rc = conv_fwd(m, Ld[0], m->din, 8, DUAL_DIMS, 0, m->a1, nullptr, 0, st))) return rc;
+    if ((rc = conv_fwd(m, Ld[1], m->a1, 32, DUAL_DIMS, 0, m->a2, nullptr, 0, st))) return rc;
+    if ((rc = conv_fwd(m, Ld[2], m->a2, 32, DUAL_DIMS, 1, nullptr, h_out, NP, st))) return rc;
+    // primal block input [f (M), bp_scale P^T (w h_1)]
+    k_scale_cols<<<grid_n(NP), 256, 0, st>>>(h_out + 1 * NP, m->wred, NP, m->g->dev.nu, 1.f, m->tproj);
+    rc = back_project(m->g, m->tproj, m->tvol, 1, 0, sv);
+    if (rc) return rc;
+    Planes pp{};
+    for (int c = 0; c < M; ++c) { pp.p[c] = f_in + c * NV; pp.s[c] = 1.f; }
+    pp.p[M] = m->tvol; pp.s[M] = m->bp_scale;
+    k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
+    if (f_out != f_in) cudaMemcpyAsync(f_out, f_in, sizeof(float) * M * NV, cudaMemcpyDeviceToDevice, st);
+    if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) return rc;
+    if ((rc = conv_fwd(m, Lp[1], m->b1, 32, PRIM_DIMS, 0, m->b2, nullptr, 0, st))) return rc;
+    if ((rc = conv_fwd(m, Lp[2], m->b2, 32, PRIM_DIMS, 1, nullptr, f_out, NV, st))) return rc;
+    CBCT_LAUNCH_CHECK("lpd iteration");
+    return 0;
+}
+
+extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lpd **out) {
+    if (!g || !desc || !out) return fail(CBCT_EINVAL, "lpd_create: NULL argument");
+    *out = nullptr;
+    const cbct_lpd_desc &d = *desc;
+    if (d.n_iter < 1 || d.n_iter > 64 || d.n_mem < 2 || d.n_mem > 6 || d.width != 32 || !(d.mu_ref > 0))
+        return fail(CBCT_EINVAL, "lpd_create: need 1 <= n_iter <= 64, 2 <= n_mem <= 6, width == 32, mu_ref > 0");
+    cbct_lpd *m = new (std::nothrow) cbct_lpd();
+    if (!m) return fail(CBCT_ENOMEM, "lpd_create: host allocation");
+    m->g = g;
+    m->d = d;
+    m->nvox = (long long)g->dev.n[0] * g->dev.n[1] * g->dev.n[2];
+    m->nproj = (long long)g->dev.na * g->dev.nv * g->dev.nu;
+    const int M = d.n_mem, W = d.width;
+    long long off = 0;
+    auto add = [&](int cin, int cout, int t3) {
+        LayerSpec L;
+        L.cin = cin; L.cout = cout; L.taps3d = t3;
+        L.w_off = off; off += (long long)cout * (t3 ? 27 : 9) * cin;
+        L.b_off = off; off += cout;
+        m->layers.push_back(L);
+    };
+    for (int n = 0; n < d.n_iter; ++n) {
+        add(M + 2, W, 0); add(W, W, 0); add(W, M, 0);   // dual
+        add(M + 1, W, 1); add(W, W, 1); add(W, M, 1);   // primal
+    }
+    m->nparams = off;
+    // initial weights: He normal for hidden layers, 0.1 x that for the last layer of each block
+    std::vector<float> hp(off, 0.f);
+    InitRng rng{d.seed};
+    for (size_t i = 0; i < m->layers.size(); ++i) {
+        const LayerSpec &L = m->layers[i];
+        const int taps = L.taps3d ? 27 : 9;
+        const double sd = sqrt(2.0 / (L.cin * taps)) * ((i % 3 == 2) ? 0.1 : 1.0);
+        for (long long k = 0; k < (long long)L.cout * taps * L.cin; ++k) hp[L.w_off + k] = (float)(sd * rng.normal());
+    }
+    const long long NV = m->nvox, NP = m->nproj;
+    const int S = d.n_iter + 1;
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    al((void **)&m->params, sizeof(float) * off);
+    al((void **)&m->grads, sizeof(float) * off);
+    al((void **)&m->adam_m, sizeof(float) * off);
+    al((void **)&m->adam_v, sizeof(float) * off);
+    al((void **)&m->wred, sizeof(float) * g->dev.nu);
+    al((void **)&m->f, sizeof(float) * S * M * NV);
+    al((void **)&m->h, sizeof(float) * S * M * NP);
+    al((void **)&m->y, sizeof(float) * NP);
+    al((void **)&m->tproj, sizeof(float) * NP);
+    al((void **)&m->tproj2, sizeof(float) * NP);
+    al((void **)&m->tvol, sizeof(float) * NV);
+    al((void **)&m->din, sizeof(__nv_bfloat16) * NP * 8);
+    al((void **)&m->a1, sizeof(__nv_bfloat16) * NP * 32);
+    al((void **)&m->a2, sizeof(__nv_bfloat16) * NP * 32);
+    al((void **)&m->pin, sizeof(__nv_bfloat16) * NV * 8);
+    al((void **)&m->b1, sizeof(__nv_bfloat16) * NV * 32);
+    al((void **)&m->b2, sizeof(__nv_bfloat16) * NV * 32);
+    al((void **)&m->g32a, sizeof(__nv_bfloat16) * std::max(NP, NV) * 32);
+    al((void **)&m->g32b, sizeof(__nv_bfloat16) * std::max(NP, NV) * 32);
+    al((void **)&m->gsmall, sizeof(__nv_bfloat16) * std::max(NP, NV) * 8);
+    al((void **)&m->gf, sizeof(float) * (M + 1) * NV);
+    al((void **)&m->gh, sizeof(float) * (M + 2) * NP);
+    al((void **)&m->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(m->params, hp.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(m->grads, 0, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMemset(m->adam_m, 0, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMemset(m->adam_v, 0, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        lpd_destroy(m);
+        return cuda_fail(e, "lpd_create: allocation");
+    }
+    int rc = cbct_redundancy_weight(g, m->wred, nullptr);
+    // backprojection scale: 1 / max_voxel P^T(w 1)
+    if (rc == 0) {
+        if (d.bp_scale > 0) {
+            m->bp_scale = d.bp_scale;
+        } else {
+            k_fill_f<<<grid_n(NP), 256>>>(m->tproj2, NP, 1.f);
+            k_scale_cols<<<grid_n(NP), 256>>>(m->tproj2, m->wred, NP, g->dev.nu, 1.f, m->tproj);
+            rc = back_project(g, m->tproj, m->tvol, 1, 0, nullptr);
+            float mx = 0.f;
+            if (rc == 0) {
+                cudaMemset(m->tproj2, 0, sizeof(float));
+                k_max_reduce<<<grid_n(NV), 256>>>(m->tvol, NV, m->tproj2);
+                e = cudaMemcpy(&mx, m->tproj2, sizeof(float), cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess) rc = cuda_fail(e, "lpd_create: bp scale");
+            }
+            m->bp_scale = mx > 0.f ? 1.f / mx : 1.f;
+        }
+    }
+    if (rc == 0) {
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) rc = cuda_fail(e, "lpd_create");
+    }
+    if (rc) {
+        lpd_destroy(m);
+        return rc;
+    }
+    *out = m;
+    return 0;
+}
+
+extern "C" void lpd_destroy(cbct_lpd *m) {
+    if (!m) return;
+    cudaDeviceSynchronize();
+    void *ptrs[] = {m->params, m->grads, m->adam_m, m->adam_v, m->wred, m->f, m->h, m->y, m->tproj, m->tproj2,
+                    m->tvol, m->din, m->a1, m->a2, m->pin, m->b1, m->b2, m->g32a, m->g32b, m->gsmall, m->gf, m->gh,
+                    m->status};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete m;
+}
+
+extern "C" int lpd_info(const cbct_lpd *m, long long *nparams, float **params, float **grads, float *bp_scale) {
+    if (!m) return fail(CBCT_EINVAL, "lpd_info: NULL model");
+    if (nparams) *nparams = m->nparams;
+    if (params) *params = m->params;
+    if (grads) *grads = m->grads;
+    if (bp_scale) *bp_scale = m->bp_scale;
+    return 0;
+}
+
+extern "C" int lpd_forward(cbct_lpd *m, const float *y, const float *x0, float *x_out, int batch, int save_for_backward,
+                           void *stream) {
+    if (!m || !y || !x0 || !x_out) return fail(CBCT_EINVAL, "lpd_forward: NULL argument");
+    if (batch != 1) return fail(CBCT_EINVAL, "lpd_forward: batch must be 1 (accumulate gradients over calls)");
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long NV = m->nvox, NP = m->nproj;
+    const int M = m->d.n_mem, N = m->d.n_iter;
+    cudaMemcpyAsync(m->y, y, sizeof(float) * NP, cudaMemcpyDeviceToDevice, st);
+    k_init_f<<<grid_n(NV), 256, 0, st>>>(x0, m->f, NV, M, 1.f / m->d.mu_ref);
+    cudaMemsetAsync(m->h, 0, sizeof(float) * M * NP, st);
+    for (int n = 0; n < N; ++n) {
+        const int si = save_for_backward ? n : 0, so = save_for_backward ? n + 1 : 0;
+        int rc = lpd_iter_fwd(m, n, m->f + (long long)si * M * NV, m->h + (long long)si * M * NP,
+                              m->f + (long long)so * M * NV, m->h + (long long)so * M * NP, st);
+        if (rc) return rc;
+    }
+    const long long last = save_for_backward ? N : 0;
+    k_sum_channels<<<grid_n(NV), 256, 0, st>>>(m->f + last * M * NV, 1, NV, m->d.mu_ref, x_out, 0);
+    m->saved = save_for_backward;
+    CBCT_LAUNCH_CHECK("lpd_forward");
+    return 0;
+}
+
+extern "C" int lpd_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float *grad_x0, void *stream) {
+    if (!m || !grad_x) return fail(CBCT_EINVAL, "lpd_backward: NULL argument");
+    if (!m->saved) return fail(CBCT_EINVAL, "lpd_backward: call lpd_forward with save_for_backward = 1 first");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *sv = stream;
+    const long long NV = m->nvox, NP = m->nproj;
+    const int M = m->d.n_mem, N = m->d.n_iter;
+    float *gf = m->gf, *gh = m->gh;  // gf: [M + 1][NV] (last = grad of the bp channel), gh: [M + 2][NP]
+    // dL/df_N: channel 0 = mu_ref dL/dx; dL/dh_N = 0
+    cudaMemsetAsync(gf, 0, sizeof(float) * (M + 1) * NV, st);
+    cudaMemsetAsync(gh, 0, sizeof(float) * (M + 2) * NP, st);
+    k_axpy<<<grid_n(NV), 256, 0, st>>>(gf, grad_x, NV, m->d.mu_ref);
+    if (grad_y) cudaMemsetAsync(grad_y, 0, sizeof(float) * NP, st);
+    int rc = 0;
+    for (int n = N - 1; n >= 0 && rc == 0; --n) {
+        const float *f_n = m->f + (long long)n * M * NV, *h_n = m->h + (long long)n * M * NP;
+        const float *h_n1 = m->h + (long long)(n + 1) * M * NP;
+        const LayerSpec *Ld = &m->layers[6 * n], *Lp = &m->layers[6 * n + 3];
+        float *dW = m->grads;
+        // recompute the dual block input and activations of iteration n
+        if ((rc = forward_project(m->g, f_n + NV, m->tproj, 1, 0, sv))) break;
+        Planes pl{};
+        for (int c = 0; c < M; ++c) { pl.p[c] = h_n + c * NP; pl.s[c] = 1.f; }
+        pl.p[M] = m->tproj; pl.s[M] = m->d.mu_ref;
+        pl.p[M + 1] = m->y; pl.s[M + 1] = 1.f;
+        k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
+        if ((rc = conv_fwd(m, Ld[0], m->din, 8, DUAL_DIMS, 0, m->a1, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Ld[1], m->a1, 32, DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
+        // recompute the primal block input and activations (needs h_{n+1}, saved)
+        k_scale_cols<<<grid_n(NP), 256, 0, st>>>(h_n1 + NP, m->wred, NP, m->g->dev.nu, 1.f, m->tproj2);
+        if ((rc = back_project(m->g, m->tproj2, m->tvol, 1, 0, sv))) break;
+        Planes pp{};
+        for (int c = 0; c < M; ++c) { pp.p[c] = f_n + c * NV; pp.s[c] = 1.f; }
+        pp.p[M] = m->tvol; pp.s[M] = m->bp_scale;
+        k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
+        if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Lp[1], m->b1, 32, PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
+
+        // ---- primal block backward: upstream gf[0..M) = dL/df_{n+1}
+        Planes gp{};
+        for (int c = 0; c < M; ++c) { gp.p[c] = gf + c * NV; gp.s[c] = 1.f; }
+        k_pack8<<<grid_n(NV), 256, 0, st>>>(gp, NV, m->gsmall);
+        if ((rc = conv_wgrad(m->b2, 32, Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].w_off,
+                             dW + Lp[2].b_off, 1, st))) break;
+        if ((rc = conv_dx(m, Lp[2], m->gsmall, 8, PRIM_DIMS, 2, m->g32a, m->b2, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->b1, 32, Lp[1].cin, m->g32a, 32, Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].w_off,
+                             dW + Lp[1].b_off, 1, st))) break;
+        if ((rc = conv_dx(m, Lp[1], m->g32a, 32, PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, 32, Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].w_off,
+                             dW + Lp[0].b_off, 1, st))) break;
+        // dL/d(primal input) -> gf[0..M) += (residual path kept), gf[M] = dL/d(bp channel)
+        cudaMemsetAsync(gf + (long long)M * NV, 0, sizeof(float) * NV, st);
+        if ((rc = conv_dx(m, Lp[0], m->g32b, 32, PRIM_DIMS, 1, nullptr, nullptr, gf, NV, st))) break;
+        // bp = bp_scale P^T (w h_1)  =>  dL/dh_{n+1}[1] += w * bp_scale * P (dL/dbp)
+        if ((rc = forward_project(m->g, gf + (long long)M * NV, m->tproj, 1, 0, sv))) break;
+        k_scale_cols<<<grid_n(NP), 256, 0, st>>>(m->tproj, m->wred, NP, m->g->dev.nu, m->bp_scale, m->tproj2);
+        k_axpy<<<grid_n(NP), 256, 0, st>>>(gh + NP, m->tproj2, NP, 1.f);
+
+        // ---- dual block backward: upstream gh[0..M) = dL/dh_{n+1}
+        Planes gd{};
+        for (int c = 0; c < M; ++c) { gd.p[c] = gh + c * NP; gd.s[c] = 1.f; }
+        k_pack8<<<grid_n(NP), 256, 0, st>>>(gd, NP, m->gsmall);
+        if ((rc = conv_wgrad(m->a2, 32, Ld[2].cin, m->gsmall, 8, Ld[2].cout, DUAL_DIMS, 0, dW + Ld[2].w_off,
+                             dW + Ld[2].b_off, 1, st))) break;
+        if ((rc = conv_dx(m, Ld[2], m->gsmall, 8, DUAL_DIMS, 2, m->g32a, m->a2, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->a1, 32, Ld[1].cin, m->g32a, 32, Ld[1].cout, DUAL_DIMS, 0, dW + Ld[1].w_off,
+                             dW + Ld[1].b_off, 1, st))) break;
+        if ((rc = conv_dx(m, Ld[1], m->g32a, 32, DUAL_DIMS, 2, m->g32b, m->a1, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, 32, Ld[0].cout, DUAL_DIMS, 0, dW + Ld[0].w_off,
+                             dW + Ld[0].b_off, 1, st))) break;
+        // dL/d(dual input): gh[0..M) += (residual), gh[M] = dL/d(P f_1 channel), gh[M+1] = dL/dy
+        cudaMemsetAsync(gh + (long long)M * NP, 0, sizeof(float) * 2 * NP, st);
+        if ((rc = conv_dx(m, Ld[0], m->g32b, 32, DUAL_DIMS, 1, nullptr, nullptr, gh, NP, st))) break;
+        if (grad_y) k_axpy<<<grid_n(NP), 256, 0, st>>>(grad_y, gh + (long long)(M + 1) * NP, NP, 1.f);
+        // pf = mu_ref P f_1  =>  dL/df_n[1] += mu_ref P^T (dL/dpf)
+        if ((rc = back_project(m->g, gh + (long long)M * NP, m->tvol, 1, 0, sv))) break;
+        k_axpy<<<grid_n(NV), 256, 0, st>>>(gf + NV, m->tvol, NV, m->d.mu_ref);
+    }
+    if (rc) return rc;
+    // f_0 = x0 / mu_ref repeated  =>  dL/dx0 = sum_c gf[c] / mu_ref
+    if (grad_x0) k_sum_channels<<<grid_n(NV), 256, 0, st>>>(gf, M, NV, 1.f / m->d.mu_ref, grad_x0, 0);
+    CBCT_LAUNCH_CHECK("lpd_backward");
+    return 0;
+}
+
+extern "C" int lpd_zero_grad(cbct_lpd *m, void *stream) {
+    if (!m) return fail(CBCT_EINVAL, "lpd_zero_grad: NULL model");
+    CBCT_CUDA_TRY(cudaMemsetAsync(m->grads, 0, sizeof(float) * m->nparams, (cudaStream_t)stream));
+    return 0;
+}
+
+extern "C" int lpd_adam_step(cbct_lpd *m, float lr, float beta1, float beta2, float eps, int step, float grad_scale,
+                             void *stream) {
+    if (!m || step < 1) return fail(CBCT_EINVAL, "lpd_adam_step: invalid argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
+    k_adam<<<grid_n(m->nparams), 256, 0, st>>>(m->params, m->grads, m->adam_m, m->adam_v, m->nparams, lr, beta1, beta2,
+                                               eps, c1, c2, grad_scale);
+    CBCT_LAUNCH_CHECK("lpd_adam_step");
+    return 0;
+}
+
+extern "C" int lpd_set_params(cbct_lpd *m, const float *host, long long n) {
+    if (!m || !host || n != m->nparams) return fail(CBCT_EINVAL, "lpd_set_params: size mismatch");
+    CBCT_CUDA_TRY(cudaMemcpy(m->params, host, sizeof(float) * n, cudaMemcpyHostToDevice));
+    return 0;
+}
+
+extern "C" int lpd_get_params(const cbct_lpd *m, float *host, long long n) {
+    if (!m || !host || n != m->nparams) return fail(CBCT_EINVAL, "lpd_get_params: size mismatch");
+    CBCT_CUDA_TRY(cudaMemcpy(host, m->params, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    return 0;
+}
+
+extern "C" int lpd_get_grads(const cbct_lpd *m, float *host, long long n) {
+    if (!m || !host || n != m->nparams) return fail(CBCT_EINVAL, "lpd_get_grads: size mismatch");
+    CBCT_CUDA_TRY(cudaMemcpy(host, m->grads, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    return 0;
+}
+
+extern "C" int cbct_masked_mse(const float *x, const float *ref, const float *V, float thr, long long n, float *loss,
+                               float *grad, void *stream) {
+    if (!x || !ref || !loss || n < 1) return fail(CBCT_EINVAL, "cbct_masked_mse: invalid argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nb = 256;
+    double *part = nullptr;
+    CBCT_CUDA_TRY(cudaMallocAsync((void **)&part, sizeof(double) * 2 * nb + 16, st));
+    float *cnt = reinterpret_cast<float *>(part + 2 * nb);
+    k_mse_partial<<<nb, 256, 0, st>>>(x, ref, V, thr, n, part, part + nb);
+    k_mse_final<<<1, 1, 0, st>>>(part, part + nb, nb, loss, cnt);
+    if (grad) k_mse_grad<<<grid_n(n), 256, 0, st>>>(x, ref, V, thr, n, cnt, grad);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(part, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cbct_masked_mse");
+    return 0;
+}

@@ -153,3 +153,16 @@ def smooth_volume(n, seed: int, n_blobs: int = 12) -> np.ndarray:
 def line_integrals(shape, seed: int, lo: float = 0.0, hi: float = 12.0) -> np.ndarray:
     """Random line-integral values for photon-count sampling tests (float32)."""
     return np.random.default_rng(seed).uniform(lo, hi, size=shape).astype(np.float32)
+
+
+def lpd_weights(layer_shapes, seed: int, last_scale: float = 0.1) -> np.ndarray:
+    """Seeded network weights in the library's flat order: per layer (cout, taps,
+    cin) a He-normal weight [cout][taps][cin] (x last_scale for the last layer of each
+    3-layer block) followed by a small normal bias [cout]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, (cout, taps, cin) in enumerate(layer_shapes):
+        sd = math.sqrt(2.0 / (cin * taps)) * (last_scale if i % 3 == 2 else 1.0)
+        out.append(rng.standard_normal(cout * taps * cin) * sd)
+        out.append(rng.standard_normal(cout) * 0.01)
+    return np.concatenate(out).astype(np.float32)

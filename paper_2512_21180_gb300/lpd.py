@@ -1,0 +1,114 @@
+"""Python binding of the learned primal-dual module (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import LpdDesc, check
+from .projector import Geometry
+
+
+def _st() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+class LPD:
+    """Unrolled learned primal-dual network on the GPU (weights live in libcbct)."""
+
+    def __init__(self, geom: Geometry, n_iter: int = 8, n_mem: int = 5, width: int = 32, slope: float = 0.2,
+                 mu_ref: float = 0.02, bp_scale: float = 0.0, seed: int = 0):
+        self.geom = geom
+        d = LpdDesc(n_iter, n_mem, width, slope, mu_ref, bp_scale, seed)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(geom.device):
+            check(_lib.load().lpd_create(geom.handle, ctypes.byref(d), ctypes.byref(h)), "lpd_create")
+        self.handle = h
+        self.n_iter, self.n_mem, self.width, self.mu_ref = n_iter, n_mem, width, mu_ref
+        n = ctypes.c_longlong()
+        pp, gp = ctypes.c_void_p(), ctypes.c_void_p()
+        bs = ctypes.c_float()
+        check(_lib.load().lpd_info(h, ctypes.byref(n), ctypes.byref(pp), ctypes.byref(gp), ctypes.byref(bs)),
+              "lpd_info")
+        self.nparams = int(n.value)
+        self.bp_scale = float(bs.value)
+        self.step = 0
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.load().lpd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # parameters -----------------------------------------------------------------
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.nparams, dtype=np.float32)
+        check(_lib.load().lpd_get_params(self.handle, out.ctypes.data, self.nparams), "lpd_get_params")
+        return out
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        check(_lib.load().lpd_set_params(self.handle, p.ctypes.data, self.nparams), "lpd_set_params")
+
+    def grads(self) -> np.ndarray:
+        """Host copy of the accumulated parameter gradients."""
+        out = np.zeros(self.nparams, dtype=np.float32)
+        check(_lib.load().lpd_get_grads(self.handle, out.ctypes.data, self.nparams), "lpd_get_grads")
+        return out
+
+    # compute ----------------------------------------------------------------------
+    def forward(self, y: torch.Tensor, x0: torch.Tensor, save_for_backward: bool = False) -> torch.Tensor:
+        g = self.geom
+        yy = y.reshape(g.proj_shape).contiguous()
+        xx = x0.reshape(g.vol_shape).contiguous()
+        out = torch.empty(g.vol_shape, device=yy.device, dtype=torch.float32)
+        check(_lib.load().lpd_forward(self.handle, yy.data_ptr(), xx.data_ptr(), out.data_ptr(), 1,
+                                      int(save_for_backward), _st()), "lpd_forward")
+        return out
+
+    def backward(self, grad_x: torch.Tensor, want_y: bool = False, want_x0: bool = False):
+        g = self.geom
+        gx = grad_x.reshape(g.vol_shape).contiguous()
+        gy = torch.empty(g.proj_shape, device=gx.device) if want_y else None
+        g0 = torch.empty(g.vol_shape, device=gx.device) if want_x0 else None
+        check(_lib.load().lpd_backward(self.handle, gx.data_ptr(), None if gy is None else gy.data_ptr(),
+                                       None if g0 is None else g0.data_ptr(), _st()), "lpd_backward")
+        return gy, g0
+
+    def zero_grad(self):
+        check(_lib.load().lpd_zero_grad(self.handle, _st()), "lpd_zero_grad")
+
+    def adam_step(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                  grad_scale: float = 1.0):
+        self.step += 1
+        check(_lib.load().lpd_adam_step(self.handle, lr, beta1, beta2, eps, self.step, grad_scale, _st()),
+              "lpd_adam_step")
+
+
+def masked_mse(x: torch.Tensor, ref: torch.Tensor, V: torch.Tensor | None = None, thr: float = 0.5,
+               want_grad: bool = True):
+    """(loss [device scalar], grad) of the mean squared error over V >= thr."""
+    x = x.contiguous()
+    ref = ref.contiguous()
+    loss = torch.zeros(1, device=x.device)
+    grad = torch.empty_like(x) if want_grad else None
+    check(_lib.load().cbct_masked_mse(x.data_ptr(), ref.data_ptr(), None if V is None else V.contiguous().data_ptr(),
+                                      float(thr), x.numel(), loss.data_ptr(),
+                                      None if grad is None else grad.data_ptr(), _st()), "cbct_masked_mse")
+    return loss, grad
+
+
+def layer_shapes(n_iter: int, n_mem: int = 5, width: int = 32):
+    """[(cout, taps, cin)] in the library's parameter order."""
+    out = []
+    for _ in range(n_iter):
+        out += [(width, 9, n_mem + 2), (width, 9, width), (n_mem, 9, width),
+                (width, 27, n_mem + 1), (width, 27, width), (n_mem, 27, width)]
+    return out

@@ -1,0 +1,104 @@
+"""Learned primal-dual on the GPU (tcgen05 convs + projector pair) against the FP64
+reference network with the same weights; gradients; a short training run."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2512_21180_gb300 import inputs as I
+
+from gpu_util import rel_l2, to_gpu, to_np
+
+pytestmark = pytest.mark.gpu
+
+GEOM = I.scaled(I.geometry("tiny16"), n=(24, 24, 16), vox=(8.0, 8.0, 8.0), nu=40, nv=16, du=4.0, dv=4.0,
+                n_angles=12, u_offset=20.0)
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_2512_21180_gb300 import build
+    build.build()
+    from paper_2512_21180_gb300 import lpd, projector
+    return projector, lpd
+
+
+def oracle_params(flat, shapes):
+    out, o = [], 0
+    for cout, taps, cin in shapes:
+        w = torch.tensor(flat[o:o + cout * taps * cin], dtype=torch.float64).reshape(cout, taps, cin)
+        o += cout * taps * cin
+        b = torch.tensor(flat[o:o + cout], dtype=torch.float64)
+        o += cout
+        k = (3, 3, 3) if taps == 27 else (3, 3)
+        out.append((w.permute(0, 2, 1).reshape((cout, cin) + k).contiguous().requires_grad_(True),
+                    b.clone().requires_grad_(True)))
+    return out
+
+
+def test_lpd_forward_and_gradients_match_oracle(O, M):
+    from oracle import lpd_ref as R
+    P, L = M
+    G = O.Geom(GEOM)
+    geom = P.Geometry(GEOM)
+    n_iter, mu, bps = 2, 0.02, 2e-3
+    model = L.LPD(geom, n_iter=n_iter, mu_ref=mu, bp_scale=bps)
+    shapes = L.layer_shapes(n_iter)
+    flat = I.lpd_weights(shapes, seed=3, last_scale=0.5)
+    model.set_params(flat)
+    x_true = O.phantom(G, I.ellipsoids(GEOM, 5, n_soft=6, axes_mm=(15.0, 60.0)))
+    y = O.forward(G, x_true) + 0.01 * I.random_normal(G.proj_shape, 6).astype(np.float64)
+    x0 = 0.8 * x_true + 0.002 * I.random_normal(G.vol_shape, 7).astype(np.float64)
+    r = I.random_normal(G.vol_shape, 8).astype(np.float64)
+
+    xg = model.forward(to_gpu(y), to_gpu(x0), save_for_backward=True)
+    prm = oracle_params(flat, shapes)
+    dual = [prm[6 * n:6 * n + 3] for n in range(n_iter)]
+    prim = [prm[6 * n + 3:6 * n + 6] for n in range(n_iter)]
+    yt = torch.tensor(y, requires_grad=True)
+    x0t = torch.tensor(x0, requires_grad=True)
+    ref = R.lpd(G, yt, x0t, torch.tensor(O.redundancy(G)), dual, prim, n_mem=5, round_bf16=True, mu_ref=mu,
+                bp_scale=bps)
+    assert rel_l2(to_np(xg), ref.detach().numpy()) <= 1e-2
+    # the network changed its input: the check is not vacuous
+    assert rel_l2(ref.detach().numpy(), x0) > 1e-3
+
+    (ref * torch.tensor(r)).sum().backward()
+    model.zero_grad()
+    gy, g0 = model.backward(to_gpu(r), want_y=True, want_x0=True)
+    gg = model.grads().astype(np.float64)
+    gref = np.concatenate([np.concatenate([w.grad.permute(0, *range(2, w.dim()), 1).reshape(-1).numpy(),
+                                           b.grad.numpy()]) for w, b in prm])
+    assert rel_l2(gg, gref) <= 5e-2, rel_l2(gg, gref)
+    assert rel_l2(to_np(gy), yt.grad.numpy()) <= 5e-2
+    assert rel_l2(to_np(g0), x0t.grad.numpy()) <= 5e-2
+
+
+def test_lpd_training_reduces_loss(O, M):
+    """A few Adam steps on simulated phantoms reduce the FoV-masked loss."""
+    P, L = M
+    from paper_2512_21180_gb300 import ops
+    geom = P.Geometry(GEOM)
+    model = L.LPD(geom, n_iter=3, seed=1)
+    V = ops.fov(geom)
+    data = []
+    for s in range(4):
+        x = ops.phantom(geom, I.ellipsoids(GEOM, 100 + s, n_soft=6, axes_mm=(15.0, 60.0)))
+        _, y = ops.simulate(geom, x, 1e5, seed=s)
+        x0 = ops.fdk(geom, y)[0]
+        data.append((x, y[0], x0))
+    def loss_all():
+        tot = 0.0
+        for x, y, x0 in data:
+            out = model.forward(y, x0)
+            tot += L.masked_mse(out, x, V, want_grad=False)[0].item()
+        return tot
+    l0 = loss_all()
+    for it in range(30):
+        model.zero_grad()
+        for x, y, x0 in data:
+            out = model.forward(y, x0, save_for_backward=True)
+            _, g = L.masked_mse(out, x, V)
+            model.backward(g)
+        model.adam_step(1e-3, grad_scale=1.0 / len(data))
+    l1 = loss_all()
+    assert np.isfinite(l1) and l1 < 0.7 * l0, (l0, l1)

@@ -56,16 +56,16 @@ def test_lpd_gradient_by_finite_differences(O):
                  torch.tensor(r.standard_normal(s[0]) * 0.1, requires_grad=True)) for s in shapes]
     dual = [params([(4, 5, 3, 3), (4, 4, 3, 3), (3, 4, 3, 3)], 2)]
     prim = [params([(4, 4, 3, 3, 3), (4, 4, 3, 3, 3), (3, 4, 3, 3, 3)], 3)]
-    loss = R.lpd(G, y, x0, w, dual, prim, n_mem=3, round_bf16=False, scale=0.05).pow(2).sum()
+    loss = R.lpd(G, y, x0, w, dual, prim, n_mem=3, round_bf16=False, mu_ref=0.5, bp_scale=0.05).pow(2).sum()
     loss.backward()
     wt = prim[0][1][0]
     i = (1, 2, 1, 0, 2)
     eps = 1e-6
     with torch.no_grad():
         wt[i] += eps
-        lp = R.lpd(G, y, x0, w, dual, prim, n_mem=3, round_bf16=False, scale=0.05).pow(2).sum().item()
+        lp = R.lpd(G, y, x0, w, dual, prim, n_mem=3, round_bf16=False, mu_ref=0.5, bp_scale=0.05).pow(2).sum().item()
         wt[i] -= 2 * eps
-        lm = R.lpd(G, y, x0, w, dual, prim, n_mem=3, round_bf16=False, scale=0.05).pow(2).sum().item()
+        lm = R.lpd(G, y, x0, w, dual, prim, n_mem=3, round_bf16=False, mu_ref=0.5, bp_scale=0.05).pow(2).sum().item()
         wt[i] += eps
     fd = (lp - lm) / (2 * eps)
     assert abs(fd - wt.grad[i].item()) <= 1e-6 * max(1.0, abs(fd))
@@ -73,9 +73,9 @@ def test_lpd_gradient_by_finite_differences(O):
     j = (2, 4, 1, 1)
     with torch.no_grad():
         wd[j] += eps
-        lp = R.lpd(G, y, x0, w, dual, prim, n_mem=3, round_bf16=False, scale=0.05).pow(2).sum().item()
+        lp = R.lpd(G, y, x0, w, dual, prim, n_mem=3, round_bf16=False, mu_ref=0.5, bp_scale=0.05).pow(2).sum().item()
         wd[j] -= 2 * eps
-        lm = R.lpd(G, y, x0, w, dual, prim, n_mem=3, round_bf16=False, scale=0.05).pow(2).sum().item()
+        lm = R.lpd(G, y, x0, w, dual, prim, n_mem=3, round_bf16=False, mu_ref=0.5, bp_scale=0.05).pow(2).sum().item()
         wd[j] += eps
     fd = (lp - lm) / (2 * eps)
     assert abs(fd - wd.grad[j].item()) <= 1e-6 * max(1.0, abs(fd))

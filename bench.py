@@ -156,11 +156,20 @@ def main():
     ap.add_argument("--ref-angles", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-lpd", action="store_true", help="skip the learned primal-dual vs PDHG timing leg")
+    ap.add_argument("--lpd-only", action="store_true", help="run only the learned primal-dual timing leg")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="geometry name from paper_2512_21180_gb300.inputs (profiling runs use smaller ones)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.lpd_only:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_2512_21180_gb300 import build as B
+        B.build()
+        print(json.dumps(lpd_timing(args.warmup, max(1, args.steps))), flush=True)
+        return 0
 
     import numpy as np
     import torch
@@ -283,6 +292,57 @@ def e2e_leg(args, geom, vol, proj, back, stream, dist):
     return ms_e2e
 
 
+def lpd_timing(warmup: int, reps: int) -> dict:
+    """Seconds per volume of the learned primal-dual reconstruction (FDK_w start + 8
+    unrolled iterations, BF16 tensor-core blocks) and of 100 iterations of FP32
+    PDHG-TV from the same start, on the 128^3 / 200-angle / 256x192 learned workload
+    (Poisson I0 = 1e5). Timing does not depend on the weights; the reconstruction
+    quality at equal PSNR comes from the trained network (experiment_lpd)."""
+    import math
+
+    import torch
+
+    from paper_2512_21180_gb300 import inputs as I
+    from paper_2512_21180_gb300 import ops
+    from paper_2512_21180_gb300.lpd import LPD
+    from paper_2512_21180_gb300.projector import Geometry
+
+    g = I.geometry("lpd128")
+    geom = Geometry(g)
+    x = ops.phantom(geom, I.phantom_params("lpd128", 30_000))
+    _, y = ops.simulate(geom, x, 1e5, seed=1)
+    y = y[0]
+    model = LPD(geom, n_iter=8, seed=1)
+    nP = ops.opnorm(geom, 0.0, 20)
+    gam = nP / math.sqrt(12.0)
+    nK = ops.opnorm(geom, gam, 20)
+    st = torch.cuda.current_stream()
+
+    def run_lpd():
+        x0 = ops.fdk(geom, y)[0]
+        return model.forward(y, x0)
+
+    def run_pdhg():
+        x0 = ops.fdk(geom, y)[0]
+        return ops.pdhg(geom, y, x0, 100, 3e-3, gam, 0.99 / nK, 0.99 / nK)
+
+    out = {}
+    for name, fn, n in (("lpd", run_lpd, reps), ("pdhg100", run_pdhg, 1)):
+        for _ in range(max(1, warmup if name == "lpd" else 1)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(n):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        out[name + "_s_per_volume"] = e0.elapsed_time(e1) / n / 1e3
+    out["pdhg100_over_lpd"] = out["pdhg100_s_per_volume"] / out["lpd_s_per_volume"]
+    out["workload"] = "128^3 at 4 mm, 200 angles, 256x192 at 1.6 mm, +80 mm offset; 8 iterations, width 32"
+    return out
+
+
 def report(args, geom, world, S_fwd, samples_step, value, ms, ms_fwd, ms_adj, e2e, clk, g, dist):
     import numpy as np
 
@@ -313,6 +373,8 @@ def report(args, geom, world, S_fwd, samples_step, value, ms, ms_fwd, ms_adj, e2
         line["cpu_baseline"] = {"value": r["value"], "unit": "Gsamples/s", "cores": r["cores"], "kind": "oracle",
                                 "sample": f"{r['angles']} of 400 evenly spaced angles of the same workload, "
                                           f"forward + adjoint, FP64, one step"}
+    if not args.no_lpd and world == 1 and args.workload == WORKLOAD:
+        line["lpd_vs_pdhg"] = lpd_timing(1, 2)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -5,11 +5,12 @@
 //
 // Forward (and input-gradient) convolution = implicit GEMM on the fifth-generation
 // tensor cores: D[128 pixels][N out channels] = sum_K A[pixel][K] B[n][K], K = (tap,
-// input channel). A CTA (4 warps) owns a TMEM accumulator of N columns and walks
-// 128-pixel tiles; for every K chunk of 64 the threads gather the shifted input
-// pixels (16-byte pieces of 8 channels, zero outside the grid) into a
-// double-buffered shared-memory A tile in the K-major core-matrix layout, thread 0
-// issues four 128 x N x 16 tcgen05.mma and commits to the stage's mbarrier. The
+// input channel). A CTA walks a contiguous range of tiles of 128 consecutive
+// output pixels along W; for every K chunk of 64 it loads the shifted input
+// pixels with TMA: one box of [128 output pixels][8 channels] per (tap, channel
+// group) is exactly one K-major core-matrix column, zero-filled outside the image.
+// A producer warp fills a 4-stage ring, one thread issues 128 x N x 16 tcgen05.mma
+// into double-buffered TMEM accumulators, four epilogue warps drain them. The
 // packed weights (B) stay in shared memory for the CTA's lifetime. The epilogue
 // reads TMEM with tcgen05.ld and applies bias + LeakyReLU (BF16 channels-last
 // out), a residual update of an FP32 channel-first state, or an activation mask.
@@ -64,30 +65,116 @@ __device__ __forceinline__ void tap_offset(int tap, int taps3d, int &dd, int &dh
     }
 }
 
+constexpr int kStages = 4;          // A ring: kStages x 16 KiB
+constexpr int kWsThreads = 192;     // warps 0-3 epilogue, 4 producer, 5 MMA
+
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5, %6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Tile t = ((img * D + d) * H + h) * ntw + wt covers output pixels (img, d, h, 128 wt + r).
+struct TileCoord {
+    int img, d, h, w0;
+};
+__device__ __forceinline__ TileCoord tile_coord(long long t, int D, int H, int ntw) {
+    TileCoord c;
+    c.w0 = (int)(t % ntw) * 128; t /= ntw;
+    c.h = (int)(t % H); t /= H;
+    c.d = (int)(t % D);
+    c.img = (int)(t / D);
+    return c;
+}
+
+// Epilogue of one tile row: TMEM accumulators -> bias / activation / residual.
 template <int NPAD, int EPI>
-__global__ void __launch_bounds__(kConvThreads) k_conv_tc(ConvArgs a) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char *sm = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+__device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *acc, long long p) {
+    if constexpr (EPI == EPI_RESIDUAL_F32) {
+#pragma unroll
+        for (int c = 0; c < NPAD; ++c) {
+            if (c < a.cout) {
+                const float v = acc[c] + (a.bias ? __ldg(a.bias + c) : 0.f);
+                float *o = a.state + c * a.sstride + p;
+                *o += v;
+            }
+        }
+    } else {
+        __nv_bfloat16 *o = a.y + p * a.cpout;
+        const __nv_bfloat16 *mk = EPI == EPI_MASK_BF16 ? a.mask + p * a.cpout : nullptr;
+#pragma unroll
+        for (int c0 = 0; c0 < NPAD; c0 += 8) {
+            if (c0 >= a.cpout) break;
+            __align__(16) __nv_bfloat16 out8[8];
+            uint4 mv = make_uint4(0u, 0u, 0u, 0u);
+            if constexpr (EPI == EPI_MASK_BF16) mv = *reinterpret_cast<const uint4 *>(mk + c0);
+            const __nv_bfloat16 *m8 = reinterpret_cast<const __nv_bfloat16 *>(&mv);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = c0 + j;
+                float v = 0.f;
+                if (c < a.cout) {
+                    v = acc[c];
+                    if constexpr (EPI == EPI_ACT_BF16) {
+                        if (a.bias) v += __ldg(a.bias + c);
+                        v = v > 0.f ? v : v * a.slope;
+                    } else {
+                        v = __bfloat162float(m8[j]) > 0.f ? v : v * a.slope;
+                    }
+                }
+                out8[j] = __float2bfloat16_rn(v);
+            }
+            *reinterpret_cast<uint4 *>(o + c0) = *reinterpret_cast<const uint4 *>(out8);
+        }
+    }
+}
+
+// Warp-specialized convolution tile loop. Item i of a CTA = (tile t_begin + i / nch,
+// K chunk i % nch) on ring stage i % kStages.
+//  producer (warp 4, one lane): waits until the stage is free (empty[s]), then TMA-loads
+//    the chunk's K groups, each a [128 pixels][8 channels] box = one K-major core-matrix
+//    column (16 B rows, 128 B between 8-row groups); taps outside the image and K padding
+//    come back as zeros.
+//  MMA (warp 5, one lane): per tile picks TMEM accumulator j & 1 once the epilogue has
+//    drained it (acce), waits for each chunk (full[s]), issues 128 x N x 16 MMAs, commits
+//    the stage to empty[s] and, after the tile's last chunk, the accumulator to accf.
+//  epilogue (warps 0-3): waits for accf, reads its 32 TMEM lanes, releases the
+//    accumulator, applies the epilogue and stores.
+template <int NPAD, int EPI>
+__global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ CUtensorMap xmap, ConvArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int bbytes = a.kgroups * NPAD * 16;
-    unsigned char *sB = sm;
-    unsigned char *sA = sm + ((bbytes + 127) & ~127);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sA + 2 * kAStageBytes);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2);
+    unsigned char *sA = sm;                                         // kStages x 16 KiB
+    unsigned char *sB = sm + kStages * kAStageBytes;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sB + ((bbytes + 127) & ~127));
+    uint64_t *empty = full + kStages;
+    uint64_t *accf = empty + kStages;
+    uint64_t *acce = accf + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acce + 2);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr uint32_t kCols = NPAD < 32 ? 32 : NPAD;
+    constexpr uint32_t kCols = 2 * NPAD < 32 ? 32 : 2 * NPAD;
     constexpr uint32_t kIdesc = idesc_bf16_f32(128, NPAD);
 
     if (warp == 0) tmem_alloc(tmem_slot, kCols);
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+    if (tid == 32) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int j = 0; j < 2; ++j) {
+            mbar_init(&accf[j], 1);
+            mbar_init(&acce[j], 4);
+        }
         *abort_flag = 0;
         fence_mbar_init();
     }
-    // weights -> shared memory (once per CTA)
-    for (int i = tid; i < bbytes / 16; i += kConvThreads)
+    for (int i = tid; i < bbytes / 16; i += kWsThreads)
         reinterpret_cast<uint4 *>(sB)[i] = __ldg(reinterpret_cast<const uint4 *>(a.wpk) + i);
     fence_async_smem();
     tc_fence_before();
@@ -95,117 +182,97 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_tc(ConvArgs a) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const long long npix = (long long)a.nimg * a.D * a.H * a.W;
-    const long long ntiles = (npix + 127) / 128;
+    const int ntw = (a.W + 127) / 128;
+    const long long ntiles = (long long)a.nimg * a.D * a.H * ntw;
     const int ntaps = a.taps3d ? 27 : 9;
-    const int nchunks = (a.kgroups + kChunkGroups - 1) / kChunkGroups;
-    const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
-    long long q = 0;  // chunks issued by this CTA (stage = q & 1, use = q >> 1)
+    const int nch = (a.kgroups + kChunkGroups - 1) / kChunkGroups;
+    const long long per_cta = (ntiles + gridDim.x - 1) / gridDim.x;
+    const long long t_begin = (long long)blockIdx.x * per_cta;
+    const long long my_tiles = t_begin < ntiles ? min(per_cta, ntiles - t_begin) : 0;
+    const long long total = my_tiles * nch;
 
-    for (long long tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
-        // this thread's output pixel (row tid of the tile)
-        const long long p = tile * 128 + tid;
-        const bool prow = p < npix;
-        int w_ = 0, h_ = 0, d_ = 0;
-        long long img = 0;
-        if (prow) {
-            long long t = p;
-            w_ = (int)(t % a.W); t /= a.W;
-            h_ = (int)(t % a.H); t /= a.H;
-            d_ = (int)(t % a.D);
-            img = t / a.D;
+    if (warp == 4) {
+        if (lane == 0) {
+            prefetch_tmap(&xmap);
+            for (long long i = 0; i < total; ++i) {
+                const int s = (int)(i % kStages), c = (int)(i % nch);
+                const long long u = i / kStages;
+                if (u > 0 && !mbar_wait(&empty[s], (uint32_t)((u - 1) & 1), a.status)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                const TileCoord tc = tile_coord(t_begin + i / nch, a.D, a.H, ntw);
+                const int gn = min(kChunkGroups, a.kgroups - c * kChunkGroups);
+                mbar_arrive_expect_tx(&full[s], (uint32_t)gn * 2048u);
+                for (int kj = 0; kj < gn; ++kj) {
+                    const int G = c * kChunkGroups + kj;
+                    const int tap = G / a.cin_groups, cg = G - tap * a.cin_groups;
+                    int dd = 0, dh = 0, dw = 0;
+                    int x1 = a.W + 256;  // K padding: a box entirely outside the image (zeros)
+                    if (tap < ntaps) {
+                        tap_offset(tap, a.taps3d, dd, dh, dw);
+                        x1 = tc.w0 + dw;
+                    }
+                    tma_load_5d(sA + s * kAStageBytes + kj * 2048, &xmap, cg * 8, x1, tc.h + dh, tc.d + dd, tc.img,
+                                &full[s]);
+                }
+            }
         }
-        for (int c = 0; c < nchunks; ++c, ++q) {
-            const int s = (int)(q & 1);
-            if (q >= 2 && !mbar_wait(&bar[s], (uint32_t)(((q >> 1) - 1) & 1), a.status)) {
+    } else if (warp == 5) {
+        if (lane == 0) {
+            const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
+            long long i = 0;
+            for (long long j = 0; j < my_tiles && !*abort_flag; ++j) {
+                const int ab = (int)(j & 1);
+                if (j >= 2 && !mbar_wait(&acce[ab], (uint32_t)(((j >> 1) - 1) & 1), a.status)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem + (uint32_t)(ab * NPAD);
+                for (int c = 0; c < nch; ++c, ++i) {
+                    const int s = (int)(i % kStages);
+                    if (!mbar_wait(&full[s], (uint32_t)((i / kStages) & 1), a.status)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const int ksteps = min(kChunkGroups, a.kgroups - c * kChunkGroups) / 2;
+                    for (int ks = 0; ks < ksteps; ++ks) {
+                        const uint64_t ad = smem_desc_kmajor(sA_u + s * kAStageBytes + ks * 2 * 2048, 2048, 128);
+                        const uint64_t bd = smem_desc_kmajor(sB_u + (c * kChunkGroups + ks * 2) * (NPAD / 8) * 128,
+                                                             (NPAD / 8) * 128, 128);
+                        mma_bf16(dt, ad, bd, kIdesc, (c > 0 || ks > 0) ? 1u : 0u);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (*abort_flag) break;
+                mma_commit(&accf[ab]);
+            }
+        }
+    } else {
+        // epilogue warps 0-3: TMEM lanes 32 warp .. + 31 = tile rows
+        for (long long j = 0; j < my_tiles; ++j) {
+            const int ab = (int)(j & 1);
+            if (!mbar_wait(&accf[ab], (uint32_t)((j >> 1) & 1), a.status)) {
                 *abort_flag = 1;
                 break;
             }
-            // gather A chunk: row tid, K groups 8c .. 8c+7
-            unsigned char *st = sA + s * kAStageBytes;
+            tc_fence_after();
+            float acc[NPAD];
 #pragma unroll
-            for (int kj = 0; kj < kChunkGroups; ++kj) {
-                const int G = c * kChunkGroups + kj;
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (prow && G < a.kgroups) {
-                    const int tap = G / a.cin_groups, cg = G - tap * a.cin_groups;
-                    if (tap < ntaps) {
-                        int dd, dh, dw;
-                        tap_offset(tap, a.taps3d, dd, dh, dw);
-                        const int d2 = d_ + dd, h2 = h_ + dh, w2 = w_ + dw;
-                        if (d2 >= 0 && d2 < a.D && h2 >= 0 && h2 < a.H && w2 >= 0 && w2 < a.W) {
-                            const long long src = (((img * a.D + d2) * a.H + h2) * a.W + w2) * a.cpin + cg * 8;
-                            v = __ldg(reinterpret_cast<const uint4 *>(a.x + src));
-                        }
-                    }
-                }
-                *reinterpret_cast<uint4 *>(st + (kj * 16 + (tid >> 3)) * 128 + (tid & 7) * 16) = v;
-            }
-            fence_async_smem();
+            for (int c0 = 0; c0 < NPAD; c0 += 16)
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * NPAD + c0), acc + c0);
             tc_fence_before();
-            __syncthreads();
-            if (*abort_flag) break;
-            if (tid == 0) {
-                tc_fence_after();
-                const int ksteps = min(kChunkGroups, a.kgroups - c * kChunkGroups) / 2;
-                for (int ks = 0; ks < ksteps; ++ks) {
-                    const uint64_t ad = smem_desc_kmajor(sA_u + s * kAStageBytes + ks * 2 * 2048, 2048, 128);
-                    const uint64_t bd =
-                        smem_desc_kmajor(sB_u + (c * kChunkGroups + ks * 2) * (NPAD / 8) * 128, (NPAD / 8) * 128, 128);
-                    mma_bf16(tmem, ad, bd, kIdesc, (c > 0 || ks > 0) ? 1u : 0u);
-                }
-                mma_commit(&bar[s]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[ab]);
+            const TileCoord tc = tile_coord(t_begin + j, a.D, a.H, ntw);
+            const int w = tc.w0 + tid;
+            if (w < a.W) {
+                const long long p = (((long long)tc.img * a.D + tc.d) * a.H + tc.h) * a.W + w;
+                conv_epilogue<NPAD, EPI>(a, acc, p);
             }
         }
-        if (*abort_flag) break;
-        // epilogue: wait for the tile's last commit
-        const long long ql = q - 1;
-        if (!mbar_wait(&bar[ql & 1], (uint32_t)((ql >> 1) & 1), a.status)) {
-            *abort_flag = 1;
-            break;
-        }
-        tc_fence_after();
-        float acc[NPAD];
-#pragma unroll
-        for (int c0 = 0; c0 < NPAD; c0 += 16) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, acc + c0);
-        tc_fence_before();
-        if (prow) {
-            if constexpr (EPI == EPI_RESIDUAL_F32) {
-                for (int c = 0; c < a.cout; ++c) {
-                    float v = acc[c] + (a.bias ? __ldg(a.bias + c) : 0.f);
-                    float *o = a.state + c * a.sstride + p;
-                    *o += v;
-                }
-            } else {
-                __nv_bfloat16 *o = a.y + p * a.cpout;
-                const __nv_bfloat16 *mk = EPI == EPI_MASK_BF16 ? a.mask + p * a.cpout : nullptr;
-#pragma unroll
-                for (int c0 = 0; c0 < NPAD; c0 += 8) {
-                    if (c0 >= a.cpout) break;
-                    __align__(16) __nv_bfloat16 out8[8];
-                    uint4 mv = make_uint4(0u, 0u, 0u, 0u);
-                    if constexpr (EPI == EPI_MASK_BF16) mv = *reinterpret_cast<const uint4 *>(mk + c0);
-                    const __nv_bfloat16 *m8 = reinterpret_cast<const __nv_bfloat16 *>(&mv);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int c = c0 + j;
-                        float v = 0.f;
-                        if (c < a.cout) {
-                            v = acc[c];
-                            if constexpr (EPI == EPI_ACT_BF16) {
-                                if (a.bias) v += __ldg(a.bias + c);
-                                v = v > 0.f ? v : v * a.slope;
-                            } else {
-                                v = __bfloat162float(m8[j]) > 0.f ? v : v * a.slope;
-                            }
-                        }
-                        out8[j] = __float2bfloat16_rn(v);
-                    }
-                    *reinterpret_cast<uint4 *>(o + c0) = *reinterpret_cast<const uint4 *>(out8);
-                }
-            }
-        }
-        __syncthreads();  // TMEM reads of this tile precede the next tile's first MMA
     }
     __syncthreads();
     if (warp == 0) {
@@ -338,15 +405,26 @@ int conv_pack(const float *w, int cout, int ntaps, int cin, int cp_in, int flip,
 template <int NPAD, int EPI>
 static int launch_conv(const ConvArgs &a, cudaStream_t st) {
     const int bbytes = a.kgroups * NPAD * 16;
-    const size_t smem = 128 + ((bbytes + 127) & ~127) + 2 * kAStageBytes + 64;
-    if (smem > 200 * 1024) return fail(CBCT_EINVAL, "conv: weights do not fit in shared memory");
+    const size_t smem = 1024 + kStages * kAStageBytes + ((bbytes + 127) & ~127) + 8 * (2 * kStages + 4) + 64;
+    if (smem > 220 * 1024) return fail(CBCT_EINVAL, "conv: weights do not fit in shared memory");
     cudaError_t e = cudaFuncSetAttribute(k_conv_tc<NPAD, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "conv smem attribute");
-    const long long npix = (long long)a.nimg * a.D * a.H * a.W;
-    const long long ntiles = (npix + 127) / 128;
-    const int per_sm = smem > 110 * 1024 ? 1 : 2;
-    const int grid = (int)std::min<long long>(ntiles, 152LL * per_sm);
-    k_conv_tc<NPAD, EPI><<<grid, kConvThreads, smem, st>>>(a);
+    // x as a 5-D tensor (channels, W, H, D, images); one box = 8 channels x 128 pixels
+    CUtensorMap xmap;
+    const uint64_t cp = (uint64_t)a.cpin;
+    const uint64_t dims[5] = {cp, (uint64_t)a.W, (uint64_t)a.H, (uint64_t)a.D, (uint64_t)a.nimg};
+    const uint64_t strides[4] = {cp * 2, cp * 2 * a.W, cp * 2 * a.W * a.H, cp * 2 * a.W * a.H * a.D};
+    const uint32_t box[5] = {8, 128, 1, 1, 1};
+    int rc = encode_tmap(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, a.x, dims, strides, box);
+    if (rc) return rc;
+    int dev = 0, nsm = 152, smem_sm = 228 * 1024;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const int per_sm = std::max(1, std::min(8, smem_sm / (int)(smem + 1024)));
+    const long long ntiles = (long long)a.nimg * a.D * a.H * ((a.W + 127) / 128);
+    const int grid = (int)std::min<long long>(ntiles, (long long)nsm * per_sm);
+    k_conv_tc<NPAD, EPI><<<grid, kWsThreads, smem, st>>>(xmap, a);
     CBCT_LAUNCH_CHECK("conv launch");
     return 0;
 }

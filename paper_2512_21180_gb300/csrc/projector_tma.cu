@@ -54,6 +54,18 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+int encode_tmap(CUtensorMap *map, CUtensorMapDataType dt, int rank, const void *base, const uint64_t *dims,
+                const uint64_t *strides, const uint32_t *box) {
+    auto fn = encode_fn();
+    if (!fn) return fail(CBCT_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = fn(map, dt, (cuuint32_t)rank, const_cast<void *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(CBCT_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return 0;
+}
+
 static int encode_4d(CUtensorMap *map, const float *base, const uint64_t dims[4], const uint64_t strides[3],
                      const uint32_t box[4]) {
     auto fn = encode_fn();

@@ -82,8 +82,9 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
-// Host: encode a tiled tensor map (driver entry point looked up through the runtime).
-int encode_tmap_f32_3d(CUtensorMap *map, const void *base, const uint64_t dims[3], const uint64_t strides_bytes[2],
-                       const uint32_t box[3]);
+// Host: encode a tiled tensor map of rank <= 5 without swizzle, zero fill outside
+// (driver entry point looked up through the runtime). strides: bytes, dims 1..rank-1.
+int encode_tmap(CUtensorMap *map, CUtensorMapDataType dt, int rank, const void *base, const uint64_t *dims,
+                const uint64_t *strides, const uint32_t *box);
 
 }  // namespace cbct

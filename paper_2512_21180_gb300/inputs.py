@@ -76,20 +76,22 @@ ELL_COLS = 17  # cx cy cz | ax ay az | R (row-major 3x3, rows = ellipsoid axes) 
 
 
 def ellipsoids(g: dict, seed: int, n_soft: int = 10, n_bone: int = 0, n_air: int = 0,
-               body: bool = False, axes_mm=(10.0, 100.0), mu=(0.01, 0.03)) -> np.ndarray:
+               body: bool = False, axes_mm=(10.0, 100.0), mu=(0.01, 0.03),
+               body_frac=(0.42, 0.36, 0.47), center_frac: float = 0.8) -> np.ndarray:
     """Seeded random-ellipsoid phantom parameters, one row per ellipsoid.
 
     Rows are applied in order: mode 0 adds `value` inside the ellipsoid, mode 1
     overwrites with `value` (bone-like 0.04/mm and air-like 0 inserts). Centres are
-    uniform in a cylinder of radius 0.8 x the half-width of the volume and axial
-    extent 0.8 x its height; orientations are uniform random rotations.
+    uniform in a cylinder of radius center_frac x the half-width of the volume and
+    axial extent 0.8 x its height; orientations are uniform random rotations. The
+    optional body ellipsoid has semi-axes body_frac x the volume's extent.
     """
     rng = np.random.default_rng(seed)
     n = np.asarray(g["n"], dtype=np.int64)
     vox = np.asarray(g["vox"], dtype=np.float64)
     ext = n * vox
     ctr = np.asarray(g["center"], dtype=np.float64)
-    r_cyl = 0.8 * 0.5 * min(ext[0], ext[1])
+    r_cyl = center_frac * 0.5 * min(ext[0], ext[1])
     h_cyl = 0.8 * 0.5 * ext[2]
     rows = []
 
@@ -102,7 +104,7 @@ def ellipsoids(g: dict, seed: int, n_soft: int = 10, n_bone: int = 0, n_air: int
         return np.concatenate([c, a, rot.reshape(-1), [val, mode]])
 
     if body:
-        a = np.array([0.42 * ext[0], 0.36 * ext[1], 0.47 * ext[2]])
+        a = np.asarray(body_frac) * ext
         rows.append(row(ctr.copy(), a, np.eye(3), 0.02, 0))
     for _ in range(n_soft):
         a = rng.uniform(axes_mm[0], axes_mm[1], size=3)
@@ -123,7 +125,9 @@ def phantom_params(name: str, seed: int) -> np.ndarray:
         # body + 31 soft-tissue + 4 bone-like + 4 air-like = 40 ellipsoids
         return ellipsoids(g, seed, n_soft=31, n_bone=4, n_air=4, body=True)
     if name in ("diff128", "lpd128", "coarse128"):
-        return ellipsoids(g, seed, n_soft=15, n_bone=3, n_air=2, body=True, axes_mm=(8.0, 60.0))
+        # the body stays inside the field of view of the +80 mm panel (radius ~182 mm)
+        return ellipsoids(g, seed, n_soft=15, n_bone=3, n_air=2, body=True, axes_mm=(8.0, 60.0),
+                          body_frac=(0.30, 0.26, 0.47), center_frac=0.5)
     return ellipsoids(g, seed, n_soft=10)
 
 

@@ -195,36 +195,43 @@ __global__ void __launch_bounds__(256) k_backproject(GeomDev g, const T *__restr
     }
 }
 
-// Gather v2 (FP32, geometries whose x- and y-principal columns form intervals).
-// CTA = 32 x 32 voxel columns x ZS voxels in z, 256 threads. For x-principal rays
-// warps run along x (all lanes share the voxel's in-plane coordinate y, hence the
-// detector columns), for y-principal rays along y; each thread owns 4 columns per
-// mapping and the two mappings meet in shared memory at the end. Along a detector
-// column the rows hit the voxel's plane at q_z = Sz + t rz(v), increasing with v;
-// the rows falling in each unit interval (L, L + 1] of z are summed once as
-// S0 = sum p and S1 = sum p (q_z - L), which gives the lower voxel S0 - S1 and the
-// upper voxel S1: two bilinear z-weights per row for two additions. The row that
-// opens an interval takes q_z exactly as the forward computes it; the rows after
-// it step by t * drz.
-template <int ZS>
-__global__ void __launch_bounds__(256) k_backproject_v2(GeomDev g, const float *__restrict__ pw,
-                                                        float *__restrict__ vol, int accumulate, int nparts,
-                                                        float *__restrict__ partial) {
-    // acc[slot][thread], slot = (mapping * 4 + column) * ZS + z: private per thread,
-    // dynamically indexed without local memory
-    __shared__ float acc[2 * 4 * ZS][256];
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
-    const int nzs = (g.n[2] + ZS - 1) / ZS;
+// Segment gather (FP32, geometries whose x- and y-principal columns form intervals).
+// CTA = brick of 16 x 16 voxel columns x 16 voxels in z, 288 threads. For the rays
+// of principal axis a at angle k, plane i of the brick is crossed at
+// q_b(u) = fma(di, dqb(u), qcb(u)), monotone in the detector column u. The columns
+// with floor(q_b) = s form segment s of the plane; their samples lie between voxels
+// s and s + 1 with weights 1 - frac(q_b) and frac(q_b). Thread (segment, plane)
+// sweeps the rows of each of its columns once, summing the rows of every unit
+// z-interval (L, L + 1] as S0 = sum p and S1 = sum p (q_z - L) (lower voxel
+// S0 - S1, upper voxel S1), and accumulates SA[z] for voxel s and SB[z] for voxel
+// s + 1. SB reaches the thread of segment s + 1 through shared memory and each
+// voxel adds SA + SB of its two segments to its shared accumulator, always in the
+// same order, so the result does not depend on scheduling.
+constexpr int kB3 = 16, kZ3 = 16, kThreads3 = 288;
+constexpr int kVacc3 = kZ3 * kB3 * (kB3 + 1);  // [z][y][x], y stride 17 (bank-conflict free both ways)
+constexpr int kSbuf3 = kB3 * kB3 * (kZ3 + 1);  // [voxel][plane][z], plane stride 17
+constexpr size_t kSmem3 = sizeof(float) * (kVacc3 + 2 * kSbuf3);
+
+__global__ void __launch_bounds__(kThreads3, 2) k_backproject_v3(GeomDev g, const float *__restrict__ pw,
+                                                                 float *__restrict__ vol, int accumulate,
+                                                                 int nparts, float *__restrict__ partial) {
+    extern __shared__ float sm3[];
+    float *vacc = sm3;
+    float *sbuf = sm3 + kVacc3;
+    const int tid = threadIdx.x;
+    const int il = tid & 15, seg = tid >> 4;  // plane il of the brick; segment j0 - 1 + seg
+    const bool item = seg <= kB3;             // 17 segments x 16 planes
+    const int x0 = blockIdx.x * kB3, y0 = blockIdx.y * kB3;
+    const int nzb = (g.n[2] + kZ3 - 1) / kZ3;
     const int part = blockIdx.z % nparts, zb = blockIdx.z / nparts;
-    const int z0 = (zb % nzs) * ZS, b = zb / nzs;
+    const int z0 = (zb % nzb) * kZ3, b = zb / nzb;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nu = g.nu, nv = g.nv;
-    // this CTA's share of the angles (the parts are summed in a fixed order later)
     const int k_begin = (int)((long long)g.na * part / nparts), k_end = (int)((long long)g.na * (part + 1) / nparts);
-    for (int sl = 0; sl < 2 * 4 * ZS; ++sl) acc[sl][tid] = 0.f;
+    for (int e = tid; e < kVacc3; e += kThreads3) vacc[e] = 0.f;
     const float Sz = g.Sz;
     const float rz0 = g.rz32[0], drz = nv > 1 ? g.rz32[1] - g.rz32[0] : 1.0f;
     const float *PB = pw + (long long)b * g.na * nv * nu;
+    int pass = 0;
 
 #pragma unroll 1
     for (int k = k_begin; k < k_end; ++k) {
@@ -233,47 +240,43 @@ __global__ void __launch_bounds__(256) k_backproject_v2(GeomDev g, const float *
 #pragma unroll 1
         for (int a = 0; a < 2; ++a) {
             const int alo = a == 0 ? F.ux_lo : F.uy_lo, ahi = a == 0 ? F.ux_hi : F.uy_hi;
-            if (alo > ahi) continue;
-            const float ca = 0.5f * (float)(g.n[a] - 1);
-#pragma unroll 1
-            for (int r = 0; r < 4; ++r) {
-                const int ix = a == 0 ? x0 + lane : x0 + w + 8 * r;
-                const int iy = a == 0 ? y0 + w + 8 * r : y0 + lane;
-                if (ix >= nx || iy >= ny) continue;
-                const int i = a == 0 ? ix : iy, jb = a == 0 ? iy : ix;
-                const float di = (float)i - ca;
+            if (alo > ahi) continue;  // uniform over the CTA
+            const int j0 = a == 0 ? y0 : x0;
+            const int i = (a == 0 ? x0 : y0) + il, s = j0 - 1 + seg;
+            float SA[kZ3], SB[kZ3];
+#pragma unroll
+            for (int m = 0; m < kZ3; ++m) SA[m] = SB[m] = 0.f;
+            if (item && i < g.n[a] && s < g.n[1 - a]) {
+                const float di = (float)i - 0.5f * (float)(g.n[a] - 1);
+                // candidate columns for q_b in [s, s + 1), one column of margin
                 float u1, u2;
-                if (a == 0) { u1 = column_of(F, (float)ix, (float)(iy - 1)); u2 = column_of(F, (float)ix, (float)(iy + 1)); }
-                else { u1 = column_of(F, (float)(ix - 1), (float)iy); u2 = column_of(F, (float)(ix + 1), (float)iy); }
+                if (a == 0) { u1 = column_of(F, (float)i, (float)s); u2 = column_of(F, (float)i, (float)(s + 1)); }
+                else { u1 = column_of(F, (float)s, (float)i); u2 = column_of(F, (float)(s + 1), (float)i); }
                 int ulo = alo, uhi = ahi;
                 if (isfinite(u1) && isfinite(u2)) {
                     ulo = max(ulo, (int)floorf(fmaxf(fminf(u1, u2), -1.0e6f)) - 1);
                     uhi = min(uhi, (int)ceilf(fminf(fmaxf(u1, u2), 1.0e6f)) + 1);
                 }
-                if (ulo > uhi) continue;
-                // rows of the z-run for the extreme columns (t is monotone in u): skip the
-                // column loop when no row of the panel reaches the run
-                {
+                if (ulo <= uhi) {
+                    // skip the columns when no row of the panel reaches the z-run
                     const ColT<float> cl = col_of<float>(g, k, ulo), ch = col_of<float>(g, k, uhi);
                     const float tl = fma_rn(di, cl.inv, cl.tc), th = fma_rn(di, ch.inv, ch.tc);
                     const float tmin = fminf(tl, th), tmax = fmaxf(tl, th);
-                    if (!(tmax > 0.f)) continue;
-                    // q_z = Sz + t rz(v) in (z0 - 1, z0 + ZS)  <=>  rz in a range
-                    const float zlo = (float)(z0 - 1) - Sz, zhi = (float)(z0 + ZS) - Sz;
+                    const float zlo = (float)(z0 - 1) - Sz, zhi = (float)(z0 + kZ3) - Sz;
                     const float t1 = fmaxf(tmin, 1e-6f);
                     const float rlo = fminf(zlo / t1, zlo / tmax), rhi = fmaxf(zhi / t1, zhi / tmax);
                     const float vlo = (rlo - rz0) / drz - 2.f, vhi = (rhi - rz0) / drz + 2.f;
-                    if (vhi < 0.f || vlo > (float)(nv - 1)) continue;
+                    if (!(tmax > 0.f) || vhi < 0.f || vlo > (float)(nv - 1)) uhi = ulo - 1;
                 }
-                float *slot = &acc[(a * 4 + r) * ZS][tid];
 #pragma unroll 1
                 for (int u = ulo; u <= uhi; ++u) {
                     const ColT<float> c = col_of<float>(g, k, u);
                     const float t = fma_rn(di, c.inv, c.tc);
                     if (!(t > 0.f && t < 1.f)) continue;
                     const float qb = fma_rn(di, c.dqb, c.qcb);
-                    const float wb = 1.0f - fabsf(qb - (float)jb);
-                    if (!(wb > 0.f)) continue;
+                    const float fb = floorf(qb);
+                    if (fb != (float)s) continue;  // the column belongs to another segment
+                    const float wu = qb - fb, wl = 1.0f - wu;
                     const float step = t * drz, irs = 1.0f / step, voff = fmaf(t, rz0, Sz);
                     // first row whose sample lies above z0 - 1 + m
                     auto row_above = [&](int m) {
@@ -281,19 +284,17 @@ __global__ void __launch_bounds__(256) k_backproject_v2(GeomDev g, const float *
                         return min(max((int)floorf(fminf(fmaxf(vs, -1.0e6f), 1.0e6f)) + 1, 0), nv);
                     };
                     int va = row_above(0);
-                    float carry = 0.f;  // lower-voxel share of the previous interval
-#pragma unroll 1
-                    for (int m = 0; m < ZS + 1; ++m) {
+                    float carry = 0.f;  // upper-voxel share of the previous interval
+#pragma unroll
+                    for (int m = 0; m < kZ3 + 1; ++m) {
                         const int ve = row_above(m + 1);
                         float S0 = 0.f, S1 = 0.f;
                         if (va < ve) {
-                            const float rz = rz_of<float>(g, va);
                             float dqz, qcz;
-                            ray_row(g, c, rz, dqz, qcz);
-                            const float qf0 = fma_rn(di, dqz, qcz) - (float)(z0 - 1 + m);
+                            ray_row(g, c, rz_of<float>(g, va), dqz, qcz);
+                            float qf = fma_rn(di, dqz, qcz) - (float)(z0 - 1 + m);
                             const float *pp = Pk + (long long)va * nu + u;
                             const int n = ve - va;
-                            float qf = qf0;
 #pragma unroll 4
                             for (int rr = 0; rr < n; ++rr) {
                                 const float p = __ldg(pp);
@@ -303,34 +304,48 @@ __global__ void __launch_bounds__(256) k_backproject_v2(GeomDev g, const float *
                                 qf += step;
                             }
                         }
-                        // voxel z0 - 1 + m takes the upper share of interval m - 1
-                        // (carry) and the lower share of interval m
-                        if (m >= 1) slot[(m - 1) * 256] += wb * (carry + S0 - S1);
+                        // voxel z0 - 1 + m: upper share of interval m - 1, lower share of interval m
+                        if (m >= 1) {
+                            const float R = carry + S0 - S1;
+                            SA[m - 1] = fmaf(wl, R, SA[m - 1]);
+                            SB[m - 1] = fmaf(wu, R, SB[m - 1]);
+                        }
                         carry = S1;
                         va = ve;
                     }
                 }
             }
+            // SB of segment j0 - 1 + seg belongs to voxel seg of the brick
+            float *sb = sbuf + (pass & 1) * kSbuf3;
+            if (seg < kB3) {
+                float *d = sb + (seg * kB3 + il) * (kZ3 + 1);
+#pragma unroll
+                for (int m = 0; m < kZ3; ++m) d[m] = SB[m];
+            }
+            __syncthreads();
+            if (seg >= 1 && seg <= kB3) {
+                const int vl = seg - 1;  // this segment's voxel: own SA + SB of segment vl - 1
+                const int xl = a == 0 ? il : vl, yl = a == 0 ? vl : il;
+                float *v = vacc + yl * (kB3 + 1) + xl;
+                const float *src = sb + (vl * kB3 + il) * (kZ3 + 1);
+#pragma unroll
+                for (int m = 0; m < kZ3; ++m) v[m * kB3 * (kB3 + 1)] += SA[m] + src[m];
+            }
+            ++pass;  // the other buffer next time: one barrier per pass suffices
         }
     }
     __syncthreads();
-    // combine: voxel (x_local = lane, y_local = w + 8 r) collects mapping-x slot of
-    // thread (lane, w), column r, and mapping-y slot of thread (y_local % 8 ... )
     const long long nxy = (long long)nx * ny;
-    const int nb_ = (int)(gridDim.z / nparts / nzs);  // batch
-    float *out = nparts > 1 ? partial + ((long long)part * nb_ + b) * nxy * nz : vol + (long long)b * nxy * nz;
+    const int nbatch = (int)(gridDim.z / nparts / nzb);
+    float *out = nparts > 1 ? partial + ((long long)part * nbatch + b) * nxy * nz : vol + (long long)b * nxy * nz;
     const int acc_mode = nparts > 1 ? 0 : accumulate;
-    const int ix = x0 + lane;
-    for (int j = 0; j < ZS; ++j) {
-        if (z0 + j >= nz) continue;
-        for (int r = 0; r < 4; ++r) {
-            const int yl = w + 8 * r, iy = y0 + yl;
-            // mapping x: thread (lane, w), column r; mapping y: thread (lane' = yl, w' = lane % 8), column lane / 8
-            const float v = acc[(0 * 4 + r) * ZS + j][w * 32 + lane] + acc[(1 * 4 + lane / 8) * ZS + j][(lane % 8) * 32 + yl];
-            if (ix < nx && iy < ny) {
-                float *o = out + ((long long)(z0 + j) * ny + iy) * nx + ix;
-                *o = acc_mode ? *o + v : v;
-            }
+    for (int e = tid; e < kZ3 * kB3 * kB3; e += kThreads3) {
+        const int xl = e & (kB3 - 1), yl = (e / kB3) & (kB3 - 1), zl = e / (kB3 * kB3);
+        const int ix = x0 + xl, iy = y0 + yl, iz = z0 + zl;
+        if (ix < nx && iy < ny && iz < nz) {
+            float *o = out + ((long long)iz * ny + iy) * nx + ix;
+            const float v = vacc[zl * kB3 * (kB3 + 1) + yl * (kB3 + 1) + xl];
+            *o = acc_mode ? *o + v : v;
         }
     }
 }
@@ -442,26 +457,27 @@ static int backward_impl(const cbct_geom *g, const T *proj, T *vol, int batch, i
     if (e == cudaSuccess) {
         if constexpr (sizeof(T) == 4) {
             if (g->axis_contiguous) {
-                constexpr int ZS2 = 4;
-                const int nz2 = (d.n[2] + ZS2 - 1) / ZS2;
-                const long long base = (long long)((d.n[0] + 31) / 32) * ((d.n[1] + 31) / 32) * nz2 * batch;
-                // split the angles so that about 24 CTAs per SM are available
-                int nparts = (int)std::min<long long>(16, std::max<long long>(1, (152LL * 24 + base - 1) / base));
+                const int nzb = (d.n[2] + kZ3 - 1) / kZ3;
+                const long long base = (long long)((d.n[0] + kB3 - 1) / kB3) * ((d.n[1] + kB3 - 1) / kB3) * nzb * batch;
+                // split the angles so that about 6 CTAs per SM are available
+                int nparts = (int)std::min<long long>(16, std::max<long long>(1, (152LL * 6 + base - 1) / base));
                 nparts = std::min(nparts, d.na);
-                while (nparts > 1 && (long long)nz2 * batch * nparts > 65535) --nparts;
+                while (nparts > 1 && (long long)nzb * batch * nparts > 65535) --nparts;
+                if ((long long)nzb * batch * nparts > 65535) e = cudaErrorInvalidConfiguration;
                 float *partial = nullptr;
                 const long long nvol = (long long)batch * d.n[0] * d.n[1] * d.n[2];
-                if (nparts > 1) e = cudaMallocAsync((void **)&partial, sizeof(float) * nvol * nparts, st);
+                if (e == cudaSuccess && nparts > 1) e = cudaMallocAsync((void **)&partial, sizeof(float) * nvol * nparts, st);
+                if (e == cudaSuccess) e = cudaFuncSetAttribute(k_backproject_v3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem3);
                 if (e == cudaSuccess) {
-                    dim3 gb2((d.n[0] + 31) / 32, (d.n[1] + 31) / 32, nz2 * batch * nparts);
-                    k_backproject_v2<ZS2><<<gb2, 256, 0, st>>>(d, pw, vol, accumulate, nparts, partial);
+                    dim3 gb3((d.n[0] + kB3 - 1) / kB3, (d.n[1] + kB3 - 1) / kB3, nzb * batch * nparts);
+                    k_backproject_v3<<<gb3, kThreads3, kSmem3, st>>>(d, pw, vol, accumulate, nparts, partial);
                     e = cudaGetLastError();
                     if (e == cudaSuccess && nparts > 1) {
                         k_sum_parts<<<152 * 8, 256, 0, st>>>(partial, nparts, nvol, vol, accumulate);
                         e = cudaGetLastError();
                     }
-                    if (partial) cudaFreeAsync(partial, st);
                 }
+                if (partial) cudaFreeAsync(partial, st);
                 cudaFreeAsync(pw, st);
                 if (e != cudaSuccess) return cuda_fail(e, "back_project launch");
                 return 0;

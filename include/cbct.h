@@ -239,24 +239,29 @@ int cbct_landweber(const cbct_geom *g, const float *y, float *x, int batch, int 
 /* One 3x3 (taps3d = 0: over (H, W) of each of nimg * D images) or 3x3x3 (taps3d = 1)
  * "same" cross-correlation, stride 1, on the tensor cores (tcgen05.mma, BF16
  * operands, FP32 accumulation in TMEM): the learned blocks of Sec. 2.4 (Algorithm 1,
- * Gamma and Lambda). x: BF16 channels-last [nimg][D][H][W][cpin] (cpin multiple of
- * 8, channels >= cin zero), w: FP32 [cout][taps][cin], bias: FP32 [cout] or NULL.
+ * Gamma and Lambda). Activations are BF16 "row-blocked": image row (img, d, h) holds
+ * its channel groups one after the other, element (img, d, h, w, c) at
+ * ((((img * D + d) * H + h) * (cp / 8) + c / 8) * W + w) * 8 + c % 8 for cp channel
+ * slots per pixel. x: cpin = 8, 16 or 32 slots (slots >= cin zero); w: FP32
+ * [cout][taps][cin]; bias: FP32 [cout] or NULL.
  * flip = 0: y = conv(x) with cout outputs; flip = 1: the input-gradient convolution
  * (x holds cout channels, mirrored taps, cin outputs). At most 32 outputs.
- * epi 0: y = BF16 LeakyReLU(acc + bias) channels-last [..][cpout] (padding channels 0)
+ * epi 0: y = BF16 LeakyReLU(acc + bias), row-blocked with cpout slots (padding 0)
  * epi 1: state[c * sstride + pixel] += acc + bias (FP32, channel-first), c < outputs
- * epi 2: y = BF16 acc * (mask > 0 ? 1 : slope), mask BF16 [..][cpout] (LeakyReLU
- *        derivative from the forward activation).
+ * epi 2: y = BF16 acc * (mask > 0 ? 1 : slope), mask BF16 row-blocked like y (the
+ *        LeakyReLU derivative from the forward activation).
  * status: device int, set to 1 if a kernel gives up waiting on its tensor cores.
- * Scratch: the packed weights (at most 64 KiB). */
+ * Errors: CBCT_EINVAL for cpin not in {8, 16, 32}, cpin below the input channels,
+ * more than 32 outputs or a missing output buffer. Scratch: the packed weights. */
 int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d, const float *w,
               const float *bias, int cin, int cout, int flip, int epi, float slope, void *y, int cpout,
               const void *mask, float *state, long long sstride, int *status, void *stream);
 
 /* Weight and bias gradients of the convolution above: dw[co][tap][ci] (+)=
- * sum_p dy[p][co] x[p + tap][ci], db[co] (+)= sum_p dy[p][co]; x BF16 [..][cpin],
- * dy BF16 [..][cpout]. CUDA cores, FP32; partial sums over pixel chunks reduced in
- * a fixed order (deterministic). */
+ * sum_p dy[p][co] x[p + tap][ci], db[co] (+)= sum_p dy[p][co]; x BF16 row-blocked
+ * with cpin slots, dy BF16 row-blocked with cpout slots (both multiples of 8). CUDA
+ * cores, FP32; partial sums over pixel chunks reduced in a fixed order
+ * (deterministic). */
 int cbct_conv_wgrad(const void *x, int cpin, int cin, const void *dy, int cpout, int cout, int nimg, int D, int H,
                     int W, int taps3d, float *dw, float *db, int accumulate, void *stream);
 

@@ -6,14 +6,16 @@
 // Forward (and input-gradient) convolution = implicit GEMM on the fifth-generation
 // tensor cores: D[128 pixels][N out channels] = sum_K A[pixel][K] B[n][K], K = (tap,
 // input channel). A CTA walks a contiguous range of tiles of 128 consecutive
-// output pixels along W; for every K chunk of 64 it loads the shifted input
-// pixels with TMA: one box of [128 output pixels][8 channels] per (tap, channel
-// group) is exactly one K-major core-matrix column, zero-filled outside the image.
-// A producer warp fills a 4-stage ring, one thread issues 128 x N x 16 tcgen05.mma
-// into double-buffered TMEM accumulators, four epilogue warps drain them. The
-// packed weights (B) stay in shared memory for the CTA's lifetime. The epilogue
-// reads TMEM with tcgen05.ld and applies bias + LeakyReLU (BF16 channels-last
-// out), a residual update of an FP32 channel-first state, or an activation mask.
+// output pixels along W. Four producer warps copy, per tile and input plane, the
+// three input rows the 3x3 taps touch (130 pixels with the halo, zero outside the
+// image) into a 4-stage ring; since a K-major core matrix is 8 pixels x 16 B
+// contiguous, every tap is the same row region addressed 16 B per pixel later, so
+// each input row is read once per tile rather than once per tap. One thread issues
+// 128 x N x 16 tcgen05.mma (one per tap and pair of channel groups) into
+// double-buffered TMEM accumulators, four epilogue warps drain them. The packed
+// weights (B) stay in shared memory for the CTA's lifetime. The epilogue reads TMEM
+// with tcgen05.ld and applies bias + LeakyReLU (BF16 channels-last out), a residual
+// update of an FP32 channel-first state, or an activation mask.
 //
 // Weight gradients run on the CUDA cores (register-blocked FP32 accumulation over
 // pixel chunks, partial sums reduced in a fixed order).
@@ -29,23 +31,20 @@
 
 namespace cbct {
 
-constexpr int kConvThreads = 128;
-constexpr int kChunkGroups = 8;  // K groups (of 8 channels) per A chunk = 64 K elements
-constexpr int kAStageBytes = kChunkGroups * 16 * 128;  // 8 K-groups x 16 row groups x 128 B
-
 enum ConvEpi { EPI_ACT_BF16 = 0, EPI_RESIDUAL_F32 = 1, EPI_MASK_BF16 = 2 };
 
 struct ConvArgs {
-    const __nv_bfloat16 *x;  // [nimg][D][H][W][cpin], channels-last
+    const __nv_bfloat16 *x;  // [nimg][D][H][cpin / 8][W][8]: rows of channel groups
     const uint8_t *wpk;      // packed B operand: kgroups x (NPAD/8) core matrices
     const float *bias;       // [cout] or null
     int nimg, D, H, W;
-    int cpin, cin_groups;    // channel stride (multiple of 8), cpin / 8
+    int cpin, cin_groups;    // channels per pixel (8, 16 or 32), cpin / 8
+    int G;                   // pixels per TMA box row (4, 2 or 1: the largest dividing W)
     int taps3d;              // 1: 3x3x3, 0: 3x3 over (H, W)
     int kgroups;             // padded K / 8 (even)
     int cout;
     float slope;
-    __nv_bfloat16 *y;        // EPI_ACT_BF16 / EPI_MASK_BF16 output, channel stride cpout
+    __nv_bfloat16 *y;        // EPI_ACT_BF16 / EPI_MASK_BF16 output [nimg][D][H][cpout / 8][W][8]
     int cpout;
     const __nv_bfloat16 *mask;  // EPI_MASK_BF16: forward activation (same layout as y); out *= (mask > 0 ? 1 : slope)
     float *state;            // EPI_RESIDUAL_F32: state[c * sstride + pixel] += v
@@ -65,61 +64,50 @@ __device__ __forceinline__ void tap_offset(int tap, int taps3d, int &dd, int &dh
     }
 }
 
-constexpr int kStages = 4;          // A ring: kStages x 16 KiB
-constexpr int kWsThreads = 192;     // warps 0-3 epilogue, 4 producer, 5 MMA
-
-__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
-                                            uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-        "%5, %6}], [%7];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// Tile t = ((img * D + d) * H + h) * ntw + wt covers output pixels (img, d, h, 128 wt + r).
-struct TileCoord {
-    int img, d, h, w0;
-};
-__device__ __forceinline__ TileCoord tile_coord(long long t, int D, int H, int ntw) {
-    TileCoord c;
-    c.w0 = (int)(t % ntw) * 128; t /= ntw;
-    c.h = (int)(t % H); t /= H;
-    c.d = (int)(t % D);
-    c.img = (int)(t / D);
-    return c;
-}
-
-// Epilogue of one tile row: TMEM accumulators -> bias / activation / residual.
+// Epilogue of one output pixel: TMEM accumulators -> bias / activation / residual.
+// `row` = (img * D + d) * H + h, `w` the column; `bias` points to shared memory
+// (zeros when the layer has none; every lane reads the same word, a broadcast). Every global load is issued before the first
+// store so that one memory latency covers the row.
 template <int NPAD, int EPI>
-__device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *acc, long long p) {
+__device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *acc, const float *bias, long long row,
+                                              int w) {
+    const long long p = row * a.W + w;
     if constexpr (EPI == EPI_RESIDUAL_F32) {
 #pragma unroll
-        for (int c = 0; c < NPAD; ++c) {
-            if (c < a.cout) {
-                const float v = acc[c] + (a.bias ? __ldg(a.bias + c) : 0.f);
-                float *o = a.state + c * a.sstride + p;
-                *o += v;
-            }
+        for (int c0 = 0; c0 < NPAD; c0 += 8) {  // 8 channels per batch of loads
+            if (c0 >= a.cout) break;
+            float old[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) old[c] = c0 + c < a.cout ? a.state[(c0 + c) * a.sstride + p] : 0.f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (c0 + c < a.cout) a.state[(c0 + c) * a.sstride + p] = old[c] + (acc[c0 + c] + bias[c0 + c]);
         }
     } else {
-        __nv_bfloat16 *o = a.y + p * a.cpout;
-        const __nv_bfloat16 *mk = EPI == EPI_MASK_BF16 ? a.mask + p * a.cpout : nullptr;
+        // channel group q of this pixel: (row * (cpout / 8) + q) * W * 8 + w * 8
+        const long long o0 = (row * (a.cpout / 8) * a.W + w) * 8, gstride = (long long)a.W * 8;
+        __nv_bfloat16 *o = a.y + o0;
+        constexpr int kG = NPAD / 8;
+        uint4 mv[kG];
 #pragma unroll
-        for (int c0 = 0; c0 < NPAD; c0 += 8) {
-            if (c0 >= a.cpout) break;
+        for (int q = 0; q < kG; ++q) {
+            mv[q] = make_uint4(0u, 0u, 0u, 0u);
+            if constexpr (EPI == EPI_MASK_BF16)
+                if (q * 8 < a.cpout) mv[q] = *reinterpret_cast<const uint4 *>(a.mask + o0 + q * gstride);
+        }
+#pragma unroll
+        for (int q = 0; q < kG; ++q) {
+            if (q * 8 >= a.cpout) break;
+            const __nv_bfloat16 *m8 = reinterpret_cast<const __nv_bfloat16 *>(&mv[q]);
             __align__(16) __nv_bfloat16 out8[8];
-            uint4 mv = make_uint4(0u, 0u, 0u, 0u);
-            if constexpr (EPI == EPI_MASK_BF16) mv = *reinterpret_cast<const uint4 *>(mk + c0);
-            const __nv_bfloat16 *m8 = reinterpret_cast<const __nv_bfloat16 *>(&mv);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const int c = c0 + j;
+                const int c = q * 8 + j;
                 float v = 0.f;
                 if (c < a.cout) {
                     v = acc[c];
                     if constexpr (EPI == EPI_ACT_BF16) {
-                        if (a.bias) v += __ldg(a.bias + c);
+                        v += bias[c];
                         v = v > 0.f ? v : v * a.slope;
                     } else {
                         v = __bfloat162float(m8[j]) > 0.f ? v : v * a.slope;
@@ -127,151 +115,286 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *ac
                 }
                 out8[j] = __float2bfloat16_rn(v);
             }
-            *reinterpret_cast<uint4 *>(o + c0) = *reinterpret_cast<const uint4 *>(out8);
+            *reinterpret_cast<uint4 *>(o + q * gstride) = *reinterpret_cast<const uint4 *>(out8);
         }
     }
 }
 
-// Warp-specialized convolution tile loop. Item i of a CTA = (tile t_begin + i / nch,
-// K chunk i % nch) on ring stage i % kStages.
-//  producer (warp 4, one lane): waits until the stage is free (empty[s]), then TMA-loads
-//    the chunk's K groups, each a [128 pixels][8 channels] box = one K-major core-matrix
-//    column (16 B rows, 128 B between 8-row groups); taps outside the image and K padding
-//    come back as zeros.
-//  MMA (warp 5, one lane): per tile picks TMEM accumulator j & 1 once the epilogue has
-//    drained it (acce), waits for each chunk (full[s]), issues 128 x N x 16 MMAs, commits
-//    the stage to empty[s] and, after the tile's last chunk, the accumulator to accf.
-//  epilogue (warps 0-3): waits for accf, reads its 32 TMEM lanes, releases the
-//    accumulator, applies the epilogue and stores.
-template <int NPAD, int EPI>
-__global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ CUtensorMap xmap, ConvArgs a) {
+// Row-halo layout. A tile is 128 consecutive output pixels along W of RPT output
+// rows h0 .. h0 + RPT - 1 (RPT = 2 for the 2-D blocks, 1 for 3-D); an A stage holds
+// the NR = RPT + 2 input rows h0 - 1 .. h0 + RPT of one input plane as NR * CGP
+// regions (CGP = CG rounded up to even) of RS = 16 G R bytes (2176, 2112 or 2080;
+// at most kRowStride). Region r * CG + g holds channel group g of input row h0 - 1 + r
+// as 8-channel pixels 16 B apart from column w0 - G on, where G (4, 2 or 1) is the
+// TMA box row width in pixels. In
+// the row-blocked input layout a row's channel group is W x 16 contiguous bytes, so
+// one TMA box {G pixels x 8 channels, R = ceil((129 + G) / G), CG groups, NR image
+// rows} fills a stage (zero outside the image); stages start on 128-byte boundaries
+// as a tiled TMA destination must. A K-major core matrix is 8 rows x 16 B = 128
+// contiguous bytes, so with the 8-row group stride SBO = 128 the A operand for input
+// row r and column tap dw is region r started (G - 1 + dw) pixels in, and the
+// K-adjacent core matrix (next channel group) lies LBO = RS further. The B operand for (r, dw) stacks, for each output row o, the
+// weights of tap (dh = r - 1 - o, dw) (zero when |dh| > 1): N = RPT x NPAD, so one
+// MMA serves RPT output rows. With a single channel group (CG = 1) the two K halves
+// of an MMA are instead two consecutive input rows (LBO = RS) and only region NR, the
+// partner of the last row when NR is odd, stays zero. Every input row is loaded once
+// per tile.
+constexpr int kRowStride = 2176;         // 17 x 128 >= RS = 16 R G for G = 1, 2, 4
+__host__ __device__ constexpr int conv_box_rows(int G) { return (129 + G + G - 1) / G; }
+constexpr int kMaxStages = 8;            // A ring depth (chosen per launch, <= 8)
+constexpr int kAcc = 8;                  // TMEM accumulators (tiles in flight past the MMA)
+constexpr int kEpiGroups = 4;            // epilogue warpgroups; group q drains the tiles j = q mod 4
+constexpr int kWsThreads = 32 * (4 * kEpiGroups + 2);  // epilogue warps, then the TMA producer and the MMA warp
+constexpr int kProdWarp = 4 * kEpiGroups, kMmaWarp = 4 * kEpiGroups + 1;
+
+__host__ __device__ constexpr int conv_cgp(int cg) { return (cg + 1) & ~1; }
+__host__ __device__ constexpr int conv_stage_bytes(int cg, int rpt) { return (rpt + 2) * conv_cgp(cg) * kRowStride; }
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5, %6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Tile t = ((img * D + d) * nh + th) * ntw + wt: output rows th * RPT .. + RPT - 1 of
+// plane (img, d), columns w0 = 128 wt .. w0 + 127. Consecutive tiles are stepped
+// without divisions.
+struct TileCoord {
+    int img, d, th, w0;
+};
+__device__ __forceinline__ TileCoord tile_coord(long long t, int D, int nh, int ntw) {
+    TileCoord c;
+    c.w0 = (int)(t % ntw) * 128; t /= ntw;
+    c.th = (int)(t % nh); t /= nh;
+    c.d = (int)(t % D);
+    c.img = (int)(t / D);
+    return c;
+}
+__device__ __forceinline__ void tile_next(TileCoord &c, int D, int nh, int W) {
+    c.w0 += 128;
+    if (c.w0 < W) return;
+    c.w0 = 0;
+    if (++c.th < nh) return;
+    c.th = 0;
+    if (++c.d < D) return;
+    c.d = 0;
+    ++c.img;
+}
+
+// Warp-specialized convolution over row-halo stages. Item i of a CTA = (tile
+// t_begin + i / nch, input plane dd = i % nch - 1 for 3-D, the tile's own plane for
+// 2-D) on ring stage i % nst.
+//  producer (warp 16, one lane): waits until the stage is free (empty[s]) and loads
+//    the item's NR input rows with one TMA box, completion counted on full[s]; an
+//    input plane outside the volume only arrives (its MMAs are skipped).
+//  MMA (warp 17, one lane): per tile picks TMEM accumulator j % 8 once the epilogue
+//    has drained it (acce), waits for each item (full[s]), issues one 128 x N x 16
+//    MMA per (input row, column tap, pair of channel groups) or, for CG = 1, per
+//    (pair of input rows, column tap), commits the stage to
+//    empty[s] and, after the tile's last item, the accumulator to accf.
+//  epilogue (warps 0-15): warpgroup q takes the tiles j = q mod 4; each warp waits
+//    for accf, reads its 32 TMEM lanes (= pixels), releases the accumulator, applies
+//    the epilogue to each of the RPT output rows and stores.
+template <int NPAD, int EPI, int CG, int RPT>
+__global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ CUtensorMap xmap, ConvArgs a, int nst) {
+    constexpr int kCGP = conv_cgp(CG);
+    constexpr int kNR = RPT + 2;
+    constexpr int kN = RPT * NPAD;
+    constexpr bool kPair = CG == 1;               // K halves = consecutive input rows
+    constexpr int kNRP = (kNR + 1) / 2;           // row pairs per item (kPair)
+    constexpr int kStageBytes = conv_stage_bytes(CG, RPT);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    const int bbytes = a.kgroups * NPAD * 16;
-    unsigned char *sA = sm;                                         // kStages x 16 KiB
-    unsigned char *sB = sm + kStages * kAStageBytes;
+    const int bbytes = a.kgroups * kN * 16;
+    unsigned char *sA = sm;
+    unsigned char *sB = sm + nst * kStageBytes;
     uint64_t *full = reinterpret_cast<uint64_t *>(sB + ((bbytes + 127) & ~127));
-    uint64_t *empty = full + kStages;
-    uint64_t *accf = empty + kStages;
-    uint64_t *acce = accf + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acce + 2);
+    uint64_t *empty = full + kMaxStages;
+    uint64_t *accf = empty + kMaxStages;
+    uint64_t *acce = accf + kAcc;
+    float *sbias = reinterpret_cast<float *>(acce + kAcc);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sbias + NPAD);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr uint32_t kCols = 2 * NPAD < 32 ? 32 : 2 * NPAD;
-    constexpr uint32_t kIdesc = idesc_bf16_f32(128, NPAD);
+    constexpr uint32_t kCols = kAcc * kN;  // 128, 256 or 512: a power of two >= 32
+    constexpr uint32_t kIdesc = idesc_bf16_f32(128, kN);
+    const int rs = 16 * a.G * conv_box_rows(a.G);  // region stride (bytes)
 
     if (warp == 0) tmem_alloc(tmem_slot, kCols);
     if (tid == 32) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < nst; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < kAcc; ++j) {
             mbar_init(&accf[j], 1);
             mbar_init(&acce[j], 4);
         }
         *abort_flag = 0;
         fence_mbar_init();
     }
+    if (tid < NPAD) sbias[tid] = (a.bias && tid < a.cout) ? a.bias[tid] : 0.f;
     for (int i = tid; i < bbytes / 16; i += kWsThreads)
         reinterpret_cast<uint4 *>(sB)[i] = __ldg(reinterpret_cast<const uint4 *>(a.wpk) + i);
+    if constexpr (kPair && (kNR & 1)) {
+        // CG = 1, odd NR: region NR is the zero partner of the last row (its weights
+        // are zero too)
+        constexpr int kQ = kRowStride / 16;
+        for (int i = tid; i < nst * kQ; i += kWsThreads) {
+            const int s = i / kQ, q = i - s * kQ;
+            reinterpret_cast<uint4 *>(sA + s * kStageBytes + kNR * rs)[q] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int ntw = (a.W + 127) / 128;
-    const long long ntiles = (long long)a.nimg * a.D * a.H * ntw;
-    const int ntaps = a.taps3d ? 27 : 9;
-    const int nch = (a.kgroups + kChunkGroups - 1) / kChunkGroups;
+    const int ntw = (a.W + 127) / 128, nh = (a.H + RPT - 1) / RPT;
+    const long long ntiles = (long long)a.nimg * a.D * nh * ntw;
+    const int nch = a.taps3d ? 3 : 1;
     const long long per_cta = (ntiles + gridDim.x - 1) / gridDim.x;
     const long long t_begin = (long long)blockIdx.x * per_cta;
     const long long my_tiles = t_begin < ntiles ? min(per_cta, ntiles - t_begin) : 0;
     const long long total = my_tiles * nch;
+    const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
 
-    if (warp == 4) {
+    if (warp == kProdWarp) {
         if (lane == 0) {
             prefetch_tmap(&xmap);
+            TileCoord tc = tile_coord(t_begin, a.D, nh, ntw);
+            const uint32_t box_bytes = (uint32_t)(kNR * CG * rs);
+            int c = 0, s = 0;
+            uint32_t ph = 0;
             for (long long i = 0; i < total; ++i) {
-                const int s = (int)(i % kStages), c = (int)(i % nch);
-                const long long u = i / kStages;
-                if (u > 0 && !mbar_wait(&empty[s], (uint32_t)((u - 1) & 1), a.status)) {
+                if (i >= nst && !mbar_wait(&empty[s], ph ^ 1u, a.status)) {
                     *abort_flag = 1;
                     break;
                 }
-                const TileCoord tc = tile_coord(t_begin + i / nch, a.D, a.H, ntw);
-                const int gn = min(kChunkGroups, a.kgroups - c * kChunkGroups);
-                mbar_arrive_expect_tx(&full[s], (uint32_t)gn * 2048u);
-                for (int kj = 0; kj < gn; ++kj) {
-                    const int G = c * kChunkGroups + kj;
-                    const int tap = G / a.cin_groups, cg = G - tap * a.cin_groups;
-                    int dd = 0, dh = 0, dw = 0;
-                    int x1 = a.W + 256;  // K padding: a box entirely outside the image (zeros)
-                    if (tap < ntaps) {
-                        tap_offset(tap, a.taps3d, dd, dh, dw);
-                        x1 = tc.w0 + dw;
-                    }
-                    tma_load_5d(sA + s * kAStageBytes + kj * 2048, &xmap, cg * 8, x1, tc.h + dh, tc.d + dd, tc.img,
-                                &full[s]);
+                const int d2 = tc.d + (nch == 3 ? c - 1 : 0);
+                if (d2 < 0 || d2 >= a.D) {
+                    mbar_arrive_expect_tx(&full[s], 0u);  // plane outside the volume: no MMAs either
+                } else {
+                    mbar_arrive_expect_tx(&full[s], box_bytes);
+                    tma_load_5d(sA_u + (uint32_t)(s * kStageBytes), &xmap, 0, tc.w0 / a.G - 1, 0, tc.th * RPT - 1,
+                                tc.img * a.D + d2, &full[s]);
+                }
+                if (++c == nch) {
+                    c = 0;
+                    tile_next(tc, a.D, nh, a.W);
+                }
+                if (++s == nst) {
+                    s = 0;
+                    ph ^= 1u;
                 }
             }
         }
-    } else if (warp == 5) {
+    } else if (warp == kMmaWarp) {
         if (lane == 0) {
-            const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
-            long long i = 0;
+            // column tap dw of input row r reads region r from pixel G - 1 + dw on
+            const uint32_t rs16 = (uint32_t)(rs / 16);
+            const uint64_t adesc0 = smem_desc_kmajor(sA_u + (uint32_t)((a.G - 1) * 16), rs, 128);
+            const uint64_t bdesc0 = smem_desc_kmajor(sB_u, kN * 16, 128);
+            TileCoord tc = tile_coord(t_begin, a.D, nh, ntw);
+            int s = 0;
+            uint32_t ph = 0;
             for (long long j = 0; j < my_tiles && !*abort_flag; ++j) {
-                const int ab = (int)(j & 1);
-                if (j >= 2 && !mbar_wait(&acce[ab], (uint32_t)(((j >> 1) - 1) & 1), a.status)) {
+                const int ab = (int)(j % kAcc);
+                if (j >= kAcc && !mbar_wait(&acce[ab], (uint32_t)(((j / kAcc) - 1) & 1), a.status)) {
                     *abort_flag = 1;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t dt = tmem + (uint32_t)(ab * NPAD);
-                for (int c = 0; c < nch; ++c, ++i) {
-                    const int s = (int)(i % kStages);
-                    if (!mbar_wait(&full[s], (uint32_t)((i / kStages) & 1), a.status)) {
+                const uint32_t dt = tmem + (uint32_t)(ab * kN);
+                uint32_t acc_flag = 0;  // the tile's first MMA overwrites the accumulator
+                for (int c = 0; c < nch; ++c) {
+                    if (!mbar_wait(&full[s], ph, a.status)) {
                         *abort_flag = 1;
                         break;
                     }
-                    tc_fence_after();
-                    const int ksteps = min(kChunkGroups, a.kgroups - c * kChunkGroups) / 2;
-                    for (int ks = 0; ks < ksteps; ++ks) {
-                        const uint64_t ad = smem_desc_kmajor(sA_u + s * kAStageBytes + ks * 2 * 2048, 2048, 128);
-                        const uint64_t bd = smem_desc_kmajor(sB_u + (c * kChunkGroups + ks * 2) * (NPAD / 8) * 128,
-                                                             (NPAD / 8) * 128, 128);
-                        mma_bf16(dt, ad, bd, kIdesc, (c > 0 || ks > 0) ? 1u : 0u);
+                    const int d2 = tc.d + (nch == 3 ? c - 1 : 0);
+                    if (d2 >= 0 && d2 < a.D) {
+                        tc_fence_after();
+                        // descriptor start-address fields are address >> 4: offsets add directly
+                        const uint64_t ad = adesc0 + (uint64_t)((s * kStageBytes) >> 4);
+                        if constexpr (kPair) {
+                            const uint64_t bd = bdesc0 + (uint64_t)((c * kNRP * 3 * 2 * kN * 16) >> 4);
+#pragma unroll
+                            for (int rp = 0; rp < kNRP; ++rp)
+#pragma unroll
+                                for (int dw = 0; dw < 3; ++dw) {
+                                    const uint32_t ao = (uint32_t)(2 * rp) * rs16 + (uint32_t)dw;
+                                    const uint32_t bo = (uint32_t)((((rp * 3 + dw) * 2) * kN * 16) >> 4);
+                                    mma_bf16(dt, ad + ao, bd + bo, kIdesc, acc_flag);
+                                    acc_flag = 1;
+                                }
+                        } else {
+                            const uint64_t bd = bdesc0 + (uint64_t)((c * kNR * 3 * kCGP * kN * 16) >> 4);
+#pragma unroll
+                            for (int r = 0; r < kNR; ++r)
+#pragma unroll
+                                for (int dw = 0; dw < 3; ++dw)
+#pragma unroll
+                                    for (int kp = 0; kp < kCGP; kp += 2) {
+                                        const uint32_t ao = (uint32_t)(r * CG + kp) * rs16 + (uint32_t)dw;
+                                        const uint32_t bo = (uint32_t)((((r * 3 + dw) * kCGP + kp) * kN * 16) >> 4);
+                                        mma_bf16(dt, ad + ao, bd + bo, kIdesc, acc_flag);
+                                        acc_flag = 1;
+                                    }
+                        }
                     }
                     mma_commit(&empty[s]);
+                    if (++s == nst) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
                 }
                 if (*abort_flag) break;
                 mma_commit(&accf[ab]);
+                tile_next(tc, a.D, nh, a.W);
             }
         }
     } else {
-        // epilogue warps 0-3: TMEM lanes 32 warp .. + 31 = tile rows
-        for (long long j = 0; j < my_tiles; ++j) {
-            const int ab = (int)(j & 1);
-            if (!mbar_wait(&accf[ab], (uint32_t)((j >> 1) & 1), a.status)) {
+        // epilogue: warpgroup q = warp / 4 takes tiles q, q + 4, ...; warp w reads TMEM
+        // lanes 32 (w % 4) .. + 31 = tile pixels
+        const int q = warp >> 2, wq = warp & 3;
+        TileCoord tc = tile_coord(t_begin + q, a.D, nh, ntw);
+        for (long long j = q; j < my_tiles; j += kEpiGroups) {
+            const int ab = (int)(j % kAcc);
+            if (!mbar_wait(&accf[ab], (uint32_t)((j / kAcc) & 1), a.status)) {
                 *abort_flag = 1;
                 break;
             }
             tc_fence_after();
-            float acc[NPAD];
+            const int w = tc.w0 + wq * 32 + lane;
+            // one output row at a time (NPAD accumulator columns each); the accumulator is
+            // released after the last row's columns are in registers
 #pragma unroll
-            for (int c0 = 0; c0 < NPAD; c0 += 16)
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * NPAD + c0), acc + c0);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acce[ab]);
-            const TileCoord tc = tile_coord(t_begin + j, a.D, a.H, ntw);
-            const int w = tc.w0 + tid;
-            if (w < a.W) {
-                const long long p = (((long long)tc.img * a.D + tc.d) * a.H + tc.h) * a.W + w;
-                conv_epilogue<NPAD, EPI>(a, acc, p);
+            for (int o = 0; o < RPT; ++o) {
+                uint32_t raw[NPAD];
+#pragma unroll
+                for (int c0 = 0; c0 < NPAD; c0 += 16)
+                    tmem_ld16_issue(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(ab * kN + o * NPAD + c0), raw + c0);
+                tmem_wait_ld();
+                if (o == RPT - 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acce[ab]);
+                }
+                const int h = tc.th * RPT + o;
+                float acc[NPAD];
+#pragma unroll
+                for (int c = 0; c < NPAD; ++c) acc[c] = __uint_as_float(raw[c]);
+                if (w < a.W && h < a.H)
+                    conv_epilogue<NPAD, EPI>(a, acc, sbias, ((long long)tc.img * a.D + tc.d) * a.H + h, w);
             }
+#pragma unroll
+            for (int k = 0; k < kEpiGroups; ++k) tile_next(tc, a.D, nh, a.W);
         }
     }
     __syncthreads();
@@ -283,28 +406,49 @@ __global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ 
 
 // ---- weight packing ---------------------------------------------------------------------
 
-// B operand of the forward convolution: row n = output channel, K = (tap, input
-// channel) with the input channels padded to cpin. w: FP32 [cout][taps][cin].
-// flip = 1 packs the input-gradient convolution instead: row n = input channel, K =
-// (tap, output channel) with the mirrored tap (cpin = padded output channels).
-__global__ void k_pack_weights(const float *__restrict__ w, int cout, int ntaps, int cin, int cpin, int npad,
-                               int kgroups, int flip, uint8_t *__restrict__ out) {
-    const long long total = (long long)npad * kgroups * 8;
+// B operand in the row-halo order: group G = ((c * NR + r) * 3 + dw) * cgp + cg (input
+// plane c of nch, input row r of NR = rpt + 2, column tap dw, channel group cg) holds
+// rows n = o * npad + co (output row o < rpt, output channel co) x 8 channels, as
+// K-major core matrices; with pair_rows (one channel group) G = ((c * NRP + p) * 3 +
+// dw) * 2 + half holds input row r = 2 p + half instead (NRP = ceil(NR / 2); zero for
+// r = NR). The weight is that of tap (dd = c - 1, dh = r - 1 - o, dw - 1) (zero when
+// |dh| > 1). w: FP32 [cout][taps][cin]. flip = 1 packs the input-gradient
+// convolution instead: output channel co = ci, input channel = co of w, mirrored tap.
+__global__ void k_pack_weights(const float *__restrict__ w, int cout, int taps3d, int cin, int cgp, int npad, int rpt,
+                               int pair_rows, int flip, uint8_t *__restrict__ out) {
+    const int ntaps = taps3d ? 27 : 9, nch = taps3d ? 3 : 1, nr = rpt + 2, n2 = rpt * npad;
+    const int nrp = (nr + 1) / 2;
+    const long long ngroups = pair_rows ? (long long)nch * nrp * 3 * 2 : (long long)nch * nr * 3 * cgp;
+    const long long total = ngroups * n2 * 8;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        const int n = (int)(e / (kgroups * 8));
-        const int k = (int)(e - (long long)n * kgroups * 8);
-        const int tap = k / cpin, ch = k - tap * cpin;
+        const int kin = (int)(e & 7);
+        const int n = (int)((e >> 3) % n2);
+        const long long G = (e >> 3) / n2;
+        int c, r, dw, cg;
+        if (pair_rows) {
+            const int half = (int)(G & 1);
+            dw = (int)(G / 2 % 3);
+            const int p = (int)(G / 6 % nrp);
+            c = (int)(G / 6 / nrp);
+            r = 2 * p + half;
+            cg = 0;
+        } else {
+            cg = (int)(G % cgp);
+            dw = (int)(G / cgp % 3);
+            r = (int)(G / cgp / 3 % nr);
+            c = (int)(G / cgp / 3 / nr);
+        }
+        const int o = n / npad, co = n - o * npad, ch = cg * 8 + kin, dh = r - 1 - o;
         float v = 0.f;
-        if (tap < ntaps) {
+        if (r < nr && dh >= -1 && dh <= 1) {
+            const int tap = taps3d ? (c * 3 + dh + 1) * 3 + dw : (dh + 1) * 3 + dw;
             if (!flip) {
-                if (n < cout && ch < cin) v = w[((long long)n * ntaps + tap) * cin + ch];
+                if (co < cout && ch < cin) v = w[((long long)co * ntaps + tap) * cin + ch];
             } else {
-                // input-gradient conv: out channel n = ci, in channel ch = co, tap mirrored
-                if (n < cin && ch < cout) v = w[((long long)ch * ntaps + (ntaps - 1 - tap)) * cin + n];
+                if (co < cin && ch < cout) v = w[((long long)ch * ntaps + (ntaps - 1 - tap)) * cin + co];
             }
         }
-        const int kg = k >> 3, kin = k & 7;
-        const long long off = ((long long)kg * (npad / 8) + (n >> 3)) * 128 + (n & 7) * 16 + kin * 2;
+        const long long off = (G * (n2 / 8) + (n >> 3)) * 128 + (n & 7) * 16 + kin * 2;
         *reinterpret_cast<__nv_bfloat16 *>(out + off) = __float2bfloat16_rn(v);
     }
 }
@@ -342,9 +486,10 @@ __global__ void k_conv_wgrad(const __nv_bfloat16 *__restrict__ x, int cpin, int 
             const long long ic = img;
             if (++w_ == W) { w_ = 0; if (++h_ == H) { h_ = 0; if (++d_ == D) { d_ = 0; ++img; } } }
             if (!inside) continue;
-            (void)wc; (void)hc; (void)dc; (void)ic;
-            const __nv_bfloat16 *xs = x + (((ic * D + d2) * H + h2) * W + w2) * cpin + ci0;
-            const __nv_bfloat16 *ds = dy + p * cpout + co0;
+            // row-blocked layouts: (row * (cp / 8) + c / 8) * W * 8 + w * 8 + c % 8
+            const __nv_bfloat16 *xs =
+                x + ((((ic * D + d2) * H + h2) * (cpin / 8) + ci0 / 8) * W + w2) * 8 + (ci0 & 7);
+            const __nv_bfloat16 *ds = dy + ((((ic * D + dc) * H + hc) * (cpout / 8) + co0 / 8) * W + wc) * 8 + (co0 & 7);
             float xv[4], dv[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -366,7 +511,11 @@ __global__ void k_conv_wgrad(const __nv_bfloat16 *__restrict__ x, int cpin, int 
     // bias gradient
     for (int co = threadIdx.x; co < cout; co += blockDim.x) {
         float s = 0.f;
-        for (long long p = p0; p < p1; ++p) s += __bfloat162float(dy[p * cpout + co]);
+        for (long long p = p0; p < p1; ++p) {
+            const long long row = p / W;
+            const int w = (int)(p - row * W);
+            s += __bfloat162float(dy[((row * (cpout / 8) + co / 8) * W + w) * 8 + (co & 7)]);
+        }
         partial_b[(long long)blockIdx.x * cout + co] = s;
     }
 }
@@ -384,68 +533,96 @@ __global__ void k_reduce_rows(const float *__restrict__ partial, int nblk, int n
 // ---- host launchers -------------------------------------------------------------------------
 
 static int pad_npad(int cout) { return cout <= 16 ? 16 : 32; }
+// Output rows per tile: two for the 2-D (dual) blocks, one for 3-D (whose stacked
+// weights would not fit in shared memory next to the input stages).
+static int conv_rpt(int taps3d, int H) { return (!taps3d && H >= 2) ? 2 : 1; }
 
-int conv_packed_bytes(int n_out, int ntaps, int cp_in) {
-    const int npad = pad_npad(n_out);
-    const int k = ntaps * cp_in, kpad = (k + 15) & ~15;
-    return npad * kpad * 2;
+// K groups (8 channels each) of the B operand: per input plane, (row, column tap,
+// channel group) or, with one channel group, (row pair, column tap, half).
+static int conv_kgroups(int taps3d, int cpin, int rpt) {
+    const int nr = rpt + 2, cg = cpin / 8;
+    return (taps3d ? 3 : 1) * 3 * (cg == 1 ? 2 * ((nr + 1) / 2) : nr * ((cg + 1) & ~1));
+}
+static long long conv_packed_bytes(int n_out, int taps3d, int cpin, int rpt) {
+    return (long long)conv_kgroups(taps3d, cpin, rpt) * rpt * pad_npad(n_out) * 16;
 }
 
-int conv_pack(const float *w, int cout, int ntaps, int cin, int cp_in, int flip, uint8_t *out, cudaStream_t st) {
+static int conv_pack(const float *w, int cout, int taps3d, int cin, int cpin, int flip, int rpt, uint8_t *out,
+                     cudaStream_t st) {
     const int n_out = flip ? cin : cout;
-    const int npad = pad_npad(n_out);
-    const int k = ntaps * cp_in, kpad = (k + 15) & ~15;
-    const long long total = (long long)npad * kpad;
-    k_pack_weights<<<(int)std::min<long long>(4096, (total + 255) / 256), 256, 0, st>>>(w, cout, ntaps, cin, cp_in,
-                                                                                       npad, kpad / 8, flip, out);
+    const long long total = conv_packed_bytes(n_out, taps3d, cpin, rpt) / 2;
+    k_pack_weights<<<(int)std::min<long long>(4096, (total + 255) / 256), 256, 0, st>>>(
+        w, cout, taps3d, cin, ((cpin / 8) + 1) & ~1, pad_npad(n_out), rpt, cpin == 8, flip, out);
     CBCT_LAUNCH_CHECK("conv weight pack");
     return 0;
 }
 
-template <int NPAD, int EPI>
+template <int NPAD, int EPI, int CG, int RPT>
 static int launch_conv(const ConvArgs &a, cudaStream_t st) {
-    const int bbytes = a.kgroups * NPAD * 16;
-    const size_t smem = 1024 + kStages * kAStageBytes + ((bbytes + 127) & ~127) + 8 * (2 * kStages + 4) + 64;
-    if (smem > 220 * 1024) return fail(CBCT_EINVAL, "conv: weights do not fit in shared memory");
-    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<NPAD, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr int kN = RPT * NPAD;
+    const int bbytes = a.kgroups * kN * 16;
+    const size_t fixed = 1024 + ((bbytes + 127) & ~127) + 8 * (2 * kMaxStages + 2 * kAcc) + 4 * NPAD + 64;
+    const size_t limit = 220 * 1024, stage = conv_stage_bytes(CG, RPT);
+    if (fixed + 2 * stage > limit) return fail(CBCT_EINVAL, "conv: input rows and weights do not fit in shared memory");
+    const int nst = (int)std::min<size_t>(6, (limit - fixed) / stage);
+    const size_t smem = fixed + (size_t)nst * stage;
+    cudaError_t e =
+        cudaFuncSetAttribute(k_conv_tc<NPAD, EPI, CG, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "conv smem attribute");
-    // x as a 5-D tensor (channels, W, H, D, images); one box = 8 channels x 128 pixels
+    // x as a 5-D tensor (G pixels x 8 channels, W / G, channel groups, H, D * images);
+    // one box = R rows of G pixels, all channel groups, RPT + 2 image rows
     CUtensorMap xmap;
-    const uint64_t cp = (uint64_t)a.cpin;
-    const uint64_t dims[5] = {cp, (uint64_t)a.W, (uint64_t)a.H, (uint64_t)a.D, (uint64_t)a.nimg};
-    const uint64_t strides[4] = {cp * 2, cp * 2 * a.W, cp * 2 * a.W * a.H, cp * 2 * a.W * a.H * a.D};
-    const uint32_t box[5] = {8, 128, 1, 1, 1};
+    const uint64_t G = (uint64_t)a.G, W = (uint64_t)a.W, cg = (uint64_t)a.cin_groups;
+    const uint64_t dims[5] = {8 * G, W / G, cg, (uint64_t)a.H, (uint64_t)a.D * a.nimg};
+    const uint64_t strides[4] = {16 * G, 16 * W, 16 * W * cg, 16 * W * cg * a.H};
+    const uint32_t box[5] = {(uint32_t)(8 * G), (uint32_t)conv_box_rows(a.G), (uint32_t)cg, (uint32_t)(RPT + 2), 1};
     int rc = encode_tmap(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, a.x, dims, strides, box);
     if (rc) return rc;
-    int dev = 0, nsm = 152, smem_sm = 228 * 1024;
+    int dev = 0, nsm = 152, occ = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    const int per_sm = std::max(1, std::min(8, smem_sm / (int)(smem + 1024)));
-    const long long ntiles = (long long)a.nimg * a.D * a.H * ((a.W + 127) / 128);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv_tc<NPAD, EPI, CG, RPT>, kWsThreads, smem);
+    // TMEM: kAcc x kN columns per CTA, 512 per SM
+    const int per_sm = std::max(1, std::min({4, occ, 512 / (kAcc * kN)}));
+    const long long ntiles = (long long)a.nimg * a.D * ((a.H + RPT - 1) / RPT) * ((a.W + 127) / 128);
     const int grid = (int)std::min<long long>(ntiles, (long long)nsm * per_sm);
-    k_conv_tc<NPAD, EPI><<<grid, kWsThreads, smem, st>>>(xmap, a);
+    k_conv_tc<NPAD, EPI, CG, RPT><<<grid, kWsThreads, smem, st>>>(xmap, a, nst);
     CBCT_LAUNCH_CHECK("conv launch");
     return 0;
 }
 
-// Runs one convolution with packed weights (see conv_pack). n_out = number of GEMM
-// output channels (cout, or cin for the input-gradient convolution).
-int conv_run(const ConvArgs &a0, int n_out, int epi, cudaStream_t st) {
+template <int NPAD, int EPI, int RPT>
+static int launch_conv_cg(const ConvArgs &a, cudaStream_t st) {
+    switch (a.cin_groups) {
+        case 1: return launch_conv<NPAD, EPI, 1, RPT>(a, st);
+        case 2: return launch_conv<NPAD, EPI, 2, RPT>(a, st);
+        case 4: return launch_conv<NPAD, EPI, 4, RPT>(a, st);
+        default: return fail(CBCT_EINVAL, "conv: channel stride must be 8, 16 or 32");
+    }
+}
+
+template <int NPAD, int EPI>
+static int launch_conv_rpt(const ConvArgs &a, int rpt, cudaStream_t st) {
+    return rpt == 2 ? launch_conv_cg<NPAD, EPI, 2>(a, st) : launch_conv_cg<NPAD, EPI, 1>(a, st);
+}
+
+// Runs one convolution with weights packed by conv_pack for the same rpt. n_out =
+// number of GEMM output channels (cout, or cin for the input-gradient convolution).
+static int conv_run(const ConvArgs &a0, int n_out, int epi, int rpt, cudaStream_t st) {
     ConvArgs a = a0;
     const int npad = pad_npad(n_out);
     if (a.cpin % 8 || (epi != EPI_RESIDUAL_F32 && a.cpout % 8)) return fail(CBCT_EINVAL, "conv: channel strides must be multiples of 8");
     a.cin_groups = a.cpin / 8;
-    const int k = (a.taps3d ? 27 : 9) * a.cpin;
-    a.kgroups = ((k + 15) & ~15) / 8;
+    a.kgroups = conv_kgroups(a.taps3d, a.cpin, rpt);
+    a.G = a.W % 4 == 0 ? 4 : (a.W % 2 == 0 ? 2 : 1);
     if (npad == 16) {
-        if (epi == EPI_ACT_BF16) return launch_conv<16, EPI_ACT_BF16>(a, st);
-        if (epi == EPI_RESIDUAL_F32) return launch_conv<16, EPI_RESIDUAL_F32>(a, st);
-        return launch_conv<16, EPI_MASK_BF16>(a, st);
+        if (epi == EPI_ACT_BF16) return launch_conv_rpt<16, EPI_ACT_BF16>(a, rpt, st);
+        if (epi == EPI_RESIDUAL_F32) return launch_conv_rpt<16, EPI_RESIDUAL_F32>(a, rpt, st);
+        return launch_conv_rpt<16, EPI_MASK_BF16>(a, rpt, st);
     }
-    if (epi == EPI_ACT_BF16) return launch_conv<32, EPI_ACT_BF16>(a, st);
-    if (epi == EPI_RESIDUAL_F32) return launch_conv<32, EPI_RESIDUAL_F32>(a, st);
-    return launch_conv<32, EPI_MASK_BF16>(a, st);
+    if (epi == EPI_ACT_BF16) return launch_conv_rpt<32, EPI_ACT_BF16>(a, rpt, st);
+    if (epi == EPI_RESIDUAL_F32) return launch_conv_rpt<32, EPI_RESIDUAL_F32>(a, rpt, st);
+    return launch_conv_rpt<32, EPI_MASK_BF16>(a, rpt, st);
 }
 
 // dW (+)= sum_p dY[p] x X[p + tap], db (+)= sum_p dY[p]; partial sums in scratch.
@@ -475,8 +652,8 @@ using namespace cbct;
 extern "C" int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d, const float *w,
                          const float *bias, int cin, int cout, int flip, int epi, float slope, void *y, int cpout,
                          const void *mask, float *state, long long sstride, int *status, void *stream) {
-    if (!x || !w || nimg < 1 || D < 1 || H < 1 || W < 1 || cin < 1 || cout < 1 || cpin % 8 ||
-        cpin < (flip ? cout : cin))
+    if (!x || !w || nimg < 1 || D < 1 || H < 1 || W < 1 || cin < 1 || cout < 1 ||
+        (cpin != 8 && cpin != 16 && cpin != 32) || cpin < (flip ? cout : cin))
         return fail(CBCT_EINVAL, "cbct_conv: invalid argument (sizes, or cpin below the input channels)");
     const int n_out = flip ? cin : cout;
     if (n_out > 32) return fail(CBCT_EINVAL, "cbct_conv: at most 32 output channels");
@@ -485,11 +662,11 @@ extern "C" int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin,
         (epi == EPI_MASK_BF16 && !mask) || !status)
         return fail(CBCT_EINVAL, "cbct_conv: missing output");
     cudaStream_t st = (cudaStream_t)stream;
-    const int ntaps = taps3d ? 27 : 9;
-    const int bytes = conv_packed_bytes(n_out, ntaps, cpin);
+    const int rpt = conv_rpt(taps3d, H);
+    const long long bytes = conv_packed_bytes(n_out, taps3d, cpin, rpt);
     uint8_t *pk = nullptr;
     CBCT_CUDA_TRY(cudaMallocAsync((void **)&pk, bytes, st));
-    int rc = conv_pack(w, cout, ntaps, cin, cpin, flip, pk, st);
+    int rc = conv_pack(w, cout, taps3d, cin, cpin, flip, rpt, pk, st);
     if (rc == 0) {
         ConvArgs a{};
         a.x = static_cast<const __nv_bfloat16 *>(x);
@@ -506,7 +683,7 @@ extern "C" int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin,
         a.state = state;
         a.sstride = sstride;
         a.status = status;
-        rc = conv_run(a, n_out, epi, st);
+        rc = conv_run(a, n_out, epi, rpt, st);
     }
     cudaFreeAsync(pk, st);
     return rc;

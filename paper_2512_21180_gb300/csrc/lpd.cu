@@ -28,8 +28,6 @@ namespace cbct {
 
 // from conv.cu
 struct ConvArgs;
-int conv_packed_bytes(int n_out, int ntaps, int cp_in);
-int conv_pack(const float *w, int cout, int ntaps, int cin, int cp_in, int flip, uint8_t *out, cudaStream_t st);
 int conv_wgrad(const __nv_bfloat16 *x, int cpin, int cin, const __nv_bfloat16 *dy, int cpout, int cout, int nimg,
                int D, int H, int W, int taps3d, float *dw, float *db, int accumulate, cudaStream_t st);
 

@@ -18,14 +18,20 @@ def L():
 
 
 def to_cl(x, cp):
-    """[N, C, *S] float64 -> BF16 channels-last [N, *S, cp] on the GPU (zero padded)."""
+    """[N, C, *S] float64 -> BF16 row-blocked [N, *S[:-1], cp / 8, W, 8] on the GPU
+    (channel slots >= C zero)."""
     n, c = x.shape[:2]
     y = torch.zeros((n,) + tuple(x.shape[2:]) + (cp,), dtype=torch.float64)
     y[..., :c] = x.movedim(1, -1)
+    W = x.shape[-1]
+    y = y.reshape(y.shape[:-2] + (W, cp // 8, 8)).transpose(-3, -2)
     return y.to(torch.bfloat16).cuda().contiguous()
 
 
 def from_cl(y, c):
+    """Inverse of to_cl: row-blocked [N, *S[:-1], cp / 8, W, 8] -> [N, c, *S] float64."""
+    y = y.transpose(-3, -2)
+    y = y.reshape(y.shape[:-2] + (-1,))
     return y[..., :c].double().movedim(-1, 1).cpu()
 
 
@@ -33,11 +39,12 @@ def run_conv(L, x_cl, dims, taps3d, w, b, cin, cout, flip, epi, cpout, mask=None
     nimg = x_cl.shape[0]
     D, H, W = dims if taps3d else (1,) + dims
     n_out = cin if flip else cout
-    y = torch.zeros((nimg,) + tuple(x_cl.shape[1:-1]) + (cpout,), dtype=torch.bfloat16, device="cuda")
+    W = x_cl.shape[-2]
+    y = torch.zeros((nimg,) + tuple(x_cl.shape[1:-3]) + (cpout // 8, W, 8), dtype=torch.bfloat16, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     sp = state.data_ptr() if state is not None else None
     ss = state[0].numel() if state is not None else 0
-    rc = L.load().cbct_conv(x_cl.data_ptr(), nimg, D, H, W, x_cl.shape[-1], taps3d, w.data_ptr(),
+    rc = L.load().cbct_conv(x_cl.data_ptr(), nimg, D, H, W, x_cl.shape[-3] * 8, taps3d, w.data_ptr(),
                             b.data_ptr() if b is not None else None, cin, cout, flip, epi, SLOPE,
                             y.data_ptr(), cpout, mask.data_ptr() if mask is not None else None, sp, ss,
                             status.data_ptr(), torch.cuda.current_stream().cuda_stream)

@@ -65,8 +65,9 @@ __device__ __forceinline__ void tap_offset(int tap, int taps3d, int &dd, int &dh
 }
 
 // Epilogue of one output pixel: TMEM accumulators -> bias / activation / residual.
-// `row` = (img * D + d) * H + h, `w` the column; `bias` points to shared memory
-// (zeros when the layer has none; every lane reads the same word, a broadcast). Every global load is issued before the first
+// `row` = (img * D + d) * H + h, `w` the column; `bias` is held in registers (zeros
+// when the layer has none). The mask is read through the read-only path so that no
+// load waits behind the stores of earlier rows. Every global load is issued before the first
 // store so that one memory latency covers the row.
 template <int NPAD, int EPI>
 __device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *acc, const float *bias, long long row,
@@ -93,7 +94,7 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *ac
         for (int q = 0; q < kG; ++q) {
             mv[q] = make_uint4(0u, 0u, 0u, 0u);
             if constexpr (EPI == EPI_MASK_BF16)
-                if (q * 8 < a.cpout) mv[q] = *reinterpret_cast<const uint4 *>(a.mask + o0 + q * gstride);
+                if (q * 8 < a.cpout) mv[q] = __ldg(reinterpret_cast<const uint4 *>(a.mask + o0 + q * gstride));
         }
 #pragma unroll
         for (int q = 0; q < kG; ++q) {
@@ -121,7 +122,8 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *ac
 }
 
 // Row-halo layout. A tile is 128 consecutive output pixels along W of RPT output
-// rows h0 .. h0 + RPT - 1 (RPT = 2 for the 2-D blocks, 1 for 3-D); an A stage holds
+// rows h0 .. h0 + RPT - 1 (RPT = 4, 3, 2 or 1, the most whose weights fit in shared
+// memory next to the input stages); an A stage holds
 // the NR = RPT + 2 input rows h0 - 1 .. h0 + RPT of one input plane as NR * CGP
 // regions (CGP = CG rounded up to even) of RS = 16 G R bytes (2176, 2112 or 2080;
 // at most kRowStride). Region r * CG + g holds channel group g of input row h0 - 1 + r
@@ -142,7 +144,9 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *ac
 constexpr int kRowStride = 2176;         // 17 x 128 >= RS = 16 R G for G = 1, 2, 4
 __host__ __device__ constexpr int conv_box_rows(int G) { return (129 + G + G - 1) / G; }
 constexpr int kMaxStages = 8;            // A ring depth (chosen per launch, <= 8)
-constexpr int kAcc = 8;                  // TMEM accumulators (tiles in flight past the MMA)
+constexpr int kMaxAcc = 8;               // TMEM accumulators (tiles in flight past the MMA), at most
+__host__ __device__ constexpr int conv_nacc(int n) { return 512 / n < kMaxAcc ? 512 / n : kMaxAcc; }
+__host__ __device__ constexpr int conv_pow2(int n) { return n <= 32 ? 32 : 2 * conv_pow2((n + 1) / 2); }
 constexpr int kEpiGroups = 4;            // epilogue warpgroups; group q drains the tiles j = q mod 4
 constexpr int kWsThreads = 32 * (4 * kEpiGroups + 2);  // epilogue warps, then the TMA producer and the MMA warp
 constexpr int kProdWarp = 4 * kEpiGroups, kMmaWarp = 4 * kEpiGroups + 1;
@@ -190,7 +194,7 @@ __device__ __forceinline__ void tile_next(TileCoord &c, int D, int nh, int W) {
 //  producer (warp 16, one lane): waits until the stage is free (empty[s]) and loads
 //    the item's NR input rows with one TMA box, completion counted on full[s]; an
 //    input plane outside the volume only arrives (its MMAs are skipped).
-//  MMA (warp 17, one lane): per tile picks TMEM accumulator j % 8 once the epilogue
+//  MMA (warp 17, one lane): per tile picks TMEM accumulator j % nacc once the epilogue
 //    has drained it (acce), waits for each item (full[s]), issues one 128 x N x 16
 //    MMA per (input row, column tap, pair of channel groups) or, for CG = 1, per
 //    (pair of input rows, column tap), commits the stage to
@@ -214,13 +218,14 @@ __global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ 
     uint64_t *full = reinterpret_cast<uint64_t *>(sB + ((bbytes + 127) & ~127));
     uint64_t *empty = full + kMaxStages;
     uint64_t *accf = empty + kMaxStages;
-    uint64_t *acce = accf + kAcc;
-    float *sbias = reinterpret_cast<float *>(acce + kAcc);
+    uint64_t *acce = accf + kMaxAcc;
+    float *sbias = reinterpret_cast<float *>(acce + kMaxAcc);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sbias + NPAD);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr uint32_t kCols = kAcc * kN;  // 128, 256 or 512: a power of two >= 32
+    constexpr int kAcc = conv_nacc(kN);
+    constexpr uint32_t kCols = conv_pow2(kAcc * kN);  // TMEM allocation: a power of two >= 32
     constexpr uint32_t kIdesc = idesc_bf16_f32(128, kN);
     const int rs = 16 * a.G * conv_box_rows(a.G);  // region stride (bytes)
 
@@ -363,6 +368,9 @@ __global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ 
         // epilogue: warpgroup q = warp / 4 takes tiles q, q + 4, ...; warp w reads TMEM
         // lanes 32 (w % 4) .. + 31 = tile pixels
         const int q = warp >> 2, wq = warp & 3;
+        float bias[NPAD];
+#pragma unroll
+        for (int c = 0; c < NPAD; ++c) bias[c] = sbias[c];
         TileCoord tc = tile_coord(t_begin + q, a.D, nh, ntw);
         for (long long j = q; j < my_tiles; j += kEpiGroups) {
             const int ab = (int)(j % kAcc);
@@ -391,7 +399,7 @@ __global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ 
 #pragma unroll
                 for (int c = 0; c < NPAD; ++c) acc[c] = __uint_as_float(raw[c]);
                 if (w < a.W && h < a.H)
-                    conv_epilogue<NPAD, EPI>(a, acc, sbias, ((long long)tc.img * a.D + tc.d) * a.H + h, w);
+                    conv_epilogue<NPAD, EPI>(a, acc, bias, ((long long)tc.img * a.D + tc.d) * a.H + h, w);
             }
 #pragma unroll
             for (int k = 0; k < kEpiGroups; ++k) tile_next(tc, a.D, nh, a.W);
@@ -533,9 +541,6 @@ __global__ void k_reduce_rows(const float *__restrict__ partial, int nblk, int n
 // ---- host launchers -------------------------------------------------------------------------
 
 static int pad_npad(int cout) { return cout <= 16 ? 16 : 32; }
-// Output rows per tile: two for the 2-D (dual) blocks, one for 3-D (whose stacked
-// weights would not fit in shared memory next to the input stages).
-static int conv_rpt(int taps3d, int H) { return (!taps3d && H >= 2) ? 2 : 1; }
 
 // K groups (8 channels each) of the B operand: per input plane, (row, column tap,
 // channel group) or, with one channel group, (row pair, column tap, half).
@@ -545,6 +550,19 @@ static int conv_kgroups(int taps3d, int cpin, int rpt) {
 }
 static long long conv_packed_bytes(int n_out, int taps3d, int cpin, int rpt) {
     return (long long)conv_kgroups(taps3d, cpin, rpt) * rpt * pad_npad(n_out) * 16;
+}
+// Output rows per tile: the most of 4, 3, 2 with N = rows x NPAD <= 128 whose
+// stacked weights fit in shared memory next to two input stages; 1 otherwise. A
+// channel stride of 16 takes at most 2.
+static int conv_rpt(int taps3d, int H, int cpin, int n_out) {
+    const int npad = pad_npad(n_out);
+    for (int rpt = 4; rpt >= 2; --rpt) {
+        if (rpt > H || rpt * npad > 128 || (cpin == 16 && rpt > 2)) continue;
+        const long long fixed = 1024 + ((conv_packed_bytes(n_out, taps3d, cpin, rpt) + 127) & ~127LL) +
+                                8 * (2 * kMaxStages + 2 * kMaxAcc) + 4 * npad + 64;
+        if (fixed + 2LL * conv_stage_bytes(cpin / 8, rpt) <= 220 * 1024) return rpt;
+    }
+    return 1;
 }
 
 static int conv_pack(const float *w, int cout, int taps3d, int cin, int cpin, int flip, int rpt, uint8_t *out,
@@ -561,7 +579,7 @@ template <int NPAD, int EPI, int CG, int RPT>
 static int launch_conv(const ConvArgs &a, cudaStream_t st) {
     constexpr int kN = RPT * NPAD;
     const int bbytes = a.kgroups * kN * 16;
-    const size_t fixed = 1024 + ((bbytes + 127) & ~127) + 8 * (2 * kMaxStages + 2 * kAcc) + 4 * NPAD + 64;
+    const size_t fixed = 1024 + ((bbytes + 127) & ~127) + 8 * (2 * kMaxStages + 2 * kMaxAcc) + 4 * NPAD + 64;
     const size_t limit = 220 * 1024, stage = conv_stage_bytes(CG, RPT);
     if (fixed + 2 * stage > limit) return fail(CBCT_EINVAL, "conv: input rows and weights do not fit in shared memory");
     const int nst = (int)std::min<size_t>(6, (limit - fixed) / stage);
@@ -582,8 +600,8 @@ static int launch_conv(const ConvArgs &a, cudaStream_t st) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv_tc<NPAD, EPI, CG, RPT>, kWsThreads, smem);
-    // TMEM: kAcc x kN columns per CTA, 512 per SM
-    const int per_sm = std::max(1, std::min({4, occ, 512 / (kAcc * kN)}));
+    // TMEM: conv_nacc(kN) x kN columns per CTA, 512 per SM
+    const int per_sm = std::max(1, std::min({4, occ, 512 / conv_pow2(conv_nacc(kN) * kN)}));
     const long long ntiles = (long long)a.nimg * a.D * ((a.H + RPT - 1) / RPT) * ((a.W + 127) / 128);
     const int grid = (int)std::min<long long>(ntiles, (long long)nsm * per_sm);
     k_conv_tc<NPAD, EPI, CG, RPT><<<grid, kWsThreads, smem, st>>>(xmap, a, nst);
@@ -595,7 +613,9 @@ template <int NPAD, int EPI, int RPT>
 static int launch_conv_cg(const ConvArgs &a, cudaStream_t st) {
     switch (a.cin_groups) {
         case 1: return launch_conv<NPAD, EPI, 1, RPT>(a, st);
-        case 2: return launch_conv<NPAD, EPI, 2, RPT>(a, st);
+        case 2:
+            if constexpr (RPT <= 2) return launch_conv<NPAD, EPI, 2, RPT>(a, st);
+            return fail(CBCT_EINVAL, "conv: no tile shape for this channel stride");
         case 4: return launch_conv<NPAD, EPI, 4, RPT>(a, st);
         default: return fail(CBCT_EINVAL, "conv: channel stride must be 8, 16 or 32");
     }
@@ -603,7 +623,12 @@ static int launch_conv_cg(const ConvArgs &a, cudaStream_t st) {
 
 template <int NPAD, int EPI>
 static int launch_conv_rpt(const ConvArgs &a, int rpt, cudaStream_t st) {
-    return rpt == 2 ? launch_conv_cg<NPAD, EPI, 2>(a, st) : launch_conv_cg<NPAD, EPI, 1>(a, st);
+    switch (rpt) {
+        case 4: return launch_conv_cg<NPAD, EPI, 4>(a, st);
+        case 3: return launch_conv_cg<NPAD, EPI, 3>(a, st);
+        case 2: return launch_conv_cg<NPAD, EPI, 2>(a, st);
+        default: return launch_conv_cg<NPAD, EPI, 1>(a, st);
+    }
 }
 
 // Runs one convolution with weights packed by conv_pack for the same rpt. n_out =
@@ -662,7 +687,7 @@ extern "C" int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin,
         (epi == EPI_MASK_BF16 && !mask) || !status)
         return fail(CBCT_EINVAL, "cbct_conv: missing output");
     cudaStream_t st = (cudaStream_t)stream;
-    const int rpt = conv_rpt(taps3d, H);
+    const int rpt = conv_rpt(taps3d, H, cpin, n_out);
     const long long bytes = conv_packed_bytes(n_out, taps3d, cpin, rpt);
     uint8_t *pk = nullptr;
     CBCT_CUDA_TRY(cudaMallocAsync((void **)&pk, bytes, st));

@@ -47,7 +47,8 @@ struct ConvArgs {
     __nv_bfloat16 *y;        // EPI_ACT_BF16 / EPI_MASK_BF16 output [nimg][D][H][cpout / 8][W][8]
     int cpout;
     const __nv_bfloat16 *mask;  // EPI_MASK_BF16: forward activation (same layout as y); out *= (mask > 0 ? 1 : slope)
-    float *state;            // EPI_RESIDUAL_F32: state[c * sstride + pixel] += v
+    float *state;            // EPI_RESIDUAL_F32: state[c * sstride + pixel] = state_in[..] + v
+    const float *state_in;   // (may equal state)
     long long sstride;
     int *status;
 };
@@ -79,7 +80,7 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *ac
             if (c0 >= a.cout) break;
             float old[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) old[c] = c0 + c < a.cout ? a.state[(c0 + c) * a.sstride + p] : 0.f;
+            for (int c = 0; c < 8; ++c) old[c] = c0 + c < a.cout ? a.state_in[(c0 + c) * a.sstride + p] : 0.f;
 #pragma unroll
             for (int c = 0; c < 8; ++c)
                 if (c0 + c < a.cout) a.state[(c0 + c) * a.sstride + p] = old[c] + (acc[c0 + c] + bias[c0 + c]);
@@ -674,19 +675,18 @@ int conv_wgrad(const __nv_bfloat16 *x, int cpin, int cin, const __nv_bfloat16 *d
 
 using namespace cbct;
 
-extern "C" int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d, const float *w,
-                         const float *bias, int cin, int cout, int flip, int epi, float slope, void *y, int cpout,
-                         const void *mask, float *state, long long sstride, int *status, void *stream) {
+int cbct::conv_apply(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d, const float *w, const float *bias,
+                     int cin, int cout, int flip, int epi, float slope, void *y, int cpout, const void *mask,
+                     const float *state_in, float *state, long long sstride, int *status, cudaStream_t st) {
     if (!x || !w || nimg < 1 || D < 1 || H < 1 || W < 1 || cin < 1 || cout < 1 ||
         (cpin != 8 && cpin != 16 && cpin != 32) || cpin < (flip ? cout : cin))
-        return fail(CBCT_EINVAL, "cbct_conv: invalid argument (sizes, or cpin below the input channels)");
+        return fail(CBCT_EINVAL, "conv: invalid argument (sizes, or cpin below the input channels)");
     const int n_out = flip ? cin : cout;
-    if (n_out > 32) return fail(CBCT_EINVAL, "cbct_conv: at most 32 output channels");
-    if (epi < 0 || epi > 2) return fail(CBCT_EINVAL, "cbct_conv: bad epilogue");
+    if (n_out > 32) return fail(CBCT_EINVAL, "conv: at most 32 output channels");
+    if (epi < 0 || epi > 2) return fail(CBCT_EINVAL, "conv: bad epilogue");
     if ((epi == EPI_RESIDUAL_F32 && !state) || (epi != EPI_RESIDUAL_F32 && (!y || cpout < n_out)) ||
         (epi == EPI_MASK_BF16 && !mask) || !status)
-        return fail(CBCT_EINVAL, "cbct_conv: missing output");
-    cudaStream_t st = (cudaStream_t)stream;
+        return fail(CBCT_EINVAL, "conv: missing output");
     const int rpt = conv_rpt(taps3d, H, cpin, n_out);
     const long long bytes = conv_packed_bytes(n_out, taps3d, cpin, rpt);
     uint8_t *pk = nullptr;
@@ -706,12 +706,20 @@ extern "C" int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin,
         a.cpout = cpout;
         a.mask = static_cast<const __nv_bfloat16 *>(mask);
         a.state = state;
+        a.state_in = state_in ? state_in : state;
         a.sstride = sstride;
         a.status = status;
         rc = conv_run(a, n_out, epi, rpt, st);
     }
     cudaFreeAsync(pk, st);
     return rc;
+}
+
+extern "C" int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d, const float *w,
+                         const float *bias, int cin, int cout, int flip, int epi, float slope, void *y, int cpout,
+                         const void *mask, float *state, long long sstride, int *status, void *stream) {
+    return conv_apply(x, nimg, D, H, W, cpin, taps3d, w, bias, cin, cout, flip, epi, slope, y, cpout, mask, state,
+                      state, sstride, status, (cudaStream_t)stream);
 }
 
 extern "C" int cbct_conv_wgrad(const void *x, int cpin, int cin, const void *dy, int cpout, int cout, int nimg, int D,

@@ -27,6 +27,14 @@ namespace cbct {
 // ||P|| by power iteration on P^T P (FP32 operators, FP64 norms), used for the
 // normalised operators. Synchronises the current device.
 int operator_norm(cbct_geom *g, int iters, double *out);
+// P^T (colw[u] * proj): adjoint of a column-weighted projection (colw: [nu] device).
+int back_project_colw(const cbct_geom *g, const float *proj, const float *colw, float *vol, int batch, int accumulate,
+                      cudaStream_t st);
+// cbct_conv with the residual epilogue reading its old state from state_in (which may
+// equal state) and writing state = state_in + conv.
+int conv_apply(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d, const float *w, const float *bias,
+               int cin, int cout, int flip, int epi, float slope, void *y, int cpout, const void *mask,
+               const float *state_in, float *state, long long sstride, int *status, cudaStream_t st);
 // Staged (TMA) forward: returns 1 if it ran, 0 if the direct kernel must be used.
 int forward_staged(const cbct_geom *g, const float *vol, float *proj, int batch, int accumulate, cudaStream_t st);
 int choose_forward_cfg(double need_b, double need_z);

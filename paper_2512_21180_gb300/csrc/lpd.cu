@@ -206,10 +206,12 @@ int grid_n(long long n) {
 
 }  // namespace
 
+// forward conv of layer L; the residual epilogue (epi 1) writes state = state_in + conv
 static int conv_fwd(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *x, int cpin, int nimg, int D, int H, int W,
-                    int epi, __nv_bfloat16 *y, float *state, long long sstride, cudaStream_t st) {
-    return cbct_conv(x, nimg, D, H, W, cpin, L.taps3d, m->params + L.w_off, m->params + L.b_off, L.cin, L.cout, 0, epi,
-                     m->d.slope, y, 32, nullptr, state, sstride, m->status, st);
+                    int epi, __nv_bfloat16 *y, float *state, long long sstride, cudaStream_t st,
+                    const float *state_in = nullptr) {
+    return conv_apply(x, nimg, D, H, W, cpin, L.taps3d, m->params + L.w_off, m->params + L.b_off, L.cin, L.cout, 0, epi,
+                      m->d.slope, y, 32, nullptr, state_in, state, sstride, m->status, st);
 }
 
 // input-gradient conv of layer L: dy (BF16 [..][cp_dy], L.cout channels) -> L.cin outputs
@@ -240,22 +242,19 @@ static int lpd_iter_fwd(cbct_lpd *m, int n, const float *f_in, const float *h_in
     pl.p[M] = m->tproj; pl.s[M] = m->d.mu_ref;
     pl.p[M + 1] = m->y; pl.s[M + 1] = 1.f;
     k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
-    if (h_out != h_in) cudaMemcpyAsync(h_out, h_in, sizeof(float) * M * NP, cudaMemcpyDeviceToDevice, st);
     if ((rc = conv_fwd(m, Ld[0], m->din, 8, DUAL_DIMS, 0, m->a1, nullptr, 0, st))) return rc;
     if ((rc = conv_fwd(m, Ld[1], m->a1, 32, DUAL_DIMS, 0, m->a2, nullptr, 0, st))) return rc;
-    if ((rc = conv_fwd(m, Ld[2], m->a2, 32, DUAL_DIMS, 1, nullptr, h_out, NP, st))) return rc;
+    if ((rc = conv_fwd(m, Ld[2], m->a2, 32, DUAL_DIMS, 1, nullptr, h_out, NP, st, h_in))) return rc;
     // primal block input [f (M), bp_scale P^T (w h_1)]
-    k_scale_cols<<<grid_n(NP), 256, 0, st>>>(h_out + 1 * NP, m->wred, NP, m->g->dev.nu, 1.f, m->tproj);
-    rc = back_project(m->g, m->tproj, m->tvol, 1, 0, sv);
+    rc = back_project_colw(m->g, h_out + 1 * NP, m->wred, m->tvol, 1, 0, st);
     if (rc) return rc;
     Planes pp{};
     for (int c = 0; c < M; ++c) { pp.p[c] = f_in + c * NV; pp.s[c] = 1.f; }
     pp.p[M] = m->tvol; pp.s[M] = m->bp_scale;
     k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
-    if (f_out != f_in) cudaMemcpyAsync(f_out, f_in, sizeof(float) * M * NV, cudaMemcpyDeviceToDevice, st);
     if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) return rc;
     if ((rc = conv_fwd(m, Lp[1], m->b1, 32, PRIM_DIMS, 0, m->b2, nullptr, 0, st))) return rc;
-    if ((rc = conv_fwd(m, Lp[2], m->b2, 32, PRIM_DIMS, 1, nullptr, f_out, NV, st))) return rc;
+    if ((rc = conv_fwd(m, Lp[2], m->b2, 32, PRIM_DIMS, 1, nullptr, f_out, NV, st, f_in))) return rc;
     CBCT_LAUNCH_CHECK("lpd iteration");
     return 0;
 }
@@ -340,8 +339,7 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
             m->bp_scale = d.bp_scale;
         } else {
             k_fill_f<<<grid_n(NP), 256>>>(m->tproj2, NP, 1.f);
-            k_scale_cols<<<grid_n(NP), 256>>>(m->tproj2, m->wred, NP, g->dev.nu, 1.f, m->tproj);
-            rc = back_project(g, m->tproj, m->tvol, 1, 0, nullptr);
+            rc = back_project_colw(g, m->tproj2, m->wred, m->tvol, 1, 0, nullptr);
             float mx = 0.f;
             if (rc == 0) {
                 cudaMemset(m->tproj2, 0, sizeof(float));
@@ -436,8 +434,7 @@ extern "C" int lpd_backward(cbct_lpd *m, const float *grad_x, float *grad_y, flo
         if ((rc = conv_fwd(m, Ld[0], m->din, 8, DUAL_DIMS, 0, m->a1, nullptr, 0, st))) break;
         if ((rc = conv_fwd(m, Ld[1], m->a1, 32, DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
         // recompute the primal block input and activations (needs h_{n+1}, saved)
-        k_scale_cols<<<grid_n(NP), 256, 0, st>>>(h_n1 + NP, m->wred, NP, m->g->dev.nu, 1.f, m->tproj2);
-        if ((rc = back_project(m->g, m->tproj2, m->tvol, 1, 0, sv))) break;
+        if ((rc = back_project_colw(m->g, h_n1 + NP, m->wred, m->tvol, 1, 0, st))) break;
         Planes pp{};
         for (int c = 0; c < M; ++c) { pp.p[c] = f_n + c * NV; pp.s[c] = 1.f; }
         pp.p[M] = m->tvol; pp.s[M] = m->bp_scale;

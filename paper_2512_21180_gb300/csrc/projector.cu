@@ -91,9 +91,9 @@ __global__ void __launch_bounds__(256) k_forward(GeomDev g, const T *__restrict_
 
 // ---- backprojection -------------------------------------------------------------
 
-// pw = proj * step(ray) * scale
+// pw = proj * step(ray) * scale (* colw[column] when colw is given)
 template <typename T>
-__global__ void k_weight_rays(GeomDev g, const T *__restrict__ proj, T *__restrict__ pw) {
+__global__ void k_weight_rays(GeomDev g, const T *__restrict__ proj, T *__restrict__ pw, const T *__restrict__ colw) {
     const int iu = blockIdx.x * 32 + threadIdx.x;
     const int iv = blockIdx.y * 8 + threadIdx.y;
     const int k = blockIdx.z % g.na, b = blockIdx.z / g.na;
@@ -105,7 +105,8 @@ __global__ void k_weight_rays(GeomDev g, const T *__restrict__ proj, T *__restri
     T scale;
     if constexpr (sizeof(T) == 4) scale = g.scale; else scale = g.scaled;
     const long long o = (((long long)b * g.na + k) * g.nv + iv) * g.nu + iu;
-    pw[o] = proj[o] * ray_step<T>(g, a, c.dqb, dqz) * scale;
+    const T v = proj[o] * ray_step<T>(g, a, c.dqb, dqz) * scale;
+    pw[o] = colw ? v * colw[iu] : v;
 }
 
 // Detector column (continuous) hit by the ray from the source through the xy
@@ -442,7 +443,8 @@ static int forward_impl(const cbct_geom *g, const T *vol, T *proj, int batch, in
 constexpr int kZS = 4;
 
 template <typename T>
-static int backward_impl(const cbct_geom *g, const T *proj, T *vol, int batch, int accumulate, cudaStream_t st) {
+static int backward_impl(const cbct_geom *g, const T *proj, T *vol, int batch, int accumulate, cudaStream_t st,
+                         const T *colw = nullptr) {
     int rc = check_common(g, proj, vol, batch, accumulate);
     if (rc) return rc;
     const GeomDev &d = g->dev;
@@ -452,7 +454,7 @@ static int backward_impl(const cbct_geom *g, const T *proj, T *vol, int batch, i
     T *pw = nullptr;
     CBCT_CUDA_TRY(cudaMallocAsync((void **)&pw, sizeof(T) * nproj, st));
     dim3 blk(32, 8), gw((d.nu + 31) / 32, (d.nv + 7) / 8, d.na * batch);
-    k_weight_rays<T><<<gw, blk, 0, st>>>(d, proj, pw);
+    k_weight_rays<T><<<gw, blk, 0, st>>>(d, proj, pw, colw);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
         if constexpr (sizeof(T) == 4) {
@@ -490,6 +492,14 @@ static int backward_impl(const cbct_geom *g, const T *proj, T *vol, int batch, i
     cudaFreeAsync(pw, st);
     if (e != cudaSuccess) return cuda_fail(e, "back_project launch");
     return 0;
+}
+
+// P^T (colw x proj): the adjoint of a projection scaled per detector column (the
+// redundancy weight of the learned primal block), the scaling folded into the
+// per-ray weighting pass.
+int back_project_colw(const cbct_geom *g, const float *proj, const float *colw, float *vol, int batch, int accumulate,
+                      cudaStream_t st) {
+    return backward_impl<float>(g, proj, vol, batch, accumulate, st, colw);
 }
 
 int operator_norm(cbct_geom *g, int iters, double *out) {
@@ -637,7 +647,7 @@ extern "C" int back_project_noalloc(const cbct_geom *g, const float *proj, float
             v.col64 = d.col64 + (long long)k0 * d.nu;
             const float *pb = proj + ((long long)b * d.na + k0) * per_angle;
             dim3 gw((d.nu + 31) / 32, (d.nv + 7) / 8, kc);
-            k_weight_rays<float><<<gw, blk, 0, st>>>(v, pb, scratch);
+            k_weight_rays<float><<<gw, blk, 0, st>>>(v, pb, scratch, nullptr);
             dim3 gb((d.n[0] + 31) / 32, (d.n[1] + 7) / 8, nzs);
             k_backproject<float, kZS><<<gb, blk, 0, st>>>(v, scratch, vol + b * nvox, k0 == 0 ? accumulate : 1);
             CBCT_LAUNCH_CHECK("back_project_noalloc launch");

@@ -365,7 +365,9 @@ def report(args, geom, world, S_fwd, samples_step, value, ms, ms_fwd, ms_adj, e2
                    "gsamples_s_adjoint": S_fwd / (ms_adj * 1e-3) / 1e9},
         "roofline": roof,
         "e2e": {"value": e2e, "unit": "Gsamples/s", "h2d_bytes_per_step": nvox * 4, "d2h_bytes_per_step": nvox * 4},
-        "gpu_launches": 3 * args.steps,
+        # per step: forward = two plane transposes + the TMA ray kernel; adjoint = ray
+        # weighting + segment gather (+ the fixed-order sum of angle parts when split)
+        "gpu_launches": launches_per_step(geom) * args.steps,
         "clocks": clk,
     }
     if not args.no_cpu_baseline and world == 1 and args.workload == WORKLOAD:
@@ -379,6 +381,15 @@ def report(args, geom, world, S_fwd, samples_step, value, ms, ms_fwd, ms_adj, e2
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def launches_per_step(geom) -> int:
+    """Kernels one forward + adjoint step launches (mirrors the launchers: 3 for the
+    staged forward, 2 for the segment gather, +1 when its angles are split)."""
+    nx, ny, nz = geom.g["n"]
+    bricks = -(-nx // 16) * -(-ny // 16) * -(-nz // 16)
+    parts = min(16, max(1, -(-152 * 6 // bricks)), geom.g["n_angles"])
+    return 3 + 2 + (1 if parts > 1 else 0)
 
 
 def roofline(kernel, ms, S_fwd, nvox, nray, pk, pk_kind, clk):

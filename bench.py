@@ -353,6 +353,7 @@ def report(args, geom, world, S_fwd, samples_step, value, ms, ms_fwd, ms_adj, e2
     dom = "back_project" if ms_adj >= ms_fwd else "forward_project"
     ms_dom = max(ms_adj, ms_fwd)
     roof = roofline(dom, ms_dom, S_fwd, nvox, nray, pk, pk_kind, clk)
+    roof["traffic"] = MEASURED_TRAFFIC.get(args.workload, {}).get(dom)
     line = {
         "metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -381,6 +382,12 @@ def report(args, geom, world, S_fwd, samples_step, value, ms, ms_fwd, ms_adj, e2
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from one ncu
+# --set full capture of the clinical workload with the current kernels; None elsewhere
+# and whenever the kernel changes after the capture.
+MEASURED_TRAFFIC = {"clinical": {"back_project": 686.565e6 + 38.120e6, "forward_project": 137.302e6 + 281.002e6}}
 
 
 def launches_per_step(geom) -> int:

@@ -265,6 +265,22 @@ int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d
 int cbct_conv_wgrad(const void *x, int cpin, int cin, const void *dy, int cpout, int cout, int nimg, int D, int H,
                     int W, int taps3d, float *dw, float *db, int accumulate, void *stream);
 
+/* ---- resampling between multiscale levels (a11; Sec. 2.4, multiscale scheme) ---- */
+
+/* nch independent 3-D FP32 arrays [n0][n1][n2] (last index fastest), device.
+ * cbct_resample_down: out[c][i][j][k] = scale * sum of in over the box
+ * (i f0 + a, j f1 + b, k f2 + d), b < f1, d < f2, a < f0 — or a = 0 only when pick0
+ * (axis 0 subsampled). Average pooling of a volume: f = (2, 2, 2), scale 1/8; the
+ * coarse level's projections (every second angle, 2 x 2 binned pixels): f = (2, 2, 2),
+ * pick0, scale 1/4; adjoint of nearest upsampling: scale 1. out has
+ * (n0 / f0) x (n1 / f1) x (n2 / f2) per array; each n must be divisible by its f.
+ * cbct_resample_up: out[c][i][j][k] = in[c][i / f0][j / f1][k / f2] (nearest), out of
+ * size n0 f0 x n1 f1 x n2 f2. Errors: CBCT_EINVAL for NULL pointers or bad sizes. */
+int cbct_resample_down(const float *in, long long nch, int n0, int n1, int n2, int f0, int f1, int f2, int pick0,
+                       float scale, float *out, void *stream);
+int cbct_resample_up(const float *in, long long nch, int n0, int n1, int n2, int f0, int f1, int f2, float *out,
+                     void *stream);
+
 /* ---- learned primal-dual reconstruction (a7-a9, a12; Sec. 2.4, Algorithm 1) ---- */
 
 typedef struct cbct_lpd cbct_lpd; /* opaque: weights (FP32 master), gradients, Adam moments, workspaces */
@@ -303,6 +319,22 @@ int lpd_forward(cbct_lpd *m, const float *y, const float *x0, float *x_out, int 
  * saved iterate, ADDS the parameter gradients to the model's gradient buffer, writes
  * dL/dy and dL/dx0 when those pointers are not NULL. */
 int lpd_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float *grad_x0, void *stream);
+
+/* Latent-state variants for the multiscale scheme (a11; Sec. 2.4: a coarser level's
+ * result initialises the next level). The primal state f is [n_mem][nvox] FP32 in units
+ * of mu_ref, the dual state h is [n_mem][nproj] FP32 (y's units), both device.
+ * lpd_forward_latent: f_0 = f0 (NULL: x0 / mu_ref in every channel, then x0 is
+ * required), h_0 = h0 (NULL: zero); x_out (nullable) = mu_ref f_N[0].
+ * lpd_get_state: copies the final f_N / h_N of the last forward pass (either nullable).
+ * lpd_backward_latent: upstream dL/dx_out (grad_x) and/or dL/df_N, dL/dh_N (each
+ * nullable, at least one given; needs save_for_backward); accumulates parameter
+ * gradients; writes dL/dy, dL/dx0, dL/df_0, dL/dh_0 where non-NULL. Errors: CBCT_EINVAL
+ * for missing inputs or no saved forward pass. */
+int lpd_forward_latent(cbct_lpd *m, const float *y, const float *x0, const float *f0, const float *h0, float *x_out,
+                       int save_for_backward, void *stream);
+int lpd_get_state(const cbct_lpd *m, float *f_out, float *h_out, void *stream);
+int lpd_backward_latent(cbct_lpd *m, const float *grad_x, const float *grad_fN, const float *grad_hN, float *grad_y,
+                        float *grad_x0, float *grad_f0, float *grad_h0, void *stream);
 
 int lpd_zero_grad(cbct_lpd *m, void *stream);
 

@@ -81,18 +81,19 @@ def backproject(G, y):
     return _Back.apply(G, y)
 
 
-def lpd(G, y: torch.Tensor, x0: torch.Tensor, w_red: torch.Tensor, dual_params, primal_params,
-        n_mem: int = 5, round_bf16: bool = True, mu_ref: float = 1.0, bp_scale: float = 1.0):
+def lpd(G, y: torch.Tensor, x0: torch.Tensor | None, w_red: torch.Tensor, dual_params, primal_params,
+        n_mem: int = 5, round_bf16: bool = True, mu_ref: float = 1.0, bp_scale: float = 1.0,
+        f0: torch.Tensor | None = None, h0: torch.Tensor | None = None, return_state: bool = False):
     """Learned primal-dual (Adler-style memory of n_mem channels, the reading of the
     paper's primal/dual latents for this workload), in units of mu_ref:
-        f <- x0 / mu_ref repeated, h <- 0
+        f <- x0 / mu_ref repeated (or the given f0), h <- 0 (or the given h0)
         h <- h + Gamma_n([h, mu_ref P f_1, y])                  (per projection image, 2D)
         f <- f + Lambda_n([f, bp_scale P^T (w h_1)])            (3D)
-        output mu_ref f_0.
+        output mu_ref f_0 (and the final f, h with return_state).
     y: [na, nv, nu]; x0: [nz, ny, nx]; w_red: [nu] redundancy weight."""
     na, nv, nu = y.shape
-    f = (x0 / mu_ref).unsqueeze(0).repeat(n_mem, 1, 1, 1)
-    h = torch.zeros((n_mem, na, nv, nu), dtype=torch.float64)
+    f = (x0 / mu_ref).unsqueeze(0).repeat(n_mem, 1, 1, 1) if f0 is None else f0
+    h = torch.zeros((n_mem, na, nv, nu), dtype=torch.float64) if h0 is None else h0
     for dp, pp in zip(dual_params, primal_params):
         pf = mu_ref * project(G, f[1])
         inp = torch.cat([h, pf.unsqueeze(0), y.unsqueeze(0)], 0)         # [n_mem + 2, na, nv, nu]
@@ -100,4 +101,6 @@ def lpd(G, y: torch.Tensor, x0: torch.Tensor, w_red: torch.Tensor, dual_params, 
         bp = bp_scale * backproject(G, w_red.view(1, 1, -1) * h[1])
         inp = torch.cat([f, bp.unsqueeze(0)], 0).unsqueeze(0)             # [1, n_mem + 1, nz, ny, nx]
         f = f + block(inp, pp, round_bf16)[0]
+    if return_state:
+        return mu_ref * f[0], f, h
     return mu_ref * f[0]

@@ -70,6 +70,11 @@ SIGNATURES = {
     "lpd_info": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(F32)]),
     "lpd_forward": (I32, [P, P, P, P, I32, I32, P]),
     "lpd_backward": (I32, [P, P, P, P, P]),
+    "lpd_forward_latent": (I32, [P, P, P, P, P, P, I32, P]),
+    "lpd_get_state": (I32, [P, P, P, P]),
+    "lpd_backward_latent": (I32, [P, P, P, P, P, P, P, P, P]),
+    "cbct_resample_down": (I32, [P, I64, I32, I32, I32, I32, I32, I32, I32, F32, P, P]),
+    "cbct_resample_up": (I32, [P, I64, I32, I32, I32, I32, I32, I32, P, P]),
     "lpd_zero_grad": (I32, [P, P]),
     "lpd_adam_step": (I32, [P, F32, F32, F32, F32, I32, F32, P]),
     "lpd_set_params": (I32, [P, P, I64]),

@@ -52,6 +52,7 @@ struct cbct_lpd {
     float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
     float *wred = nullptr;  // redundancy weight [nu]
     float bp_scale = 1.f;
+    int last = -1;  // slot of the final states after a forward pass
     // saved iterates: f[n_iter + 1][n_mem][nvox], h[n_iter + 1][n_mem][nproj]
     float *f = nullptr, *h = nullptr;
     float *y = nullptr;  // the data of the last forward (copied)
@@ -382,16 +383,24 @@ extern "C" int lpd_info(const cbct_lpd *m, long long *nparams, float **params, f
     return 0;
 }
 
-extern "C" int lpd_forward(cbct_lpd *m, const float *y, const float *x0, float *x_out, int batch, int save_for_backward,
-                           void *stream) {
-    if (!m || !y || !x0 || !x_out) return fail(CBCT_EINVAL, "lpd_forward: NULL argument");
-    if (batch != 1) return fail(CBCT_EINVAL, "lpd_forward: batch must be 1 (accumulate gradients over calls)");
-    cudaStream_t st = (cudaStream_t)stream;
+// Forward pass from the initial states f_0 (f0, or x0 / mu_ref in every channel) and
+// h_0 (h0, or zero); x_out = mu_ref f_N[0] when given. The final states stay in the
+// model (slot N with save_for_backward, else slot 0) for lpd_get_state.
+static int lpd_forward_impl(cbct_lpd *m, const float *y, const float *x0, const float *f0, const float *h0,
+                            float *x_out, int save_for_backward, cudaStream_t st) {
     const long long NV = m->nvox, NP = m->nproj;
     const int M = m->d.n_mem, N = m->d.n_iter;
-    cudaMemcpyAsync(m->y, y, sizeof(float) * NP, cudaMemcpyDeviceToDevice, st);
-    k_init_f<<<grid_n(NV), 256, 0, st>>>(x0, m->f, NV, M, 1.f / m->d.mu_ref);
-    cudaMemsetAsync(m->h, 0, sizeof(float) * M * NP, st);
+    CBCT_CUDA_TRY(cudaMemcpyAsync(m->y, y, sizeof(float) * NP, cudaMemcpyDeviceToDevice, st));
+    if (f0) {
+        CBCT_CUDA_TRY(cudaMemcpyAsync(m->f, f0, sizeof(float) * M * NV, cudaMemcpyDeviceToDevice, st));
+    } else {
+        k_init_f<<<grid_n(NV), 256, 0, st>>>(x0, m->f, NV, M, 1.f / m->d.mu_ref);
+    }
+    if (h0) {
+        CBCT_CUDA_TRY(cudaMemcpyAsync(m->h, h0, sizeof(float) * M * NP, cudaMemcpyDeviceToDevice, st));
+    } else {
+        CBCT_CUDA_TRY(cudaMemsetAsync(m->h, 0, sizeof(float) * M * NP, st));
+    }
     for (int n = 0; n < N; ++n) {
         const int si = save_for_backward ? n : 0, so = save_for_backward ? n + 1 : 0;
         int rc = lpd_iter_fwd(m, n, m->f + (long long)si * M * NV, m->h + (long long)si * M * NP,
@@ -399,24 +408,54 @@ extern "C" int lpd_forward(cbct_lpd *m, const float *y, const float *x0, float *
         if (rc) return rc;
     }
     const long long last = save_for_backward ? N : 0;
-    k_sum_channels<<<grid_n(NV), 256, 0, st>>>(m->f + last * M * NV, 1, NV, m->d.mu_ref, x_out, 0);
+    if (x_out) k_sum_channels<<<grid_n(NV), 256, 0, st>>>(m->f + last * M * NV, 1, NV, m->d.mu_ref, x_out, 0);
     m->saved = save_for_backward;
+    m->last = (int)last;
     CBCT_LAUNCH_CHECK("lpd_forward");
     return 0;
 }
 
-extern "C" int lpd_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float *grad_x0, void *stream) {
-    if (!m || !grad_x) return fail(CBCT_EINVAL, "lpd_backward: NULL argument");
-    if (!m->saved) return fail(CBCT_EINVAL, "lpd_backward: call lpd_forward with save_for_backward = 1 first");
+extern "C" int lpd_forward(cbct_lpd *m, const float *y, const float *x0, float *x_out, int batch, int save_for_backward,
+                           void *stream) {
+    if (!m || !y || !x0 || !x_out) return fail(CBCT_EINVAL, "lpd_forward: NULL argument");
+    if (batch != 1) return fail(CBCT_EINVAL, "lpd_forward: batch must be 1 (accumulate gradients over calls)");
+    return lpd_forward_impl(m, y, x0, nullptr, nullptr, x_out, save_for_backward, (cudaStream_t)stream);
+}
+
+extern "C" int lpd_forward_latent(cbct_lpd *m, const float *y, const float *x0, const float *f0, const float *h0,
+                                  float *x_out, int save_for_backward, void *stream) {
+    if (!m || !y || (!x0 && !f0)) return fail(CBCT_EINVAL, "lpd_forward_latent: need y and x0 or f0");
+    return lpd_forward_impl(m, y, x0, f0, h0, x_out, save_for_backward, (cudaStream_t)stream);
+}
+
+extern "C" int lpd_get_state(const cbct_lpd *m, float *f_out, float *h_out, void *stream) {
+    if (!m || m->last < 0) return fail(CBCT_EINVAL, "lpd_get_state: no forward pass yet");
     cudaStream_t st = (cudaStream_t)stream;
-    void *sv = stream;
+    const long long NV = m->nvox, NP = m->nproj, M = m->d.n_mem;
+    if (f_out)
+        CBCT_CUDA_TRY(cudaMemcpyAsync(f_out, m->f + (long long)m->last * M * NV, sizeof(float) * M * NV,
+                                      cudaMemcpyDeviceToDevice, st));
+    if (h_out)
+        CBCT_CUDA_TRY(cudaMemcpyAsync(h_out, m->h + (long long)m->last * M * NP, sizeof(float) * M * NP,
+                                      cudaMemcpyDeviceToDevice, st));
+    return 0;
+}
+
+// Backward pass: upstream dL/dx_out (grad_x) and/or dL/df_N, dL/dh_N (the final
+// states, e.g. from a finer level); accumulates the parameter gradients and returns
+// dL/dy, dL/dx0 and dL/df_0, dL/dh_0 where asked.
+static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad_fN, const float *grad_hN,
+                             float *grad_y, float *grad_x0, float *grad_f0, float *grad_h0, cudaStream_t st) {
+    void *sv = (void *)st;
     const long long NV = m->nvox, NP = m->nproj;
     const int M = m->d.n_mem, N = m->d.n_iter;
     float *gf = m->gf, *gh = m->gh;  // gf: [M + 1][NV] (last = grad of the bp channel), gh: [M + 2][NP]
-    // dL/df_N: channel 0 = mu_ref dL/dx; dL/dh_N = 0
+    // dL/df_N: channel 0 gets mu_ref dL/dx; plus the given state gradients
     cudaMemsetAsync(gf, 0, sizeof(float) * (M + 1) * NV, st);
     cudaMemsetAsync(gh, 0, sizeof(float) * (M + 2) * NP, st);
-    k_axpy<<<grid_n(NV), 256, 0, st>>>(gf, grad_x, NV, m->d.mu_ref);
+    if (grad_x) k_axpy<<<grid_n(NV), 256, 0, st>>>(gf, grad_x, NV, m->d.mu_ref);
+    if (grad_fN) k_axpy<<<grid_n((long long)M * NV), 256, 0, st>>>(gf, grad_fN, (long long)M * NV, 1.f);
+    if (grad_hN) k_axpy<<<grid_n((long long)M * NP), 256, 0, st>>>(gh, grad_hN, (long long)M * NP, 1.f);
     if (grad_y) cudaMemsetAsync(grad_y, 0, sizeof(float) * NP, st);
     int rc = 0;
     for (int n = N - 1; n >= 0 && rc == 0; --n) {
@@ -485,8 +524,23 @@ extern "C" int lpd_backward(cbct_lpd *m, const float *grad_x, float *grad_y, flo
     if (rc) return rc;
     // f_0 = x0 / mu_ref repeated  =>  dL/dx0 = sum_c gf[c] / mu_ref
     if (grad_x0) k_sum_channels<<<grid_n(NV), 256, 0, st>>>(gf, M, NV, 1.f / m->d.mu_ref, grad_x0, 0);
+    if (grad_f0) CBCT_CUDA_TRY(cudaMemcpyAsync(grad_f0, gf, sizeof(float) * M * NV, cudaMemcpyDeviceToDevice, st));
+    if (grad_h0) CBCT_CUDA_TRY(cudaMemcpyAsync(grad_h0, gh, sizeof(float) * M * NP, cudaMemcpyDeviceToDevice, st));
     CBCT_LAUNCH_CHECK("lpd_backward");
     return 0;
+}
+
+extern "C" int lpd_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float *grad_x0, void *stream) {
+    if (!m || !grad_x) return fail(CBCT_EINVAL, "lpd_backward: NULL argument");
+    if (!m->saved) return fail(CBCT_EINVAL, "lpd_backward: call lpd_forward with save_for_backward = 1 first");
+    return lpd_backward_impl(m, grad_x, nullptr, nullptr, grad_y, grad_x0, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int lpd_backward_latent(cbct_lpd *m, const float *grad_x, const float *grad_fN, const float *grad_hN,
+                                   float *grad_y, float *grad_x0, float *grad_f0, float *grad_h0, void *stream) {
+    if (!m || (!grad_x && !grad_fN && !grad_hN)) return fail(CBCT_EINVAL, "lpd_backward_latent: no upstream gradient");
+    if (!m->saved) return fail(CBCT_EINVAL, "lpd_backward_latent: call the forward with save_for_backward = 1 first");
+    return lpd_backward_impl(m, grad_x, grad_fN, grad_hN, grad_y, grad_x0, grad_f0, grad_h0, (cudaStream_t)stream);
 }
 
 extern "C" int lpd_zero_grad(cbct_lpd *m, void *stream) {

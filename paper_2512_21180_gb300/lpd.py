@@ -82,6 +82,42 @@ class LPD:
                                        None if g0 is None else g0.data_ptr(), _st()), "lpd_backward")
         return gy, g0
 
+    # latent states (multiscale levels) -------------------------------------------
+    def forward_latent(self, y: torch.Tensor, x0: torch.Tensor | None = None, f0: torch.Tensor | None = None,
+                       h0: torch.Tensor | None = None, save_for_backward: bool = False,
+                       want_x: bool = True) -> torch.Tensor | None:
+        """Forward from initial states f0 [n_mem, *vol] (units of mu_ref) and h0
+        [n_mem, *proj]; either may be None (x0 / mu_ref repeated, zero)."""
+        g = self.geom
+        yy = y.reshape(g.proj_shape).contiguous()
+        xx = None if x0 is None else x0.reshape(g.vol_shape).contiguous()
+        ff = None if f0 is None else f0.reshape((self.n_mem,) + g.vol_shape).contiguous()
+        hh = None if h0 is None else h0.reshape((self.n_mem,) + g.proj_shape).contiguous()
+        out = torch.empty(g.vol_shape, device=yy.device) if want_x else None
+        ptr = lambda t: None if t is None else t.data_ptr()
+        check(_lib.load().lpd_forward_latent(self.handle, yy.data_ptr(), ptr(xx), ptr(ff), ptr(hh), ptr(out),
+                                             int(save_for_backward), _st()), "lpd_forward_latent")
+        return out
+
+    def state(self):
+        """(f_N [n_mem, *vol], h_N [n_mem, *proj]) of the last forward pass."""
+        g = self.geom
+        f = torch.empty((self.n_mem,) + g.vol_shape, device="cuda")
+        h = torch.empty((self.n_mem,) + g.proj_shape, device="cuda")
+        check(_lib.load().lpd_get_state(self.handle, f.data_ptr(), h.data_ptr(), _st()), "lpd_get_state")
+        return f, h
+
+    def backward_latent(self, grad_x: torch.Tensor | None = None, grad_fN: torch.Tensor | None = None,
+                        grad_hN: torch.Tensor | None = None, want_states: bool = True):
+        """Accumulates parameter gradients; returns (dL/df_0, dL/dh_0) (or Nones)."""
+        g = self.geom
+        ptr = lambda t: None if t is None else t.contiguous().data_ptr()
+        gf0 = torch.empty((self.n_mem,) + g.vol_shape, device="cuda") if want_states else None
+        gh0 = torch.empty((self.n_mem,) + g.proj_shape, device="cuda") if want_states else None
+        check(_lib.load().lpd_backward_latent(self.handle, ptr(grad_x), ptr(grad_fN), ptr(grad_hN), None, None,
+                                              ptr(gf0), ptr(gh0), _st()), "lpd_backward_latent")
+        return gf0, gh0
+
     def zero_grad(self):
         check(_lib.load().lpd_zero_grad(self.handle, _st()), "lpd_zero_grad")
 

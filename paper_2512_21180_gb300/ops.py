@@ -119,3 +119,30 @@ def landweber(geom: Geometry, y: torch.Tensor, x: torch.Tensor, niter: int, tau:
         check(_lib.load().cbct_landweber(geom.handle, yy.data_ptr(), xx.data_ptr(), yy.shape[0], int(niter),
                                          float(tau), int(nonneg), _st(yy)), "cbct_landweber")
     return xx
+
+
+# ---- resampling between multiscale levels (a11) ----------------------------------------
+
+def resample_down(x: torch.Tensor, f=(2, 2, 2), pick0: bool = False, scale: float | None = None) -> torch.Tensor:
+    """Box sum over f (or, with pick0, every f0-th slice along the first axis) of the last
+    three axes, times scale (default: the mean over the box)."""
+    x = x.contiguous()
+    n0, n1, n2 = x.shape[-3:]
+    nch = x.numel() // (n0 * n1 * n2)
+    if scale is None:
+        scale = 1.0 / ((1 if pick0 else f[0]) * f[1] * f[2])
+    out = torch.empty(x.shape[:-3] + (n0 // f[0], n1 // f[1], n2 // f[2]), device=x.device)
+    _lib.check(_lib.load().cbct_resample_down(x.data_ptr(), nch, n0, n1, n2, f[0], f[1], f[2], int(pick0),
+                                              float(scale), out.data_ptr(), _st(x)), "cbct_resample_down")
+    return out
+
+
+def resample_up(x: torch.Tensor, f=(2, 2, 2)) -> torch.Tensor:
+    """Nearest-neighbour upsampling of the last three axes by f."""
+    x = x.contiguous()
+    n0, n1, n2 = x.shape[-3:]
+    nch = x.numel() // (n0 * n1 * n2)
+    out = torch.empty(x.shape[:-3] + (n0 * f[0], n1 * f[1], n2 * f[2]), device=x.device)
+    _lib.check(_lib.load().cbct_resample_up(x.data_ptr(), nch, n0, n1, n2, f[0], f[1], f[2], out.data_ptr(),
+                                            _st(x)), "cbct_resample_up")
+    return out

@@ -43,6 +43,7 @@ struct ConvArgs {
     int taps3d;              // 1: 3x3x3, 0: 3x3 over (H, W)
     int kgroups;             // padded K / 8 (even)
     int cout;
+    int cin;                 // weight gradient: input channels
     float slope;
     __nv_bfloat16 *y;        // EPI_ACT_BF16 / EPI_MASK_BF16 output [nimg][D][H][cpout / 8][W][8]
     int cpout;
@@ -462,6 +463,216 @@ __global__ void k_pack_weights(const float *__restrict__ w, int cout, int taps3d
     }
 }
 
+// ---- weight gradient on the tensor cores ------------------------------------------------
+//
+// dW[co][tap][ci] = sum over output pixels p of dY[p][co] X[p + tap][ci]: a GEMM whose K
+// dimension is the pixels. In the row-blocked layout a row's channel group is pixels
+// 16 B apart with 8 channels contiguous, which is exactly the MN-major canonical core
+// matrix (8 M/N elements contiguous x 8 K rows 16 B apart) — so the same row-halo TMA
+// stages feed it, with the operands marked transposed in the instruction descriptor
+// (for this layout the descriptor's leading byte offset steps along K, the stride
+// byte offset along M / N).
+// A tile is 128 output pixels of one output row h (input plane d + dd for 3-D); its
+// stage holds the input rows h - 1 .. h + 2 (4 rows x 4 channel groups, the region
+// layout of the forward) and the tile's dY row (CGO channel groups, 2048 B each, plus a
+// zero group when CGO = 1). Per column tap dw and 16-pixel K step, one MMA with
+// A = 4 rows x 32 input channels (M = 128: core matrix j = region j, M stride RS, K
+// stride 128 B) and B = dY (N = 8 NCG output channels 2048 B apart) accumulates
+// D_(dd, dw)[(r, ci)][co] in TMEM over every tile of the CTA; rows r = 0..2 are the taps
+// dh = r - 1 (r = 3 is discarded). Each CTA writes its partial dW once; a fixed-order
+// reduction sums the partials (deterministic).
+constexpr int kWgThreads = 192;  // warps 0-3 epilogue, 4 TMA producer, 5 MMA
+constexpr int kWgStages = 4;
+constexpr int kWgXBytes = 4 * 4 * kRowStride;  // 4 input rows x 4 channel groups
+
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N) {
+    return idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);  // A and B MN-major
+}
+
+template <int NCG>  // output-channel groups of B: 2 (16 outputs, second group zero when cout <= 8) or 4
+__global__ void __launch_bounds__(kWgThreads) k_conv_wgrad_tc(const __grid_constant__ CUtensorMap xmap,
+                                                              const __grid_constant__ CUtensorMap ymap, ConvArgs a,
+                                                              int cgo, float *__restrict__ partial) {
+    constexpr int kN = NCG * 8;
+    constexpr int kYBytes = NCG * 2048;
+    constexpr int kStage = kWgXBytes + kYBytes;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + kWgStages * kStage);
+    uint64_t *empty = full + kWgStages;
+    uint64_t *done = empty + kWgStages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+    int *used = abort_flag + 1;  // [9]: accumulator (dd, dw) received an MMA
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nch = a.taps3d ? 3 : 1;
+    constexpr uint32_t kIdesc = idesc_bf16_f32_mn(128, kN);
+    const uint32_t kCols = a.taps3d ? 512u : 128u;  // 9 or 3 accumulators of kN <= 32 columns
+    const int rs = 16 * a.G * conv_box_rows(a.G);
+
+    if (warp == 0) tmem_alloc(tmem_slot, kCols);
+    if (tid == 32) {
+        for (int s = 0; s < kWgStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 2);  // the MMAs' commit + the MMA thread's release of used[]
+        *abort_flag = 0;
+        for (int i = 0; i < 9; ++i) used[i] = 0;
+        fence_mbar_init();
+    }
+    if (cgo < NCG) {
+        // output-channel groups beyond the data stay zero in every stage
+        for (int i = tid; i < kWgStages * (NCG - cgo) * 128; i += kWgThreads) {
+            const int s = i / ((NCG - cgo) * 128), q = i - s * (NCG - cgo) * 128;
+            reinterpret_cast<uint4 *>(sm + s * kStage + kWgXBytes + cgo * 2048)[q] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int ntw = (a.W + 127) / 128;
+    const long long ntiles = (long long)a.nimg * a.D * a.H * ntw;
+    const long long per_cta = (ntiles + gridDim.x - 1) / gridDim.x;
+    const long long t_begin = (long long)blockIdx.x * per_cta;
+    const long long my_tiles = t_begin < ntiles ? min(per_cta, ntiles - t_begin) : 0;
+    const long long total = my_tiles * nch;
+    const uint32_t sm_u = smem_u32(sm);
+
+    if (warp == 4) {
+        if (lane == 0) {
+            prefetch_tmap(&xmap);
+            prefetch_tmap(&ymap);
+            TileCoord tc = tile_coord(t_begin, a.D, a.H, ntw);
+            const uint32_t xbytes = (uint32_t)(4 * 4 * rs), ybytes = (uint32_t)(cgo * 2048);
+            int c = 0, s = 0;
+            uint32_t ph = 0;
+            for (long long i = 0; i < total; ++i) {
+                if (i >= kWgStages && !mbar_wait(&empty[s], ph ^ 1u, a.status)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                const int d2 = tc.d + (nch == 3 ? c - 1 : 0);
+                if (d2 < 0 || d2 >= a.D) {
+                    mbar_arrive_expect_tx(&full[s], 0u);  // input plane outside the volume: no MMAs
+                } else {
+                    const uint32_t st = sm_u + (uint32_t)(s * kStage);
+                    mbar_arrive_expect_tx(&full[s], xbytes + ybytes);
+                    tma_load_5d(st, &xmap, 0, tc.w0 / a.G - 1, 0, tc.th - 1, tc.img * a.D + d2, &full[s]);
+                    tma_load_5d(st + kWgXBytes, &ymap, 0, tc.w0 / a.G, 0, tc.th, tc.img * a.D + tc.d, &full[s]);
+                }
+                if (++c == nch) {
+                    c = 0;
+                    tile_next(tc, a.D, a.H, a.W);
+                }
+                if (++s == kWgStages) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // A: M = 4 rows x 4 channel groups, core matrix j = region j (stride RS), K
+            // (pixels) steps of 8 at 128 B; B: N = output channel groups (2048 B apart)
+            TileCoord tc = tile_coord(t_begin, a.D, a.H, ntw);
+            int s = 0, c = 0;
+            uint32_t ph = 0;
+            uint32_t usedm = 0;  // bit (dd * 3 + dw): accumulator initialised
+            for (long long i = 0; i < total && !*abort_flag; ++i) {
+                if (!mbar_wait(&full[s], ph, a.status)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                const int d2 = tc.d + (nch == 3 ? c - 1 : 0);
+                if (d2 >= 0 && d2 < a.D) {
+                    tc_fence_after();
+                    const uint32_t st = sm_u + (uint32_t)(s * kStage);
+#pragma unroll
+                    for (int dw = 0; dw < 3; ++dw) {
+                        const int acc = c * 3 + dw;
+                        const uint32_t dt = tmem + (uint32_t)(acc * kN);
+#pragma unroll
+                        for (int ks = 0; ks < 8; ++ks) {
+                            // MN-major, no swizzle: the leading byte offset steps along K (8
+                            // pixels = 128 B), the stride byte offset along M / N
+                            const uint64_t ad = smem_desc_kmajor(st + (uint32_t)((a.G - 1 + dw) * 16 + ks * 256), 128, rs);
+                            const uint64_t bd = smem_desc_kmajor(st + kWgXBytes + (uint32_t)(ks * 256), 128, 2048);
+                            mma_bf16(dt, ad, bd, kIdesc, (usedm >> acc) & 1u);
+                            usedm |= 1u << acc;
+                        }
+                    }
+                }
+                mma_commit(&empty[s]);
+                if (++c == nch) {
+                    c = 0;
+                    tile_next(tc, a.D, a.H, a.W);
+                }
+                if (++s == kWgStages) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+            for (int k = 0; k < 9; ++k) used[k] = (usedm >> k) & 1u;
+            mma_commit(done);
+            mbar_arrive(done);
+        }
+    } else {
+        // epilogue (warps 0-3, once): warp w holds accumulator rows 32 w .. 32 w + 31 =
+        // input row r = w, input channel = lane; rows r = 0..2 are the taps dh = r - 1
+        const bool ok = mbar_wait(done, 0u, a.status);
+        tc_fence_after();
+        const int r = warp, ci = lane;
+        const int ntaps = a.taps3d ? 27 : 9;
+        float *pb = partial + (long long)blockIdx.x * a.cout * ntaps * a.cin;
+        for (int acc = 0; acc < nch * 3; ++acc) {
+            float v[kN];
+#pragma unroll
+            for (int c0 = 0; c0 < kN; c0 += 16)
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * kN + c0), v + c0);
+            if (r < 3 && ci < a.cin) {
+                const int cc = acc / 3, dw = acc - cc * 3;
+                const int tap = (a.taps3d ? (cc * 3 + r) * 3 : r * 3) + dw;
+                const bool valid = ok && !*abort_flag && used[acc];
+#pragma unroll
+                for (int co = 0; co < kN; ++co)
+                    if (co < a.cout) pb[((long long)co * ntaps + tap) * a.cin + ci] = valid ? v[co] : 0.f;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kCols);
+    }
+}
+
+// partial_b[blk][co] = sum over the block's pixels of dY[p][co] (row-blocked dY)
+__global__ void k_bias_grad(const __nv_bfloat16 *__restrict__ dy, int cpout, int cout, long long npix, int W,
+                            int pix_per_block, float *__restrict__ partial_b) {
+    __shared__ float red[32][33];
+    const long long p0 = (long long)blockIdx.x * pix_per_block, p1 = min(npix, p0 + pix_per_block);
+    const int co = threadIdx.x & 31, lane_p = threadIdx.x >> 5;  // 8 pixel lanes x 32 channels
+    float s = 0.f;
+    if (co < cout)
+        for (long long p = p0 + lane_p; p < p1; p += 8) {
+            const long long row = p / W;
+            const int w = (int)(p - row * W);
+            s += __bfloat162float(dy[((row * (cpout / 8) + co / 8) * W + w) * 8 + (co & 7)]);
+        }
+    red[lane_p][co] = s;
+    __syncthreads();
+    if (threadIdx.x < 32 && threadIdx.x < cout) {
+        float t = 0.f;
+        for (int k = 0; k < 8; ++k) t += red[k][threadIdx.x];
+        partial_b[(long long)blockIdx.x * cout + threadIdx.x] = t;
+    }
+}
+
 // ---- weight gradient (CUDA cores) ---------------------------------------------------------
 
 // partial[blk][co][tap][ci] = sum over this block's pixels of dY[p][co] * X[p + tap][ci]
@@ -651,9 +862,70 @@ static int conv_run(const ConvArgs &a0, int n_out, int epi, int rpt, cudaStream_
     return launch_conv_rpt<32, EPI_MASK_BF16>(a, rpt, st);
 }
 
+__device__ int g_wgrad_status;  // status word of weight-gradient launches (bounded waits)
+
+// Tensor-core weight gradient (32 input channel slots; cpout 8, 16 or 32): per-CTA
+// partial dW, then a fixed-order reduction; db on the CUDA cores.
+template <int NCG>
+static int conv_wgrad_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *dy, int cpout, int cout, int nimg,
+                         int D, int H, int W, int taps3d, float *dw, float *db, int accumulate, cudaStream_t st) {
+    ConvArgs a{};
+    a.x = x;
+    a.nimg = nimg; a.D = D; a.H = H; a.W = W;
+    a.cpin = 32; a.cin_groups = 4;
+    a.taps3d = taps3d;
+    a.cout = cout; a.cin = cin;
+    a.G = W % 4 == 0 ? 4 : (W % 2 == 0 ? 2 : 1);
+    CBCT_CUDA_TRY(cudaGetSymbolAddress((void **)&a.status, g_wgrad_status));
+    const int cgo = cpout / 8;
+    const uint64_t G = (uint64_t)a.G, Wl = (uint64_t)W;
+    CUtensorMap xmap, ymap;
+    {
+        const uint64_t dims[5] = {8 * G, Wl / G, 4, (uint64_t)H, (uint64_t)D * nimg};
+        const uint64_t strides[4] = {16 * G, 16 * Wl, 64 * Wl, 64 * Wl * H};
+        const uint32_t box[5] = {(uint32_t)(8 * G), (uint32_t)conv_box_rows(a.G), 4, 4, 1};
+        int rc = encode_tmap(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, x, dims, strides, box);
+        if (rc) return rc;
+    }
+    {
+        const uint64_t dims[5] = {8 * G, Wl / G, (uint64_t)cgo, (uint64_t)H, (uint64_t)D * nimg};
+        const uint64_t strides[4] = {16 * G, 16 * Wl, 16 * Wl * cgo, 16 * Wl * cgo * H};
+        const uint32_t box[5] = {(uint32_t)(8 * G), (uint32_t)(128 / a.G), (uint32_t)cgo, 1, 1};
+        int rc = encode_tmap(&ymap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, dy, dims, strides, box);
+        if (rc) return rc;
+    }
+    constexpr size_t kStage = kWgXBytes + NCG * 2048;
+    const size_t smem = 1024 + kWgStages * kStage + 8 * (2 * kWgStages + 1) + 4 * 12 + 64;
+    CBCT_CUDA_TRY(cudaFuncSetAttribute(k_conv_wgrad_tc<NCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int ntaps = taps3d ? 27 : 9;
+    const long long ntiles = (long long)nimg * D * H * ((W + 127) / 128);
+    const int grid = (int)std::min<long long>(ntiles, nsm);
+    const int nw = cout * ntaps * cin;
+    const long long npix = (long long)nimg * D * H * W;
+    const int nbb = (int)std::min<long long>(152LL * 4, std::max<long long>(1, (npix + 4095) / 4096));
+    const int ppb = (int)((npix + nbb - 1) / nbb);
+    float *part = nullptr;
+    CBCT_CUDA_TRY(cudaMallocAsync((void **)&part, sizeof(float) * ((long long)grid * nw + (long long)nbb * cout), st));
+    float *partb = part + (long long)grid * nw;
+    k_conv_wgrad_tc<NCG><<<grid, kWgThreads, smem, st>>>(xmap, ymap, a, cgo, part);
+    k_bias_grad<<<nbb, 256, 0, st>>>(dy, cpout, cout, npix, W, ppb, partb);
+    k_reduce_rows<<<(nw + 255) / 256, 256, 0, st>>>(part, grid, nw, dw, accumulate);
+    k_reduce_rows<<<1, 256, 0, st>>>(partb, nbb, cout, db, accumulate);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(part, st);
+    if (e != cudaSuccess) return cuda_fail(e, "conv wgrad (tensor cores)");
+    return 0;
+}
+
 // dW (+)= sum_p dY[p] x X[p + tap], db (+)= sum_p dY[p]; partial sums in scratch.
 int conv_wgrad(const __nv_bfloat16 *x, int cpin, int cin, const __nv_bfloat16 *dy, int cpout, int cout, int nimg, int D,
                int H, int W, int taps3d, float *dw, float *db, int accumulate, cudaStream_t st) {
+    if (cpin == 32 && cin <= 32 && cout <= cpout && (cpout == 8 || cpout == 16 || cpout == 32))
+        return cpout <= 16 ? conv_wgrad_tc<2>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, st)
+                           : conv_wgrad_tc<4>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, st);
     const int ntaps = taps3d ? 27 : 9;
     const long long npix = (long long)nimg * D * H * W;
     const int nblk = (int)std::min<long long>(152LL * 4, std::max<long long>(1, (npix + 1023) / 1024));

@@ -130,3 +130,33 @@ def test_conv_input_gradient_and_weight_gradient(L, taps3d, dims):
     ref_dw = wr.grad.reshape(cout, cin, -1).permute(0, 2, 1)
     assert rel(dw.double().cpu(), ref_dw) <= 1e-5
     assert rel(db.double().cpu(), br.grad) <= 1e-5
+
+
+@pytest.mark.parametrize("taps3d,dims,cin,cout,cpout", [(0, (9, 150), 20, 5, 8), (0, (13, 37), 32, 12, 16),
+                                                      (1, (5, 7, 9), 32, 5, 8), (1, (4, 6, 130), 24, 32, 32)])
+def test_conv_weight_gradient_shapes(L, taps3d, dims, cin, cout, cpout):
+    """Weight and bias gradients for fewer input channels and 5 / 12 / 32 outputs
+    (tensor-core path for 32 input slots), ragged W, 2-D and 3-D."""
+    from oracle import lpd_ref as R
+    rng = np.random.default_rng(17)
+    nimg = 2
+    x = R.bf16(torch.tensor(rng.standard_normal((nimg, cin) + dims)))
+    dy = R.bf16(torch.tensor(rng.standard_normal((nimg, cout) + dims)))
+    wr = torch.zeros((cout, cin) + (3,) * len(dims), dtype=torch.float64, requires_grad=True)
+    br = torch.zeros(cout, dtype=torch.float64, requires_grad=True)
+    (R.conv(x, wr, br) * dy).sum().backward()
+    D, H, W = dims if taps3d else (1,) + dims
+    dw = torch.zeros((cout, 27 if taps3d else 9, cin), device="cuda")
+    db = torch.zeros(cout, device="cuda")
+    x_cl, dy_cl = to_cl(x, 32), to_cl(dy, cpout)
+    L.check(L.load().cbct_conv_wgrad(x_cl.data_ptr(), 32, cin, dy_cl.data_ptr(), cpout, cout, nimg, D, H, W,
+                                     taps3d, dw.data_ptr(), db.data_ptr(), 0,
+                                     torch.cuda.current_stream().cuda_stream), "wgrad")
+    torch.cuda.synchronize()
+    ref_dw = wr.grad.reshape(cout, cin, -1).permute(0, 2, 1)
+    assert rel_l2_t(dw.double().cpu(), ref_dw) <= 1e-5
+    assert rel_l2_t(db.double().cpu(), br.grad) <= 1e-5
+
+
+def rel_l2_t(a, b):
+    return float((a - b).norm() / b.norm())

@@ -489,7 +489,10 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N) {
     return idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);  // A and B MN-major
 }
 
-template <int NCG>  // output-channel groups of B: 2 (16 outputs, second group zero when cout <= 8) or 4
+// XCG = input channel groups (4, or 1 for 8-channel inputs: each input row is then
+// loaded to region 4 r and the regions of groups 1..3 stay zero); NCG = output-channel
+// groups of B: 2 (16 outputs, the second group zero when cout <= 8) or 4.
+template <int XCG, int NCG>
 __global__ void __launch_bounds__(kWgThreads) k_conv_wgrad_tc(const __grid_constant__ CUtensorMap xmap,
                                                               const __grid_constant__ CUtensorMap ymap, ConvArgs a,
                                                               int cgo, float *__restrict__ partial) {
@@ -528,6 +531,15 @@ __global__ void __launch_bounds__(kWgThreads) k_conv_wgrad_tc(const __grid_const
             reinterpret_cast<uint4 *>(sm + s * kStage + kWgXBytes + cgo * 2048)[q] = make_uint4(0u, 0u, 0u, 0u);
         }
     }
+    if constexpr (XCG == 1) {
+        // regions 4 r + g, g = 1..3: zero input channels 8..31
+        const int q16 = rs / 16;
+        for (int i = tid; i < kWgStages * 12 * q16; i += kWgThreads) {
+            const int s = i / (12 * q16), rem = i - s * 12 * q16, k = rem / q16, q = rem - k * q16;
+            const int region = (k / 3) * 4 + 1 + k % 3;
+            reinterpret_cast<uint4 *>(sm + s * kStage + region * rs)[q] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -547,7 +559,7 @@ __global__ void __launch_bounds__(kWgThreads) k_conv_wgrad_tc(const __grid_const
             prefetch_tmap(&xmap);
             prefetch_tmap(&ymap);
             TileCoord tc = tile_coord(t_begin, a.D, a.H, ntw);
-            const uint32_t xbytes = (uint32_t)(4 * 4 * rs), ybytes = (uint32_t)(cgo * 2048);
+            const uint32_t xbytes = (uint32_t)(4 * XCG * rs), ybytes = (uint32_t)(cgo * 2048);
             int c = 0, s = 0;
             uint32_t ph = 0;
             for (long long i = 0; i < total; ++i) {
@@ -561,7 +573,14 @@ __global__ void __launch_bounds__(kWgThreads) k_conv_wgrad_tc(const __grid_const
                 } else {
                     const uint32_t st = sm_u + (uint32_t)(s * kStage);
                     mbar_arrive_expect_tx(&full[s], xbytes + ybytes);
-                    tma_load_5d(st, &xmap, 0, tc.w0 / a.G - 1, 0, tc.th - 1, tc.img * a.D + d2, &full[s]);
+                    if constexpr (XCG == 4) {
+                        tma_load_5d(st, &xmap, 0, tc.w0 / a.G - 1, 0, tc.th - 1, tc.img * a.D + d2, &full[s]);
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+                            tma_load_5d(st + (uint32_t)(4 * r * rs), &xmap, 0, tc.w0 / a.G - 1, 0, tc.th - 1 + r,
+                                        tc.img * a.D + d2, &full[s]);
+                    }
                     tma_load_5d(st + kWgXBytes, &ymap, 0, tc.w0 / a.G, 0, tc.th, tc.img * a.D + tc.d, &full[s]);
                 }
                 if (++c == nch) {
@@ -651,25 +670,34 @@ __global__ void __launch_bounds__(kWgThreads) k_conv_wgrad_tc(const __grid_const
     }
 }
 
-// partial_b[blk][co] = sum over the block's pixels of dY[p][co] (row-blocked dY)
-__global__ void k_bias_grad(const __nv_bfloat16 *__restrict__ dy, int cpout, int cout, long long npix, int W,
-                            int pix_per_block, float *__restrict__ partial_b) {
-    __shared__ float red[32][33];
-    const long long p0 = (long long)blockIdx.x * pix_per_block, p1 = min(npix, p0 + pix_per_block);
-    const int co = threadIdx.x & 31, lane_p = threadIdx.x >> 5;  // 8 pixel lanes x 32 channels
-    float s = 0.f;
-    if (co < cout)
-        for (long long p = p0 + lane_p; p < p1; p += 8) {
-            const long long row = p / W;
-            const int w = (int)(p - row * W);
-            s += __bfloat162float(dy[((row * (cpout / 8) + co / 8) * W + w) * 8 + (co & 7)]);
+// partial_b[blk][co] = sum over the block's image rows of dY[row][co] (row-blocked dY,
+// cgo channel groups): thread (group q, column lane) reads 16-byte pixels along the
+// row, then the lanes of each channel are summed in a fixed order.
+__global__ void __launch_bounds__(256) k_bias_grad(const __nv_bfloat16 *__restrict__ dy, int cgo, int cout,
+                                                   long long nrows, int W, int rows_per_block,
+                                                   float *__restrict__ partial_b) {
+    __shared__ float red[256][9];
+    const int tpq = 256 / cgo, q = threadIdx.x / tpq, l = threadIdx.x - q * tpq;
+    const long long r0 = (long long)blockIdx.x * rows_per_block, r1 = min(nrows, r0 + rows_per_block);
+    float acc[8] = {};
+    for (long long row = r0; row < r1; ++row) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(dy + (row * cgo + q) * (long long)W * 8);
+        for (int w = l; w < W; w += tpq) {
+            const uint4 v = __ldg(src + w);
+            const __nv_bfloat16 *b = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] += __bfloat162float(b[j]);
         }
-    red[lane_p][co] = s;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) red[threadIdx.x][j] = acc[j];
     __syncthreads();
-    if (threadIdx.x < 32 && threadIdx.x < cout) {
+    const int c = threadIdx.x;
+    if (c < cout) {
+        const int qc = c / 8, j = c % 8;
         float t = 0.f;
-        for (int k = 0; k < 8; ++k) t += red[k][threadIdx.x];
-        partial_b[(long long)blockIdx.x * cout + threadIdx.x] = t;
+        for (int k = 0; k < tpq; ++k) t += red[qc * tpq + k][j];
+        partial_b[(long long)blockIdx.x * cout + c] = t;
     }
 }
 
@@ -866,13 +894,13 @@ __device__ int g_wgrad_status;  // status word of weight-gradient launches (boun
 
 // Tensor-core weight gradient (32 input channel slots; cpout 8, 16 or 32): per-CTA
 // partial dW, then a fixed-order reduction; db on the CUDA cores.
-template <int NCG>
+template <int XCG, int NCG>
 static int conv_wgrad_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *dy, int cpout, int cout, int nimg,
                          int D, int H, int W, int taps3d, float *dw, float *db, int accumulate, cudaStream_t st) {
     ConvArgs a{};
     a.x = x;
     a.nimg = nimg; a.D = D; a.H = H; a.W = W;
-    a.cpin = 32; a.cin_groups = 4;
+    a.cpin = 8 * XCG; a.cin_groups = XCG;
     a.taps3d = taps3d;
     a.cout = cout; a.cin = cin;
     a.G = W % 4 == 0 ? 4 : (W % 2 == 0 ? 2 : 1);
@@ -881,9 +909,9 @@ static int conv_wgrad_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *d
     const uint64_t G = (uint64_t)a.G, Wl = (uint64_t)W;
     CUtensorMap xmap, ymap;
     {
-        const uint64_t dims[5] = {8 * G, Wl / G, 4, (uint64_t)H, (uint64_t)D * nimg};
-        const uint64_t strides[4] = {16 * G, 16 * Wl, 64 * Wl, 64 * Wl * H};
-        const uint32_t box[5] = {(uint32_t)(8 * G), (uint32_t)conv_box_rows(a.G), 4, 4, 1};
+        const uint64_t dims[5] = {8 * G, Wl / G, (uint64_t)XCG, (uint64_t)H, (uint64_t)D * nimg};
+        const uint64_t strides[4] = {16 * G, 16 * Wl, 16 * XCG * Wl, 16 * XCG * Wl * H};
+        const uint32_t box[5] = {(uint32_t)(8 * G), (uint32_t)conv_box_rows(a.G), (uint32_t)XCG, XCG == 4 ? 4u : 1u, 1};
         int rc = encode_tmap(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, x, dims, strides, box);
         if (rc) return rc;
     }
@@ -896,7 +924,7 @@ static int conv_wgrad_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *d
     }
     constexpr size_t kStage = kWgXBytes + NCG * 2048;
     const size_t smem = 1024 + kWgStages * kStage + 8 * (2 * kWgStages + 1) + 4 * 12 + 64;
-    CBCT_CUDA_TRY(cudaFuncSetAttribute(k_conv_wgrad_tc<NCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CBCT_CUDA_TRY(cudaFuncSetAttribute(k_conv_wgrad_tc<XCG, NCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -904,14 +932,14 @@ static int conv_wgrad_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *d
     const long long ntiles = (long long)nimg * D * H * ((W + 127) / 128);
     const int grid = (int)std::min<long long>(ntiles, nsm);
     const int nw = cout * ntaps * cin;
-    const long long npix = (long long)nimg * D * H * W;
-    const int nbb = (int)std::min<long long>(152LL * 4, std::max<long long>(1, (npix + 4095) / 4096));
-    const int ppb = (int)((npix + nbb - 1) / nbb);
+    const long long nrows = (long long)nimg * D * H;
+    const int nbb = (int)std::min<long long>(152LL * 4, nrows);
+    const int rpb = (int)((nrows + nbb - 1) / nbb);
     float *part = nullptr;
     CBCT_CUDA_TRY(cudaMallocAsync((void **)&part, sizeof(float) * ((long long)grid * nw + (long long)nbb * cout), st));
     float *partb = part + (long long)grid * nw;
-    k_conv_wgrad_tc<NCG><<<grid, kWgThreads, smem, st>>>(xmap, ymap, a, cgo, part);
-    k_bias_grad<<<nbb, 256, 0, st>>>(dy, cpout, cout, npix, W, ppb, partb);
+    k_conv_wgrad_tc<XCG, NCG><<<grid, kWgThreads, smem, st>>>(xmap, ymap, a, cgo, part);
+    k_bias_grad<<<nbb, 256, 0, st>>>(dy, cgo, cout, nrows, W, rpb, partb);
     k_reduce_rows<<<(nw + 255) / 256, 256, 0, st>>>(part, grid, nw, dw, accumulate);
     k_reduce_rows<<<1, 256, 0, st>>>(partb, nbb, cout, db, accumulate);
     cudaError_t e = cudaGetLastError();
@@ -923,9 +951,13 @@ static int conv_wgrad_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *d
 // dW (+)= sum_p dY[p] x X[p + tap], db (+)= sum_p dY[p]; partial sums in scratch.
 int conv_wgrad(const __nv_bfloat16 *x, int cpin, int cin, const __nv_bfloat16 *dy, int cpout, int cout, int nimg, int D,
                int H, int W, int taps3d, float *dw, float *db, int accumulate, cudaStream_t st) {
-    if (cpin == 32 && cin <= 32 && cout <= cpout && (cpout == 8 || cpout == 16 || cpout == 32))
-        return cpout <= 16 ? conv_wgrad_tc<2>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, st)
-                           : conv_wgrad_tc<4>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, st);
+    if ((cpin == 32 || cpin == 8) && cin <= cpin && cout <= cpout && (cpout == 8 || cpout == 16 || cpout == 32)) {
+        if (cpin == 8)
+            return cpout <= 16 ? conv_wgrad_tc<1, 2>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, st)
+                               : conv_wgrad_tc<1, 4>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, st);
+        return cpout <= 16 ? conv_wgrad_tc<4, 2>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, st)
+                           : conv_wgrad_tc<4, 4>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, st);
+    }
     const int ntaps = taps3d ? 27 : 9;
     const long long npix = (long long)nimg * D * H * W;
     const int nblk = (int)std::min<long long>(152LL * 4, std::max<long long>(1, (npix + 1023) / 1024));

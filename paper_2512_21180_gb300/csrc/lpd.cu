@@ -59,6 +59,9 @@ struct cbct_lpd {
     int saved = 0;
     // workspaces
     float *tproj = nullptr, *tproj2 = nullptr, *tvol = nullptr;
+    // projector outputs of each iteration kept by a training forward pass (so the
+    // backward does not recompute them): P f_1 [n_iter][nproj], P^T (w h_1) [n_iter][nvox]
+    float *pf_saved = nullptr, *bp_saved = nullptr;
     __nv_bfloat16 *din = nullptr, *a1 = nullptr, *a2 = nullptr, *pin = nullptr, *b1 = nullptr, *b2 = nullptr;
     __nv_bfloat16 *g32a = nullptr, *g32b = nullptr, *gsmall = nullptr;  // gradient buffers
     float *gf = nullptr, *gh = nullptr;  // [n_mem + 1][nvox], [n_mem + 2][nproj]
@@ -229,29 +232,31 @@ static int conv_dx(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *dy, int
 
 // One forward iteration n: (f_in, h_in) -> (f_out, h_out); activations left in the
 // workspaces (a1, a2, b1, b2, din, pin).
+// pf, bp: where the iteration's P f_1 and P^T (w h_1) go (workspaces, or the per-
+// iteration buffers of a training forward).
 static int lpd_iter_fwd(cbct_lpd *m, int n, const float *f_in, const float *h_in, float *f_out, float *h_out,
-                        cudaStream_t st) {
+                        float *pf, float *bp, cudaStream_t st) {
     const long long NV = m->nvox, NP = m->nproj;
     const int M = m->d.n_mem;
     const LayerSpec *Ld = &m->layers[6 * n], *Lp = &m->layers[6 * n + 3];
     void *sv = (void *)st;
     // dual block input [h (M), mu_ref P f_1, y]
-    int rc = forward_project(m->g, f_in + 1 * NV, m->tproj, 1, 0, sv);
+    int rc = forward_project(m->g, f_in + 1 * NV, pf, 1, 0, sv);
     if (rc) return rc;
     Planes pl{};
     for (int c = 0; c < M; ++c) { pl.p[c] = h_in + c * NP; pl.s[c] = 1.f; }
-    pl.p[M] = m->tproj; pl.s[M] = m->d.mu_ref;
+    pl.p[M] = pf; pl.s[M] = m->d.mu_ref;
     pl.p[M + 1] = m->y; pl.s[M + 1] = 1.f;
     k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
     if ((rc = conv_fwd(m, Ld[0], m->din, 8, DUAL_DIMS, 0, m->a1, nullptr, 0, st))) return rc;
     if ((rc = conv_fwd(m, Ld[1], m->a1, 32, DUAL_DIMS, 0, m->a2, nullptr, 0, st))) return rc;
     if ((rc = conv_fwd(m, Ld[2], m->a2, 32, DUAL_DIMS, 1, nullptr, h_out, NP, st, h_in))) return rc;
     // primal block input [f (M), bp_scale P^T (w h_1)]
-    rc = back_project_colw(m->g, h_out + 1 * NP, m->wred, m->tvol, 1, 0, st);
+    rc = back_project_colw(m->g, h_out + 1 * NP, m->wred, bp, 1, 0, st);
     if (rc) return rc;
     Planes pp{};
     for (int c = 0; c < M; ++c) { pp.p[c] = f_in + c * NV; pp.s[c] = 1.f; }
-    pp.p[M] = m->tvol; pp.s[M] = m->bp_scale;
+    pp.p[M] = bp; pp.s[M] = m->bp_scale;
     k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
     if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) return rc;
     if ((rc = conv_fwd(m, Lp[1], m->b1, 32, PRIM_DIMS, 0, m->b2, nullptr, 0, st))) return rc;
@@ -312,6 +317,8 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     al((void **)&m->tproj, sizeof(float) * NP);
     al((void **)&m->tproj2, sizeof(float) * NP);
     al((void **)&m->tvol, sizeof(float) * NV);
+    al((void **)&m->pf_saved, sizeof(float) * d.n_iter * NP);
+    al((void **)&m->bp_saved, sizeof(float) * d.n_iter * NV);
     al((void **)&m->din, sizeof(__nv_bfloat16) * NP * 8);
     al((void **)&m->a1, sizeof(__nv_bfloat16) * NP * 32);
     al((void **)&m->a2, sizeof(__nv_bfloat16) * NP * 32);
@@ -366,8 +373,8 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
 extern "C" void lpd_destroy(cbct_lpd *m) {
     if (!m) return;
     cudaDeviceSynchronize();
-    void *ptrs[] = {m->params, m->grads, m->adam_m, m->adam_v, m->wred, m->f, m->h, m->y, m->tproj, m->tproj2,
-                    m->tvol, m->din, m->a1, m->a2, m->pin, m->b1, m->b2, m->g32a, m->g32b, m->gsmall, m->gf, m->gh,
+    void *ptrs[] = {m->pf_saved, m->bp_saved, m->params, m->grads, m->adam_m, m->adam_v, m->wred, m->f, m->h,
+                    m->y, m->tproj, m->tproj2, m->tvol, m->din, m->a1, m->a2, m->pin, m->b1, m->b2, m->g32a, m->g32b, m->gsmall, m->gf, m->gh,
                     m->status};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -403,8 +410,10 @@ static int lpd_forward_impl(cbct_lpd *m, const float *y, const float *x0, const 
     }
     for (int n = 0; n < N; ++n) {
         const int si = save_for_backward ? n : 0, so = save_for_backward ? n + 1 : 0;
+        float *pf = save_for_backward ? m->pf_saved + (long long)n * NP : m->tproj;
+        float *bp = save_for_backward ? m->bp_saved + (long long)n * NV : m->tvol;
         int rc = lpd_iter_fwd(m, n, m->f + (long long)si * M * NV, m->h + (long long)si * M * NP,
-                              m->f + (long long)so * M * NV, m->h + (long long)so * M * NP, st);
+                              m->f + (long long)so * M * NV, m->h + (long long)so * M * NP, pf, bp, st);
         if (rc) return rc;
     }
     const long long last = save_for_backward ? N : 0;
@@ -460,23 +469,20 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
     int rc = 0;
     for (int n = N - 1; n >= 0 && rc == 0; --n) {
         const float *f_n = m->f + (long long)n * M * NV, *h_n = m->h + (long long)n * M * NP;
-        const float *h_n1 = m->h + (long long)(n + 1) * M * NP;
         const LayerSpec *Ld = &m->layers[6 * n], *Lp = &m->layers[6 * n + 3];
         float *dW = m->grads;
-        // recompute the dual block input and activations of iteration n
-        if ((rc = forward_project(m->g, f_n + NV, m->tproj, 1, 0, sv))) break;
+        // recompute the dual block input and activations of iteration n (P f_1 kept)
         Planes pl{};
         for (int c = 0; c < M; ++c) { pl.p[c] = h_n + c * NP; pl.s[c] = 1.f; }
-        pl.p[M] = m->tproj; pl.s[M] = m->d.mu_ref;
+        pl.p[M] = m->pf_saved + (long long)n * NP; pl.s[M] = m->d.mu_ref;
         pl.p[M + 1] = m->y; pl.s[M + 1] = 1.f;
         k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
         if ((rc = conv_fwd(m, Ld[0], m->din, 8, DUAL_DIMS, 0, m->a1, nullptr, 0, st))) break;
         if ((rc = conv_fwd(m, Ld[1], m->a1, 32, DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
-        // recompute the primal block input and activations (needs h_{n+1}, saved)
-        if ((rc = back_project_colw(m->g, h_n1 + NP, m->wred, m->tvol, 1, 0, st))) break;
+        // recompute the primal block input and activations (P^T (w h_{n+1}) kept)
         Planes pp{};
         for (int c = 0; c < M; ++c) { pp.p[c] = f_n + c * NV; pp.s[c] = 1.f; }
-        pp.p[M] = m->tvol; pp.s[M] = m->bp_scale;
+        pp.p[M] = m->bp_saved + (long long)n * NV; pp.s[M] = m->bp_scale;
         k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
         if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) break;
         if ((rc = conv_fwd(m, Lp[1], m->b1, 32, PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;

@@ -79,6 +79,7 @@ def main(argv=None):
     ap.add_argument("--n-iter", type=int, default=8)
     ap.add_argument("--pdhg-iters", type=int, default=100)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--save", default=None, help="write the trained parameters (.npy)")
     args = ap.parse_args(argv)
 
     torch.cuda.set_device(0)
@@ -116,6 +117,7 @@ def main(argv=None):
     model = LPD(geom, n_iter=args.n_iter, seed=1)
     t_train = time.time()
     step = 0
+    est_steps = 10 ** 9
     losses = []
     order = np.random.default_rng(0)
     done = False
@@ -130,8 +132,15 @@ def main(argv=None):
                 loss, gr = masked_mse(out, x, V, 0.5)
                 model.backward(gr)
                 tot += loss.item()
-            # loss in units of mu_ref^2 (O(1)); linear warm-up of the learning rate
-            lr = args.lr * min(1.0, (step + 1) / max(1, args.warmup))
+            # loss in units of mu_ref^2 (O(1)); linear warm-up, then cosine decay over the
+            # number of steps the time budget allows (estimated after the warm-up)
+            if step == args.warmup and step > 0:
+                est_steps = max(step + 1, int(args.minutes * 60 / ((time.time() - t_train) / step)))
+            if step < args.warmup:
+                lr = args.lr * (step + 1) / max(1, args.warmup)
+            else:
+                lr = args.lr * 0.5 * (1.0 + math.cos(math.pi * min(1.0, (step - args.warmup) /
+                                                                   max(1, est_steps - args.warmup))))
             model.adam_step(lr, grad_scale=1.0 / (args.batch * model.mu_ref ** 2))
             step += 1
             losses.append(tot / args.batch)
@@ -143,6 +152,8 @@ def main(argv=None):
                 break
         if done:
             break
+    if args.save:
+        np.save(args.save, model.get_params())
     log["training"] = {"steps": step, "effective_batch": args.batch, "lr": args.lr, "warmup": args.warmup,
                        "seconds": time.time() - t_train, "loss_first": losses[0] if losses else None,
                        "loss_last8": float(np.mean(losses[-8:])) if losses else None}

@@ -7,7 +7,7 @@ GPU library computes; it never imports or links the GPU library.
 The C part (`oracle.c`) holds the projector pair, geometry, field-of-view
 tensor, redundancy weight, FDK, PDHG-TV, Philox/Poisson simulation and phantom
 voxeliser; `lpd_ref.py` holds the learned primal-dual reference in plain
-PyTorch CPU FP64.
+PyTorch CPU FP64 and `multiscale_ref.py` the two-level scheme built on it.
 """
 from __future__ import annotations
 

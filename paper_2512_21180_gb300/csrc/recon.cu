@@ -67,20 +67,31 @@ __global__ void k_fdk_ramp(const float *__restrict__ q0, float *__restrict__ q, 
     }
 }
 
-// vol(P) (+)= (2 pi / n_angles) sum_k (sid / U)^2 bilinear(q_k, u(P), v(P))
-__global__ void k_fdk_backproject(const float *__restrict__ q, const double2 *__restrict__ cs, float *__restrict__ vol,
-                                  int nx, int ny, int nz, int na, int nue, int nv, int lo, int nu, float vx, float vy,
-                                  float vz, float cx, float cy, float cz, float sid, float sdd, float du, float dv,
-                                  float uoff, float voff, int accumulate) {
+// vol(P) (+)= (2 pi / n_angles) sum_k (sid / U)^2 bilinear(q_k, u(P), v(P)). A thread
+// owns a run of kFdkZ voxels along z: the source distance U, the magnification, the
+// detector column and the weight depend only on (x, y, angle) and are computed once
+// per angle; the detector row is linear in z.
+constexpr int kFdkZ = 8;
+__global__ void __launch_bounds__(256) k_fdk_backproject(const float *__restrict__ q, const double2 *__restrict__ cs,
+                                                         float *__restrict__ vol, int nx, int ny, int nz, int na, int nue,
+                                                         int nv, int lo, int nu, float vx, float vy, float vz, float cx,
+                                                         float cy, float cz, float sid, float sdd, float du, float dv,
+                                                         float uoff, float voff, int accumulate) {
     const int ix = blockIdx.x * 32 + threadIdx.x, iy = blockIdx.y * 8 + threadIdx.y;
-    const int iz = blockIdx.z % nz, b = blockIdx.z / nz;
+    const int nzr = (nz + kFdkZ - 1) / kFdkZ;
+    const int iz0 = (blockIdx.z % nzr) * kFdkZ, b = blockIdx.z / nzr;
     if (ix >= nx || iy >= ny) return;
     const float px = (ix - 0.5f * (nx - 1)) * vx + cx;
     const float py = (iy - 0.5f * (ny - 1)) * vy + cy;
-    const float pz = (iz - 0.5f * (nz - 1)) * vz + cz;
+    float pz[kFdkZ];
+#pragma unroll
+    for (int j = 0; j < kFdkZ; ++j) pz[j] = (iz0 + j - 0.5f * (nz - 1)) * vz + cz;
     const float hu = 0.5f * (nu - 1) + lo, hv = 0.5f * (nv - 1);
+    const float idv = 1.0f / dv;
     const float *qb = q + (long long)b * na * nv * nue;
-    float acc = 0.f;
+    float acc[kFdkZ];
+#pragma unroll
+    for (int j = 0; j < kFdkZ; ++j) acc[j] = 0.f;
     for (int k = 0; k < na; ++k) {
         const double2 t = cs[k];
         const float c = (float)t.x, s = (float)t.y;
@@ -88,24 +99,36 @@ __global__ void k_fdk_backproject(const float *__restrict__ q, const double2 *__
         if (!(U > 0.f)) continue;
         const float m = sdd / U;
         const float fu = (m * (-px * s + py * c) - uoff) / du + hu;
-        const float fv = (m * pz - voff) / dv + hv;
-        const float u0 = floorf(fu), v0 = floorf(fv);
-        const float au = fu - u0, av = fv - v0;
-        const int ju = (int)u0, jv = (int)v0;
-        if (ju < -1 || ju >= nue || jv < -1 || jv >= nv) continue;
+        const float u0 = floorf(fu), au = fu - u0;
+        const int ju = (int)u0;
+        if (ju < -1 || ju >= nue) continue;
+        const float r = sid / U, w = r * r;
         const float *qk = qb + (long long)k * nv * nue;
-        const bool u0k = ju >= 0, u1k = ju + 1 < nue, v0k = jv >= 0, v1k = jv + 1 < nv;
-        const float q00 = (u0k && v0k) ? __ldg(qk + (long long)jv * nue + ju) : 0.f;
-        const float q10 = (u1k && v0k) ? __ldg(qk + (long long)jv * nue + ju + 1) : 0.f;
-        const float q01 = (u0k && v1k) ? __ldg(qk + (long long)(jv + 1) * nue + ju) : 0.f;
-        const float q11 = (u1k && v1k) ? __ldg(qk + (long long)(jv + 1) * nue + ju + 1) : 0.f;
-        const float a0 = fmaf(au, q10 - q00, q00), a1 = fmaf(au, q11 - q01, q01);
-        const float r = sid / U;
-        acc = fmaf(r * r, fmaf(av, a1 - a0, a0), acc);
+        const bool u0k = ju >= 0, u1k = ju + 1 < nue;
+#pragma unroll
+        for (int j = 0; j < kFdkZ; ++j) {
+            const float fv = (m * pz[j] - voff) * idv + hv;
+            const float v0 = floorf(fv), av = fv - v0;
+            const int jv = (int)v0;
+            if (jv < -1 || jv >= nv) continue;
+            const bool v0k = jv >= 0, v1k = jv + 1 < nv;
+            const float *r0 = qk + (long long)jv * nue + ju;
+            const float q00 = (u0k && v0k) ? __ldg(r0) : 0.f;
+            const float q10 = (u1k && v0k) ? __ldg(r0 + 1) : 0.f;
+            const float q01 = (u0k && v1k) ? __ldg(r0 + nue) : 0.f;
+            const float q11 = (u1k && v1k) ? __ldg(r0 + nue + 1) : 0.f;
+            const float a0 = fmaf(au, q10 - q00, q00), a1 = fmaf(au, q11 - q01, q01);
+            acc[j] = fmaf(w, fmaf(av, a1 - a0, a0), acc[j]);
+        }
     }
-    acc *= 6.28318530717958647f / na;
-    float *o = vol + (((long long)b * nz + iz) * ny + iy) * nx + ix;
-    *o = accumulate ? *o + acc : acc;
+    const float sc = 6.28318530717958647f / na;
+#pragma unroll
+    for (int j = 0; j < kFdkZ; ++j) {
+        if (iz0 + j < nz) {
+            float *o = vol + (((long long)b * nz + iz0 + j) * ny + iy) * nx + ix;
+            *o = accumulate ? *o + acc[j] * sc : acc[j] * sc;
+        }
+    }
 }
 
 // ---- PDHG-TV pieces -------------------------------------------------------------------
@@ -251,7 +274,7 @@ extern "C" int cbct_fdk(const cbct_geom *g, const float *proj, float *vol, int b
                                                         d.v_offset, d.sdd);
         if (smem > 48 * 1024) cudaFuncSetAttribute(k_fdk_ramp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_fdk_ramp<<<(unsigned)rows, 256, smem, st>>>(q0, q, nue, (float)(d.du * d.sid / d.sdd));
-        dim3 grd((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz * batch);
+        dim3 grd((d.nx + 31) / 32, (d.ny + 7) / 8, ((d.nz + kFdkZ - 1) / kFdkZ) * batch);
         k_fdk_backproject<<<grd, dim3(32, 8), 0, st>>>(
             q, dcs, vol, d.nx, d.ny, d.nz, d.n_angles, nue, d.nv, lo, d.nu, (float)d.vox[0], (float)d.vox[1],
             (float)d.vox[2], (float)d.center[0], (float)d.center[1], (float)d.center[2], (float)d.sid, (float)d.sdd,

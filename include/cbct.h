@@ -338,6 +338,13 @@ int lpd_backward_latent(cbct_lpd *m, const float *grad_x, const float *grad_fN, 
 
 int lpd_zero_grad(cbct_lpd *m, void *stream);
 
+/* Global gradient-norm clipping before lpd_adam_step (unrolled networks are trained
+ * with it; without it the lpd128 training diverged after ~190 steps): n = ||grad_scale
+ * * g|| (FP64, fixed-order reduction); g *= min(1, max_norm / n), or g = 0 when n is not
+ * finite (the step is skipped). norm_out (host, nullable) receives n; giving it
+ * synchronises the stream. Errors: CBCT_EINVAL for max_norm <= 0. */
+int lpd_clip_grads(cbct_lpd *m, float max_norm, float grad_scale, double *norm_out, void *stream);
+
 /* Adam (Kingma & Ba) on the gradient buffer times grad_scale, bias-corrected for step
  * number `step` (>= 1). */
 int lpd_adam_step(cbct_lpd *m, float lr, float beta1, float beta2, float eps, int step, float grad_scale,

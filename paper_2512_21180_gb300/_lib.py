@@ -76,6 +76,7 @@ SIGNATURES = {
     "cbct_resample_down": (I32, [P, I64, I32, I32, I32, I32, I32, I32, I32, F32, P, P]),
     "cbct_resample_up": (I32, [P, I64, I32, I32, I32, I32, I32, I32, P, P]),
     "lpd_zero_grad": (I32, [P, P]),
+    "lpd_clip_grads": (I32, [P, F32, F32, P, P]),
     "lpd_adam_step": (I32, [P, F32, F32, F32, F32, I32, F32, P]),
     "lpd_set_params": (I32, [P, P, I64]),
     "lpd_get_params": (I32, [P, P, I64]),

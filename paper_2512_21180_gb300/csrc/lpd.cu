@@ -62,6 +62,7 @@ struct cbct_lpd {
     // projector outputs of each iteration kept by a training forward pass (so the
     // backward does not recompute them): P f_1 [n_iter][nproj], P^T (w h_1) [n_iter][nvox]
     float *pf_saved = nullptr, *bp_saved = nullptr;
+    double *clip = nullptr;  // gradient-norm scratch: per-block partial sums, then norm and factor
     __nv_bfloat16 *din = nullptr, *a1 = nullptr, *a2 = nullptr, *pin = nullptr, *b1 = nullptr, *b2 = nullptr;
     __nv_bfloat16 *g32a = nullptr, *g32b = nullptr, *gsmall = nullptr;  // gradient buffers
     float *gf = nullptr, *gh = nullptr;  // [n_mem + 1][nvox], [n_mem + 2][nproj]
@@ -318,6 +319,7 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     al((void **)&m->tproj2, sizeof(float) * NP);
     al((void **)&m->tvol, sizeof(float) * NV);
     al((void **)&m->pf_saved, sizeof(float) * d.n_iter * NP);
+    al((void **)&m->clip, sizeof(double) * (608 + 2));
     al((void **)&m->bp_saved, sizeof(float) * d.n_iter * NV);
     al((void **)&m->din, sizeof(__nv_bfloat16) * NP * 8);
     al((void **)&m->a1, sizeof(__nv_bfloat16) * NP * 32);
@@ -373,7 +375,7 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
 extern "C" void lpd_destroy(cbct_lpd *m) {
     if (!m) return;
     cudaDeviceSynchronize();
-    void *ptrs[] = {m->pf_saved, m->bp_saved, m->params, m->grads, m->adam_m, m->adam_v, m->wred, m->f, m->h,
+    void *ptrs[] = {m->clip, m->pf_saved, m->bp_saved, m->params, m->grads, m->adam_m, m->adam_v, m->wred, m->f, m->h,
                     m->y, m->tproj, m->tproj2, m->tvol, m->din, m->a1, m->a2, m->pin, m->b1, m->b2, m->g32a, m->g32b, m->gsmall, m->gf, m->gh,
                     m->status};
     for (void *p : ptrs)
@@ -552,6 +554,60 @@ extern "C" int lpd_backward_latent(cbct_lpd *m, const float *grad_x, const float
 extern "C" int lpd_zero_grad(cbct_lpd *m, void *stream) {
     if (!m) return fail(CBCT_EINVAL, "lpd_zero_grad: NULL model");
     CBCT_CUDA_TRY(cudaMemsetAsync(m->grads, 0, sizeof(float) * m->nparams, (cudaStream_t)stream));
+    return 0;
+}
+
+namespace {
+
+constexpr int kNormBlocks = 608;
+
+// partial[blk] = sum of g^2 over the block's grid-stride share (FP64, tree in shared
+// memory: a fixed order)
+__global__ void __launch_bounds__(256) k_sumsq_blocks(const float *__restrict__ g, long long n,
+                                                      double *__restrict__ partial) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+        s += (double)g[i] * g[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// out[0] = ||grad_scale g||, out[1] = clip factor min(1, max_norm / out[0]) (0 if not finite)
+__global__ void k_clip_factor(const double *__restrict__ partial, int nblk, double grad_scale, double max_norm,
+                              double *__restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[b];
+    const double nrm = sqrt(s) * fabs(grad_scale);
+    out[0] = nrm;
+    out[1] = isfinite(nrm) ? (nrm > max_norm ? max_norm / nrm : 1.0) : 0.0;
+}
+
+__global__ void k_scale_by_factor(float *__restrict__ g, long long n, const double *__restrict__ f) {
+    const float k = (float)f[1];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        g[i] = k == 0.f ? 0.f : g[i] * k;
+}
+
+}  // namespace
+
+extern "C" int lpd_clip_grads(cbct_lpd *m, float max_norm, float grad_scale, double *norm_out, void *stream) {
+    if (!m || !(max_norm > 0.f)) return fail(CBCT_EINVAL, "lpd_clip_grads: invalid argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    k_sumsq_blocks<<<kNormBlocks, 256, 0, st>>>(m->grads, m->nparams, m->clip);
+    k_clip_factor<<<1, 32, 0, st>>>(m->clip, kNormBlocks, grad_scale, max_norm, m->clip + kNormBlocks);
+    k_scale_by_factor<<<grid_n(m->nparams), 256, 0, st>>>(m->grads, m->nparams, m->clip + kNormBlocks);
+    CBCT_LAUNCH_CHECK("lpd_clip_grads");
+    if (norm_out) {
+        CBCT_CUDA_TRY(cudaMemcpyAsync(norm_out, m->clip + kNormBlocks, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CBCT_CUDA_TRY(cudaStreamSynchronize(st));
+    }
     return 0;
 }
 

@@ -296,26 +296,14 @@ __global__ void __launch_bounds__(kThreads3, 2) k_backproject_v3(GeomDev g, cons
                             float qf = fma_rn(di, dqz, qcz) - (float)(z0 - 1 + m);
                             const float *pp = Pk + (long long)va * nu + u;
                             const int n = ve - va;
-                            // two interleaved row chains (independent loads and sums)
-                            float S0b = 0.f, S1b = 0.f;
-                            int rr = 0;
-#pragma unroll 2
-                            for (; rr + 2 <= n; rr += 2) {
-                                const float p0 = __ldg(pp), p1 = __ldg(pp + nu);
-                                pp += 2 * nu;
-                                S0 += p0;
-                                S1 = fmaf(p0, qf, S1);
-                                S0b += p1;
-                                S1b = fmaf(p1, qf + step, S1b);
-                                qf += 2.f * step;
+#pragma unroll 4
+                            for (int rr = 0; rr < n; ++rr) {
+                                const float p = __ldg(pp);
+                                pp += nu;
+                                S0 += p;
+                                S1 = fmaf(p, qf, S1);
+                                qf += step;
                             }
-                            if (rr < n) {
-                                const float p0 = __ldg(pp);
-                                S0 += p0;
-                                S1 = fmaf(p0, qf, S1);
-                            }
-                            S0 += S0b;
-                            S1 += S1b;
                         }
                         // voxel z0 - 1 + m: upper share of interval m - 1, lower share of interval m
                         if (m >= 1) {

@@ -74,7 +74,8 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=2)
     ap.add_argument("--minutes", type=float, default=20.0, help="training time budget")
     ap.add_argument("--batch", type=int, default=8, help="effective batch (gradient accumulation)")
-    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr", type=float, default=5e-4)
+    ap.add_argument("--clip", type=float, default=1.0, help="global gradient-norm clip (loss in mu_ref^2 units)")
     ap.add_argument("--warmup", type=int, default=40, help="linear learning-rate warm-up steps")
     ap.add_argument("--n-iter", type=int, default=8)
     ap.add_argument("--pdhg-iters", type=int, default=100)
@@ -119,6 +120,7 @@ def main(argv=None):
     step = 0
     est_steps = 10 ** 9
     losses = []
+    norms = []
     order = np.random.default_rng(0)
     done = False
     for ep in range(args.epochs):
@@ -141,12 +143,15 @@ def main(argv=None):
             else:
                 lr = args.lr * 0.5 * (1.0 + math.cos(math.pi * min(1.0, (step - args.warmup) /
                                                                    max(1, est_steps - args.warmup))))
-            model.adam_step(lr, grad_scale=1.0 / (args.batch * model.mu_ref ** 2))
+            gscale = 1.0 / (args.batch * model.mu_ref ** 2)
+            norms.append(model.clip_grads(args.clip, grad_scale=gscale))
+            model.adam_step(lr, grad_scale=gscale)
             step += 1
             losses.append(tot / args.batch)
             if step % 8 == 0:
-                print(f"epoch {ep} step {step} loss {np.mean(losses[-8:]):.3e} "
-                      f"({time.time() - t_train:.0f} s)", file=sys.stderr, flush=True)
+                print(f"epoch {ep} step {step} loss {np.mean(losses[-8:]):.3e} grad norm "
+                      f"{np.median(norms[-8:]):.3e} lr {lr:.2e} ({time.time() - t_train:.0f} s)",
+                      file=sys.stderr, flush=True)
             if time.time() - t_train > args.minutes * 60:
                 done = True
                 break
@@ -155,6 +160,7 @@ def main(argv=None):
     if args.save:
         np.save(args.save, model.get_params())
     log["training"] = {"steps": step, "effective_batch": args.batch, "lr": args.lr, "warmup": args.warmup,
+                       "clip": args.clip, "grad_norm_median": float(np.median(norms)) if norms else None,
                        "seconds": time.time() - t_train, "loss_first": losses[0] if losses else None,
                        "loss_last8": float(np.mean(losses[-8:])) if losses else None}
 

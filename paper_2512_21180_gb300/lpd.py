@@ -121,6 +121,14 @@ class LPD:
     def zero_grad(self):
         check(_lib.load().lpd_zero_grad(self.handle, _st()), "lpd_zero_grad")
 
+    def clip_grads(self, max_norm: float, grad_scale: float = 1.0) -> float:
+        """Scales the accumulated gradient so that ||grad_scale g|| <= max_norm (zero if
+        the norm is not finite); returns the norm before clipping."""
+        out = ctypes.c_double(0.0)
+        check(_lib.load().lpd_clip_grads(self.handle, float(max_norm), float(grad_scale), ctypes.byref(out), _st()),
+              "lpd_clip_grads")
+        return float(out.value)
+
     def adam_step(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
                   grad_scale: float = 1.0):
         self.step += 1

@@ -102,3 +102,36 @@ def test_lpd_training_reduces_loss(O, M):
         model.adam_step(1e-3, grad_scale=1.0 / len(data))
     l1 = loss_all()
     assert np.isfinite(l1) and l1 < 0.7 * l0, (l0, l1)
+
+
+def test_gradient_clipping(O, M):
+    """lpd_clip_grads: the returned norm is ||scale g||, the clipped gradient has norm
+    max_norm, a small gradient is untouched, a non-finite one becomes zero."""
+    P, L = M
+    geom = P.Geometry(GEOM)
+    model = L.LPD(geom, n_iter=1, seed=2)
+    model.zero_grad()
+    x = torch.rand(geom.vol_shape, device="cuda")
+    y = torch.rand(geom.proj_shape, device="cuda")
+    model.forward(y, x, save_for_backward=True)
+    model.backward(torch.rand(geom.vol_shape, device="cuda"))
+    g0 = model.grads().astype(np.float64)
+    scale = 0.25
+    n0 = float(np.linalg.norm(g0) * scale)
+    n = model.clip_grads(1e30, grad_scale=scale)
+    assert abs(n - n0) <= 1e-6 * n0
+    assert np.array_equal(model.grads(), g0.astype(np.float32))      # below the limit: unchanged
+    n = model.clip_grads(0.5 * n0, grad_scale=scale)
+    g1 = model.grads().astype(np.float64)
+    assert abs(np.linalg.norm(g1) * scale - 0.5 * n0) <= 1e-5 * n0
+    model_params = model.get_params()
+    # a non-finite gradient: set through a backward of a non-finite upstream gradient
+    model.zero_grad()
+    model.forward(y, x, save_for_backward=True)
+    gx = torch.rand(geom.vol_shape, device="cuda")
+    gx[0, 0, 0] = float("inf")
+    model.backward(gx)
+    n = model.clip_grads(1.0)
+    assert not np.isfinite(n)
+    assert not np.any(model.grads())
+    assert np.array_equal(model.get_params(), model_params)

@@ -182,7 +182,8 @@ __global__ void k_pdhg_primal(float *__restrict__ x, float *__restrict__ xb, con
 }
 
 // r = p - y
-__global__ void k_sub(const float *__restrict__ p, const float *__restrict__ y, float *__restrict__ r, long long n) {
+// r = p - y elementwise; r may alias p (in-place residual), so no restrict on those two
+__global__ void k_sub(const float *p, const float *__restrict__ y, float *r, long long n) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
         r[e] = p[e] - y[e];
 }

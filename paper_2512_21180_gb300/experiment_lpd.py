@@ -66,6 +66,28 @@ def timed(fn, reps: int = 3):
     return r, e0.elapsed_time(e1) / reps / 1e3
 
 
+def profile_pass(args) -> int:
+    torch.cuda.set_device(0)
+    geom = Geometry(I.geometry(WORKLOAD))
+    V = ops.fov(geom)
+    x = ops.phantom(geom, I.phantom_params(WORKLOAD, 30_000))
+    _, y = ops.simulate(geom, x, I0, seed=1)
+    x0 = ops.fdk(geom, y)[0]
+    model = LPD(geom, n_iter=args.n_iter, seed=1)
+    for _ in range(2):
+        model.forward(y[0], x0)
+    torch.cuda.synchronize()
+    model.forward(y[0], x0)
+    out = model.forward(y[0], x0, save_for_backward=True)
+    model.zero_grad()
+    _, gr = masked_mse(out, x, V, 0.5)
+    model.backward(gr)
+    model.adam_step(1e-4)
+    torch.cuda.synchronize()
+    print("profile pass done", flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=512)
@@ -81,7 +103,12 @@ def main(argv=None):
     ap.add_argument("--pdhg-iters", type=int, default=100)
     ap.add_argument("--out", default=None)
     ap.add_argument("--save", default=None, help="write the trained parameters (.npy)")
+    ap.add_argument("--profile", action="store_true",
+                    help="only run 2 warm-up passes, then one inference and one training step on one phantom "
+                         "(a short command for profilers)")
     args = ap.parse_args(argv)
+    if args.profile:
+        return profile_pass(args)
 
     torch.cuda.set_device(0)
     g = I.geometry(WORKLOAD)

@@ -130,7 +130,7 @@ def main(argv=None):
     gam = nP / math.sqrt(12.0)
     nK = ops.opnorm(geom, gam, 30)
     sig = tau = 0.99 / nK
-    lams = [1e-3, 3e-3, 1e-2, 3e-2, 1e-1, 3e-1, 1.0]
+    lams = [1e-3, 3e-3, 1e-2, 3e-2, 1e-1, 3e-1, 1.0, 3.0, 10.0]
     best = None
     for lam in lams:
         ps = [psnr(ops.pdhg(geom, y, x0, args.pdhg_iters, lam, gam, sig, tau)[0], x, full) for x, y, x0 in tune]

@@ -135,3 +135,31 @@ def test_gradient_clipping(O, M):
     assert not np.isfinite(n)
     assert not np.any(model.grads())
     assert np.array_equal(model.get_params(), model_params)
+
+
+def test_trained_network_gains_over_fdk(M):
+    """The committed weights (8 iterations, trained on 512 phantoms of the learned
+    workload by `experiment_lpd`) reconstruct unseen test phantoms far better than
+    the FDK_w start the network is given."""
+    import math
+    import os
+    P, L = M
+    from paper_2512_21180_gb300 import ops
+    path = os.path.join(os.path.dirname(L.__file__), "weights", "lpd128_8iter.npy")
+    g = I.geometry("lpd128")
+    geom = P.Geometry(g)
+    model = L.LPD(geom, n_iter=8)
+    model.set_params(np.load(path))
+    full = ops.fov(geom) >= 0.5
+
+    def psnr(a, ref):
+        mse = torch.mean((a[full] - ref[full]).double() ** 2).item()
+        return 10 * math.log10(ref[full].max().item() ** 2 / mse)
+    gains = []
+    for j, s in enumerate((30_000, 30_001, 30_002)):   # test seeds, disjoint from training (10_000+)
+        x = ops.phantom(geom, I.phantom_params("lpd128", s))
+        _, y = ops.simulate(geom, x, 1e5, seed=90_000 + j)
+        x0 = ops.fdk(geom, y)[0]
+        out = model.forward(y[0], x0)
+        gains.append(psnr(out, x) - psnr(x0, x))
+    assert min(gains) > 8.0, gains

@@ -387,7 +387,7 @@ def report(args, geom, world, S_fwd, samples_step, value, ms, ms_fwd, ms_adj, e2
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from one ncu
 # --set full capture of the clinical workload with the current kernels; None elsewhere
 # and whenever the kernel changes after the capture.
-MEASURED_TRAFFIC = {"clinical": {"back_project": 686.565e6 + 38.120e6, "forward_project": 137.302e6 + 281.002e6}}
+MEASURED_TRAFFIC = {"clinical": {"back_project": None, "forward_project": 137.302e6 + 281.002e6}}
 
 
 def launches_per_step(geom) -> int:
@@ -395,7 +395,7 @@ def launches_per_step(geom) -> int:
     staged forward, 2 for the segment gather, +1 when its angles are split)."""
     nx, ny, nz = geom.g["n"]
     bricks = -(-nx // 16) * -(-ny // 16) * -(-nz // 16)
-    parts = min(16, max(1, -(-152 * 6 // bricks)), geom.g["n_angles"])
+    parts = min(16, max(1, -(-152 * 9 // bricks)), geom.g["n_angles"])
     return 3 + 2 + (1 if parts > 1 else 0)
 
 

@@ -208,12 +208,20 @@ __global__ void __launch_bounds__(256) k_backproject(GeomDev g, const T *__restr
 // s + 1. SB reaches the thread of segment s + 1 through shared memory and each
 // voxel adds SA + SB of its two segments to its shared accumulator, always in the
 // same order, so the result does not depend on scheduling.
+// The kernel is bound by load latency, which shapes the loops: a thread first
+// narrows its candidate columns to the first and last column of its segment (so
+// the lanes of a warp run their useful columns in the same iterations); a row's
+// z-coordinate is the affine q_z(v) = voff + v step of the row index (rz(v) =
+// rz_0 + v EV_z), so no table load sits between two intervals; and the rows of
+// an interval go through a fixed block of five predicated loads (3 to 5 rows per
+// interval at these magnifications) plus a loop for longer intervals, which makes
+// the 17-interval sweep straight-line code whose loads overlap.
 constexpr int kB3 = 16, kZ3 = 16, kThreads3 = 288;
 constexpr int kVacc3 = kZ3 * kB3 * (kB3 + 1);  // [z][y][x], y stride 17 (bank-conflict free both ways)
 constexpr int kSbuf3 = kB3 * kB3 * (kZ3 + 1);  // [voxel][plane][z], plane stride 17
 constexpr size_t kSmem3 = sizeof(float) * (kVacc3 + 2 * kSbuf3);
 
-__global__ void __launch_bounds__(kThreads3, 2) k_backproject_v3(GeomDev g, const float *__restrict__ pw,
+__global__ void __launch_bounds__(kThreads3, 3) k_backproject_v3(GeomDev g, const float *__restrict__ pw,
                                                                  float *__restrict__ vol, int accumulate,
                                                                  int nparts, float *__restrict__ partial) {
     extern __shared__ float sm3[];
@@ -230,7 +238,7 @@ __global__ void __launch_bounds__(kThreads3, 2) k_backproject_v3(GeomDev g, cons
     const int k_begin = (int)((long long)g.na * part / nparts), k_end = (int)((long long)g.na * (part + 1) / nparts);
     for (int e = tid; e < kVacc3; e += kThreads3) vacc[e] = 0.f;
     const float Sz = g.Sz;
-    const float rz0 = g.rz32[0], drz = nv > 1 ? g.rz32[1] - g.rz32[0] : 1.0f;
+    const float rz0 = g.rz32[0], drz = g.f32[0].EV[2];
     const float *PB = pw + (long long)b * g.na * nv * nu;
     int pass = 0;
 
@@ -269,6 +277,18 @@ __global__ void __launch_bounds__(kThreads3, 2) k_backproject_v3(GeomDev g, cons
                     const float vlo = (rlo - rz0) / drz - 2.f, vhi = (rhi - rz0) / drz + 2.f;
                     if (!(tmax > 0.f) || vhi < 0.f || vlo > (float)(nv - 1)) uhi = ulo - 1;
                 }
+                {  // first and last column of the segment
+                    int ua = uhi + 1, ub = uhi;
+#pragma unroll 1
+                    for (int u = ulo; u <= uhi; ++u) {
+                        const ColT<float> c = col_of<float>(g, k, u);
+                        const float t = fma_rn(di, c.inv, c.tc);
+                        const float qb = fma_rn(di, c.dqb, c.qcb);
+                        if (t > 0.f && t < 1.f && floorf(qb) == (float)s) { ua = min(ua, u); ub = u; }
+                    }
+                    ulo = ua;
+                    uhi = ub;
+                }
 #pragma unroll 1
                 for (int u = ulo; u <= uhi; ++u) {
                     const ColT<float> c = col_of<float>(g, k, u);
@@ -291,18 +311,20 @@ __global__ void __launch_bounds__(kThreads3, 2) k_backproject_v3(GeomDev g, cons
                         const int ve = row_above(m + 1);
                         float S0 = 0.f, S1 = 0.f;
                         if (va < ve) {
-                            float dqz, qcz;
-                            ray_row(g, c, rz_of<float>(g, va), dqz, qcz);
-                            float qf = fma_rn(di, dqz, qcz) - (float)(z0 - 1 + m);
+                            float qf = fmaf((float)va, step, voff) - (float)(z0 - 1 + m);
                             const float *pp = Pk + (long long)va * nu + u;
                             const int n = ve - va;
-#pragma unroll 4
-                            for (int rr = 0; rr < n; ++rr) {
-                                const float p = __ldg(pp);
-                                pp += nu;
+#pragma unroll
+                            for (int rr = 0; rr < 5; ++rr) {
+                                const float p = rr < n ? __ldg(pp + rr * nu) : 0.f;
                                 S0 += p;
-                                S1 = fmaf(p, qf, S1);
-                                qf += step;
+                                S1 = fmaf(p, fmaf((float)rr, step, qf), S1);
+                            }
+#pragma unroll 1
+                            for (int rr = 5; rr < n; ++rr) {
+                                const float p = __ldg(pp + rr * nu);
+                                S0 += p;
+                                S1 = fmaf(p, fmaf((float)rr, step, qf), S1);
                             }
                         }
                         // voxel z0 - 1 + m: upper share of interval m - 1, lower share of interval m
@@ -461,8 +483,8 @@ static int backward_impl(const cbct_geom *g, const T *proj, T *vol, int batch, i
             if (g->axis_contiguous) {
                 const int nzb = (d.n[2] + kZ3 - 1) / kZ3;
                 const long long base = (long long)((d.n[0] + kB3 - 1) / kB3) * ((d.n[1] + kB3 - 1) / kB3) * nzb * batch;
-                // split the angles so that about 6 CTAs per SM are available
-                int nparts = (int)std::min<long long>(16, std::max<long long>(1, (152LL * 6 + base - 1) / base));
+                // split the angles so that about 9 CTAs per SM are available (3 resident, 3 waves)
+                int nparts = (int)std::min<long long>(16, std::max<long long>(1, (152LL * 9 + base - 1) / base));
                 nparts = std::min(nparts, d.na);
                 while (nparts > 1 && (long long)nzb * batch * nparts > 65535) --nparts;
                 if ((long long)nzb * batch * nparts > 65535) e = cudaErrorInvalidConfiguration;

@@ -4,21 +4,22 @@
 // "same" padding. BF16 operands, FP32 accumulation.
 //
 // Forward (and input-gradient) convolution = implicit GEMM on the fifth-generation
-// tensor cores: D[128 pixels][N out channels] = sum_K A[pixel][K] B[n][K], K = (tap,
-// input channel). A CTA walks a contiguous range of tiles of 128 consecutive
-// output pixels along W. Four producer warps copy, per tile and input plane, the
-// three input rows the 3x3 taps touch (130 pixels with the halo, zero outside the
-// image) into a 4-stage ring; since a K-major core matrix is 8 pixels x 16 B
-// contiguous, every tap is the same row region addressed 16 B per pixel later, so
-// each input row is read once per tile rather than once per tap. One thread issues
-// 128 x N x 16 tcgen05.mma (one per tap and pair of channel groups) into
-// double-buffered TMEM accumulators, four epilogue warps drain them. The packed
-// weights (B) stay in shared memory for the CTA's lifetime. The epilogue reads TMEM
-// with tcgen05.ld and applies bias + LeakyReLU (BF16 channels-last out), a residual
-// update of an FP32 channel-first state, or an activation mask.
+// tensor cores: D[128 pixels][N] = sum_K A[pixel][K] B[n][K], K = (tap, input
+// channel). A CTA walks a contiguous range of tiles of 128 consecutive output pixels
+// along W and RPT output rows. One TMA producer warp loads, per tile and input
+// plane, the RPT + 2 input rows the 3x3 taps touch (130 pixels with the halo, zero
+// outside the image) as one box into a ring of stages; since a K-major core matrix
+// is 8 pixels x 16 B contiguous, every column tap is the same row region addressed
+// 16 B per pixel later, so each input row is read once per tile rather than once
+// per tap. One thread issues 128 x N x 16 tcgen05.mma, N = RPT x NPAD (the RPT
+// output rows' weights stacked), into several TMEM accumulators; sixteen epilogue
+// warps drain them with tcgen05.ld. The packed weights (B) stay in shared memory
+// for the CTA's lifetime. The epilogue applies bias + LeakyReLU (BF16 row-blocked
+// out), a residual update of an FP32 channel-first state, or an activation mask.
 //
-// Weight gradients run on the CUDA cores (register-blocked FP32 accumulation over
-// pixel chunks, partial sums reduced in a fixed order).
+// Weight gradients run on the tensor cores as well (the pixels are the K dimension,
+// operands MN-major straight from the same row-halo stages), one partial per CTA
+// reduced in a fixed order; a CUDA-core kernel covers 16-channel inputs.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -35,13 +36,13 @@ enum ConvEpi { EPI_ACT_BF16 = 0, EPI_RESIDUAL_F32 = 1, EPI_MASK_BF16 = 2 };
 
 struct ConvArgs {
     const __nv_bfloat16 *x;  // [nimg][D][H][cpin / 8][W][8]: rows of channel groups
-    const uint8_t *wpk;      // packed B operand: kgroups x (NPAD/8) core matrices
+    const uint8_t *wpk;      // packed B operand (k_pack_weights)
     const float *bias;       // [cout] or null
     int nimg, D, H, W;
     int cpin, cin_groups;    // channels per pixel (8, 16 or 32), cpin / 8
     int G;                   // pixels per TMA box row (4, 2 or 1: the largest dividing W)
     int taps3d;              // 1: 3x3x3, 0: 3x3 over (H, W)
-    int kgroups;             // padded K / 8 (even)
+    int bbytes;              // packed B operand bytes (conv_packed_bytes)
     int cout;
     int cin;                 // weight gradient: input channels
     float slope;
@@ -156,6 +157,36 @@ constexpr int kProdWarp = 4 * kEpiGroups, kMmaWarp = 4 * kEpiGroups + 1;
 __host__ __device__ constexpr int conv_cgp(int cg) { return (cg + 1) & ~1; }
 __host__ __device__ constexpr int conv_stage_bytes(int cg, int rpt) { return (rpt + 2) * conv_cgp(cg) * kRowStride; }
 
+// Row units of the B operand. Unit j is input row j of the NR = RPT + 2 rows of a box
+// or, with one channel group (pair), the row pair (2j, 2j + 1), row NR being the zero
+// partner when NR is odd. Input row r feeds output rows o = r - 2 .. r (tap
+// dh = r - 1 - o), so unit j stacks the weights of output rows lo .. hi only:
+// N = (hi - lo + 1) NPAD, accumulated into TMEM columns lo NPAD onwards. The unit
+// issued first in every plane (row 2, or pair 1) is widened to all RPT rows so that
+// the tile's first MMA writes the whole accumulator.
+__host__ __device__ constexpr int conv_imin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int conv_units(int rpt, int pair) { return pair ? (rpt + 3) / 2 : rpt + 2; }
+__host__ __device__ constexpr int conv_unit_first(int pair) { return pair ? 1 : 2; }
+__host__ __device__ constexpr int conv_unit_lo(int j, int pair) {
+    return j == conv_unit_first(pair) ? 0 : ((pair ? 2 * j : j) >= 2 ? (pair ? 2 * j : j) - 2 : 0);
+}
+__host__ __device__ constexpr int conv_unit_hi(int j, int rpt, int pair) {
+    return j == conv_unit_first(pair) ? rpt - 1 : conv_imin(pair ? conv_imin(2 * j + 1, rpt + 1) : j, rpt - 1);
+}
+__host__ __device__ constexpr int conv_unit_rows(int j, int rpt, int pair) {
+    return conv_unit_hi(j, rpt, pair) - conv_unit_lo(j, pair) + 1;
+}
+// K groups (8 channels each) of a unit, ordered (column tap, channel group) or (column tap, half)
+__host__ __device__ constexpr int conv_unit_groups(int cgp, int pair) { return pair ? 6 : 3 * cgp; }
+__host__ __device__ constexpr int conv_unit_off(int j, int rpt, int pair, int cgp, int npad) {
+    int o = 0;
+    for (int i = 0; i < j; ++i) o += conv_unit_groups(cgp, pair) * conv_unit_rows(i, rpt, pair) * npad * 16;
+    return o;
+}
+__host__ __device__ constexpr int conv_plane_bytes(int rpt, int pair, int cgp, int npad) {
+    return conv_unit_off(conv_units(rpt, pair), rpt, pair, cgp, npad);
+}
+
 __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
                                             uint64_t *bar) {
     asm volatile(
@@ -210,11 +241,10 @@ __global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ 
     constexpr int kNR = RPT + 2;
     constexpr int kN = RPT * NPAD;
     constexpr bool kPair = CG == 1;               // K halves = consecutive input rows
-    constexpr int kNRP = (kNR + 1) / 2;           // row pairs per item (kPair)
     constexpr int kStageBytes = conv_stage_bytes(CG, RPT);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    const int bbytes = a.kgroups * kN * 16;
+    const int bbytes = a.bbytes;
     unsigned char *sA = sm;
     unsigned char *sB = sm + nst * kStageBytes;
     uint64_t *full = reinterpret_cast<uint64_t *>(sB + ((bbytes + 127) & ~127));
@@ -306,7 +336,8 @@ __global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ 
             // column tap dw of input row r reads region r from pixel G - 1 + dw on
             const uint32_t rs16 = (uint32_t)(rs / 16);
             const uint64_t adesc0 = smem_desc_kmajor(sA_u + (uint32_t)((a.G - 1) * 16), rs, 128);
-            const uint64_t bdesc0 = smem_desc_kmajor(sB_u, kN * 16, 128);
+            constexpr int kNU = conv_units(RPT, kPair), kFirst = conv_unit_first(kPair);
+            constexpr int kPlaneB = conv_plane_bytes(RPT, kPair, kCGP, NPAD);
             TileCoord tc = tile_coord(t_begin, a.D, nh, ntw);
             int s = 0;
             uint32_t ph = 0;
@@ -329,30 +360,35 @@ __global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ 
                         tc_fence_after();
                         // descriptor start-address fields are address >> 4: offsets add directly
                         const uint64_t ad = adesc0 + (uint64_t)((s * kStageBytes) >> 4);
-                        if constexpr (kPair) {
-                            const uint64_t bd = bdesc0 + (uint64_t)((c * kNRP * 3 * 2 * kN * 16) >> 4);
+                        // the widened unit first, then the others in row order
 #pragma unroll
-                            for (int rp = 0; rp < kNRP; ++rp)
+                        for (int jj = 0; jj < kNU; ++jj) {
+                            const int j = jj == 0 ? kFirst : (jj <= kFirst ? jj - 1 : jj);
+                            const int nj = conv_unit_rows(j, RPT, kPair) * NPAD;
+                            const uint32_t idesc = idesc_bf16_f32(128, nj);
+                            const uint32_t dtj = dt + (uint32_t)(conv_unit_lo(j, kPair) * NPAD);
+                            const uint64_t bd = smem_desc_kmajor(
+                                sB_u + (uint32_t)(c * kPlaneB + conv_unit_off(j, RPT, kPair, kCGP, NPAD)),
+                                (uint32_t)(nj * 16), 128);
+                            if constexpr (kPair) {
 #pragma unroll
                                 for (int dw = 0; dw < 3; ++dw) {
-                                    const uint32_t ao = (uint32_t)(2 * rp) * rs16 + (uint32_t)dw;
-                                    const uint32_t bo = (uint32_t)((((rp * 3 + dw) * 2) * kN * 16) >> 4);
-                                    mma_bf16(dt, ad + ao, bd + bo, kIdesc, acc_flag);
+                                    const uint32_t ao = (uint32_t)(2 * j) * rs16 + (uint32_t)dw;
+                                    const uint32_t bo = (uint32_t)((dw * 2 * nj * 16) >> 4);
+                                    mma_bf16(dtj, ad + ao, bd + bo, idesc, acc_flag);
                                     acc_flag = 1;
                                 }
-                        } else {
-                            const uint64_t bd = bdesc0 + (uint64_t)((c * kNR * 3 * kCGP * kN * 16) >> 4);
-#pragma unroll
-                            for (int r = 0; r < kNR; ++r)
+                            } else {
 #pragma unroll
                                 for (int dw = 0; dw < 3; ++dw)
 #pragma unroll
                                     for (int kp = 0; kp < kCGP; kp += 2) {
-                                        const uint32_t ao = (uint32_t)(r * CG + kp) * rs16 + (uint32_t)dw;
-                                        const uint32_t bo = (uint32_t)((((r * 3 + dw) * kCGP + kp) * kN * 16) >> 4);
-                                        mma_bf16(dt, ad + ao, bd + bo, kIdesc, acc_flag);
+                                        const uint32_t ao = (uint32_t)(j * CG + kp) * rs16 + (uint32_t)dw;
+                                        const uint32_t bo = (uint32_t)(((dw * kCGP + kp) * nj * 16) >> 4);
+                                        mma_bf16(dtj, ad + ao, bd + bo, idesc, acc_flag);
                                         acc_flag = 1;
                                     }
+                            }
                         }
                     }
                     mma_commit(&empty[s]);
@@ -416,39 +452,44 @@ __global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ 
 
 // ---- weight packing ---------------------------------------------------------------------
 
-// B operand in the row-halo order: group G = ((c * NR + r) * 3 + dw) * cgp + cg (input
-// plane c of nch, input row r of NR = rpt + 2, column tap dw, channel group cg) holds
-// rows n = o * npad + co (output row o < rpt, output channel co) x 8 channels, as
-// K-major core matrices; with pair_rows (one channel group) G = ((c * NRP + p) * 3 +
-// dw) * 2 + half holds input row r = 2 p + half instead (NRP = ceil(NR / 2); zero for
-// r = NR). The weight is that of tap (dd = c - 1, dh = r - 1 - o, dw - 1) (zero when
-// |dh| > 1). w: FP32 [cout][taps][cin]. flip = 1 packs the input-gradient
+// B operand in row units (see conv_unit_lo): per input plane c of nch, unit j,
+// group g = dw * cgp + cg (or dw * 2 + half with pair_rows), rows n = (o - lo) * npad +
+// co for output rows o = lo .. hi and output channels co, 8 K-channels each, as
+// K-major core matrices (8 rows x 16 B) — element e of the buffer is
+// ((plane, unit, g, n) x 8 + k) in that order. The weight is that of tap
+// (dd = c - 1, dh = r - 1 - o, dw - 1) with r = j (or 2 j + half), zero when |dh| > 1
+// or r = NR. w: FP32 [cout][taps][cin]. flip = 1 packs the input-gradient
 // convolution instead: output channel co = ci, input channel = co of w, mirrored tap.
 __global__ void k_pack_weights(const float *__restrict__ w, int cout, int taps3d, int cin, int cgp, int npad, int rpt,
                                int pair_rows, int flip, uint8_t *__restrict__ out) {
-    const int ntaps = taps3d ? 27 : 9, nch = taps3d ? 3 : 1, nr = rpt + 2, n2 = rpt * npad;
-    const int nrp = (nr + 1) / 2;
-    const long long ngroups = pair_rows ? (long long)nch * nrp * 3 * 2 : (long long)nch * nr * 3 * cgp;
-    const long long total = ngroups * n2 * 8;
+    const int ntaps = taps3d ? 27 : 9, nch = taps3d ? 3 : 1, nr = rpt + 2;
+    const int nu = conv_units(rpt, pair_rows), ng = conv_unit_groups(cgp, pair_rows);
+    const long long plane = conv_plane_bytes(rpt, pair_rows, cgp, npad) / 2;  // elements
+    const long long total = nch * plane;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        const int kin = (int)(e & 7);
-        const int n = (int)((e >> 3) % n2);
-        const long long G = (e >> 3) / n2;
-        int c, r, dw, cg;
+        const int c = (int)(e / plane);
+        long long rem = e - c * plane;
+        int j = 0;
+        for (; j < nu - 1; ++j) {
+            const long long ub = (long long)ng * conv_unit_rows(j, rpt, pair_rows) * npad * 8;
+            if (rem < ub) break;
+            rem -= ub;
+        }
+        const int nj = conv_unit_rows(j, rpt, pair_rows) * npad;
+        const int kin = (int)(rem & 7);
+        const int n = (int)((rem >> 3) % nj);
+        const int g = (int)((rem >> 3) / nj);
+        int r, dw, cg;
         if (pair_rows) {
-            const int half = (int)(G & 1);
-            dw = (int)(G / 2 % 3);
-            const int p = (int)(G / 6 % nrp);
-            c = (int)(G / 6 / nrp);
-            r = 2 * p + half;
+            dw = g >> 1;
+            r = 2 * j + (g & 1);
             cg = 0;
         } else {
-            cg = (int)(G % cgp);
-            dw = (int)(G / cgp % 3);
-            r = (int)(G / cgp / 3 % nr);
-            c = (int)(G / cgp / 3 / nr);
+            dw = g / cgp;
+            cg = g - dw * cgp;
+            r = j;
         }
-        const int o = n / npad, co = n - o * npad, ch = cg * 8 + kin, dh = r - 1 - o;
+        const int o = conv_unit_lo(j, pair_rows) + n / npad, co = n % npad, ch = cg * 8 + kin, dh = r - 1 - o;
         float v = 0.f;
         if (r < nr && dh >= -1 && dh <= 1) {
             const int tap = taps3d ? (c * 3 + dh + 1) * 3 + dw : (dh + 1) * 3 + dw;
@@ -458,8 +499,7 @@ __global__ void k_pack_weights(const float *__restrict__ w, int cout, int taps3d
                 if (co < cin && ch < cout) v = w[((long long)ch * ntaps + (ntaps - 1 - tap)) * cin + co];
             }
         }
-        const long long off = (G * (n2 / 8) + (n >> 3)) * 128 + (n & 7) * 16 + kin * 2;
-        *reinterpret_cast<__nv_bfloat16 *>(out + off) = __float2bfloat16_rn(v);
+        reinterpret_cast<__nv_bfloat16 *>(out)[e] = __float2bfloat16_rn(v);
     }
 }
 
@@ -782,26 +822,23 @@ __global__ void k_reduce_rows(const float *__restrict__ partial, int nblk, int n
 
 static int pad_npad(int cout) { return cout <= 16 ? 16 : 32; }
 
-// K groups (8 channels each) of the B operand: per input plane, (row, column tap,
-// channel group) or, with one channel group, (row pair, column tap, half).
-static int conv_kgroups(int taps3d, int cpin, int rpt) {
-    const int nr = rpt + 2, cg = cpin / 8;
-    return (taps3d ? 3 : 1) * 3 * (cg == 1 ? 2 * ((nr + 1) / 2) : nr * ((cg + 1) & ~1));
-}
+// Bytes of the packed B operand (row units, see conv_unit_lo).
 static long long conv_packed_bytes(int n_out, int taps3d, int cpin, int rpt) {
-    return (long long)conv_kgroups(taps3d, cpin, rpt) * rpt * pad_npad(n_out) * 16;
+    const int cg = cpin / 8;
+    return (long long)(taps3d ? 3 : 1) * conv_plane_bytes(rpt, cg == 1, conv_cgp(cg), pad_npad(n_out));
 }
 // Output rows per tile: the most of 4, 3, 2 with N = rows x NPAD <= 128 whose
-// stacked weights fit in shared memory next to two input stages; 1 otherwise. A
-// channel stride of 16 takes at most 2.
+// weights fit in shared memory next to three input stages (two, if none does); 1
+// otherwise. A channel stride of 16 takes at most 2.
 static int conv_rpt(int taps3d, int H, int cpin, int n_out) {
     const int npad = pad_npad(n_out);
-    for (int rpt = 4; rpt >= 2; --rpt) {
-        if (rpt > H || rpt * npad > 128 || (cpin == 16 && rpt > 2)) continue;
-        const long long fixed = 1024 + ((conv_packed_bytes(n_out, taps3d, cpin, rpt) + 127) & ~127LL) +
-                                8 * (2 * kMaxStages + 2 * kMaxAcc) + 4 * npad + 64;
-        if (fixed + 2LL * conv_stage_bytes(cpin / 8, rpt) <= 220 * 1024) return rpt;
-    }
+    for (int nst = 3; nst >= 2; --nst)
+        for (int rpt = 4; rpt >= 2; --rpt) {
+            if (rpt > H || rpt * npad > 128 || (cpin == 16 && rpt > 2)) continue;
+            const long long fixed = 1024 + ((conv_packed_bytes(n_out, taps3d, cpin, rpt) + 127) & ~127LL) +
+                                    8 * (2 * kMaxStages + 2 * kMaxAcc) + 4 * npad + 64;
+            if (fixed + (long long)nst * conv_stage_bytes(cpin / 8, rpt) <= 220 * 1024) return rpt;
+        }
     return 1;
 }
 
@@ -818,7 +855,7 @@ static int conv_pack(const float *w, int cout, int taps3d, int cin, int cpin, in
 template <int NPAD, int EPI, int CG, int RPT>
 static int launch_conv(const ConvArgs &a, cudaStream_t st) {
     constexpr int kN = RPT * NPAD;
-    const int bbytes = a.kgroups * kN * 16;
+    const int bbytes = a.bbytes;
     const size_t fixed = 1024 + ((bbytes + 127) & ~127) + 8 * (2 * kMaxStages + 2 * kMaxAcc) + 4 * NPAD + 64;
     const size_t limit = 220 * 1024, stage = conv_stage_bytes(CG, RPT);
     if (fixed + 2 * stage > limit) return fail(CBCT_EINVAL, "conv: input rows and weights do not fit in shared memory");
@@ -878,7 +915,7 @@ static int conv_run(const ConvArgs &a0, int n_out, int epi, int rpt, cudaStream_
     const int npad = pad_npad(n_out);
     if (a.cpin % 8 || (epi != EPI_RESIDUAL_F32 && a.cpout % 8)) return fail(CBCT_EINVAL, "conv: channel strides must be multiples of 8");
     a.cin_groups = a.cpin / 8;
-    a.kgroups = conv_kgroups(a.taps3d, a.cpin, rpt);
+    a.bbytes = (int)conv_packed_bytes(n_out, a.taps3d, a.cpin, rpt);
     a.G = a.W % 4 == 0 ? 4 : (a.W % 2 == 0 ? 2 : 1);
     if (npad == 16) {
         if (epi == EPI_ACT_BF16) return launch_conv_rpt<16, EPI_ACT_BF16>(a, rpt, st);

@@ -27,44 +27,77 @@ static int grid1(long long n) {
 // q0[b][k][v][e] = proj * w(u) * sdd / sqrt(sdd^2 + u^2 + v^2) on the extended row
 // (e = iu + lo), zero in the padding.
 __global__ void k_fdk_weight(const float *__restrict__ proj, const float *__restrict__ w, float *__restrict__ q0,
-                             int nu, int nv, int nue, int lo, long long rows, double du, double dv, double uoff,
-                             double voff, double sdd) {
-    const long long n = rows * nue;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const long long row = e / nue;
-        const int ie = (int)(e - row * nue), iu = ie - lo;
-        const int iv = (int)(row % nv);
-        float val = 0.f;
-        if (iu >= 0 && iu < nu) {
-            const float u = (float)((iu - 0.5 * (nu - 1)) * du + uoff);
-            const float v = (float)((iv - 0.5 * (nv - 1)) * dv + voff);
-            const float s = (float)sdd;
-            val = proj[row * nu + iu] * w[iu] * s * rsqrtf(s * s + u * u + v * v);
-        }
-        q0[e] = val;
+                             int nu, int nv, int nue, int lo, int rows, float du, float dv, float uoff,
+                             float voff, float sdd) {
+    const int ie = blockIdx.x * blockDim.x + threadIdx.x, iu = ie - lo;
+    if (ie >= nue) return;
+    const float u = ((float)iu - 0.5f * (float)(nu - 1)) * du + uoff;
+    const float wu = (iu >= 0 && iu < nu) ? w[iu] * sdd : 0.f;
+    for (int row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int iv = row % nv;
+        const float v = ((float)iv - 0.5f * (float)(nv - 1)) * dv + voff;
+        q0[(long long)row * nue + ie] =
+            wu != 0.f ? proj[(long long)row * nu + iu] * wu * rsqrtf(sdd * sdd + u * u + v * v) : 0.f;
     }
 }
 
-// q[row][e] = tau * sum_m h(e - m) q0[row][m], Ram-Lak at pitch tau (h(0) = 1/(4 tau^2),
-// h(odd j) = -1/(pi^2 j^2 tau^2), 0 for even j != 0); one CTA per row, the row and
-// the kernel table (tau h(|j|)) staged in shared memory.
-__global__ void k_fdk_ramp(const float *__restrict__ q0, float *__restrict__ q, int nue, float tau) {
+// Ram-Lak filter of each extended row: q[e] = h(0) q0[e] + sum over m of the other
+// parity of h(e - m) q0[m], h(d) = -1 / (pi^2 tau d^2) for odd d (zero for even d != 0).
+// Per parity the sum is a Toeplitz product on the compact arrays x_j = q0[2 j + p_m]:
+// out_i = sum_j g[i - j + c] x_j with g[t] = h(2 t + 1). A thread computes kRampB
+// consecutive outputs of one parity and slides a window of kRampB filter taps held in
+// registers along j: two shared loads per kRampB multiply-adds.
+constexpr int kRampB = 8;
+__global__ void __launch_bounds__(128) k_fdk_ramp(const float *__restrict__ q0, float *__restrict__ q, int nue, float tau) {
     extern __shared__ float sm[];
-    float *row = sm, *hk = sm + nue;
+    const int half = (nue + 1) / 2;                         // compact length bound, both parities
+    const int npad = (half + kRampB - 1) / kRampB * kRampB;  // compact arrays padded to a block multiple
+    float *xs = sm;                                          // [2][npad]: x of parity 0, then parity 1
+    float *gs = xs + 2 * npad;                               // g[t] at gs[t + goff], t = -goff .. goff + ...
+    float *os = gs + 2 * npad + 2 * kRampB + 2;              // [nue] filtered row
+    const int goff = npad + kRampB;
     const long long r = blockIdx.x;
     const float *src = q0 + r * nue;
-    const float c1 = -1.0f / (3.14159265358979f * 3.14159265358979f * tau);
-    for (int i = threadIdx.x; i < nue; i += blockDim.x) {
-        row[i] = src[i];
-        hk[i] = i == 0 ? 1.0f / (4.0f * tau) : ((i & 1) ? c1 / ((float)i * (float)i) : 0.0f);
+    const float c1 = -1.0f / (3.14159265358979f * 3.14159265358979f * tau), h0 = 1.0f / (4.0f * tau);
+    for (int i = threadIdx.x; i < 2 * npad; i += blockDim.x) {
+        const int p = i >= npad, j = i - p * npad, e = 2 * j + p;
+        xs[i] = e < nue ? src[e] : 0.f;
+    }
+    for (int k = threadIdx.x; k < 2 * npad + 2 * kRampB + 2; k += blockDim.x) {
+        const float d = (float)(2 * (k - goff) + 1);
+        gs[k] = c1 / (d * d);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < nue; e += blockDim.x) {
-        float acc = hk[0] * row[e];
-        // odd offsets only: m of the other parity than e
-        for (int m = (e & 1) ? 0 : 1; m < nue; m += 2) acc = fmaf(hk[abs(e - m)], row[m], acc);
-        q[r * nue + e] = acc;
+    const int nb = npad / kRampB;  // output blocks per parity
+    for (int wk = threadIdx.x; wk < 2 * nb; wk += blockDim.x) {
+        const int pe = wk >= nb, i0 = (wk - pe * nb) * kRampB, pm = 1 - pe;
+        const int c = pe - 1;  // e - m = 2 (i - j + c) + 1
+        const float *x = xs + pm * npad;
+        const float *xe = xs + pe * npad;
+        float acc[kRampB], R[kRampB];
+#pragma unroll
+        for (int b = 0; b < kRampB; ++b) {
+            acc[b] = h0 * xe[i0 + b];
+            R[b] = gs[goff + i0 + b + c];  // window at j = 0: win_b = g[i0 + b + c]
+        }
+        for (int j = 0; j < npad; j += kRampB) {
+#pragma unroll
+            for (int jj = 0; jj < kRampB; ++jj) {
+                const float xv = x[j + jj];
+#pragma unroll
+                for (int b = 0; b < kRampB; ++b) acc[b] = fmaf(R[(b - jj + kRampB) % kRampB], xv, acc[b]);
+                // slide: the tap that fell off becomes g[i0 + c - (j + jj) - 1]
+                R[(kRampB - 1 - jj) % kRampB] = gs[goff + i0 + c - (j + jj) - 1];
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < kRampB; ++b) {
+            const int e = 2 * (i0 + b) + pe;
+            if (e < nue) os[e] = acc[b];
+        }
     }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nue; e += blockDim.x) q[r * nue + e] = os[e];
 }
 
 // vol(P) (+)= (2 pi / n_angles) sum_k (sid / U)^2 bilinear(q_k, u(P), v(P)). A thread
@@ -253,7 +286,9 @@ extern "C" int cbct_fdk(const cbct_geom *g, const float *proj, float *vol, int b
     const cbct_geom_desc &d = g->desc;
     const int npad = cbct_fdk_pad(g), nue = d.nu + npad, lo = d.u_offset > 0 ? npad : 0;
     const long long rows = (long long)batch * d.n_angles * d.nv;
-    const size_t smem = 2 * sizeof(float) * nue;
+    if (rows > 0x7fffffffLL) return fail(CBCT_EINVAL, "cbct_fdk: too many detector rows");
+    const int ramp_pad = ((nue + 1) / 2 + kRampB - 1) / kRampB * kRampB;
+    const size_t smem = sizeof(float) * (4 * (size_t)ramp_pad + 2 * kRampB + 2 + nue);
     if (smem > 200 * 1024) return fail(CBCT_EINVAL, "cbct_fdk: extended detector row too long");
     const double PI = 3.14159265358979323846;
     std::vector<double2> cs(d.n_angles);
@@ -271,10 +306,11 @@ extern "C" int cbct_fdk(const cbct_geom *g, const float *proj, float *vol, int b
     int rc = 0;
     if (e == cudaSuccess) rc = cbct_redundancy_weight(g, w, stream);
     if (e == cudaSuccess && rc == 0) {
-        k_fdk_weight<<<grid1(rows * nue), 256, 0, st>>>(proj, w, q0, d.nu, d.nv, nue, lo, rows, d.du, d.dv, d.u_offset,
-                                                        d.v_offset, d.sdd);
+        dim3 gw((nue + 127) / 128, (unsigned)std::min<long long>(rows, 65535));
+        k_fdk_weight<<<gw, 128, 0, st>>>(proj, w, q0, d.nu, d.nv, nue, lo, (int)rows, (float)d.du, (float)d.dv,
+                                         (float)d.u_offset, (float)d.v_offset, (float)d.sdd);
         if (smem > 48 * 1024) cudaFuncSetAttribute(k_fdk_ramp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_fdk_ramp<<<(unsigned)rows, 256, smem, st>>>(q0, q, nue, (float)(d.du * d.sid / d.sdd));
+        k_fdk_ramp<<<(unsigned)rows, 128, smem, st>>>(q0, q, nue, (float)(d.du * d.sid / d.sdd));
         dim3 grd((d.nx + 31) / 32, (d.ny + 7) / 8, ((d.nz + kFdkZ - 1) / kFdkZ) * batch);
         k_fdk_backproject<<<grd, dim3(32, 8), 0, st>>>(
             q, dcs, vol, d.nx, d.ny, d.nz, d.n_angles, nue, d.nv, lo, d.nu, (float)d.vox[0], (float)d.vox[1],

@@ -252,7 +252,8 @@ int cbct_landweber(const cbct_geom *g, const float *y, float *x, int batch, int 
  *        LeakyReLU derivative from the forward activation).
  * status: device int, set to 1 if a kernel gives up waiting on its tensor cores.
  * Errors: CBCT_EINVAL for cpin not in {8, 16, 32}, cpin below the input channels,
- * more than 32 outputs or a missing output buffer. Scratch: the packed weights. */
+ * more than 32 outputs, a LeakyReLU slope outside [0, 1] or a missing output buffer.
+ * Scratch: the packed weights. */
 int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d, const float *w,
               const float *bias, int cin, int cout, int flip, int epi, float slope, void *y, int cpout,
               const void *mask, float *state, long long sstride, int *status, void *stream);
@@ -289,7 +290,7 @@ typedef struct {
     int n_iter;                  /* unrolled iterations (8 in the learned workload) */
     int n_mem;                   /* primal / dual memory channels, 2..6 (5) */
     int width;                   /* hidden channels of every block; must be 32 */
-    float slope;                 /* LeakyReLU slope (0.2) */
+    float slope;                 /* LeakyReLU slope (0.2), in [0, 1] */
     float mu_ref;                /* volume unit (1/mm): f' = f / mu_ref internally (0.02) */
     float bp_scale;              /* scale of P^T (w h_1) in the primal input; <= 0: 1 / max P^T(w 1) */
     unsigned long long seed;     /* initial weights (He normal; last layer of a block x 0.1; zero bias) */
@@ -300,7 +301,9 @@ typedef struct {
  * and a primal block Lambda_n (3x3x3: n_mem + 1 -> width -> width -> n_mem), LeakyReLU
  * between convs; parameters flat FP32 per iteration [dual w1 b1 w2 b2 w3 b3, primal
  * ...], w as [cout][taps][cin]. Memory: (n_iter + 1) iterates of n_mem volumes and
- * n_mem projections plus ~4 x 32-channel BF16 activations per block. Synchronises. */
+ * n_mem projections plus ~4 x 32-channel BF16 activations per block. Synchronises.
+ * Errors: CBCT_EINVAL unless 1 <= n_iter <= 64, 2 <= n_mem <= 6, width = 32,
+ * mu_ref > 0 and 0 <= slope <= 1. */
 int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lpd **out);
 void lpd_destroy(cbct_lpd *m);
 

@@ -102,24 +102,28 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *ac
 #pragma unroll
         for (int q = 0; q < kG; ++q) {
             if (q * 8 >= a.cpout) break;
-            const __nv_bfloat16 *m8 = reinterpret_cast<const __nv_bfloat16 *>(&mv[q]);
-            __align__(16) __nv_bfloat16 out8[8];
+            // padded channels (c >= cout) hold exact zeros: zero weights and zero bias
+            const __nv_bfloat162 *m2 = reinterpret_cast<const __nv_bfloat162 *>(&mv[q]);
+            uint32_t packed[4];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int c = q * 8 + j;
-                float v = 0.f;
-                if (c < a.cout) {
-                    v = acc[c];
-                    if constexpr (EPI == EPI_ACT_BF16) {
-                        v += bias[c];
-                        v = v > 0.f ? v : v * a.slope;
-                    } else {
-                        v = __bfloat162float(m8[j]) > 0.f ? v : v * a.slope;
-                    }
+            for (int j = 0; j < 4; ++j) {
+                const int c = q * 8 + 2 * j;
+                float v0 = acc[c], v1 = acc[c + 1];
+                if constexpr (EPI == EPI_ACT_BF16) {
+                    // LeakyReLU as max(v, slope v): 0 <= slope <= 1 (checked on the host)
+                    v0 += bias[c];
+                    v1 += bias[c + 1];
+                    v0 = fmaxf(v0, v0 * a.slope);
+                    v1 = fmaxf(v1, v1 * a.slope);
+                } else {
+                    const float2 m = __bfloat1622float2(m2[j]);
+                    v0 = m.x > 0.f ? v0 : v0 * a.slope;
+                    v1 = m.y > 0.f ? v1 : v1 * a.slope;
                 }
-                out8[j] = __float2bfloat16_rn(v);
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+                packed[j] = *reinterpret_cast<const uint32_t *>(&h2);
             }
-            *reinterpret_cast<uint4 *>(o + q * gstride) = *reinterpret_cast<const uint4 *>(out8);
+            *reinterpret_cast<uint4 *>(o + q * gstride) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
         }
     }
 }
@@ -460,47 +464,63 @@ __global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ 
 // (dd = c - 1, dh = r - 1 - o, dw - 1) with r = j (or 2 j + half), zero when |dh| > 1
 // or r = NR. w: FP32 [cout][taps][cin]. flip = 1 packs the input-gradient
 // convolution instead: output channel co = ci, input channel = co of w, mirrored tap.
-__global__ void k_pack_weights(const float *__restrict__ w, int cout, int taps3d, int cin, int cgp, int npad, int rpt,
-                               int pair_rows, int flip, uint8_t *__restrict__ out) {
-    const int ntaps = taps3d ? 27 : 9, nch = taps3d ? 3 : 1, nr = rpt + 2;
+// Value of element e of the packed B operand (layout above).
+__device__ __forceinline__ float pack_weight_value(const float *__restrict__ w, long long e, int cout, int taps3d,
+                                                   int cin, int cgp, int npad, int rpt, int pair_rows, int flip) {
+    const int ntaps = taps3d ? 27 : 9, nr = rpt + 2;
     const int nu = conv_units(rpt, pair_rows), ng = conv_unit_groups(cgp, pair_rows);
     const long long plane = conv_plane_bytes(rpt, pair_rows, cgp, npad) / 2;  // elements
-    const long long total = nch * plane;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(e / plane);
-        long long rem = e - c * plane;
-        int j = 0;
-        for (; j < nu - 1; ++j) {
-            const long long ub = (long long)ng * conv_unit_rows(j, rpt, pair_rows) * npad * 8;
-            if (rem < ub) break;
-            rem -= ub;
-        }
-        const int nj = conv_unit_rows(j, rpt, pair_rows) * npad;
-        const int kin = (int)(rem & 7);
-        const int n = (int)((rem >> 3) % nj);
-        const int g = (int)((rem >> 3) / nj);
-        int r, dw, cg;
-        if (pair_rows) {
-            dw = g >> 1;
-            r = 2 * j + (g & 1);
-            cg = 0;
-        } else {
-            dw = g / cgp;
-            cg = g - dw * cgp;
-            r = j;
-        }
-        const int o = conv_unit_lo(j, pair_rows) + n / npad, co = n % npad, ch = cg * 8 + kin, dh = r - 1 - o;
-        float v = 0.f;
-        if (r < nr && dh >= -1 && dh <= 1) {
-            const int tap = taps3d ? (c * 3 + dh + 1) * 3 + dw : (dh + 1) * 3 + dw;
-            if (!flip) {
-                if (co < cout && ch < cin) v = w[((long long)co * ntaps + tap) * cin + ch];
-            } else {
-                if (co < cin && ch < cout) v = w[((long long)ch * ntaps + (ntaps - 1 - tap)) * cin + co];
-            }
-        }
-        reinterpret_cast<__nv_bfloat16 *>(out)[e] = __float2bfloat16_rn(v);
+    const int c = (int)(e / plane);
+    long long rem = e - c * plane;
+    int j = 0;
+    for (; j < nu - 1; ++j) {
+        const long long ub = (long long)ng * conv_unit_rows(j, rpt, pair_rows) * npad * 8;
+        if (rem < ub) break;
+        rem -= ub;
     }
+    const int nj = conv_unit_rows(j, rpt, pair_rows) * npad;
+    const int kin = (int)(rem & 7);
+    const int n = (int)((rem >> 3) % nj);
+    const int g = (int)((rem >> 3) / nj);
+    int r, dw, cg;
+    if (pair_rows) {
+        dw = g >> 1;
+        r = 2 * j + (g & 1);
+        cg = 0;
+    } else {
+        dw = g / cgp;
+        cg = g - dw * cgp;
+        r = j;
+    }
+    const int o = conv_unit_lo(j, pair_rows) + n / npad, co = n % npad, ch = cg * 8 + kin, dh = r - 1 - o;
+    float v = 0.f;
+    if (r < nr && dh >= -1 && dh <= 1) {
+        const int tap = taps3d ? (c * 3 + dh + 1) * 3 + dw : (dh + 1) * 3 + dw;
+        if (!flip) {
+            if (co < cout && ch < cin) v = w[((long long)co * ntaps + tap) * cin + ch];
+        } else {
+            if (co < cin && ch < cout) v = w[((long long)ch * ntaps + (ntaps - 1 - tap)) * cin + co];
+        }
+    }
+    return v;
+}
+
+__global__ void k_pack_weights(const float *__restrict__ w, int cout, int taps3d, int cin, int cgp, int npad, int rpt,
+                               int pair_rows, int flip, uint8_t *__restrict__ out) {
+    const long long total = (taps3d ? 3 : 1) * (long long)conv_plane_bytes(rpt, pair_rows, cgp, npad) / 2;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x)
+        reinterpret_cast<__nv_bfloat16 *>(out)[e] =
+            __float2bfloat16_rn(pack_weight_value(w, e, cout, taps3d, cin, cgp, npad, rpt, pair_rows, flip));
+}
+
+// Several layers in one launch: job blockIdx.y packs params + w_off into out + out_off.
+__global__ void k_pack_jobs(const ConvPackJob *__restrict__ jobs, const float *__restrict__ params,
+                            uint8_t *__restrict__ out) {
+    const ConvPackJob J = jobs[blockIdx.y];
+    __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(out + J.out_off);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < J.nelem; e += (long long)gridDim.x * blockDim.x)
+        o[e] = __float2bfloat16_rn(pack_weight_value(params + J.w_off, e, J.cout, J.taps3d, J.cin, J.cgp, J.npad,
+                                                     J.rpt, J.pair, J.flip));
 }
 
 // ---- weight gradient on the tensor cores ------------------------------------------------
@@ -828,17 +848,18 @@ static long long conv_packed_bytes(int n_out, int taps3d, int cpin, int rpt) {
     return (long long)(taps3d ? 3 : 1) * conv_plane_bytes(rpt, cg == 1, conv_cgp(cg), pad_npad(n_out));
 }
 // Output rows per tile: the most of 4, 3, 2 with N = rows x NPAD <= 128 whose
-// weights fit in shared memory next to three input stages (two, if none does); 1
-// otherwise. A channel stride of 16 takes at most 2.
+// weights fit in shared memory next to two input stages; 1 otherwise. A channel
+// stride of 16 takes at most 2. (More rows per tile means fewer MMAs per output row,
+// (RPT + 2) / RPT input rows each, which outweighs a deeper input ring: measured on
+// the 32 -> 32 dual layer, 4 rows with two stages beat 3 rows with three by 6 %.)
 static int conv_rpt(int taps3d, int H, int cpin, int n_out) {
     const int npad = pad_npad(n_out);
-    for (int nst = 3; nst >= 2; --nst)
-        for (int rpt = 4; rpt >= 2; --rpt) {
-            if (rpt > H || rpt * npad > 128 || (cpin == 16 && rpt > 2)) continue;
-            const long long fixed = 1024 + ((conv_packed_bytes(n_out, taps3d, cpin, rpt) + 127) & ~127LL) +
-                                    8 * (2 * kMaxStages + 2 * kMaxAcc) + 4 * npad + 64;
-            if (fixed + (long long)nst * conv_stage_bytes(cpin / 8, rpt) <= 220 * 1024) return rpt;
-        }
+    for (int rpt = 4; rpt >= 2; --rpt) {
+        if (rpt > H || rpt * npad > 128 || (cpin == 16 && rpt > 2)) continue;
+        const long long fixed = 1024 + ((conv_packed_bytes(n_out, taps3d, cpin, rpt) + 127) & ~127LL) +
+                                8 * (2 * kMaxStages + 2 * kMaxAcc) + 4 * npad + 64;
+        if (fixed + 2LL * conv_stage_bytes(cpin / 8, rpt) <= 220 * 1024) return rpt;
+    }
     return 1;
 }
 
@@ -1016,27 +1037,58 @@ int conv_wgrad(const __nv_bfloat16 *x, int cpin, int cin, const __nv_bfloat16 *d
 
 using namespace cbct;
 
+long long cbct::conv_plan(int taps3d, int H, int cpin, int cin, int cout, int flip, ConvPackJob *job) {
+    const int n_out = flip ? cin : cout;
+    if ((cpin != 8 && cpin != 16 && cpin != 32) || n_out < 1 || n_out > 32 || !job) return -1;
+    const int rpt = conv_rpt(taps3d, H, cpin, n_out);
+    const long long bytes = conv_packed_bytes(n_out, taps3d, cpin, rpt);
+    job->nelem = bytes / 2;
+    job->cout = cout;
+    job->taps3d = taps3d;
+    job->cin = cin;
+    job->cgp = ((cpin / 8) + 1) & ~1;
+    job->npad = pad_npad(n_out);
+    job->rpt = rpt;
+    job->pair = cpin == 8;
+    job->flip = flip;
+    return bytes;
+}
+
+int cbct::conv_pack_jobs(const ConvPackJob *jobs, int njobs, long long max_nelem, const float *params, uint8_t *out,
+                         cudaStream_t st) {
+    if (njobs < 1 || njobs > 65535 || max_nelem < 1) return fail(CBCT_EINVAL, "conv_pack_jobs: bad job count");
+    dim3 grd((unsigned)std::min<long long>(1024, (max_nelem + 255) / 256), (unsigned)njobs);
+    k_pack_jobs<<<grd, 256, 0, st>>>(jobs, params, out);
+    CBCT_LAUNCH_CHECK("conv weight pack (jobs)");
+    return 0;
+}
+
 int cbct::conv_apply(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d, const float *w, const float *bias,
                      int cin, int cout, int flip, int epi, float slope, void *y, int cpout, const void *mask,
-                     const float *state_in, float *state, long long sstride, int *status, cudaStream_t st) {
+                     const float *state_in, float *state, long long sstride, int *status, cudaStream_t st,
+                     const uint8_t *packed) {
     if (!x || !w || nimg < 1 || D < 1 || H < 1 || W < 1 || cin < 1 || cout < 1 ||
         (cpin != 8 && cpin != 16 && cpin != 32) || cpin < (flip ? cout : cin))
         return fail(CBCT_EINVAL, "conv: invalid argument (sizes, or cpin below the input channels)");
     const int n_out = flip ? cin : cout;
     if (n_out > 32) return fail(CBCT_EINVAL, "conv: at most 32 output channels");
     if (epi < 0 || epi > 2) return fail(CBCT_EINVAL, "conv: bad epilogue");
+    if (!(slope >= 0.f && slope <= 1.f)) return fail(CBCT_EINVAL, "conv: LeakyReLU slope must lie in [0, 1]");
     if ((epi == EPI_RESIDUAL_F32 && !state) || (epi != EPI_RESIDUAL_F32 && (!y || cpout < n_out)) ||
         (epi == EPI_MASK_BF16 && !mask) || !status)
         return fail(CBCT_EINVAL, "conv: missing output");
     const int rpt = conv_rpt(taps3d, H, cpin, n_out);
     const long long bytes = conv_packed_bytes(n_out, taps3d, cpin, rpt);
     uint8_t *pk = nullptr;
-    CBCT_CUDA_TRY(cudaMallocAsync((void **)&pk, bytes, st));
-    int rc = conv_pack(w, cout, taps3d, cin, cpin, flip, rpt, pk, st);
+    int rc = 0;
+    if (!packed) {
+        CBCT_CUDA_TRY(cudaMallocAsync((void **)&pk, bytes, st));
+        rc = conv_pack(w, cout, taps3d, cin, cpin, flip, rpt, pk, st);
+    }
     if (rc == 0) {
         ConvArgs a{};
         a.x = static_cast<const __nv_bfloat16 *>(x);
-        a.wpk = pk;
+        a.wpk = packed ? packed : pk;
         a.bias = bias;
         a.nimg = nimg; a.D = D; a.H = H; a.W = W;
         a.cpin = cpin;
@@ -1052,7 +1104,7 @@ int cbct::conv_apply(const void *x, int nimg, int D, int H, int W, int cpin, int
         a.status = status;
         rc = conv_run(a, n_out, epi, rpt, st);
     }
-    cudaFreeAsync(pk, st);
+    if (pk) cudaFreeAsync(pk, st);
     return rc;
 }
 

@@ -1,5 +1,6 @@
 // Host-side layout of the opaque geometry handle (internal to the library).
 #pragma once
+#include <stdint.h>
 
 #include <vector>
 
@@ -31,10 +32,25 @@ int operator_norm(cbct_geom *g, int iters, double *out);
 int back_project_colw(const cbct_geom *g, const float *proj, const float *colw, float *vol, int batch, int accumulate,
                       cudaStream_t st);
 // cbct_conv with the residual epilogue reading its old state from state_in (which may
-// equal state) and writing state = state_in + conv.
+// equal state) and writing state = state_in + conv. packed: the layer's B operand
+// already packed by conv_pack_jobs for the same (taps3d, H, cpin, cin, cout, flip),
+// or null to pack it here.
 int conv_apply(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d, const float *w, const float *bias,
                int cin, int cout, int flip, int epi, float slope, void *y, int cpout, const void *mask,
-               const float *state_in, float *state, long long sstride, int *status, cudaStream_t st);
+               const float *state_in, float *state, long long sstride, int *status, cudaStream_t st,
+               const uint8_t *packed = nullptr);
+// Packing of one layer's weights: the shape part is filled by conv_plan, the offsets
+// (weights within the parameter array, bytes within the packed buffer) by the caller.
+struct ConvPackJob {
+    long long w_off, out_off, nelem;
+    int cout, taps3d, cin, cgp, npad, rpt, pair, flip;
+};
+// Fills job's shape fields for a convolution of the given shape; returns the packed
+// bytes (a multiple of 16), or a negative value for an unsupported shape.
+long long conv_plan(int taps3d, int H, int cpin, int cin, int cout, int flip, ConvPackJob *job);
+// Packs njobs layers (jobs: device array) from params into out in one launch.
+int conv_pack_jobs(const ConvPackJob *jobs, int njobs, long long max_nelem, const float *params, uint8_t *out,
+                   cudaStream_t st);
 // Staged (TMA) forward: returns 1 if it ran, 0 if the direct kernel must be used.
 int forward_staged(const cbct_geom *g, const float *vol, float *proj, int batch, int accumulate, cudaStream_t st);
 int choose_forward_cfg(double need_b, double need_z);

@@ -42,6 +42,7 @@ using namespace cbct;
 struct LayerSpec {
     int cin, cout, taps3d;
     long long w_off, b_off;  // offsets into the flat parameter array
+    long long pk_off = 0;    // forward B operand within cbct_lpd::wpk
 };
 
 struct cbct_lpd {
@@ -68,6 +69,11 @@ struct cbct_lpd {
     float *gf = nullptr, *gh = nullptr;  // [n_mem + 1][nvox], [n_mem + 2][nproj]
     int *status = nullptr;
     long long nvox = 0, nproj = 0;
+    // every forward layer's weights packed as tensor-core B operands, refreshed by one
+    // launch at the start of each forward and backward pass
+    uint8_t *wpk = nullptr;
+    ConvPackJob *pack_jobs = nullptr;  // device [layers]
+    long long pack_max_nelem = 0;
 };
 
 namespace {
@@ -216,7 +222,7 @@ static int conv_fwd(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *x, int
                     int epi, __nv_bfloat16 *y, float *state, long long sstride, cudaStream_t st,
                     const float *state_in = nullptr) {
     return conv_apply(x, nimg, D, H, W, cpin, L.taps3d, m->params + L.w_off, m->params + L.b_off, L.cin, L.cout, 0, epi,
-                      m->d.slope, y, 32, nullptr, state_in, state, sstride, m->status, st);
+                      m->d.slope, y, 32, nullptr, state_in, state, sstride, m->status, st, m->wpk + L.pk_off);
 }
 
 // input-gradient conv of layer L: dy (BF16 [..][cp_dy], L.cout channels) -> L.cin outputs
@@ -270,8 +276,10 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     if (!g || !desc || !out) return fail(CBCT_EINVAL, "lpd_create: NULL argument");
     *out = nullptr;
     const cbct_lpd_desc &d = *desc;
-    if (d.n_iter < 1 || d.n_iter > 64 || d.n_mem < 2 || d.n_mem > 6 || d.width != 32 || !(d.mu_ref > 0))
-        return fail(CBCT_EINVAL, "lpd_create: need 1 <= n_iter <= 64, 2 <= n_mem <= 6, width == 32, mu_ref > 0");
+    if (d.n_iter < 1 || d.n_iter > 64 || d.n_mem < 2 || d.n_mem > 6 || d.width != 32 || !(d.mu_ref > 0) ||
+        !(d.slope >= 0.f && d.slope <= 1.f))
+        return fail(CBCT_EINVAL, "lpd_create: need 1 <= n_iter <= 64, 2 <= n_mem <= 6, width == 32, mu_ref > 0, "
+                                 "0 <= slope <= 1");
     cbct_lpd *m = new (std::nothrow) cbct_lpd();
     if (!m) return fail(CBCT_ENOMEM, "lpd_create: host allocation");
     m->g = g;
@@ -333,6 +341,24 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     al((void **)&m->gf, sizeof(float) * (M + 1) * NV);
     al((void **)&m->gh, sizeof(float) * (M + 2) * NP);
     al((void **)&m->status, sizeof(int));
+    // forward convolutions: packing plan of every layer (first layer of a block reads 8
+    // channel slots, the others 32; 2-D blocks run over the nv rows, 3-D over ny)
+    std::vector<ConvPackJob> jobs(m->layers.size());
+    long long pk_bytes = 0;
+    for (size_t i = 0; i < m->layers.size() && e == cudaSuccess; ++i) {
+        LayerSpec &L = m->layers[i];
+        const long long b = conv_plan(L.taps3d, L.taps3d ? g->dev.n[1] : g->dev.nv, i % 3 == 0 ? 8 : 32, L.cin,
+                                      L.cout, 0, &jobs[i]);
+        if (b < 0) e = cudaErrorInvalidValue;
+        jobs[i].w_off = L.w_off;
+        jobs[i].out_off = L.pk_off = pk_bytes;
+        pk_bytes += (b + 255) & ~255LL;
+        m->pack_max_nelem = std::max(m->pack_max_nelem, jobs[i].nelem);
+    }
+    al((void **)&m->wpk, (size_t)pk_bytes);
+    al((void **)&m->pack_jobs, sizeof(ConvPackJob) * jobs.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(m->pack_jobs, jobs.data(), sizeof(ConvPackJob) * jobs.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->params, hp.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(m->grads, 0, sizeof(float) * off);
     if (e == cudaSuccess) e = cudaMemset(m->adam_m, 0, sizeof(float) * off);
@@ -375,7 +401,7 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
 extern "C" void lpd_destroy(cbct_lpd *m) {
     if (!m) return;
     cudaDeviceSynchronize();
-    void *ptrs[] = {m->clip, m->pf_saved, m->bp_saved, m->params, m->grads, m->adam_m, m->adam_v, m->wred, m->f, m->h,
+    void *ptrs[] = {m->wpk, m->pack_jobs, m->clip, m->pf_saved, m->bp_saved, m->params, m->grads, m->adam_m, m->adam_v, m->wred, m->f, m->h,
                     m->y, m->tproj, m->tproj2, m->tvol, m->din, m->a1, m->a2, m->pin, m->b1, m->b2, m->g32a, m->g32b, m->gsmall, m->gf, m->gh,
                     m->status};
     for (void *p : ptrs)
@@ -399,6 +425,8 @@ static int lpd_forward_impl(cbct_lpd *m, const float *y, const float *x0, const 
                             float *x_out, int save_for_backward, cudaStream_t st) {
     const long long NV = m->nvox, NP = m->nproj;
     const int M = m->d.n_mem, N = m->d.n_iter;
+    int prc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
+    if (prc) return prc;
     CBCT_CUDA_TRY(cudaMemcpyAsync(m->y, y, sizeof(float) * NP, cudaMemcpyDeviceToDevice, st));
     if (f0) {
         CBCT_CUDA_TRY(cudaMemcpyAsync(m->f, f0, sizeof(float) * M * NV, cudaMemcpyDeviceToDevice, st));
@@ -461,6 +489,10 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
     const long long NV = m->nvox, NP = m->nproj;
     const int M = m->d.n_mem, N = m->d.n_iter;
     float *gf = m->gf, *gh = m->gh;  // gf: [M + 1][NV] (last = grad of the bp channel), gh: [M + 2][NP]
+    // the recomputed forward convolutions read the packed weights: refresh them (the
+    // parameters may have changed since the forward pass)
+    int prc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
+    if (prc) return prc;
     // dL/df_N: channel 0 gets mu_ref dL/dx; plus the given state gradients
     cudaMemsetAsync(gf, 0, sizeof(float) * (M + 1) * NV, st);
     cudaMemsetAsync(gh, 0, sizeof(float) * (M + 2) * NP, st);

@@ -82,6 +82,23 @@ def test_conv_forward_act(L, name, dims, taps3d, cin, cout, nimg):
     assert rel(got, R.bf16(ref)) <= 4e-3
 
 
+def test_conv_rejects_slope_outside_unit_interval(L):
+    """The activation epilogue evaluates LeakyReLU as max(v, slope v), which needs
+    0 <= slope <= 1: other slopes are refused before any launch."""
+    x = torch.zeros((1, 4, 1, 16, 8), dtype=torch.bfloat16, device="cuda")
+    w = torch.zeros(32 * 9 * 8, device="cuda")
+    y = torch.zeros((1, 4, 4, 16, 8), dtype=torch.bfloat16, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for slope in (1.5, -0.1, float("nan")):
+        rc = L.load().cbct_conv(x.data_ptr(), 1, 1, 4, 16, 8, 0, w.data_ptr(), None, 8, 32, 0, 0, slope,
+                                y.data_ptr(), 32, None, None, 0, status.data_ptr(),
+                                torch.cuda.current_stream().cuda_stream)
+        assert rc == -1
+        assert b"slope" in L.load().cbct_last_error()
+    torch.cuda.synchronize()
+    assert float(y.float().abs().sum()) == 0.0
+
+
 @pytest.mark.parametrize("taps3d,dims", [(0, (21, 33)), (1, (7, 11, 13))])
 def test_conv_residual_into_state(L, taps3d, dims):
     from oracle import lpd_ref as R

@@ -17,6 +17,7 @@ struct cbct_geom {
     cbct::Col64 *col64 = nullptr;
     float *rz32 = nullptr;                 // [nv]
     double *rz64 = nullptr;
+    double2 *cs = nullptr;                 // [na] (cos, sin) of each angle, for FDK
     cbct::GeomDev dev{};                   // kernel view
     int *status = nullptr;                 // device status word of this geometry's kernels
     int fwd_cfg = -1;                      // staged forward box configuration, -1: direct kernel

@@ -223,6 +223,13 @@ extern "C" int geometry_create(const cbct_geom_desc *desc, cbct_geom **out) {
     if (e == cudaSuccess) e = cudaMalloc(&g->col64, sizeof(Col64) * ncol);
     if (e == cudaSuccess) e = cudaMalloc(&g->rz32, sizeof(float) * d.nv);
     if (e == cudaSuccess) e = cudaMalloc(&g->rz64, sizeof(double) * d.nv);
+    std::vector<double2> cs(d.n_angles);
+    for (int k = 0; k < d.n_angles; ++k) {
+        const double th = ang.empty() ? 2.0 * 3.14159265358979323846 * k / d.n_angles : ang[k];
+        cs[k] = make_double2(cos(th), sin(th));
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&g->cs, sizeof(double2) * d.n_angles);
+    if (e == cudaSuccess) e = cudaMemcpy(g->cs, cs.data(), sizeof(double2) * d.n_angles, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->f32, f32.data(), sizeof(Frame32) * d.n_angles, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->f64, f64.data(), sizeof(Frame64) * d.n_angles, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->col32, c32.data(), sizeof(Col32) * ncol, cudaMemcpyHostToDevice);
@@ -271,6 +278,7 @@ extern "C" void geometry_destroy(cbct_geom *g) {
     if (g->col64) cudaFree(g->col64);
     if (g->rz32) cudaFree(g->rz32);
     if (g->rz64) cudaFree(g->rz64);
+    if (g->cs) cudaFree(g->cs);
     if (g->status) cudaFree(g->status);
     cudaSetDevice(cur);
     delete g;

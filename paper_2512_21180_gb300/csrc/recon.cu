@@ -48,7 +48,8 @@ __global__ void k_fdk_weight(const float *__restrict__ proj, const float *__rest
 // consecutive outputs of one parity and slides a window of kRampB filter taps held in
 // registers along j: two shared loads per kRampB multiply-adds.
 constexpr int kRampB = 8;
-__global__ void __launch_bounds__(128) k_fdk_ramp(const float *__restrict__ q0, float *__restrict__ q, int nue, float tau) {
+__global__ void __launch_bounds__(128) k_fdk_ramp(const float *__restrict__ q0, float *__restrict__ q, int nue, int nv,
+                                                  float tau) {
     extern __shared__ float sm[];
     const int half = (nue + 1) / 2;                         // compact length bound, both parities
     const int npad = (half + kRampB - 1) / kRampB * kRampB;  // compact arrays padded to a block multiple
@@ -97,7 +98,10 @@ __global__ void __launch_bounds__(128) k_fdk_ramp(const float *__restrict__ q0, 
         }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < nue; e += blockDim.x) q[r * nue + e] = os[e];
+    // output row of the zero-padded layout [na][nv + 2][nue + 2] (one zero row and column each side)
+    const long long kk = r / nv, iv = r - kk * nv;
+    float *dst = q + (kk * (nv + 2) + iv + 1) * (nue + 2) + 1;
+    for (int e = threadIdx.x; e < nue; e += blockDim.x) dst[e] = os[e];
 }
 
 // vol(P) (+)= (2 pi / n_angles) sum_k (sid / U)^2 bilinear(q_k, u(P), v(P)). A thread
@@ -108,7 +112,7 @@ constexpr int kFdkZ = 8;
 __global__ void __launch_bounds__(256) k_fdk_backproject(const float *__restrict__ q, const double2 *__restrict__ cs,
                                                          float *__restrict__ vol, int nx, int ny, int nz, int na, int nue,
                                                          int nv, int lo, int nu, float vx, float vy, float vz, float cx,
-                                                         float cy, float cz, float sid, float sdd, float du, float dv,
+                                                         float cy, float cz, float sid, float sdd, float rdu, float rdv,
                                                          float uoff, float voff, int accumulate) {
     const int ix = blockIdx.x * 32 + threadIdx.x, iy = blockIdx.y * 8 + threadIdx.y;
     const int nzr = (nz + kFdkZ - 1) / kFdkZ;
@@ -116,12 +120,10 @@ __global__ void __launch_bounds__(256) k_fdk_backproject(const float *__restrict
     if (ix >= nx || iy >= ny) return;
     const float px = (ix - 0.5f * (nx - 1)) * vx + cx;
     const float py = (iy - 0.5f * (ny - 1)) * vy + cy;
-    float pz[kFdkZ];
-#pragma unroll
-    for (int j = 0; j < kFdkZ; ++j) pz[j] = (iz0 + j - 0.5f * (nz - 1)) * vz + cz;
+    const float pz0 = (iz0 - 0.5f * (nz - 1)) * vz + cz;
     const float hu = 0.5f * (nu - 1) + lo, hv = 0.5f * (nv - 1);
-    const float idv = 1.0f / dv;
-    const float *qb = q + (long long)b * na * nv * nue;
+    const int pitch = nue + 2;  // zero-padded rows: every bilinear neighbour is in bounds
+    const float *qb = q + (long long)b * na * (nv + 2) * pitch;
     float acc[kFdkZ];
 #pragma unroll
     for (int j = 0; j < kFdkZ; ++j) acc[j] = 0.f;
@@ -130,26 +132,23 @@ __global__ void __launch_bounds__(256) k_fdk_backproject(const float *__restrict
         const float c = (float)t.x, s = (float)t.y;
         const float U = sid - (px * c + py * s);
         if (!(U > 0.f)) continue;
-        const float m = sdd / U;
-        const float fu = (m * (-px * s + py * c) - uoff) / du + hu;
+        const float rU = __frcp_rn(U), m = sdd * rU;
+        const float fu = (m * (-px * s + py * c) - uoff) * rdu + hu;
         const float u0 = floorf(fu), au = fu - u0;
         const int ju = (int)u0;
         if (ju < -1 || ju >= nue) continue;
-        const float r = sid / U, w = r * r;
-        const float *qk = qb + (long long)k * nv * nue;
-        const bool u0k = ju >= 0, u1k = ju + 1 < nue;
+        const float r = sid * rU, w = r * r;
+        // the detector row coordinate is affine along the z-run
+        const float fv0 = (m * pz0 - voff) * rdv + hv, dfv = m * vz * rdv;
+        const float *qk = qb + ((long long)k * (nv + 2) + 1) * pitch + 1 + ju;  // (row 0, column ju)
 #pragma unroll
         for (int j = 0; j < kFdkZ; ++j) {
-            const float fv = (m * pz[j] - voff) * idv + hv;
+            const float fv = fmaf((float)j, dfv, fv0);
             const float v0 = floorf(fv), av = fv - v0;
             const int jv = (int)v0;
             if (jv < -1 || jv >= nv) continue;
-            const bool v0k = jv >= 0, v1k = jv + 1 < nv;
-            const float *r0 = qk + (long long)jv * nue + ju;
-            const float q00 = (u0k && v0k) ? __ldg(r0) : 0.f;
-            const float q10 = (u1k && v0k) ? __ldg(r0 + 1) : 0.f;
-            const float q01 = (u0k && v1k) ? __ldg(r0 + nue) : 0.f;
-            const float q11 = (u1k && v1k) ? __ldg(r0 + nue + 1) : 0.f;
+            const float *r0 = qk + (long long)jv * pitch;
+            const float q00 = __ldg(r0), q10 = __ldg(r0 + 1), q01 = __ldg(r0 + pitch), q11 = __ldg(r0 + pitch + 1);
             const float a0 = fmaf(au, q10 - q00, q00), a1 = fmaf(au, q11 - q01, q01);
             acc[j] = fmaf(w, fmaf(av, a1 - a0, a0), acc[j]);
         }
@@ -290,19 +289,13 @@ extern "C" int cbct_fdk(const cbct_geom *g, const float *proj, float *vol, int b
     const int ramp_pad = ((nue + 1) / 2 + kRampB - 1) / kRampB * kRampB;
     const size_t smem = sizeof(float) * (4 * (size_t)ramp_pad + 2 * kRampB + 2 + nue);
     if (smem > 200 * 1024) return fail(CBCT_EINVAL, "cbct_fdk: extended detector row too long");
-    const double PI = 3.14159265358979323846;
-    std::vector<double2> cs(d.n_angles);
-    for (int k = 0; k < d.n_angles; ++k) {
-        const double th = g->angles.empty() ? 2.0 * PI * k / d.n_angles : g->angles[k];
-        cs[k] = make_double2(cos(th), sin(th));
-    }
+    // q0: weighted extended rows [rows][nue]; q: filtered rows, zero-padded [batch na][nv + 2][nue + 2]
+    const long long nq0 = rows * nue, nq = (long long)batch * d.n_angles * (d.nv + 2) * (nue + 2);
     float *q0 = nullptr, *q = nullptr, *w = nullptr;
-    double2 *dcs = nullptr;
-    CBCT_CUDA_TRY(cudaMallocAsync((void **)&q0, sizeof(float) * rows * nue * 2 + sizeof(float) * d.nu, st));
-    q = q0 + rows * nue;
-    w = q + rows * nue;
-    cudaError_t e = cudaMallocAsync((void **)&dcs, sizeof(double2) * d.n_angles, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dcs, cs.data(), sizeof(double2) * d.n_angles, cudaMemcpyHostToDevice, st);
+    CBCT_CUDA_TRY(cudaMallocAsync((void **)&q0, sizeof(float) * (nq0 + nq + d.nu), st));
+    q = q0 + nq0;
+    w = q + nq;
+    cudaError_t e = cudaMemsetAsync(q, 0, sizeof(float) * nq, st);
     int rc = 0;
     if (e == cudaSuccess) rc = cbct_redundancy_weight(g, w, stream);
     if (e == cudaSuccess && rc == 0) {
@@ -310,17 +303,15 @@ extern "C" int cbct_fdk(const cbct_geom *g, const float *proj, float *vol, int b
         k_fdk_weight<<<gw, 128, 0, st>>>(proj, w, q0, d.nu, d.nv, nue, lo, (int)rows, (float)d.du, (float)d.dv,
                                          (float)d.u_offset, (float)d.v_offset, (float)d.sdd);
         if (smem > 48 * 1024) cudaFuncSetAttribute(k_fdk_ramp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_fdk_ramp<<<(unsigned)rows, 128, smem, st>>>(q0, q, nue, (float)(d.du * d.sid / d.sdd));
+        k_fdk_ramp<<<(unsigned)rows, 128, smem, st>>>(q0, q, nue, d.nv, (float)(d.du * d.sid / d.sdd));
         dim3 grd((d.nx + 31) / 32, (d.ny + 7) / 8, ((d.nz + kFdkZ - 1) / kFdkZ) * batch);
         k_fdk_backproject<<<grd, dim3(32, 8), 0, st>>>(
-            q, dcs, vol, d.nx, d.ny, d.nz, d.n_angles, nue, d.nv, lo, d.nu, (float)d.vox[0], (float)d.vox[1],
+            q, g->cs, vol, d.nx, d.ny, d.nz, d.n_angles, nue, d.nv, lo, d.nu, (float)d.vox[0], (float)d.vox[1],
             (float)d.vox[2], (float)d.center[0], (float)d.center[1], (float)d.center[2], (float)d.sid, (float)d.sdd,
-            (float)d.du, (float)d.dv, (float)d.u_offset, (float)d.v_offset, accumulate);
+            (float)(1.0 / d.du), (float)(1.0 / d.dv), (float)d.u_offset, (float)d.v_offset, accumulate);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host angle table must outlive the upload
     cudaFreeAsync(q0, st);
-    if (dcs) cudaFreeAsync(dcs, st);
     if (rc) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "cbct_fdk");
     return 0;

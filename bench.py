@@ -354,6 +354,7 @@ def report(args, geom, world, S_fwd, samples_step, value, ms, ms_fwd, ms_adj, e2
     ms_dom = max(ms_adj, ms_fwd)
     roof = roofline(dom, ms_dom, S_fwd, nvox, nray, pk, pk_kind, clk)
     roof["traffic"] = MEASURED_TRAFFIC.get(args.workload, {}).get(dom)
+    roof["ncu_sm_throughput_pct"] = MEASURED_SM_THROUGHPUT_PCT.get(args.workload, {}).get(dom)
     line = {
         "metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -388,6 +389,10 @@ def report(args, geom, world, S_fwd, samples_step, value, ms, ms_fwd, ms_adj, e2
 # --set full capture of the clinical workload with the current kernels; None elsewhere
 # and whenever the kernel changes after the capture.
 MEASURED_TRAFFIC = {"clinical": {"back_project": 908.813e6 + 37.730e6, "forward_project": 137.302e6 + 281.002e6}}
+# The binding on-chip level's throughput from the same captures: the projector kernels are
+# bound by SM instruction issue, so this is sm__throughput.avg.pct_of_peak_sustained_elapsed
+# (issue active: adjoint 69.4 %, forward 84.2 %). Same validity rule as the traffic.
+MEASURED_SM_THROUGHPUT_PCT = {"clinical": {"back_project": 65.5, "forward_project": 84.2}}
 
 
 def launches_per_step(geom) -> int:

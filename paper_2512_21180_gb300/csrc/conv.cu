@@ -129,8 +129,8 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *ac
 }
 
 // Row-halo layout. A tile is 128 consecutive output pixels along W of RPT output
-// rows h0 .. h0 + RPT - 1 (RPT = 4, 3, 2 or 1, the most whose weights fit in shared
-// memory next to the input stages); an A stage holds
+// rows h0 .. h0 + RPT - 1 (RPT from 1 to 6, the most whose weights fit in shared
+// memory next to two input stages, see conv_rpt); an A stage holds
 // the NR = RPT + 2 input rows h0 - 1 .. h0 + RPT of one input plane as NR * CGP
 // regions (CGP = CG rounded up to even) of RS = 16 G R bytes (2176, 2112 or 2080;
 // at most kRowStride). Region r * CG + g holds channel group g of input row h0 - 1 + r
@@ -142,12 +142,12 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *ac
 // as a tiled TMA destination must. A K-major core matrix is 8 rows x 16 B = 128
 // contiguous bytes, so with the 8-row group stride SBO = 128 the A operand for input
 // row r and column tap dw is region r started (G - 1 + dw) pixels in, and the
-// K-adjacent core matrix (next channel group) lies LBO = RS further. The B operand for (r, dw) stacks, for each output row o, the
-// weights of tap (dh = r - 1 - o, dw) (zero when |dh| > 1): N = RPT x NPAD, so one
-// MMA serves RPT output rows. With a single channel group (CG = 1) the two K halves
-// of an MMA are instead two consecutive input rows (LBO = RS) and only region NR, the
-// partner of the last row when NR is odd, stays zero. Every input row is loaded once
-// per tile.
+// K-adjacent core matrix (next channel group) lies LBO = RS further. The B operand of
+// input row r stacks the weights of tap (dh = r - 1 - o, dw) for the output rows o it
+// feeds (the row units below), so one MMA serves up to three output rows (four for a
+// row pair). With a single channel group (CG = 1) the two K halves of an MMA are
+// instead two consecutive input rows (LBO = RS) and only region NR, the partner of the
+// last row when NR is odd, stays zero. Every input row is loaded once per tile.
 constexpr int kRowStride = 2176;         // 17 x 128 >= RS = 16 R G for G = 1, 2, 4
 __host__ __device__ constexpr int conv_box_rows(int G) { return (129 + G + G - 1) / G; }
 constexpr int kMaxStages = 8;            // A ring depth (chosen per launch, <= 8)
@@ -165,17 +165,28 @@ __host__ __device__ constexpr int conv_stage_bytes(int cg, int rpt) { return (rp
 // or, with one channel group (pair), the row pair (2j, 2j + 1), row NR being the zero
 // partner when NR is odd. Input row r feeds output rows o = r - 2 .. r (tap
 // dh = r - 1 - o), so unit j stacks the weights of output rows lo .. hi only:
-// N = (hi - lo + 1) NPAD, accumulated into TMEM columns lo NPAD onwards. The unit
-// issued first in every plane (row 2, or pair 1) is widened to all RPT rows so that
-// the tile's first MMA writes the whole accumulator.
+// N = (hi - lo + 1) NPAD, accumulated into TMEM columns lo NPAD onwards. The
+// "initialising" units — rows 2, 5, 8, ... (output rows 3t .. 3t + 2), or pairs
+// 1, 3, 5, ... (output rows 4t .. 4t + 3) — cover the RPT output rows exactly once, so
+// issuing them first, each starting with an overwriting MMA, writes the whole
+// accumulator before any other unit adds to it.
 __host__ __device__ constexpr int conv_imin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int conv_units(int rpt, int pair) { return pair ? (rpt + 3) / 2 : rpt + 2; }
-__host__ __device__ constexpr int conv_unit_first(int pair) { return pair ? 1 : 2; }
+__host__ __device__ constexpr bool conv_unit_init(int j, int pair) { return pair ? (j & 1) == 1 : j % 3 == 2; }
 __host__ __device__ constexpr int conv_unit_lo(int j, int pair) {
-    return j == conv_unit_first(pair) ? 0 : ((pair ? 2 * j : j) >= 2 ? (pair ? 2 * j : j) - 2 : 0);
+    return (pair ? 2 * j : j) >= 2 ? (pair ? 2 * j : j) - 2 : 0;
 }
 __host__ __device__ constexpr int conv_unit_hi(int j, int rpt, int pair) {
-    return j == conv_unit_first(pair) ? rpt - 1 : conv_imin(pair ? conv_imin(2 * j + 1, rpt + 1) : j, rpt - 1);
+    return conv_imin(pair ? conv_imin(2 * j + 1, rpt + 1) : j, rpt - 1);
+}
+// j-th unit in issue order: the initialising units, then the others, each in row order
+__host__ __device__ constexpr int conv_unit_order(int jj, int rpt, int pair) {
+    int k = 0;
+    for (int j = 0; j < conv_units(rpt, pair); ++j)
+        if (conv_unit_init(j, pair) && k++ == jj) return j;
+    for (int j = 0; j < conv_units(rpt, pair); ++j)
+        if (!conv_unit_init(j, pair) && k++ == jj) return j;
+    return 0;
 }
 __host__ __device__ constexpr int conv_unit_rows(int j, int rpt, int pair) {
     return conv_unit_hi(j, rpt, pair) - conv_unit_lo(j, pair) + 1;
@@ -261,6 +272,9 @@ __global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ 
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int kAcc = conv_nacc(kN);
+    // warpgroup q's first tile is tile q: with fewer accumulators than warpgroups it would
+    // wait on a barrier phase that has not started yet (a parity wait that passes at once)
+    static_assert(kAcc >= kEpiGroups, "need one TMEM accumulator per epilogue warpgroup");
     constexpr uint32_t kCols = conv_pow2(kAcc * kN);  // TMEM allocation: a power of two >= 32
     constexpr uint32_t kIdesc = idesc_bf16_f32(128, kN);
     const int rs = 16 * a.G * conv_box_rows(a.G);  // region stride (bytes)
@@ -340,7 +354,7 @@ __global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ 
             // column tap dw of input row r reads region r from pixel G - 1 + dw on
             const uint32_t rs16 = (uint32_t)(rs / 16);
             const uint64_t adesc0 = smem_desc_kmajor(sA_u + (uint32_t)((a.G - 1) * 16), rs, 128);
-            constexpr int kNU = conv_units(RPT, kPair), kFirst = conv_unit_first(kPair);
+            constexpr int kNU = conv_units(RPT, kPair);
             constexpr int kPlaneB = conv_plane_bytes(RPT, kPair, kCGP, NPAD);
             TileCoord tc = tile_coord(t_begin, a.D, nh, ntw);
             int s = 0;
@@ -364,23 +378,25 @@ __global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ 
                         tc_fence_after();
                         // descriptor start-address fields are address >> 4: offsets add directly
                         const uint64_t ad = adesc0 + (uint64_t)((s * kStageBytes) >> 4);
-                        // the widened unit first, then the others in row order
+                        // the initialising units first (their first MMA overwrites its columns in
+                        // the tile's first plane), then the others
 #pragma unroll
                         for (int jj = 0; jj < kNU; ++jj) {
-                            const int j = jj == 0 ? kFirst : (jj <= kFirst ? jj - 1 : jj);
+                            const int j = conv_unit_order(jj, RPT, kPair);
                             const int nj = conv_unit_rows(j, RPT, kPair) * NPAD;
                             const uint32_t idesc = idesc_bf16_f32(128, nj);
                             const uint32_t dtj = dt + (uint32_t)(conv_unit_lo(j, kPair) * NPAD);
                             const uint64_t bd = smem_desc_kmajor(
                                 sB_u + (uint32_t)(c * kPlaneB + conv_unit_off(j, RPT, kPair, kCGP, NPAD)),
                                 (uint32_t)(nj * 16), 128);
+                            uint32_t acc = conv_unit_init(j, kPair) ? acc_flag : 1u;
                             if constexpr (kPair) {
 #pragma unroll
                                 for (int dw = 0; dw < 3; ++dw) {
                                     const uint32_t ao = (uint32_t)(2 * j) * rs16 + (uint32_t)dw;
                                     const uint32_t bo = (uint32_t)((dw * 2 * nj * 16) >> 4);
-                                    mma_bf16(dtj, ad + ao, bd + bo, idesc, acc_flag);
-                                    acc_flag = 1;
+                                    mma_bf16(dtj, ad + ao, bd + bo, idesc, acc);
+                                    acc = 1u;
                                 }
                             } else {
 #pragma unroll
@@ -389,11 +405,12 @@ __global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ 
                                     for (int kp = 0; kp < kCGP; kp += 2) {
                                         const uint32_t ao = (uint32_t)(j * CG + kp) * rs16 + (uint32_t)dw;
                                         const uint32_t bo = (uint32_t)(((dw * kCGP + kp) * nj * 16) >> 4);
-                                        mma_bf16(dtj, ad + ao, bd + bo, idesc, acc_flag);
-                                        acc_flag = 1;
+                                        mma_bf16(dtj, ad + ao, bd + bo, idesc, acc);
+                                        acc = 1u;
                                     }
                             }
                         }
+                        acc_flag = 1u;
                     }
                     mma_commit(&empty[s]);
                     if (++s == nst) {
@@ -847,15 +864,18 @@ static long long conv_packed_bytes(int n_out, int taps3d, int cpin, int rpt) {
     const int cg = cpin / 8;
     return (long long)(taps3d ? 3 : 1) * conv_plane_bytes(rpt, cg == 1, conv_cgp(cg), pad_npad(n_out));
 }
-// Output rows per tile: the most of 4, 3, 2 with N = rows x NPAD <= 128 whose
-// weights fit in shared memory next to two input stages; 1 otherwise. A channel
-// stride of 16 takes at most 2. (More rows per tile means fewer MMAs per output row,
-// (RPT + 2) / RPT input rows each, which outweighs a deeper input ring: measured on
-// the 32 -> 32 dual layer, 4 rows with two stages beat 3 rows with three by 6 %.)
+// Output rows per tile: the most of 6 .. 2 with RPT x NPAD <= kMaxTileN (at least one
+// TMEM accumulator per epilogue warpgroup) whose weights fit in shared memory next to two input stages; 1
+// otherwise. A channel stride of 16 takes at most 2; row pairs (8-channel inputs) take
+// an even count (an odd one leaves a zero partner row). More rows per tile means
+// fewer MMAs per output row, (RPT + 2) / RPT input rows each, which outweighs a deeper
+// input ring: on the 32 -> 32 dual layer, 4 rows with two stages beat 3 rows with
+// three by 6 %.
+constexpr int kMaxRpt = 6, kMaxTileN = 128;
 static int conv_rpt(int taps3d, int H, int cpin, int n_out) {
     const int npad = pad_npad(n_out);
-    for (int rpt = 4; rpt >= 2; --rpt) {
-        if (rpt > H || rpt * npad > 128 || (cpin == 16 && rpt > 2)) continue;
+    for (int rpt = kMaxRpt; rpt >= 2; --rpt) {
+        if (rpt > H || rpt * npad > kMaxTileN || (cpin == 16 && rpt > 2) || (cpin == 8 && (rpt & 1))) continue;
         const long long fixed = 1024 + ((conv_packed_bytes(n_out, taps3d, cpin, rpt) + 127) & ~127LL) +
                                 8 * (2 * kMaxStages + 2 * kMaxAcc) + 4 * npad + 64;
         if (fixed + 2LL * conv_stage_bytes(cpin / 8, rpt) <= 220 * 1024) return rpt;
@@ -909,19 +929,27 @@ static int launch_conv(const ConvArgs &a, cudaStream_t st) {
 
 template <int NPAD, int EPI, int RPT>
 static int launch_conv_cg(const ConvArgs &a, cudaStream_t st) {
-    switch (a.cin_groups) {
-        case 1: return launch_conv<NPAD, EPI, 1, RPT>(a, st);
-        case 2:
-            if constexpr (RPT <= 2) return launch_conv<NPAD, EPI, 2, RPT>(a, st);
-            return fail(CBCT_EINVAL, "conv: no tile shape for this channel stride");
-        case 4: return launch_conv<NPAD, EPI, 4, RPT>(a, st);
-        default: return fail(CBCT_EINVAL, "conv: channel stride must be 8, 16 or 32");
+    if constexpr (RPT * NPAD > kMaxTileN) {
+        return fail(CBCT_EINVAL, "conv: tile too tall for this channel count");
+    } else {
+        switch (a.cin_groups) {
+            case 1:
+                if constexpr (RPT % 2 == 0 || RPT == 1) return launch_conv<NPAD, EPI, 1, RPT>(a, st);
+                return fail(CBCT_EINVAL, "conv: no tile shape for this channel stride");
+            case 2:
+                if constexpr (RPT <= 2) return launch_conv<NPAD, EPI, 2, RPT>(a, st);
+                return fail(CBCT_EINVAL, "conv: no tile shape for this channel stride");
+            case 4: return launch_conv<NPAD, EPI, 4, RPT>(a, st);
+            default: return fail(CBCT_EINVAL, "conv: channel stride must be 8, 16 or 32");
+        }
     }
 }
 
 template <int NPAD, int EPI>
 static int launch_conv_rpt(const ConvArgs &a, int rpt, cudaStream_t st) {
     switch (rpt) {
+        case 6: return launch_conv_cg<NPAD, EPI, 6>(a, st);
+        case 5: return launch_conv_cg<NPAD, EPI, 5>(a, st);
         case 4: return launch_conv_cg<NPAD, EPI, 4>(a, st);
         case 3: return launch_conv_cg<NPAD, EPI, 3>(a, st);
         case 2: return launch_conv_cg<NPAD, EPI, 2>(a, st);

@@ -99,6 +99,33 @@ def test_conv_rejects_slope_outside_unit_interval(L):
     assert float(y.float().abs().sum()) == 0.0
 
 
+@pytest.mark.parametrize("cout,epi", [(32, 0), (5, 1)])
+def test_conv_many_tiles_per_cta(L, cout, epi):
+    """40 images of 64 x 256 give every persistent CTA several tiles, so the TMEM
+    accumulators are reused and handed between the MMA issuer and the four epilogue
+    warpgroups many times; images at both ends of the batch are checked."""
+    from oracle import lpd_ref as R
+    rng = np.random.default_rng(11 + cout)
+    nimg, dims, cin = 40, (64, 256), 32
+    x = torch.tensor(rng.standard_normal((nimg, cin) + dims))
+    w = torch.tensor(rng.standard_normal((cout, cin, 3, 3)) * 0.1)
+    b = torch.tensor(rng.standard_normal(cout) * 0.1)
+    wg = w.reshape(cout, cin, -1).permute(0, 2, 1).contiguous().float().cuda()
+    pick = [0, 1, nimg - 2, nimg - 1]
+    conv = R.conv(R.bf16(x[pick]), R.bf16(w), b.float().double())
+    if epi == 0:
+        y = run_conv(L, to_cl(x, 32), dims, 0, wg, b.float().cuda(), cin, cout, 0, 0, 32)
+        got = from_cl(y[pick], cout)
+        ref = R.lrelu(conv)
+    else:
+        state0 = torch.tensor(rng.standard_normal((cout, nimg) + dims))
+        state = state0.float().cuda().contiguous()
+        run_conv(L, to_cl(x, 32), dims, 0, wg, b.float().cuda(), cin, cout, 0, 1, 8, state=state)
+        got = state.double().cpu()[:, pick]
+        ref = state0[:, pick] + conv.movedim(1, 0)
+    assert rel(got, ref) <= (1e-2 if epi == 0 else 1e-5), rel(got, ref)
+
+
 @pytest.mark.parametrize("taps3d,dims", [(0, (21, 33)), (1, (7, 11, 13))])
 def test_conv_residual_into_state(L, taps3d, dims):
     from oracle import lpd_ref as R

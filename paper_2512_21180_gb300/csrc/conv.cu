@@ -51,6 +51,7 @@ struct ConvArgs {
     const __nv_bfloat16 *mask;  // EPI_MASK_BF16: forward activation (same layout as y); out *= (mask > 0 ? 1 : slope)
     float *state;            // EPI_RESIDUAL_F32: state[c * sstride + pixel] = state_in[..] + v
     const float *state_in;   // (may equal state)
+    int state_in_zero;       // the old state is zero: state = v without reading state_in
     long long sstride;
     int *status;
 };
@@ -82,7 +83,8 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *ac
             if (c0 >= a.cout) break;
             float old[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) old[c] = c0 + c < a.cout ? a.state_in[(c0 + c) * a.sstride + p] : 0.f;
+            for (int c = 0; c < 8; ++c)
+                old[c] = (c0 + c < a.cout && !a.state_in_zero) ? a.state_in[(c0 + c) * a.sstride + p] : 0.f;
 #pragma unroll
             for (int c = 0; c < 8; ++c)
                 if (c0 + c < a.cout) a.state[(c0 + c) * a.sstride + p] = old[c] + (acc[c0 + c] + bias[c0 + c]);
@@ -1094,7 +1096,7 @@ int cbct::conv_pack_jobs(const ConvPackJob *jobs, int njobs, long long max_nelem
 int cbct::conv_apply(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d, const float *w, const float *bias,
                      int cin, int cout, int flip, int epi, float slope, void *y, int cpout, const void *mask,
                      const float *state_in, float *state, long long sstride, int *status, cudaStream_t st,
-                     const uint8_t *packed) {
+                     const uint8_t *packed, int zero_state_in) {
     if (!x || !w || nimg < 1 || D < 1 || H < 1 || W < 1 || cin < 1 || cout < 1 ||
         (cpin != 8 && cpin != 16 && cpin != 32) || cpin < (flip ? cout : cin))
         return fail(CBCT_EINVAL, "conv: invalid argument (sizes, or cpin below the input channels)");
@@ -1128,6 +1130,7 @@ int cbct::conv_apply(const void *x, int nimg, int D, int H, int W, int cpin, int
         a.mask = static_cast<const __nv_bfloat16 *>(mask);
         a.state = state;
         a.state_in = state_in ? state_in : state;
+        a.state_in_zero = zero_state_in;
         a.sstride = sstride;
         a.status = status;
         rc = conv_run(a, n_out, epi, rpt, st);

@@ -33,13 +33,13 @@ int operator_norm(cbct_geom *g, int iters, double *out);
 int back_project_colw(const cbct_geom *g, const float *proj, const float *colw, float *vol, int batch, int accumulate,
                       cudaStream_t st);
 // cbct_conv with the residual epilogue reading its old state from state_in (which may
-// equal state) and writing state = state_in + conv. packed: the layer's B operand
-// already packed by conv_pack_jobs for the same (taps3d, H, cpin, cin, cout, flip),
-// or null to pack it here.
+// equal state) and writing state = state_in + conv (state = conv without reading
+// state_in when zero_state_in). packed: the layer's B operand already packed by
+// conv_pack_jobs for the same (taps3d, H, cpin, cin, cout, flip), or null to pack it here.
 int conv_apply(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d, const float *w, const float *bias,
                int cin, int cout, int flip, int epi, float slope, void *y, int cpout, const void *mask,
                const float *state_in, float *state, long long sstride, int *status, cudaStream_t st,
-               const uint8_t *packed = nullptr);
+               const uint8_t *packed = nullptr, int zero_state_in = 0);
 // Packing of one layer's weights: the shape part is filled by conv_plan, the offsets
 // (weights within the parameter array, bytes within the packed buffer) by the caller.
 struct ConvPackJob {

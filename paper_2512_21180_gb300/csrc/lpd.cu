@@ -220,9 +220,10 @@ int grid_n(long long n) {
 // forward conv of layer L; the residual epilogue (epi 1) writes state = state_in + conv
 static int conv_fwd(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *x, int cpin, int nimg, int D, int H, int W,
                     int epi, __nv_bfloat16 *y, float *state, long long sstride, cudaStream_t st,
-                    const float *state_in = nullptr) {
+                    const float *state_in = nullptr, int zero_state_in = 0) {
     return conv_apply(x, nimg, D, H, W, cpin, L.taps3d, m->params + L.w_off, m->params + L.b_off, L.cin, L.cout, 0, epi,
-                      m->d.slope, y, 32, nullptr, state_in, state, sstride, m->status, st, m->wpk + L.pk_off);
+                      m->d.slope, y, 32, nullptr, state_in, state, sstride, m->status, st, m->wpk + L.pk_off,
+                      zero_state_in);
 }
 
 // input-gradient conv of layer L: dy (BF16 [..][cp_dy], L.cout channels) -> L.cin outputs
@@ -240,9 +241,9 @@ static int conv_dx(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *dy, int
 // One forward iteration n: (f_in, h_in) -> (f_out, h_out); activations left in the
 // workspaces (a1, a2, b1, b2, din, pin).
 // pf, bp: where the iteration's P f_1 and P^T (w h_1) go (workspaces, or the per-
-// iteration buffers of a training forward).
+// iteration buffers of a training forward). h_zero: h_in is zero and is not read.
 static int lpd_iter_fwd(cbct_lpd *m, int n, const float *f_in, const float *h_in, float *f_out, float *h_out,
-                        float *pf, float *bp, cudaStream_t st) {
+                        float *pf, float *bp, cudaStream_t st, bool h_zero = false) {
     const long long NV = m->nvox, NP = m->nproj;
     const int M = m->d.n_mem;
     const LayerSpec *Ld = &m->layers[6 * n], *Lp = &m->layers[6 * n + 3];
@@ -251,13 +252,13 @@ static int lpd_iter_fwd(cbct_lpd *m, int n, const float *f_in, const float *h_in
     int rc = forward_project(m->g, f_in + 1 * NV, pf, 1, 0, sv);
     if (rc) return rc;
     Planes pl{};
-    for (int c = 0; c < M; ++c) { pl.p[c] = h_in + c * NP; pl.s[c] = 1.f; }
+    for (int c = 0; c < M; ++c) { pl.p[c] = h_zero ? nullptr : h_in + c * NP; pl.s[c] = 1.f; }
     pl.p[M] = pf; pl.s[M] = m->d.mu_ref;
     pl.p[M + 1] = m->y; pl.s[M + 1] = 1.f;
     k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
     if ((rc = conv_fwd(m, Ld[0], m->din, 8, DUAL_DIMS, 0, m->a1, nullptr, 0, st))) return rc;
     if ((rc = conv_fwd(m, Ld[1], m->a1, 32, DUAL_DIMS, 0, m->a2, nullptr, 0, st))) return rc;
-    if ((rc = conv_fwd(m, Ld[2], m->a2, 32, DUAL_DIMS, 1, nullptr, h_out, NP, st, h_in))) return rc;
+    if ((rc = conv_fwd(m, Ld[2], m->a2, 32, DUAL_DIMS, 1, nullptr, h_out, NP, st, h_in, h_zero))) return rc;
     // primal block input [f (M), bp_scale P^T (w h_1)]
     rc = back_project_colw(m->g, h_out + 1 * NP, m->wred, bp, 1, 0, st);
     if (rc) return rc;
@@ -433,9 +434,12 @@ static int lpd_forward_impl(cbct_lpd *m, const float *y, const float *x0, const 
     } else {
         k_init_f<<<grid_n(NV), 256, 0, st>>>(x0, m->f, NV, M, 1.f / m->d.mu_ref);
     }
+    // h_0 = 0: an inference pass does not store it (the first dual block reads no h);
+    // a training pass keeps it for the backward
+    const bool h_zero = !h0 && !save_for_backward;
     if (h0) {
         CBCT_CUDA_TRY(cudaMemcpyAsync(m->h, h0, sizeof(float) * M * NP, cudaMemcpyDeviceToDevice, st));
-    } else {
+    } else if (!h_zero) {
         CBCT_CUDA_TRY(cudaMemsetAsync(m->h, 0, sizeof(float) * M * NP, st));
     }
     for (int n = 0; n < N; ++n) {
@@ -443,7 +447,8 @@ static int lpd_forward_impl(cbct_lpd *m, const float *y, const float *x0, const 
         float *pf = save_for_backward ? m->pf_saved + (long long)n * NP : m->tproj;
         float *bp = save_for_backward ? m->bp_saved + (long long)n * NV : m->tvol;
         int rc = lpd_iter_fwd(m, n, m->f + (long long)si * M * NV, m->h + (long long)si * M * NP,
-                              m->f + (long long)so * M * NV, m->h + (long long)so * M * NP, pf, bp, st);
+                              m->f + (long long)so * M * NV, m->h + (long long)so * M * NP, pf, bp, st,
+                              h_zero && n == 0);
         if (rc) return rc;
     }
     const long long last = save_for_backward ? N : 0;

@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(kThreads3, 3) k_backproject_v3(GeomDev g, cons
                     // first row whose sample lies above z0 - 1 + m
                     auto row_above = [&](int m) {
                         const float vs = ((float)(z0 - 1 + m) - voff) * irs;
-                        return min(max((int)floorf(fminf(fmaxf(vs, -1.0e6f), 1.0e6f)) + 1, 0), nv);
+                        return min(max(__float2int_rd(fminf(fmaxf(vs, -1.0e6f), 1.0e6f)) + 1, 0), nv);
                     };
                     int va = row_above(0);
                     float carry = 0.f;  // upper-voxel share of the previous interval
@@ -314,18 +314,20 @@ __global__ void __launch_bounds__(kThreads3, 3) k_backproject_v3(GeomDev g, cons
                             float qf = fmaf((float)va, step, voff) - (float)(z0 - 1 + m);
                             const float *pp = Pk + (long long)va * nu + u;
                             const int n = ve - va;
+                            float T = 0.f;  // sum of rr p: S1 = qf S0 + step T
 #pragma unroll
                             for (int rr = 0; rr < 5; ++rr) {
                                 const float p = rr < n ? __ldg(pp + rr * nu) : 0.f;
                                 S0 += p;
-                                S1 = fmaf(p, fmaf((float)rr, step, qf), S1);
+                                if (rr > 0) T = fmaf((float)rr, p, T);
                             }
 #pragma unroll 1
                             for (int rr = 5; rr < n; ++rr) {
                                 const float p = __ldg(pp + rr * nu);
                                 S0 += p;
-                                S1 = fmaf(p, fmaf((float)rr, step, qf), S1);
+                                T = fmaf((float)rr, p, T);
                             }
+                            S1 = fmaf(qf, S0, step * T);
                         }
                         // voxel z0 - 1 + m: upper share of interval m - 1, lower share of interval m
                         if (m >= 1) {

@@ -270,7 +270,8 @@ __global__ void __launch_bounds__(kThreads) k_forward_tma(const __grid_constant_
                                 const float qz = fma_rn(di, dqz, qcz);
                                 const float fb0 = floorf(qb), fz0 = floorf(qz);
                                 const float fb = qb - fb0, fz = qz - fz0;
-                                int off = (int)fz0 * BW + (int)fb0 + base;
+                                // fz0 BW + fb0 is an exact small integer in FP32: one conversion
+                                int off = (int)fmaf(fz0, (float)BW, fb0) + base;
                                 off = (int)min((unsigned)off, (unsigned)(ZH * BW - BW - 2));
                                 const float *r = st + p * ZH * BW + off;
                                 const float v00 = r[0], v10 = r[1], v01 = r[BW], v11 = r[BW + 1];

@@ -71,6 +71,10 @@ def test_lpd_forward_and_gradients_match_oracle(O, M):
     assert rel_l2(gg, gref) <= 5e-2, rel_l2(gg, gref)
     assert rel_l2(to_np(gy), yt.grad.numpy()) <= 5e-2
     assert rel_l2(to_np(g0), x0t.grad.numpy()) <= 5e-2
+    # an inference pass (no stored states; the zero initial dual memory is never read)
+    # runs the same arithmetic as the training pass above
+    xi = model.forward(to_gpu(y), to_gpu(x0))
+    assert torch.equal(xi, xg)
 
 
 def test_lpd_training_reduces_loss(O, M):

@@ -97,21 +97,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_reference(steps: int, warmup: int, sample_angles: int):
-    """FP64 CPU checker on a bounded sample: the clinical geometry restricted to
+def cpu_reference(steps: int, warmup: int, sample_angles: int, workload: str = WORKLOAD, best: bool = False):
+    """FP64 CPU checker on a bounded sample: the workload's geometry restricted to
     `sample_angles` evenly spaced angles (same volume, panel and ray count per
-    angle); throughput in Gsamples/s of forward + adjoint."""
+    angle); throughput in Gsamples/s of forward + adjoint (mean of the timed steps,
+    or the best one)."""
     import numpy as np
 
     import oracle as O
     from paper_2512_21180_gb300 import inputs as I
 
-    g = I.geometry(WORKLOAD)
+    g = I.geometry(workload)
     ang = 2 * np.pi * np.arange(0, g["n_angles"], g["n_angles"] // sample_angles)[:sample_angles] / g["n_angles"]
     gs = dict(g)
     gs["n_angles"] = len(ang)
     G = O.Geom(gs, angles=ang)
-    vol = O.phantom(G, I.phantom_params(WORKLOAD, 2))
+    vol = O.phantom(G, I.phantom_params(workload, 2))
     _, ns = O.forward(G, vol, return_count=True)
     times = []
     for it in range(warmup + steps):
@@ -121,9 +122,21 @@ def cpu_reference(steps: int, warmup: int, sample_angles: int):
         dt = time.perf_counter() - t0
         if it >= warmup:
             times.append(dt)
-    mean = sum(times) / len(times)
+    mean = min(times) if best else sum(times) / len(times)
     return {"value": 2 * ns / mean / 1e9, "sec_per_step": mean, "samples_per_step": 2 * ns,
             "cores": O.num_threads(), "angles": len(ang)}
+
+
+def cpu_reference_single_core(sample_angles: int = 1) -> dict:
+    """The same FP64 checker restricted to one OpenMP thread (a child process, since
+    the thread count is fixed when OpenMP starts), on `sample_angles` clinical angles."""
+    import subprocess
+    env = dict(os.environ, OMP_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.cpu_reference(1, 0, %d)))" % (os.path.dirname(os.path.abspath(__file__)),
+                                                                   sample_angles))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
 
 
 def run_reference(args):
@@ -377,6 +390,13 @@ def report(args, geom, world, S_fwd, samples_step, value, ms, ms_fwd, ms_adj, e2
         line["cpu_baseline"] = {"value": r["value"], "unit": "Gsamples/s", "cores": r["cores"], "kind": "oracle",
                                 "sample": f"{r['angles']} of 400 evenly spaced angles of the same workload, "
                                           f"forward + adjoint, FP64, one step"}
+        # the same checker on one core, and on the 64^3 / 64-angle operator-test workload
+        r1 = cpu_reference_single_core(1)
+        rs = cpu_reference(3, 0, 64, workload="small64", best=True)
+        line["cpu_baseline"]["single_core"] = {"value": r1["value"], "cores": r1["cores"],
+                                               "sample": "1 of 400 angles of the same workload, one step"}
+        line["cpu_baseline"]["small64"] = {"value": rs["value"], "cores": rs["cores"],
+                                           "sample": "64^3 at 4 mm, all 64 angles, 96x64 panel; best of 3"}
     if not args.no_lpd and world == 1 and args.workload == WORKLOAD:
         line["lpd_vs_pdhg"] = lpd_timing(1, 2)
     print(json.dumps(line), flush=True)

@@ -97,6 +97,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(vals, dist, device):
+    """Element-wise maximum of per-rank timings, returned on every rank (the slowest
+    rank defines the step time); the values themselves on a single rank."""
+    if dist is None:
+        return list(vals)
+    import torch
+    t = torch.tensor(list(vals), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_value(samples_per_rank_step: float, world: int, ms: float) -> float:
+    """Gsamples/s of the whole job: every rank projects its own volume (weak scaling),
+    so the samples of all ranks over the slowest rank's step time."""
+    return samples_per_rank_step * world / (ms * 1e-3) / 1e9
+
+
 def cpu_reference(steps: int, warmup: int, sample_angles: int, workload: str = WORKLOAD, best: bool = False):
     """FP64 CPU checker on a bounded sample: the workload's geometry restricted to
     `sample_angles` evenly spaced angles (same volume, panel and ray count per
@@ -248,11 +265,8 @@ def main():
     t_adj = [b.elapsed_time(c) for _, b, c in ev]
     ms = sum(f + a for f, a in zip(t_fwd, t_adj)) / args.steps
     ms_fwd, ms_adj = sum(t_fwd) / args.steps, sum(t_adj) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms, ms_fwd, ms_adj], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_fwd, ms_adj = t.tolist()
-    value = samples_step * world / (ms * 1e-3) / 1e9
+    ms, ms_fwd, ms_adj = max_over_ranks([ms, ms_fwd, ms_adj], dist, "cuda")
+    value = whole_job_value(samples_step, world, ms)
 
     # end to end through the public API with host buffers: pinned host volume in,
     # backprojected volume out, copies inside the timed region
@@ -260,7 +274,7 @@ def main():
         ms_e2e = float("nan")
     else:
         ms_e2e = e2e_leg(args, geom, vol, proj, back, stream, dist)
-    e2e = samples_step * world / (ms_e2e * 1e-3) / 1e9
+    e2e = whole_job_value(samples_step, world, ms_e2e)
 
     if rank != 0:
         if dist is not None:
@@ -299,9 +313,7 @@ def e2e_leg(args, geom, vol, proj, back, stream, dist):
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1) / args.steps
     if dist is not None:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = t.item()
+        ms_e2e = max_over_ranks([ms_e2e], dist, "cuda")[0]
     return ms_e2e
 
 

@@ -258,6 +258,13 @@ int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d
               const float *bias, int cin, int cout, int flip, int epi, float slope, void *y, int cpout,
               const void *mask, float *state, long long sstride, int *status, void *stream);
 
+/* Tile plan cbct_conv uses for a convolution of this shape (host only: no GPU call):
+ * output rows per tile (rpt), bytes of the packed weights (B operand in row units),
+ * input stages in shared memory and TMEM accumulators per CTA. Arguments as for
+ * cbct_conv; any output pointer may be NULL. Errors: CBCT_EINVAL for an invalid shape. */
+int cbct_conv_plan(int taps3d, int H, int cpin, int cin, int cout, int flip, int *rpt, long long *packed_bytes,
+                   int *stages, int *accumulators);
+
 /* Weight and bias gradients of the convolution above: dw[co][tap][ci] (+)=
  * sum_p dy[p][co] x[p + tap][ci], db[co] (+)= sum_p dy[p][co]; x BF16 row-blocked
  * with cpin slots, dy BF16 row-blocked with cpout slots (both multiples of 8). CUDA

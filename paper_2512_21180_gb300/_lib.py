@@ -65,6 +65,8 @@ SIGNATURES = {
     "cbct_landweber": (I32, [P, P, P, I32, I32, F64, I32, P]),
     "cbct_conv": (I32, [P, I32, I32, I32, I32, I32, I32, P, P, I32, I32, I32, I32, F32, P, I32, P, P, I64, P, P]),
     "cbct_conv_wgrad": (I32, [P, I32, I32, P, I32, I32, I32, I32, I32, I32, I32, P, P, I32, P]),
+    "cbct_conv_plan": (I32, [I32, I32, I32, I32, I32, I32, ctypes.POINTER(I32), ctypes.POINTER(I64),
+                             ctypes.POINTER(I32), ctypes.POINTER(I32)]),
     "lpd_create": (I32, [P, ctypes.POINTER(LpdDesc), ctypes.POINTER(P)]),
     "lpd_destroy": (None, [P]),
     "lpd_info": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(F32)]),

@@ -1146,6 +1146,23 @@ extern "C" int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin,
                       state, sstride, status, (cudaStream_t)stream);
 }
 
+extern "C" int cbct_conv_plan(int taps3d, int H, int cpin, int cin, int cout, int flip, int *rpt,
+                              long long *packed_bytes, int *stages, int *accumulators) {
+    const int n_out = flip ? cin : cout;
+    if (H < 1 || cin < 1 || cout < 1 || n_out > 32 || (cpin != 8 && cpin != 16 && cpin != 32) ||
+        cpin < (flip ? cout : cin))
+        return fail(CBCT_EINVAL, "cbct_conv_plan: invalid shape");
+    const int r = conv_rpt(taps3d ? 1 : 0, H, cpin, n_out), npad = pad_npad(n_out);
+    const long long bytes = conv_packed_bytes(n_out, taps3d ? 1 : 0, cpin, r);
+    const long long fixed = 1024 + ((bytes + 127) & ~127LL) + 8 * (2 * kMaxStages + 2 * kMaxAcc) + 4 * npad + 64;
+    const long long st = std::min<long long>(6, (220LL * 1024 - fixed) / conv_stage_bytes(cpin / 8, r));
+    if (rpt) *rpt = r;
+    if (packed_bytes) *packed_bytes = bytes;
+    if (stages) *stages = (int)st;
+    if (accumulators) *accumulators = conv_nacc(r * npad);
+    return 0;
+}
+
 extern "C" int cbct_conv_wgrad(const void *x, int cpin, int cin, const void *dy, int cpout, int cout, int nimg, int D,
                                int H, int W, int taps3d, float *dw, float *db, int accumulate, void *stream) {
     if (!x || !dy || !dw || !db || cin < 1 || cout < 1) return fail(CBCT_EINVAL, "cbct_conv_wgrad: invalid argument");

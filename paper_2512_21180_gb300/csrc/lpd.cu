@@ -346,11 +346,14 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     // channel slots, the others 32; 2-D blocks run over the nv rows, 3-D over ny)
     std::vector<ConvPackJob> jobs(m->layers.size());
     long long pk_bytes = 0;
-    for (size_t i = 0; i < m->layers.size() && e == cudaSuccess; ++i) {
+    for (size_t i = 0; i < m->layers.size(); ++i) {
         LayerSpec &L = m->layers[i];
         const long long b = conv_plan(L.taps3d, L.taps3d ? g->dev.n[1] : g->dev.nv, i % 3 == 0 ? 8 : 32, L.cin,
                                       L.cout, 0, &jobs[i]);
-        if (b < 0) e = cudaErrorInvalidValue;
+        if (b < 0) {
+            lpd_destroy(m);
+            return fail(CBCT_EINVAL, "lpd_create: no convolution plan for layer " + std::to_string(i));
+        }
         jobs[i].w_off = L.w_off;
         jobs[i].out_off = L.pk_off = pk_bytes;
         pk_bytes += (b + 255) & ~255LL;

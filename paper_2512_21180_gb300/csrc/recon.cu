@@ -1,4 +1,4 @@
-// Classical reconstructions used by the learned method and as its judge:
+// Classical reconstructions: the learned method's start and the baseline it is compared with:
 //  - FDK with redundancy weighting (paper Algorithm 1 initialisation "FDK_w",
 //    Sec. 2.4; Feldkamp, Davis, Kress 1984): cosine and redundancy weights, Ram-Lak
 //    ramp filter along detector rows at the isocentre pitch, distance-weighted

@@ -112,19 +112,25 @@ int cbct_forward_config(const cbct_geom *g, int *cfg, double *need_b, double *ne
  * accumulate = 0 overwrites proj, 1 adds to it. FP32 in, FP32 accumulation.
  * batch >= 1; batch * n_angles <= 65535. Scratch: two plane-major copies of the
  * volumes (2 * batch * nx * ny * nz floats, rows padded to 4), from the
- * stream-ordered pool. */
+ * stream-ordered pool. Errors: CBCT_EINVAL (before any launch) for a NULL pointer,
+ * batch < 1, accumulate not 0 or 1, batch * n_angles > 65535 or a current device
+ * other than the geometry's; CBCT_ENOMEM when the scratch cannot be allocated;
+ * CBCT_ECUDA for a failed launch. */
 int forward_project(const cbct_geom *g, const float *vol, float *proj, int batch, int accumulate,
                     void *stream);
 
 /* Backprojection (a3, Sec. 2.1): vol[b] (+)= P* proj[b], the exact transpose of
  * forward_project (same rays, planes and bilinear weights), computed as an
  * atomic-free voxel-driven gather. Scratch: batch * n_angles * nv * nu floats
- * (the ray-weighted projections), from the stream-ordered pool. */
+ * (the ray-weighted projections, plus up to 16 partial volumes when small volumes
+ * split the angles), from the stream-ordered pool. Errors: as forward_project, and
+ * CBCT_EINVAL when batch * ceil(nz / 16) exceeds the 65535-CTA grid limit. */
 int back_project(const cbct_geom *g, const float *proj, float *vol, int batch, int accumulate,
                  void *stream);
 
 /* FP64 instantiations of the same operators (tests and finite-difference checks;
- * the principal-axis decision stays the FP32 one). */
+ * the principal-axis decision stays the FP32 one). Same arguments, layouts and
+ * errors as the FP32 calls, with double buffers. */
 int forward_project_f64(const cbct_geom *g, const double *vol, double *proj, int batch,
                         int accumulate, void *stream);
 int back_project_f64(const cbct_geom *g, const double *proj, double *vol, int batch,

@@ -124,7 +124,7 @@ int forward_project(const cbct_geom *g, const float *vol, float *proj, int batch
  * atomic-free voxel-driven gather. Scratch: batch * n_angles * nv * nu floats
  * (the ray-weighted projections, plus up to 16 partial volumes when small volumes
  * split the angles), from the stream-ordered pool. Errors: as forward_project, and
- * CBCT_EINVAL when batch * ceil(nz / 16) exceeds the 65535-CTA grid limit. */
+ * CBCT_EINVAL when batch * ceil(nz / 4) exceeds 65535 (a grid dimension limit). */
 int back_project(const cbct_geom *g, const float *proj, float *vol, int batch, int accumulate,
                  void *stream);
 

@@ -28,7 +28,9 @@
  *        CBCT_EINVAL  -1  invalid argument (nothing was launched)
  *        CBCT_ECUDA   -2  CUDA runtime error (launch or allocation)
  *        CBCT_ENOMEM  -3  out of device memory
- *        CBCT_EDEVICE -4  a kernel reported an error through its status word
+ *        CBCT_EDEVICE -4  reserved: kernels report a bounded wait that gave up through
+ *                         a device status word the caller reads (cbct_device_status,
+ *                         the status argument of cbct_conv), not through a return code
  *
  * Geometry (the paper's scanner, Sec. 2.1: circular orbit, offset flat panel):
  * isocentre at the origin, rotation axis z. At angle theta the source sits at

@@ -368,6 +368,11 @@ int lpd_clip_grads(cbct_lpd *m, float max_norm, float grad_scale, double *norm_o
 int lpd_adam_step(cbct_lpd *m, float lr, float beta1, float beta2, float eps, int step, float grad_scale,
                   void *stream);
 
+/* Read (and with clear = 1 reset) the model's device status word: 0 = ok, 1 = one of
+ * its convolution kernels gave up waiting on its tensor-core pipeline (it then left
+ * its outputs unwritten). Synchronises the device. Errors: CBCT_EINVAL for NULL. */
+int lpd_device_status(const cbct_lpd *m, int *out, int clear);
+
 /* Copy the n FP32 parameters to / from host memory (checkpoints). Synchronous. */
 int lpd_set_params(cbct_lpd *m, const float *host, long long n);
 int lpd_get_params(const cbct_lpd *m, float *host, long long n);

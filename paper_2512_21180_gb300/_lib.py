@@ -51,6 +51,7 @@ SIGNATURES = {
     "back_project_noalloc": (I32, [P, P, P, I32, I32, P]),
     "cbct_count_samples": (I32, [P, ctypes.POINTER(I64), P]),
     "cbct_device_status": (I32, [P, ctypes.POINTER(I32), I32]),
+    "lpd_device_status": (I32, [P, ctypes.POINTER(I32), I32]),
     "cbct_forward_config": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(F64), ctypes.POINTER(F64)]),
     "cbct_phantom": (I32, [P, P, I32, I32, P, P]),
     "cbct_poisson": (I32, [P, I64, F64, U64, P, P]),

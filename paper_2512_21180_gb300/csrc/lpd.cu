@@ -662,6 +662,15 @@ extern "C" int lpd_adam_step(cbct_lpd *m, float lr, float beta1, float beta2, fl
     return 0;
 }
 
+extern "C" int lpd_device_status(const cbct_lpd *m, int *out, int clear) {
+    if (!m || !out) return fail(CBCT_EINVAL, "lpd_device_status: NULL argument");
+    int v = 0;
+    CBCT_CUDA_TRY(cudaMemcpy(&v, m->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (clear && v) CBCT_CUDA_TRY(cudaMemset(m->status, 0, sizeof(int)));
+    *out = v;
+    return 0;
+}
+
 extern "C" int lpd_set_params(cbct_lpd *m, const float *host, long long n) {
     if (!m || !host || n != m->nparams) return fail(CBCT_EINVAL, "lpd_set_params: size mismatch");
     CBCT_CUDA_TRY(cudaMemcpy(m->params, host, sizeof(float) * n, cudaMemcpyHostToDevice));

@@ -57,6 +57,12 @@ class LPD:
         p = np.ascontiguousarray(p, dtype=np.float32)
         check(_lib.load().lpd_set_params(self.handle, p.ctypes.data, self.nparams), "lpd_set_params")
 
+    def device_status(self, clear: bool = False) -> int:
+        """The model's device status word (0 = no convolution kernel gave up a bounded wait)."""
+        out = ctypes.c_int(0)
+        check(_lib.load().lpd_device_status(self.handle, ctypes.byref(out), int(clear)), "lpd_device_status")
+        return int(out.value)
+
     def grads(self) -> np.ndarray:
         """Host copy of the accumulated parameter gradients."""
         out = np.zeros(self.nparams, dtype=np.float32)

@@ -75,6 +75,13 @@ class Geometry:
     def proj_shape(self):
         return (self.na, self.nv, self.nu)
 
+    def device_status(self, clear: bool = False) -> int:
+        """The geometry's device status word (0 = no kernel gave up a bounded wait)."""
+        out = ctypes.c_int(0)
+        with torch.cuda.device(self.device):
+            check(_lib.load().cbct_device_status(self.handle, ctypes.byref(out), int(clear)), "device_status")
+        return int(out.value)
+
     def count_samples(self) -> int:
         out = ctypes.c_longlong(0)
         with torch.cuda.device(self.device):

@@ -167,3 +167,18 @@ def test_trained_network_gains_over_fdk(M):
         out = model.forward(y[0], x0)
         gains.append(psnr(out, x) - psnr(x0, x))
     assert min(gains) > 8.0, gains
+
+
+def test_status_words_stay_clear(M):
+    """After a forward and backward pass no kernel of the model or of its geometry
+    gave up a bounded wait: both device status words read 0."""
+    P, L = M
+    geom = P.Geometry(GEOM)
+    model = L.LPD(geom, n_iter=1, seed=2)
+    y = torch.rand((1,) + geom.proj_shape, device="cuda")
+    x0 = torch.rand((1,) + geom.vol_shape, device="cuda")
+    out = model.forward(y[0], x0[0], save_for_backward=True)
+    model.zero_grad()
+    model.backward(torch.ones_like(out))
+    assert model.device_status() == 0
+    assert geom.device_status(clear=True) == 0

@@ -12,6 +12,9 @@
 // gathers step * bilinear weight * projection over exactly the (ray, plane,
 // neighbour) triples the forward visits. The per-ray step is folded into the
 // projection beforehand (k_weight_rays) so the gather needs no square root.
+// This kernel serves the FP64 instantiation and geometries whose principal-axis
+// columns do not form intervals; FP32 calls otherwise use the segment gather
+// k_backproject_v3 further down, which visits the same triples.
 #include <algorithm>
 #include <cmath>
 #include <mutex>

@@ -1,13 +1,17 @@
 """FP64 reference of the learned primal-dual blocks (test infrastructure only).
 
 Plain PyTorch CPU in float64. The convolution blocks of the paper's dual and primal
-updates (Sec. 2.4, Algorithm 1: Gamma and Lambda; here 3-layer width-32 blocks
+updates (Sec. 2.6, Algorithm 1: Gamma and Lambda; here 3-layer width-32 blocks
 with LeakyReLU between layers, 2D over the detector plane for the dual block, 3D
 over the volume for the primal block) and one unrolled iteration pair, with the
 projector pair taken from the FP64 C oracle through autograd functions.
 
 BF16 operands are emulated by rounding the inputs and weights to bfloat16 before
-the FP64 arithmetic, exactly where the GPU path rounds them.
+the FP64 arithmetic, exactly where the GPU path rounds them. With round_grad the
+backward pass does the same for the gradient operands of the tensor-core
+contractions: the gradient reaching each convolution's output (the operand of the
+input-gradient and weight-gradient convolutions) is rounded to bfloat16, and the
+rest of the backward stays FP64.
 """
 from __future__ import annotations
 
@@ -22,8 +26,29 @@ SLOPE = 0.2
 
 
 def bf16(t: torch.Tensor) -> torch.Tensor:
-    """Round to bfloat16 (round to nearest even) and back to float64."""
-    return t.to(torch.bfloat16).to(torch.float64)
+    """Round to bfloat16 (round to nearest even) and back to float64. The rounded value
+    is an operand copy of the FP32/FP64 master value, so the gradient passes through to
+    the master unchanged (a plain dtype cast would round the gradient as well)."""
+    r = t.detach().to(torch.bfloat16).to(torch.float64)
+    if not t.requires_grad:
+        return r
+    return t + (r - t.detach())
+
+
+class _RoundGrad(torch.autograd.Function):
+    """Identity whose backward rounds the incoming gradient to bfloat16."""
+
+    @staticmethod
+    def forward(ctx, x):
+        return x.view_as(x)
+
+    @staticmethod
+    def backward(ctx, g):
+        return g.to(torch.bfloat16).to(torch.float64)
+
+
+def round_grad(t: torch.Tensor) -> torch.Tensor:
+    return _RoundGrad.apply(t)
 
 
 def conv(x: torch.Tensor, w: torch.Tensor, b: torch.Tensor | None) -> torch.Tensor:
@@ -38,14 +63,18 @@ def lrelu(x: torch.Tensor) -> torch.Tensor:
     return torch.where(x > 0, x, SLOPE * x)
 
 
-def block(x: torch.Tensor, params, round_bf16: bool = True) -> torch.Tensor:
+def block(x: torch.Tensor, params, round_bf16: bool = True, round_grads: bool = False) -> torch.Tensor:
     """conv -> LReLU -> conv -> LReLU -> conv; params = [(w1, b1), (w2, b2), (w3, b3)].
     With round_bf16 the conv inputs and weights are rounded to bfloat16 first (the
-    GPU's operand precision); accumulation stays FP64."""
+    GPU's operand precision); accumulation stays FP64. With round_grads the gradient
+    with respect to each convolution's output is rounded to bfloat16 in the backward
+    pass (the GPU's operand precision of its input- and weight-gradient convolutions)."""
     r = bf16 if round_bf16 else (lambda t: t)
     h = x
     for i, (w, b) in enumerate(params):
         h = conv(r(h), r(w), b)
+        if round_grads:
+            h = round_grad(h)
         if i < len(params) - 1:
             h = lrelu(h)
     return h
@@ -83,24 +112,32 @@ def backproject(G, y):
 
 def lpd(G, y: torch.Tensor, x0: torch.Tensor | None, w_red: torch.Tensor, dual_params, primal_params,
         n_mem: int = 5, round_bf16: bool = True, mu_ref: float = 1.0, bp_scale: float = 1.0,
-        f0: torch.Tensor | None = None, h0: torch.Tensor | None = None, return_state: bool = False):
+        f0: torch.Tensor | None = None, h0: torch.Tensor | None = None, return_state: bool = False,
+        round_grads: bool = False, residual_input: bool = False):
     """Learned primal-dual (Adler-style memory of n_mem channels, the reading of the
     paper's primal/dual latents for this workload), in units of mu_ref:
         f <- x0 / mu_ref repeated (or the given f0), h <- 0 (or the given h0)
         h <- h + Gamma_n([h, mu_ref P f_1, y])                  (per projection image, 2D)
         f <- f + Lambda_n([f, bp_scale P^T (w h_1)])            (3D)
         output mu_ref f_0 (and the final f, h with return_state).
-    y: [na, nv, nu]; x0: [nz, ny, nx]; w_red: [nu] redundancy weight."""
+    y: [na, nv, nu]; x0: [nz, ny, nx]; w_red: [nu] redundancy weight. round_bf16 /
+    round_grads: bfloat16 operands of the forward / backward convolutions (block).
+    residual_input: the dual block also receives the data residual mu_ref P f_1 - y
+    (the projection-domain form of the Landweber input of Algorithm 1):
+        h <- h + Gamma_n([h, mu_ref P f_1, y, mu_ref P f_1 - y])."""
     na, nv, nu = y.shape
     f = (x0 / mu_ref).unsqueeze(0).repeat(n_mem, 1, 1, 1) if f0 is None else f0
     h = torch.zeros((n_mem, na, nv, nu), dtype=torch.float64) if h0 is None else h0
     for dp, pp in zip(dual_params, primal_params):
         pf = mu_ref * project(G, f[1])
-        inp = torch.cat([h, pf.unsqueeze(0), y.unsqueeze(0)], 0)         # [n_mem + 2, na, nv, nu]
-        h = h + block(inp.permute(1, 0, 2, 3), dp, round_bf16).permute(1, 0, 2, 3)
+        chans = [h, pf.unsqueeze(0), y.unsqueeze(0)]
+        if residual_input:
+            chans.append((pf - y).unsqueeze(0))                            # the data residual
+        inp = torch.cat(chans, 0)                                          # [n_mem + 2 (+ 1), na, nv, nu]
+        h = h + block(inp.permute(1, 0, 2, 3), dp, round_bf16, round_grads).permute(1, 0, 2, 3)
         bp = bp_scale * backproject(G, w_red.view(1, 1, -1) * h[1])
         inp = torch.cat([f, bp.unsqueeze(0)], 0).unsqueeze(0)             # [1, n_mem + 1, nz, ny, nx]
-        f = f + block(inp, pp, round_bf16)[0]
+        f = f + block(inp, pp, round_bf16, round_grads)[0]
     if return_state:
         return mu_ref * f[0], f, h
     return mu_ref * f[0]

@@ -1,6 +1,6 @@
 """FP64 reference of the multiscale scheme (test infrastructure only).
 
-The paper's multiscale reconstruction (Sec. 2.4) runs a coarse level on
+The paper's multiscale reconstruction (Sec. 2.6) runs a coarse level on
 half-resolution data first and carries its result to the fine level. Written out
 from the definitions, in NumPy / PyTorch float64:
   * coarse volume grid: voxels twice as large, half as many per axis (same centre);
@@ -49,11 +49,13 @@ def up(x):
 
 
 def lpd_multiscale(Gc, Gf, y: torch.Tensor, x0: torch.Tensor, wc: torch.Tensor, wf: torch.Tensor,
-                   params_c, params_f, n_mem: int = 5, mu_ref: float = 1.0, bp_c: float = 1.0, bp_f: float = 1.0):
-    """(fine output, coarse output). params_* = (dual_params, primal_params) of each level."""
+                   params_c, params_f, n_mem: int = 5, mu_ref: float = 1.0, bp_c: float = 1.0, bp_f: float = 1.0,
+                   round_grads: bool = False):
+    """(fine output, coarse output). params_* = (dual_params, primal_params) of each level;
+    round_grads as in lpd_ref.lpd."""
     yc = proj_down(y)
     xc, fc, hc = lpd_ref.lpd(Gc, yc, vol_down(x0), wc, params_c[0], params_c[1], n_mem=n_mem, mu_ref=mu_ref,
-                             bp_scale=bp_c, return_state=True)
+                             bp_scale=bp_c, return_state=True, round_grads=round_grads)
     x = lpd_ref.lpd(Gf, y, None, wf, params_f[0], params_f[1], n_mem=n_mem, mu_ref=mu_ref, bp_scale=bp_f,
-                    f0=up(fc), h0=up(hc))
+                    f0=up(fc), h0=up(hc), round_grads=round_grads)
     return x, xc

@@ -8,22 +8,22 @@
  *
  * What is computed (citations are to the paper, arXiv 2512.21180):
  *  - the cone-beam transform P(mu)(t,u) = integral of mu along the line from the
- *    source to detector element u at time t, and its adjoint P* (Sec. 2.1, the
+ *    source to detector element u at time t, and its adjoint P* (Sec. 2.2, the
  *    projection-operator equation). The paper does not say how P is discretised;
  *    this oracle fixes the Joseph-style reading: for each ray choose the principal
  *    axis, sample the volume on every voxel-centre plane perpendicular to it by
  *    bilinear interpolation (zero outside the grid) and sum with the step length.
  *    The adjoint scatters with exactly the same weights.
- *  - the circular-orbit, laterally offset flat-panel geometry (Sec. 2.1: SID 1000,
+ *  - the circular-orbit, laterally offset flat-panel geometry (Sec. 2.2: SID 1000,
  *    isocentre-detector 536 mm, panel offset in the direction of rotation).
- *  - the field-of-view tensor V (Sec. 2.4, definition of V).
- *  - the offset-detector redundancy weight w (Sec. 2.4; the paper names no scheme,
+ *  - the field-of-view tensor V (Sec. 2.6, definition of V).
+ *  - the offset-detector redundancy weight w (Sec. 2.6; the paper names no scheme,
  *    the reading used is Wang's smooth sin^2 weight over the overlap band).
- *  - FDK with redundancy weighting (Sec. 2.4, Algorithm 1 initialisation; Feldkamp
+ *  - FDK with redundancy weighting (Sec. 2.6, Algorithm 1 initialisation; Feldkamp
  *    et al. 1984).
- *  - PDHG with isotropic TV and x >= 0 (Sec. 2.3 baseline; Chambolle-Pock 2011).
- *  - Poisson photon counts and the normalised -log transform (Sec. 2.1 primary
- *    model, Sec. 2.3 normalisation equations), monochromatic.
+ *  - PDHG with isotropic TV and x >= 0 (Sec. 2.5 baseline; Chambolle-Pock 2011).
+ *  - Poisson photon counts and the normalised -log transform (Sec. 2.2 primary
+ *    model, Sec. 2.4 normalisation equations), monochromatic.
  *  - Philox4x32-10 (Salmon et al., SC'11), the counter-based generator that feeds
  *    the Poisson sampler on both sides; Poisson sampling by inversion for small
  *    means and Hoermann's PTRS transformed rejection (1993) otherwise.
@@ -180,7 +180,7 @@ int o_principal_axis(const int *dims, const double *par, const double *ang, int 
     return paxis32(D0S, EU, EV, iu, iv);
 }
 
-/* ---- exported: projector pair (P: Sec. 2.1; discretisation as described above) ---- */
+/* ---- exported: projector pair (P: Sec. 2.2; discretisation as described above) ---- */
 
 /* proj[k][iv][iu] = (P vol); returns the number of samples in *nsamples. */
 void o_forward(const int *dims, const double *par, const double *ang, const double *vol,
@@ -270,7 +270,7 @@ void o_adjoint_voxels(const int *dims, const double *par, const double *ang, con
     }
 }
 
-/* ---- exported: field-of-view tensor V (Sec. 2.4) ----
+/* ---- exported: field-of-view tensor V (Sec. 2.6) ----
  * V[voxel] = (number of angles whose projection of the voxel centre falls on the
  * panel, i.e. continuous pixel coordinates in [-1/2, n - 1/2]) / n_angles. */
 void o_fov(const int *dims, const double *par, const double *ang, double *V)
@@ -298,7 +298,7 @@ void o_fov(const int *dims, const double *par, const double *ang, double *V)
     }
 }
 
-/* ---- exported: offset-detector redundancy weight w (Sec. 2.4) ----
+/* ---- exported: offset-detector redundancy weight w (Sec. 2.6) ----
  * u' = (iu - (nu-1)/2) du + u_offset is the signed distance of the pixel column
  * from the central ray. Overlap half-width D = nu du / 2 - |u_offset|. For a
  * positive offset w = 0 below -D, sin^2(pi/4 (u' + D)/D) on [-D, D], 1 above D
@@ -320,7 +320,7 @@ void o_redundancy(const int *dims, const double *par, double *w)
     }
 }
 
-/* ---- exported: FDK with redundancy weighting (Feldkamp 1984; Sec. 2.4 FDK_w) ----
+/* ---- exported: FDK with redundancy weighting (Feldkamp 1984; Sec. 2.6 FDK_w) ----
  * 1. q0 = proj * w(u') * sdd / sqrt(sdd^2 + u'^2 + v'^2)      (redundancy, cosine)
  * 2. q  = tau * sum_m h(e - m) q0[m] along each detector row, with the Ram-Lak
  *    kernel at the isocentre pitch tau = du sid/sdd: h(0) = 1/(4 tau^2),
@@ -404,7 +404,7 @@ void o_fdk(const int *dims, const double *par, const double *ang, const double *
     free(w);
 }
 
-/* ---- exported: TV pieces and PDHG (Chambolle-Pock 2011; Sec. 2.3 baseline) ----
+/* ---- exported: TV pieces and PDHG (Chambolle-Pock 2011; Sec. 2.5 baseline) ----
  * grad: forward differences in voxel units, zero on the last index (Neumann).
  * div = -grad^T. */
 void o_grad(const int *n, const double *x, double *g3)
@@ -545,7 +545,7 @@ static int32_t poisson_one(double lam, uint64_t e, uint64_t seed)
     return (int32_t)floor(lam + 0.5);
 }
 
-/* counts[e] ~ Poisson(I0 exp(-p[e])), the monochromatic primary model (Sec. 2.1). */
+/* counts[e] ~ Poisson(I0 exp(-p[e])), the monochromatic primary model (Sec. 2.2). */
 void o_poisson(const float *p, long n, double I0, uint64_t seed, int32_t *counts)
 {
 #pragma omp parallel for schedule(static)
@@ -558,7 +558,7 @@ void o_poisson_lam(const double *lam, long n, uint64_t seed, int32_t *counts)
     for (long e = 0; e < n; ++e) counts[e] = poisson_one(lam[e], (uint64_t)e, seed);
 }
 
-/* y = -log(min(max(N, 1) / I0, 1)): the normalised log transform (Sec. 2.3), with
+/* y = -log(min(max(N, 1) / I0, 1)): the normalised log transform (Sec. 2.4), with
  * zero counts clamped to one so the logarithm stays finite. */
 void o_neglog(const int32_t *counts, long n, double I0, double *y)
 {

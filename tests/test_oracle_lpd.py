@@ -79,3 +79,35 @@ def test_lpd_gradient_by_finite_differences(O):
         wd[j] += eps
     fd = (lp - lm) / (2 * eps)
     assert abs(fd - wd.grad[j].item()) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_residual_channel_is_the_data_residual(O):
+    """The dual block's extra input is mu_ref P f_1 - y: with weights a, -a, +a on the
+    residual, P f_1 and y channels its contribution cancels exactly (FP64, no rounding),
+    and with zero residual weights the network equals the one without the channel."""
+    from oracle import lpd_ref as R
+    g = I.scaled(I.geometry("tiny16"), n=(8, 8, 6), nu=10, nv=6, du=6.0, dv=6.0, n_angles=6, u_offset=4.0)
+    G = O.Geom(g)
+    rng = np.random.default_rng(5)
+    y = torch.tensor(rng.random(G.proj_shape))
+    x0 = torch.tensor(rng.random(G.vol_shape))
+    w = torch.tensor(O.redundancy(G))
+    M = 3
+    r = np.random.default_rng(6)
+    mk = lambda s: torch.tensor(r.standard_normal(s) * 0.1)
+    d_rest = [(mk((4, 4, 3, 3)), mk(4)), (mk((3, 4, 3, 3)), mk(3))]
+    prim = [[(mk((4, 4, 3, 3, 3)), mk(4)), (mk((4, 4, 3, 3, 3)), mk(4)), (mk((3, 4, 3, 3, 3)), mk(3))]]
+    w1, b1 = mk((4, M + 2, 3, 3)), mk(4)
+    run = lambda first, res: R.lpd(G, y, x0, w, [[first] + d_rest], prim, n_mem=M, round_bf16=False, mu_ref=0.5,
+                                   bp_scale=0.05, residual_input=res)
+    base = run((w1, b1), False)
+    # zero weights on the residual channel
+    w1z = torch.cat([w1, torch.zeros((4, 1, 3, 3), dtype=torch.float64)], 1)
+    assert torch.allclose(run((w1z, b1), True), base, rtol=0, atol=1e-13)
+    # a (P f_1 - y) - a P f_1 + a y = 0
+    a = mk((4, 1, 3, 3))
+    w1c = torch.cat([w1[:, :M], w1[:, M:M + 1] - a, w1[:, M + 1:M + 2] + a, a], 1)
+    assert torch.allclose(run((w1c, b1), True), base, rtol=0, atol=1e-12)
+    # a wrong sign on y would not cancel
+    w1x = torch.cat([w1[:, :M], w1[:, M:M + 1] - a, w1[:, M + 1:M + 2] - a, a], 1)
+    assert (run((w1x, b1), True) - base).abs().max().item() > 1e-6

@@ -16,7 +16,7 @@ from paper_2512_21180_gb300 import inputs as I
 
 def world_rays(g, k_angles=None):
     """Source and pixel-centre positions in mm, written from the geometry's
-    definition (Sec. 2.1 setup: source on a circle of radius SID about z, flat panel
+    definition (Sec. 2.2 setup: source on a circle of radius SID about z, flat panel
     at SDD facing it, panel axis e_u along the direction of rotation)."""
     na = g["n_angles"]
     ks = range(na) if k_angles is None else k_angles

@@ -3,13 +3,13 @@
  *
  * The library computes the discretised cone-beam transform P and its exact
  * adjoint P* (paper: "Equivariant Multiscale Learned Invertible Reconstruction
- * for Cone Beam CT", arXiv 2512.21180, Sec. 2.1, projection-operator equation:
+ * for Cone Beam CT", arXiv 2512.21180, Sec. 2.2, projection-operator equation:
  * P(mu)(t,u) is the integral of mu along the line from the source to detector
  * element u at time t, and P* is its adjoint, the backprojection), the
  * field-of-view tensor V and redundancy weight w used by the reconstruction
- * (Sec. 2.4), FDK with redundancy weighting, PDHG-TV (Sec. 2.3 baselines), the
- * primary-signal simulation (Sec. 2.1 primary model with Poisson noise, Sec. 2.3
- * log normalisation) and the learned primal-dual reconstruction (Sec. 2.4,
+ * (Sec. 2.6), FDK with redundancy weighting, PDHG-TV (Sec. 2.5 baselines), the
+ * primary-signal simulation (Sec. 2.2 primary model with Poisson noise, Sec. 2.4
+ * log normalisation) and the learned primal-dual reconstruction (Sec. 2.6,
  * Algorithm 1).
  *
  * Conventions for every call
@@ -30,9 +30,10 @@
  *        CBCT_ENOMEM  -3  out of device memory
  *        CBCT_EDEVICE -4  reserved: kernels report a bounded wait that gave up through
  *                         a device status word the caller reads (cbct_device_status,
- *                         the status argument of cbct_conv), not through a return code
+ *                         lpd_device_status, the status argument of cbct_conv and
+ *                         cbct_conv_wgrad), not through a return code
  *
- * Geometry (the paper's scanner, Sec. 2.1: circular orbit, offset flat panel):
+ * Geometry (the paper's scanner, Sec. 2.2: circular orbit, offset flat panel):
  * isocentre at the origin, rotation axis z. At angle theta the source sits at
  * sid (cos theta, sin theta, 0), the panel centre at sid - sdd along that
  * direction, the panel axes are e_u = (-sin theta, cos theta, 0) (the direction
@@ -77,7 +78,7 @@ typedef struct {
     double sid, sdd;         /* source-isocentre and source-detector distances, mm */
     int n_angles;            /* projections over the orbit */
     const double *angles;    /* host array of n_angles radians, or NULL for 2 pi k / n_angles */
-    int normalize;           /* 1: scale P and P* by 1/||P|| (Sec. 2.4, "normalized
+    int normalize;           /* 1: scale P and P* by 1/||P|| (Sec. 2.6, "normalized
                                 operators"); ||P|| from 30 FP64-accumulated power
                                 iterations at creation. 0: unscaled. */
 } cbct_geom_desc;
@@ -110,7 +111,7 @@ int cbct_device_status(const cbct_geom *g, int *out, int clear);
  * be NULL. */
 int cbct_forward_config(const cbct_geom *g, int *cfg, double *need_b, double *need_z);
 
-/* Forward projection (a2, Sec. 2.1): proj[b] (+)= P vol[b] for b < batch.
+/* Forward projection (a2, Sec. 2.2): proj[b] (+)= P vol[b] for b < batch.
  * accumulate = 0 overwrites proj, 1 adds to it. FP32 in, FP32 accumulation.
  * batch >= 1; batch * n_angles <= 65535. Scratch: two plane-major copies of the
  * volumes (2 * batch * nx * ny * nz floats, rows padded to 4), from the
@@ -121,7 +122,7 @@ int cbct_forward_config(const cbct_geom *g, int *cfg, double *need_b, double *ne
 int forward_project(const cbct_geom *g, const float *vol, float *proj, int batch, int accumulate,
                     void *stream);
 
-/* Backprojection (a3, Sec. 2.1): vol[b] (+)= P* proj[b], the exact transpose of
+/* Backprojection (a3, Sec. 2.2): vol[b] (+)= P* proj[b], the exact transpose of
  * forward_project (same rays, planes and bilinear weights), computed as an
  * atomic-free voxel-driven gather. Scratch: batch * n_angles * nv * nu floats
  * (the ray-weighted projections, plus up to 16 partial volumes when small volumes
@@ -143,14 +144,15 @@ int back_project_f64(const cbct_geom *g, const double *proj, double *vol, int ba
  * framework that owns the whole device memory budget through its own allocator,
  * or a latency-critical loop that must not enter the CUDA allocator). Same
  * arguments and result as back_project, up to FP32 summation order. Its scratch
- * is a fixed 8 Mi-float (32 MiB) device array inside the library, which every GPU
- * that loads the library holds until the process exits; the angles are processed
- * in chunks that fit it. Limit: nu * nv <= 8388608 (one projection must fit),
- * else CBCT_EINVAL before any launch. The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress) and should come before any stream
- * capture on that device. All calls share the one array: calls whose executions
- * overlap on the GPU (different streams, or different host threads) race and give
- * wrong results. Nothing in the array needs to start at zero. */
+ * is a fixed 8 Mi-float (32 MiB) device array inside the library, placed on a GPU
+ * when geometry_create first runs there (it looks up the array's device address with
+ * cudaGetSymbolAddress, which loads the library's projector module on that device)
+ * and held until the process exits; this call itself neither allocates nor loads
+ * anything. The angles are processed in chunks that fit the array. Limit: nu * nv <=
+ * 8388608 (one projection must fit), else CBCT_EINVAL before any launch. All calls
+ * share the one array: calls whose executions overlap on the GPU (different streams,
+ * or different host threads) race and give wrong results. Nothing in the array needs
+ * to start at zero. */
 int back_project_noalloc(const cbct_geom *g, const float *proj, float *vol, int batch, int accumulate,
                          void *stream);
 
@@ -171,11 +173,11 @@ int cbct_count_samples(const cbct_geom *g, long long *out, void *stream);
  * supersample = s in [1, 8] each voxel is the mean over s^3 sub-points at offsets
  * ((j + 1/2)/s - 1/2) vox. Writes one volume [nz][ny][nx]. Synchronises `stream`
  * before returning (the host rows may be reused at once). Stand-in for the
- * paper's CT volumes (Sec. 2.3). */
+ * paper's CT volumes (Sec. 2.4). */
 int cbct_phantom(const cbct_geom *g, const double *ell_host, int n_ell, int supersample, float *vol,
                  void *stream);
 
-/* Photon counts (Sec. 2.1, primary model, one energy): counts[e] ~
+/* Photon counts (Sec. 2.2, primary model, one energy): counts[e] ~
  * Poisson(I0 exp(-line_integrals[e])) for e < n, device arrays. Random words come
  * from Philox4x32-10 (Salmon et al., SC'11) with key (seed lo, seed hi) and counter
  * (e lo, e hi, block, 0x50303031); means below 10 are sampled by inversion, others
@@ -183,7 +185,7 @@ int cbct_phantom(const cbct_geom *g, const double *ell_host, int n_ell, int supe
 int cbct_poisson(const float *line_integrals, long long n, double I0, unsigned long long seed, int32_t *counts,
                  void *stream);
 
-/* Normalised log transform (Sec. 2.3): y[e] = -log(min(max(counts[e], 1) / I0, 1)). */
+/* Normalised log transform (Sec. 2.4): y[e] = -log(min(max(counts[e], 1) / I0, 1)). */
 int cbct_neglog(const int32_t *counts, long long n, double I0, float *y, void *stream);
 
 /* Simulated measurement of `batch` volumes: line_integrals = P vol (forward_project),
@@ -192,14 +194,14 @@ int cbct_neglog(const int32_t *counts, long long n, double I0, float *y, void *s
 int cbct_simulate(const cbct_geom *g, const float *vol, int batch, double I0, unsigned long long seed,
                   float *line_integrals, float *y, void *stream);
 
-/* Offset-detector redundancy weight w[nu] (device), Sec. 2.4 (the paper names no
+/* Offset-detector redundancy weight w[nu] (device), Sec. 2.6 (the paper names no
  * scheme; this is Wang's): u' = (iu - (nu-1)/2) du + u_offset, D = nu du/2 -
  * |u_offset|; for u_offset > 0 w = 0 below -D, sin^2(pi/4 (u' + D)/D) on [-D, D],
  * 1 above D (mirrored for u_offset < 0); w = 1/2 for a centred panel, so that
  * conjugate rays sum to one. */
 int cbct_redundancy_weight(const cbct_geom *g, float *w, void *stream);
 
-/* Field-of-view tensor V[nz][ny][nx] (device), Sec. 2.4: the fraction of angles at
+/* Field-of-view tensor V[nz][ny][nx] (device), Sec. 2.6: the fraction of angles at
  * which the voxel centre projects onto the panel (continuous pixel coordinates in
  * [-1/2, n - 1/2]), FP64. Synchronises `stream`. */
 int cbct_fov(const cbct_geom *g, float *V, void *stream);
@@ -210,7 +212,7 @@ int cbct_fov(const cbct_geom *g, float *V, void *stream);
  * ceil(2 |u_offset| / du). */
 int cbct_fdk_pad(const cbct_geom *g);
 
-/* FDK with redundancy weighting (Algorithm 1 initialisation, Sec. 2.4; Feldkamp
+/* FDK with redundancy weighting (Algorithm 1 initialisation, Sec. 2.6; Feldkamp
  * 1984): rows weighted by w(u') sdd / sqrt(sdd^2 + u'^2 + v'^2), zero-padded on the
  * short side (cbct_fdk_pad), filtered by the Ram-Lak kernel at the isocentre pitch
  * tau = du sid / sdd (tau h(0) = 1/(4 tau), tau h(odd j) = -1/(pi^2 j^2 tau)), then
@@ -225,7 +227,7 @@ int cbct_fdk(const cbct_geom *g, const float *proj, float *vol, int batch, int a
 int cbct_opnorm(const cbct_geom *g, double gamma, int iters, double *out, void *stream);
 
 /* PDHG (Chambolle-Pock 2011) for min_x 1/2 ||P x - y||^2 + lam ||grad x||_{2,1}
- * (+ x >= 0 when nonneg), the paper's TV baseline (Sec. 2.3), on K = [P; gamma grad]
+ * (+ x >= 0 when nonneg), the paper's TV baseline (Sec. 2.5), on K = [P; gamma grad]
  * with F2 = (lam/gamma) ||.||_{2,1}: per iteration
  *   z1 <- (z1 + sigma (P xbar - y)) / (1 + sigma)
  *   z2 <- project_{|.| <= lam/gamma}(z2 + sigma gamma grad xbar)
@@ -246,7 +248,7 @@ int cbct_landweber(const cbct_geom *g, const float *y, float *x, int batch, int 
 
 /* One 3x3 (taps3d = 0: over (H, W) of each of nimg * D images) or 3x3x3 (taps3d = 1)
  * "same" cross-correlation, stride 1, on the tensor cores (tcgen05.mma, BF16
- * operands, FP32 accumulation in TMEM): the learned blocks of Sec. 2.4 (Algorithm 1,
+ * operands, FP32 accumulation in TMEM): the learned blocks of Sec. 2.6 (Algorithm 1,
  * Gamma and Lambda). Activations are BF16 "row-blocked": image row (img, d, h) holds
  * its channel groups one after the other, element (img, d, h, w, c) at
  * ((((img * D + d) * H + h) * (cp / 8) + c / 8) * W + w) * 8 + c % 8 for cp channel
@@ -275,13 +277,17 @@ int cbct_conv_plan(int taps3d, int H, int cpin, int cin, int cout, int flip, int
 
 /* Weight and bias gradients of the convolution above: dw[co][tap][ci] (+)=
  * sum_p dy[p][co] x[p + tap][ci], db[co] (+)= sum_p dy[p][co]; x BF16 row-blocked
- * with cpin slots, dy BF16 row-blocked with cpout slots (both multiples of 8). CUDA
- * cores, FP32; partial sums over pixel chunks reduced in a fixed order
- * (deterministic). */
+ * with cpin slots, dy BF16 row-blocked with cpout slots (both multiples of 8). With
+ * cpin 8 or 32 and cpout 8, 16 or 32 the weight gradient runs on the tensor cores
+ * (BF16 operands, FP32 accumulation in TMEM; one partial per CTA), otherwise on the
+ * CUDA cores (FP32); partials are reduced in a fixed order (deterministic). status:
+ * device int, set to 1 if a tensor-core kernel gives up waiting on its pipeline (its
+ * partial is then written as zero). Errors: CBCT_EINVAL for NULL pointers (status
+ * included) or non-positive channel counts. Scratch: the partial sums. */
 int cbct_conv_wgrad(const void *x, int cpin, int cin, const void *dy, int cpout, int cout, int nimg, int D, int H,
-                    int W, int taps3d, float *dw, float *db, int accumulate, void *stream);
+                    int W, int taps3d, float *dw, float *db, int accumulate, int *status, void *stream);
 
-/* ---- resampling between multiscale levels (a11; Sec. 2.4, multiscale scheme) ---- */
+/* ---- resampling between multiscale levels (a11; Sec. 2.6, multiscale scheme) ---- */
 
 /* nch independent 3-D FP32 arrays [n0][n1][n2] (last index fastest), device.
  * cbct_resample_down: out[c][i][j][k] = scale * sum of in over the box
@@ -297,7 +303,7 @@ int cbct_resample_down(const float *in, long long nch, int n0, int n1, int n2, i
 int cbct_resample_up(const float *in, long long nch, int n0, int n1, int n2, int f0, int f1, int f2, float *out,
                      void *stream);
 
-/* ---- learned primal-dual reconstruction (a7-a9, a12; Sec. 2.4, Algorithm 1) ---- */
+/* ---- learned primal-dual reconstruction (a7-a9, a12; Sec. 2.6, Algorithm 1) ---- */
 
 typedef struct cbct_lpd cbct_lpd; /* opaque: weights (FP32 master), gradients, Adam moments, workspaces */
 
@@ -309,41 +315,73 @@ typedef struct {
     float mu_ref;                /* volume unit (1/mm): f' = f / mu_ref internally (0.02) */
     float bp_scale;              /* scale of P^T (w h_1) in the primal input; <= 0: 1 / max P^T(w 1) */
     unsigned long long seed;     /* initial weights (He normal; last layer of a block x 0.1; zero bias) */
+    int residual_input;          /* 1: the dual block also receives mu_ref P f_1 - y, formed in FP32
+                                    before its BF16 rounding (n_mem <= 5); 0: not */
+    int max_batch;               /* volumes per lpd_forward call the workspaces hold (0 means 1) */
+    int reversible;              /* 1: additive coupling with channel permutations (Sec. 2.6,
+                                    Algorithm 1 split / update / combine / permute; n_mem even):
+                                    the backward recovers every iterate from the final states
+                                    instead of storing them. 0: Adler-style memory update. */
 } cbct_lpd_desc;
 
 /* Network on geometry g (which must outlive it): per iteration n a dual block
- * Gamma_n (3x3 convs over each projection image: n_mem + 2 -> width -> width -> n_mem)
- * and a primal block Lambda_n (3x3x3: n_mem + 1 -> width -> width -> n_mem), LeakyReLU
- * between convs; parameters flat FP32 per iteration [dual w1 b1 w2 b2 w3 b3, primal
- * ...], w as [cout][taps][cin]. Memory: (n_iter + 1) iterates of n_mem volumes and
- * n_mem projections plus ~4 x 32-channel BF16 activations per block. Synchronises.
- * Errors: CBCT_EINVAL unless 1 <= n_iter <= 64, 2 <= n_mem <= 6, width = 32,
- * mu_ref > 0 and 0 <= slope <= 1. */
+ * Gamma_n (3x3 convs over each projection image: n_mem + 2 (+ 1 with residual_input)
+ * -> width -> width -> n_mem) and a primal block Lambda_n (3x3x3: n_mem + 1 -> width ->
+ * width -> n_mem), LeakyReLU between convs; parameters flat FP32 per iteration [dual w1
+ * b1 w2 b2 w3 b3, primal ...], w as [cout][taps][cin]. Memory, for max_batch volumes:
+ * (n_iter + 1) iterates of n_mem volumes and n_mem projections plus ~4 x 32-channel BF16
+ * activations per block. Synchronises. Errors: CBCT_EINVAL unless 1 <= n_iter <= 64,
+ * 2 <= n_mem <= 6 (<= 5 with residual_input), width = 32, mu_ref > 0, 0 <= slope <= 1,
+ * residual_input is 0 or 1, max_batch <= 64 and max_batch * n_angles <= 65535. */
 int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lpd **out);
 void lpd_destroy(cbct_lpd *m);
+
+/* Reversible mode (desc.reversible = 1), per iteration n with halves of K = n_mem / 2
+ * channels, f = [p1, p2], h = [d1, d2]:
+ *   d2 <- d2 + Gamma_n([d1, mu_ref P p2[0], y (, mu_ref P p2[0] - y)])
+ *   p2 <- p2 + Lambda_n([p1, bp_scale P^T(w d2[0])])
+ *   f <- f[perm_f[n]],  h <- h[perm_h[n]]        (new channel c = old channel perm[c])
+ * output mu_ref f[0]. Blocks: dual K + 2 (+ 1) -> width -> width -> K, primal K + 1 ->
+ * width -> width -> K. The permutations are drawn from desc.seed at creation so that each
+ * mixes the halves (the new first half takes a channel of the old second half); a
+ * training forward keeps only the final states, and lpd_backward undoes the iterations
+ * one by one (p2 -= Lambda_n(..), d2 -= Gamma_n(..)), exact up to one FP32 rounding of each
+ * state update. The latent-state entries below refuse a reversible model.
+ * lpd_get_perms / lpd_set_perms copy the n_iter x 2 x n_mem permutation table (per
+ * iteration perm_f then perm_h) to / from host memory; set checks that each row is a
+ * permutation that mixes the halves. Errors: CBCT_EINVAL for a model that is not
+ * reversible, NULL pointers or (set) an invalid table. */
+int lpd_get_perms(const cbct_lpd *m, int *host);
+int lpd_set_perms(cbct_lpd *m, const int *host);
 
 /* Parameter count and device pointers to the parameters and the gradient buffer. */
 int lpd_info(const cbct_lpd *m, long long *nparams, float **params, float **grads, float *bp_scale);
 
-/* x_out = LPD(y, x0): f <- x0 / mu_ref repeated, h <- 0; for n < n_iter:
- *   h <- h + Gamma_n([h, mu_ref P f_1, y]);  f <- f + Lambda_n([f, bp_scale P^T(w h_1)])
- * (w = the redundancy weight per detector column), x_out = mu_ref f_0. batch must be 1
- * (gradient accumulation covers larger effective batches). save_for_backward = 1 keeps
- * the iterates for lpd_backward. */
+/* x_out = LPD(y, x0) for `batch` volumes at once (1 <= batch <= max_batch; y
+ * [batch][n_angles][nv][nu], x0 and x_out [batch][nz][ny][nx]): f <- x0 / mu_ref
+ * repeated, h <- 0; for n < n_iter:
+ *   h <- h + Gamma_n([h, mu_ref P f_1, y (, mu_ref P f_1 - y)]);
+ *   f <- f + Lambda_n([f, bp_scale P^T(w h_1)])
+ * (w = the redundancy weight per detector column), x_out = mu_ref f_0. Every projector
+ * call and convolution runs on the whole batch. save_for_backward = 1 keeps the iterates
+ * for lpd_backward. Errors: CBCT_EINVAL for NULL pointers or a batch out of range. */
 int lpd_forward(cbct_lpd *m, const float *y, const float *x0, float *x_out, int batch, int save_for_backward,
                 void *stream);
 
-/* Reverse sweep for dL/dx_out = grad_x: recomputes each block's activations from the
- * saved iterate, ADDS the parameter gradients to the model's gradient buffer, writes
- * dL/dy and dL/dx0 when those pointers are not NULL. */
+/* Reverse sweep for dL/dx_out = grad_x (the last forward's batch): recomputes each
+ * block's activations from the saved iterate, ADDS the parameter gradients (summed over
+ * the batch) to the model's gradient buffer, writes dL/dy and dL/dx0 when those pointers
+ * are not NULL. */
 int lpd_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float *grad_x0, void *stream);
 
-/* Latent-state variants for the multiscale scheme (a11; Sec. 2.4: a coarser level's
- * result initialises the next level). The primal state f is [n_mem][nvox] FP32 in units
+/* Latent-state variants for the multiscale scheme (a11; Sec. 2.6: a coarser level's
+ * result initialises the next level), one volume per call. The primal state f is [n_mem][nvox] FP32 in units
  * of mu_ref, the dual state h is [n_mem][nproj] FP32 (y's units), both device.
  * lpd_forward_latent: f_0 = f0 (NULL: x0 / mu_ref in every channel, then x0 is
  * required), h_0 = h0 (NULL: zero); x_out (nullable) = mu_ref f_N[0].
- * lpd_get_state: copies the final f_N / h_N of the last forward pass (either nullable).
+ * lpd_get_state: copies the final f_N / h_N of the last forward pass (either nullable);
+ * for a reversible model, the states it holds in logical channel order: f_N / h_N after
+ * a forward pass, the recovered f_0 / h_0 after lpd_backward.
  * lpd_backward_latent: upstream dL/dx_out (grad_x) and/or dL/df_N, dL/dh_N (each
  * nullable, at least one given; needs save_for_backward); accumulates parameter
  * gradients; writes dL/dy, dL/dx0, dL/df_0, dL/dh_0 where non-NULL. Errors: CBCT_EINVAL
@@ -368,9 +406,22 @@ int lpd_clip_grads(cbct_lpd *m, float max_norm, float grad_scale, double *norm_o
 int lpd_adam_step(cbct_lpd *m, float lr, float beta1, float beta2, float eps, int step, float grad_scale,
                   void *stream);
 
+/* Test of the library's bounded waits (the paper has no counterpart: this checks the
+ * failure handling of the pipelined kernels). Launches one CTA whose two warps wait on
+ * a shared-memory barrier that nothing completes, each for at most limit_ns
+ * nanoseconds (1 .. 1e8) of the GPU's global timer: the same wait the TMA and
+ * tensor-core pipelines use, with a short limit instead of their 2 s. When a wait
+ * runs out the kernel sets the geometry's device status word to 1, the timeout code
+ * the projector kernels write (read and cleared by cbct_device_status), and returns;
+ * *waited_ok (device int) is incremented once per wait that completed (none do).
+ * Asynchronous on `stream`. Errors: CBCT_EINVAL for NULL pointers or a limit out of
+ * range. */
+int cbct_wait_probe(const cbct_geom *g, long long limit_ns, int *waited_ok, void *stream);
+
 /* Read (and with clear = 1 reset) the model's device status word: 0 = ok, 1 = one of
- * its convolution kernels gave up waiting on its tensor-core pipeline (it then left
- * its outputs unwritten). Synchronises the device. Errors: CBCT_EINVAL for NULL. */
+ * its convolution kernels (forward, input-gradient or weight-gradient) gave up waiting
+ * on its tensor-core pipeline (it then left its outputs unwritten, or wrote a zero
+ * weight-gradient partial). Synchronises the device. Errors: CBCT_EINVAL for NULL. */
 int lpd_device_status(const cbct_lpd *m, int *out, int clear);
 
 /* Copy the n FP32 parameters to / from host memory (checkpoints). Synchronous. */

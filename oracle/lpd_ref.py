@@ -141,3 +141,75 @@ def lpd(G, y: torch.Tensor, x0: torch.Tensor | None, w_red: torch.Tensor, dual_p
     if return_state:
         return mu_ref * f[0], f, h
     return mu_ref * f[0]
+
+
+def lpd_reversible(G, y: torch.Tensor, x0: torch.Tensor, w_red: torch.Tensor, dual_params, primal_params, perms_f,
+                   perms_h, n_mem: int = 6, round_bf16: bool = True, mu_ref: float = 1.0, bp_scale: float = 1.0,
+                   round_grads: bool = False, residual_input: bool = False, return_state: bool = False):
+    """Learned primal-dual with additive coupling and channel permutations (Algorithm 1:
+    split, update the second half from the first, combine, permute), in units of mu_ref.
+    With M = n_mem (even), f = [p1, p2] and h = [d1, d2] halves of M / 2 channels:
+        f <- x0 / mu_ref in every channel, h <- 0
+        per iteration n:
+          d2 <- d2 + Gamma_n([d1, mu_ref P p2[0], y (, mu_ref P p2[0] - y)])
+          p2 <- p2 + Lambda_n([p1, bp_scale P^T (w d2[0])])
+          h <- (h[perms_h[n][c]])_c,   f <- (f[perms_f[n][c]])_c
+        output mu_ref f[0].
+    Each update reads only the half it does not change, so the iteration is inverted
+    by undoing the permutations and subtracting the same block outputs in reverse order
+    (lpd_reversible_inverse); the permutations mix the two halves."""
+    M = n_mem
+    K = M // 2
+    na, nv, nu = y.shape
+    f = (x0 / mu_ref).unsqueeze(0).repeat(M, 1, 1, 1)
+    h = torch.zeros((M, na, nv, nu), dtype=torch.float64)
+    for n, (dp, pp) in enumerate(zip(dual_params, primal_params)):
+        d1, d2 = h[:K], h[K:]
+        p1, p2 = f[:K], f[K:]
+        pf = mu_ref * project(G, p2[0])
+        chans = [d1, pf.unsqueeze(0), y.unsqueeze(0)]
+        if residual_input:
+            chans.append((pf - y).unsqueeze(0))
+        d2 = d2 + block(torch.cat(chans, 0).permute(1, 0, 2, 3), dp, round_bf16, round_grads).permute(1, 0, 2, 3)
+        bp = bp_scale * backproject(G, w_red.view(1, 1, -1) * d2[0])
+        p2 = p2 + block(torch.cat([p1, bp.unsqueeze(0)], 0).unsqueeze(0), pp, round_bf16, round_grads)[0]
+        h = torch.cat([d1, d2], 0)[list(perms_h[n])]
+        f = torch.cat([p1, p2], 0)[list(perms_f[n])]
+    if return_state:
+        return mu_ref * f[0], f, h
+    return mu_ref * f[0]
+
+
+def lpd_reversible_inverse(G, y: torch.Tensor, f: torch.Tensor, h: torch.Tensor, w_red: torch.Tensor, dual_params,
+                           primal_params, perms_f, perms_h, n_mem: int = 6, round_bf16: bool = True,
+                           mu_ref: float = 1.0, bp_scale: float = 1.0, residual_input: bool = False):
+    """The initial states (f_0, h_0) recovered from the final ones by running
+    lpd_reversible's iterations backwards: undo the permutations, then p2 -= Lambda_n(...)
+    and d2 -= Gamma_n(...) with the same block inputs the forward pass used."""
+    M = n_mem
+    K = M // 2
+    with torch.no_grad():
+        for n in reversed(range(len(dual_params))):
+            inv_f = np.argsort(perms_f[n])
+            inv_h = np.argsort(perms_h[n])
+            f = f[list(inv_f)]
+            h = h[list(inv_h)]
+            p1, p2 = f[:K], f[K:]
+            d1, d2 = h[:K], h[K:]
+            bp = bp_scale * backproject(G, w_red.view(1, 1, -1) * d2[0])
+            p2 = p2 - block(torch.cat([p1, bp.unsqueeze(0)], 0).unsqueeze(0), primal_params[n], round_bf16)[0]
+            pf = mu_ref * project(G, p2[0])
+            chans = [d1, pf.unsqueeze(0), y.unsqueeze(0)]
+            if residual_input:
+                chans.append((pf - y).unsqueeze(0))
+            d2 = d2 - block(torch.cat(chans, 0).permute(1, 0, 2, 3), dual_params[n], round_bf16).permute(1, 0, 2, 3)
+            f = torch.cat([p1, p2], 0)
+            h = torch.cat([d1, d2], 0)
+    return f, h
+
+
+def mixes_halves(perm) -> bool:
+    """A permutation of 2K channels mixes the halves when the new first half takes at
+    least one channel from the old second half (and so, by counting, the reverse)."""
+    K = len(perm) // 2
+    return any(p >= K for p in perm[:K])

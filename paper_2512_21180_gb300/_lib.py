@@ -24,7 +24,8 @@ U64 = ctypes.c_uint64
 
 class LpdDesc(ctypes.Structure):
     _fields_ = [("n_iter", I32), ("n_mem", I32), ("width", I32), ("slope", F32), ("mu_ref", F32),
-                ("bp_scale", F32), ("seed", U64)]
+                ("bp_scale", F32), ("seed", U64), ("residual_input", I32), ("max_batch", I32),
+                ("reversible", I32)]
 
 
 class GeomDesc(ctypes.Structure):
@@ -65,7 +66,7 @@ SIGNATURES = {
     "cbct_pdhg": (I32, [P, P, P, P, I32, I32, F64, F64, F64, F64, I32, P]),
     "cbct_landweber": (I32, [P, P, P, I32, I32, F64, I32, P]),
     "cbct_conv": (I32, [P, I32, I32, I32, I32, I32, I32, P, P, I32, I32, I32, I32, F32, P, I32, P, P, I64, P, P]),
-    "cbct_conv_wgrad": (I32, [P, I32, I32, P, I32, I32, I32, I32, I32, I32, I32, P, P, I32, P]),
+    "cbct_conv_wgrad": (I32, [P, I32, I32, P, I32, I32, I32, I32, I32, I32, I32, P, P, I32, P, P]),
     "cbct_conv_plan": (I32, [I32, I32, I32, I32, I32, I32, ctypes.POINTER(I32), ctypes.POINTER(I64),
                              ctypes.POINTER(I32), ctypes.POINTER(I32)]),
     "lpd_create": (I32, [P, ctypes.POINTER(LpdDesc), ctypes.POINTER(P)]),
@@ -85,6 +86,9 @@ SIGNATURES = {
     "lpd_get_params": (I32, [P, P, I64]),
     "lpd_get_grads": (I32, [P, P, I64]),
     "cbct_masked_mse": (I32, [P, P, P, F32, I64, P, P, P]),
+    "cbct_wait_probe": (I32, [P, I64, P, P]),
+    "lpd_get_perms": (I32, [P, P]),
+    "lpd_set_perms": (I32, [P, P]),
 }
 
 EXTRA_SIGNATURES: dict = {}

@@ -1,5 +1,5 @@
 // 3x3 (2D, dual block) and 3x3x3 (3D, primal block) convolutions of the learned
-// primal-dual network (paper Sec. 2.4, Algorithm 1 blocks Gamma and Lambda; here
+// primal-dual network (paper Sec. 2.6, Algorithm 1 blocks Gamma and Lambda; here
 // the 3-layer width-32 blocks of the learned primal-dual workload), stride 1, zero
 // "same" padding. BF16 operands, FP32 accumulation.
 //
@@ -53,6 +53,9 @@ struct ConvArgs {
     const float *state_in;   // (may equal state)
     int state_in_zero;       // the old state is zero: state = v without reading state_in
     long long sstride;
+    int smap_on;             // EPI_RESIDUAL_F32: channel c lives in plane smap[c] (c < 8) instead of c
+    int smap[8];
+    int ssub;                // EPI_RESIDUAL_F32: state = state_in - v (undoes an additive update)
     int *status;
 };
 
@@ -82,12 +85,17 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *ac
         for (int c0 = 0; c0 < NPAD; c0 += 8) {  // 8 channels per batch of loads
             if (c0 >= a.cout) break;
             float old[8];
+            long long off[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) off[c] = (long long)(a.smap_on && c0 == 0 ? a.smap[c] : c0 + c) * a.sstride + p;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) old[c] = (c0 + c < a.cout && !a.state_in_zero) ? a.state_in[off[c]] : 0.f;
 #pragma unroll
             for (int c = 0; c < 8; ++c)
-                old[c] = (c0 + c < a.cout && !a.state_in_zero) ? a.state_in[(c0 + c) * a.sstride + p] : 0.f;
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-                if (c0 + c < a.cout) a.state[(c0 + c) * a.sstride + p] = old[c] + (acc[c0 + c] + bias[c0 + c]);
+                if (c0 + c < a.cout) {
+                    const float v = acc[c0 + c] + bias[c0 + c];
+                    a.state[off[c]] = a.ssub ? old[c] - v : old[c] + v;
+                }
         }
     } else {
         // channel group q of this pixel: (row * (cpout / 8) + q) * W * 8 + w * 8
@@ -978,13 +986,12 @@ static int conv_run(const ConvArgs &a0, int n_out, int epi, int rpt, cudaStream_
     return launch_conv_rpt<32, EPI_MASK_BF16>(a, rpt, st);
 }
 
-__device__ int g_wgrad_status;  // status word of weight-gradient launches (bounded waits)
-
 // Tensor-core weight gradient (32 input channel slots; cpout 8, 16 or 32): per-CTA
 // partial dW, then a fixed-order reduction; db on the CUDA cores.
 template <int XCG, int NCG>
 static int conv_wgrad_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *dy, int cpout, int cout, int nimg,
-                         int D, int H, int W, int taps3d, float *dw, float *db, int accumulate, cudaStream_t st) {
+                         int D, int H, int W, int taps3d, float *dw, float *db, int accumulate, int *status,
+                         cudaStream_t st) {
     ConvArgs a{};
     a.x = x;
     a.nimg = nimg; a.D = D; a.H = H; a.W = W;
@@ -992,7 +999,7 @@ static int conv_wgrad_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *d
     a.taps3d = taps3d;
     a.cout = cout; a.cin = cin;
     a.G = W % 4 == 0 ? 4 : (W % 2 == 0 ? 2 : 1);
-    CBCT_CUDA_TRY(cudaGetSymbolAddress((void **)&a.status, g_wgrad_status));
+    a.status = status;
     const int cgo = cpout / 8;
     const uint64_t G = (uint64_t)a.G, Wl = (uint64_t)W;
     CUtensorMap xmap, ymap;
@@ -1038,13 +1045,16 @@ static int conv_wgrad_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *d
 
 // dW (+)= sum_p dY[p] x X[p + tap], db (+)= sum_p dY[p]; partial sums in scratch.
 int conv_wgrad(const __nv_bfloat16 *x, int cpin, int cin, const __nv_bfloat16 *dy, int cpout, int cout, int nimg, int D,
-               int H, int W, int taps3d, float *dw, float *db, int accumulate, cudaStream_t st) {
+               int H, int W, int taps3d, float *dw, float *db, int accumulate, int *status, cudaStream_t st) {
     if ((cpin == 32 || cpin == 8) && cin <= cpin && cout <= cpout && (cpout == 8 || cpout == 16 || cpout == 32)) {
+        if (!status) return fail(CBCT_EINVAL, "conv wgrad: NULL status word");
         if (cpin == 8)
-            return cpout <= 16 ? conv_wgrad_tc<1, 2>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, st)
-                               : conv_wgrad_tc<1, 4>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, st);
-        return cpout <= 16 ? conv_wgrad_tc<4, 2>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, st)
-                           : conv_wgrad_tc<4, 4>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, st);
+            return cpout <= 16
+                       ? conv_wgrad_tc<1, 2>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, status, st)
+                       : conv_wgrad_tc<1, 4>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, status, st);
+        return cpout <= 16
+                   ? conv_wgrad_tc<4, 2>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, status, st)
+                   : conv_wgrad_tc<4, 4>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, status, st);
     }
     const int ntaps = taps3d ? 27 : 9;
     const long long npix = (long long)nimg * D * H * W;
@@ -1096,7 +1106,7 @@ int cbct::conv_pack_jobs(const ConvPackJob *jobs, int njobs, long long max_nelem
 int cbct::conv_apply(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d, const float *w, const float *bias,
                      int cin, int cout, int flip, int epi, float slope, void *y, int cpout, const void *mask,
                      const float *state_in, float *state, long long sstride, int *status, cudaStream_t st,
-                     const uint8_t *packed, int zero_state_in) {
+                     const uint8_t *packed, int zero_state_in, const int *smap, int ssub) {
     if (!x || !w || nimg < 1 || D < 1 || H < 1 || W < 1 || cin < 1 || cout < 1 ||
         (cpin != 8 && cpin != 16 && cpin != 32) || cpin < (flip ? cout : cin))
         return fail(CBCT_EINVAL, "conv: invalid argument (sizes, or cpin below the input channels)");
@@ -1107,6 +1117,8 @@ int cbct::conv_apply(const void *x, int nimg, int D, int H, int W, int cpin, int
     if ((epi == EPI_RESIDUAL_F32 && !state) || (epi != EPI_RESIDUAL_F32 && (!y || cpout < n_out)) ||
         (epi == EPI_MASK_BF16 && !mask) || !status)
         return fail(CBCT_EINVAL, "conv: missing output");
+    if (smap && (epi != EPI_RESIDUAL_F32 || n_out > 8))
+        return fail(CBCT_EINVAL, "conv: a plane map needs the residual epilogue and at most 8 outputs");
     const int rpt = conv_rpt(taps3d, H, cpin, n_out);
     const long long bytes = conv_packed_bytes(n_out, taps3d, cpin, rpt);
     uint8_t *pk = nullptr;
@@ -1132,6 +1144,9 @@ int cbct::conv_apply(const void *x, int nimg, int D, int H, int W, int cpin, int
         a.state_in = state_in ? state_in : state;
         a.state_in_zero = zero_state_in;
         a.sstride = sstride;
+        a.smap_on = smap ? 1 : 0;
+        for (int c = 0; c < 8; ++c) a.smap[c] = smap ? smap[c < n_out ? c : 0] : c;
+        a.ssub = ssub ? 1 : 0;
         a.status = status;
         rc = conv_run(a, n_out, epi, rpt, st);
     }
@@ -1164,8 +1179,10 @@ extern "C" int cbct_conv_plan(int taps3d, int H, int cpin, int cin, int cout, in
 }
 
 extern "C" int cbct_conv_wgrad(const void *x, int cpin, int cin, const void *dy, int cpout, int cout, int nimg, int D,
-                               int H, int W, int taps3d, float *dw, float *db, int accumulate, void *stream) {
-    if (!x || !dy || !dw || !db || cin < 1 || cout < 1) return fail(CBCT_EINVAL, "cbct_conv_wgrad: invalid argument");
+                               int H, int W, int taps3d, float *dw, float *db, int accumulate, int *status,
+                               void *stream) {
+    if (!x || !dy || !dw || !db || !status || cin < 1 || cout < 1)
+        return fail(CBCT_EINVAL, "cbct_conv_wgrad: invalid argument");
     return conv_wgrad(static_cast<const __nv_bfloat16 *>(x), cpin, cin, static_cast<const __nv_bfloat16 *>(dy), cpout,
-                      cout, nimg, D, H, W, taps3d, dw, db, accumulate, (cudaStream_t)stream);
+                      cout, nimg, D, H, W, taps3d, dw, db, accumulate, status, (cudaStream_t)stream);
 }

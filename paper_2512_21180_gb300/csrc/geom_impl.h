@@ -34,12 +34,15 @@ int back_project_colw(const cbct_geom *g, const float *proj, const float *colw, 
                       cudaStream_t st);
 // cbct_conv with the residual epilogue reading its old state from state_in (which may
 // equal state) and writing state = state_in + conv (state = conv without reading
-// state_in when zero_state_in). packed: the layer's B operand already packed by
-// conv_pack_jobs for the same (taps3d, H, cpin, cin, cout, flip), or null to pack it here.
+// state_in when zero_state_in; state_in - conv with ssub). packed: the layer's B operand
+// already packed by conv_pack_jobs for the same (taps3d, H, cpin, cin, cout, flip), or
+// null to pack it here. smap (host, up to 8 entries, residual epilogue only): output
+// channel c lives in plane smap[c] of state / state_in (stride sstride), or plane c
+// when null.
 int conv_apply(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d, const float *w, const float *bias,
                int cin, int cout, int flip, int epi, float slope, void *y, int cpout, const void *mask,
                const float *state_in, float *state, long long sstride, int *status, cudaStream_t st,
-               const uint8_t *packed = nullptr, int zero_state_in = 0);
+               const uint8_t *packed = nullptr, int zero_state_in = 0, const int *smap = nullptr, int ssub = 0);
 // Packing of one layer's weights: the shape part is filled by conv_plan, the offsets
 // (weights within the parameter array, bytes within the packed buffer) by the caller.
 struct ConvPackJob {
@@ -52,6 +55,10 @@ long long conv_plan(int taps3d, int H, int cpin, int cin, int cout, int flip, Co
 // Packs njobs layers (jobs: device array) from params into out in one launch.
 int conv_pack_jobs(const ConvPackJob *jobs, int njobs, long long max_nelem, const float *params, uint8_t *out,
                    cudaStream_t st);
+// Looks up (once per device) the device address of back_project_noalloc's fixed
+// scratch array on `dev`, the current device. geometry_create calls it so that the
+// module holding the array is loaded, and the array placed, when the geometry is made.
+int noalloc_prime(int dev);
 // Staged (TMA) forward: returns 1 if it ran, 0 if the direct kernel must be used.
 int forward_staged(const cbct_geom *g, const float *vol, float *proj, int batch, int accumulate, cudaStream_t st);
 int choose_forward_cfg(double need_b, double need_z);

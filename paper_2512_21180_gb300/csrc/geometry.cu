@@ -1,7 +1,7 @@
 // Geometry object of the cone-beam library (a1): per-angle ray tables in voxel-index
 // coordinates, validation, status reporting.
 //
-// The frame of angle theta (paper Sec. 2.1 scanner: source on a circle of radius
+// The frame of angle theta (paper Sec. 2.2 scanner: source on a circle of radius
 // SID about z, flat panel at SDD, panel offset along the direction of rotation):
 //   S   = ((sid cos - cx)/vx + (nx-1)/2, (sid sin - cy)/vy + (ny-1)/2, -cz/vz + (nz-1)/2)
 //   D0S = ((-sdd cos - a sin)/vx, (-sdd sin + a cos)/vy, b/vz)      pixel (0,0) - source
@@ -261,6 +261,13 @@ extern "C" int geometry_create(const cbct_geom_desc *desc, cbct_geom **out) {
         if (!(nrm > 0.0)) { geometry_destroy(g); return fail(CBCT_EINVAL, "geometry_create: ||P|| is zero"); }
         v.scaled = 1.0 / nrm;
         v.scale = (float)v.scaled;
+    }
+    // resolve the fixed scratch array of back_project_noalloc on this device now: the
+    // lookup loads the projector module (and so places the array) here, so that the
+    // no-allocation entry point itself never reaches the allocator
+    {
+        int rc = cbct::noalloc_prime(dev);
+        if (rc != 0) { geometry_destroy(g); return rc; }
     }
     *out = g;
     return 0;

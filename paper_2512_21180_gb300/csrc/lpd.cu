@@ -1,13 +1,18 @@
-// Learned primal-dual reconstruction (paper Sec. 2.4, Algorithm 1; the unrolled
+// Learned primal-dual reconstruction (paper Sec. 2.6, Algorithm 1; the unrolled
 // primal-dual network with additive primal and dual updates), in the form of the
 // learned-primal-dual workload: n_iter iterations of
-//     h <- h + Gamma_n([h, P f_1, y])            dual block, 2D convs per projection
-//     f <- f + Lambda_n([f, P^T (w h_1)])        primal block, 3D convs
+//     h <- h + Gamma_n([h, P f_1, y (, P f_1 - y)])  dual block, 2D convs per projection
+//     f <- f + Lambda_n([f, P^T (w h_1)])            primal block, 3D convs
 // with n_mem-channel primal/dual memories, f starting from the FDK-style initial
 // volume repeated, h from zero, output f_0. Every block is conv3x3(x3) -> LReLU ->
 // conv -> LReLU -> conv at width `width`, BF16 operands on the tensor cores, FP32
 // states. Internally volumes are in units of mu_ref (f' = f / mu_ref, so mu_ref P f'
-// is in the units of y) and the backprojection is scaled by bp_scale.
+// is in the units of y) and the backprojection is scaled by bp_scale. The optional
+// data-residual channel mu_ref P f_1 - y is formed in FP32 before its BF16 rounding:
+// the projection-domain counterpart of the paper's Landweber input P*(P x - y)
+// (Algorithm 1), which a block could otherwise only form from two BF16-rounded
+// operands. A batch of volumes runs through every kernel at once: states are laid
+// out [channel][batch][pixels].
 //
 // Backward: the iterates (f_n, h_n) are the only saved tensors; each block's
 // activations are recomputed from its saved input during the reverse sweep
@@ -15,6 +20,7 @@
 // P and P^T.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -29,7 +35,7 @@ namespace cbct {
 // from conv.cu
 struct ConvArgs;
 int conv_wgrad(const __nv_bfloat16 *x, int cpin, int cin, const __nv_bfloat16 *dy, int cpout, int cout, int nimg,
-               int D, int H, int W, int taps3d, float *dw, float *db, int accumulate, cudaStream_t st);
+               int D, int H, int W, int taps3d, float *dw, float *db, int accumulate, int *status, cudaStream_t st);
 
 }  // namespace cbct
 
@@ -48,13 +54,21 @@ struct LayerSpec {
 struct cbct_lpd {
     const cbct_geom *g = nullptr;
     cbct_lpd_desc d{};
+    int maxb = 1;    // largest batch the workspaces hold
+    int batch = 1;   // batch of the last forward pass (the backward uses the same)
+    int nd = 7;      // dual input channels: n_mem + 2 (+ 1 with the residual channel); half of n_mem when reversible
+    // reversible mode: fixed channel permutations per iteration (new[c] = old[perm[c]]) and
+    // the plane of each logical channel after the last forward pass
+    std::vector<std::vector<int>> perm_f, perm_h;
+    int fin_f[8] = {}, fin_h[8] = {};
+    int cur_f[8] = {}, cur_h[8] = {};  // plane of each logical channel of the states held now
     std::vector<LayerSpec> layers;  // per iteration: 3 dual then 3 primal
     long long nparams = 0;
     float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
     float *wred = nullptr;  // redundancy weight [nu]
     float bp_scale = 1.f;
     int last = -1;  // slot of the final states after a forward pass
-    // saved iterates: f[n_iter + 1][n_mem][nvox], h[n_iter + 1][n_mem][nproj]
+    // saved iterates: f[n_iter + 1][n_mem][batch][nvox], h[n_iter + 1][n_mem][batch][nproj]
     float *f = nullptr, *h = nullptr;
     float *y = nullptr;  // the data of the last forward (copied)
     int saved = 0;
@@ -66,9 +80,9 @@ struct cbct_lpd {
     double *clip = nullptr;  // gradient-norm scratch: per-block partial sums, then norm and factor
     __nv_bfloat16 *din = nullptr, *a1 = nullptr, *a2 = nullptr, *pin = nullptr, *b1 = nullptr, *b2 = nullptr;
     __nv_bfloat16 *g32a = nullptr, *g32b = nullptr, *gsmall = nullptr;  // gradient buffers
-    float *gf = nullptr, *gh = nullptr;  // [n_mem + 1][nvox], [n_mem + 2][nproj]
+    float *gf = nullptr, *gh = nullptr;  // [n_mem + 1][batch][nvox], [nd][batch][nproj]
     int *status = nullptr;
-    long long nvox = 0, nproj = 0;
+    long long nvox = 0, nproj = 0;  // per volume
     // every forward layer's weights packed as tensor-core B operands, refreshed by one
     // launch at the start of each forward and backward pass
     uint8_t *wpk = nullptr;
@@ -107,18 +121,32 @@ __global__ void k_init_f(const float *__restrict__ x0, float *__restrict__ f, lo
     }
 }
 
-// channels-last BF16 [n][8] from up to 8 FP32 channel-first planes (null = zero)
+// channels-last BF16 [n][8] from up to 8 FP32 channel-first planes: channel c =
+// s[c] p[c][i] - q[c][i] (p null: 0; q null: no subtrahend), formed in FP32 and rounded
+// once to BF16
 struct Planes {
     const float *p[8];
     float s[8];
+    const float *q[8];
 };
 __global__ void k_pack8(Planes pl, long long n, __nv_bfloat16 *__restrict__ out) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) v[c] = __float2bfloat16_rn(pl.p[c] ? pl.p[c][i] * pl.s[c] : 0.f);
+        for (int c = 0; c < 8; ++c) {
+            float x = pl.p[c] ? pl.p[c][i] * pl.s[c] : 0.f;
+            if (pl.q[c]) x -= pl.q[c][i];
+            v[c] = __float2bfloat16_rn(x);
+        }
         *reinterpret_cast<uint4 *>(out + i * 8) = *reinterpret_cast<const uint4 *>(v);
     }
+}
+
+// acc[i] += a[i] - b[i]
+__global__ void k_add_diff(float *__restrict__ acc, const float *__restrict__ a, const float *__restrict__ b,
+                           long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc[i] += a[i] - b[i];
 }
 
 // out[k][v][u] = w[u] * in[k][v][u] * s
@@ -210,6 +238,14 @@ __global__ void k_mse_grad(const float *__restrict__ x, const float *__restrict_
         g[i] = (V && V[i] < thr) ? 0.f : inv * (x[i] - r[i]);
 }
 
+// a permutation of 2K channels mixes the halves when the new first half takes at least
+// one channel of the old second half
+bool perm_mixes(const int *p, int M) {
+    for (int c = 0; c < M / 2; ++c)
+        if (p[c] >= M / 2) return true;
+    return false;
+}
+
 int grid_n(long long n) {
     long long b = (n + 255) / 256;
     return (int)std::max<long long>(1, std::min<long long>(b, 152LL * 32));
@@ -234,9 +270,21 @@ static int conv_dx(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *dy, int
                      m->d.slope, y, 32, mask, state, sstride, m->status, st);
 }
 
-// geometry of the two blocks' tensors: dual = na images of nv x nu (2D), primal = nz x ny x nx (3D)
-#define DUAL_DIMS m->g->dev.na, 1, m->g->dev.nv, m->g->dev.nu
-#define PRIM_DIMS 1, m->g->dev.n[2], m->g->dev.n[1], m->g->dev.n[0]
+// geometry of the two blocks' tensors for a batch of B volumes: dual = B na images of nv x nu
+// (2D), primal = B volumes nz x ny x nx (3D)
+#define DUAL_DIMS B * m->g->dev.na, 1, m->g->dev.nv, m->g->dev.nu
+#define PRIM_DIMS B, m->g->dev.n[2], m->g->dev.n[1], m->g->dev.n[0]
+
+// dual block input [h (M), mu_ref pf, y (, mu_ref pf - y)] of a batch: planes of n elements
+static Planes dual_planes(const cbct_lpd *m, const float *h, const float *pf, const float *y) {
+    const int M = m->d.n_mem;
+    Planes pl{};
+    for (int c = 0; c < M; ++c) { pl.p[c] = h ? h + c * (long long)m->batch * m->nproj : nullptr; pl.s[c] = 1.f; }
+    pl.p[M] = pf; pl.s[M] = m->d.mu_ref;
+    pl.p[M + 1] = y; pl.s[M + 1] = 1.f;
+    if (m->d.residual_input) { pl.p[M + 2] = pf; pl.s[M + 2] = m->d.mu_ref; pl.q[M + 2] = y; }
+    return pl;
+}
 
 // One forward iteration n: (f_in, h_in) -> (f_out, h_out); activations left in the
 // workspaces (a1, a2, b1, b2, din, pin).
@@ -244,23 +292,21 @@ static int conv_dx(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *dy, int
 // iteration buffers of a training forward). h_zero: h_in is zero and is not read.
 static int lpd_iter_fwd(cbct_lpd *m, int n, const float *f_in, const float *h_in, float *f_out, float *h_out,
                         float *pf, float *bp, cudaStream_t st, bool h_zero = false) {
-    const long long NV = m->nvox, NP = m->nproj;
+    const int B = m->batch;
+    const long long NV = m->nvox * B, NP = m->nproj * B;  // one channel of the batch
     const int M = m->d.n_mem;
     const LayerSpec *Ld = &m->layers[6 * n], *Lp = &m->layers[6 * n + 3];
     void *sv = (void *)st;
-    // dual block input [h (M), mu_ref P f_1, y]
-    int rc = forward_project(m->g, f_in + 1 * NV, pf, 1, 0, sv);
+    // dual block input [h (M), mu_ref P f_1, y (, mu_ref P f_1 - y)]
+    int rc = forward_project(m->g, f_in + 1 * NV, pf, B, 0, sv);
     if (rc) return rc;
-    Planes pl{};
-    for (int c = 0; c < M; ++c) { pl.p[c] = h_zero ? nullptr : h_in + c * NP; pl.s[c] = 1.f; }
-    pl.p[M] = pf; pl.s[M] = m->d.mu_ref;
-    pl.p[M + 1] = m->y; pl.s[M + 1] = 1.f;
+    const Planes pl = dual_planes(m, h_zero ? nullptr : h_in, pf, m->y);
     k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
     if ((rc = conv_fwd(m, Ld[0], m->din, 8, DUAL_DIMS, 0, m->a1, nullptr, 0, st))) return rc;
     if ((rc = conv_fwd(m, Ld[1], m->a1, 32, DUAL_DIMS, 0, m->a2, nullptr, 0, st))) return rc;
     if ((rc = conv_fwd(m, Ld[2], m->a2, 32, DUAL_DIMS, 1, nullptr, h_out, NP, st, h_in, h_zero))) return rc;
     // primal block input [f (M), bp_scale P^T (w h_1)]
-    rc = back_project_colw(m->g, h_out + 1 * NP, m->wred, bp, 1, 0, st);
+    rc = back_project_colw(m->g, h_out + 1 * NP, m->wred, bp, B, 0, st);
     if (rc) return rc;
     Planes pp{};
     for (int c = 0; c < M; ++c) { pp.p[c] = f_in + c * NV; pp.s[c] = 1.f; }
@@ -277,14 +323,24 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     if (!g || !desc || !out) return fail(CBCT_EINVAL, "lpd_create: NULL argument");
     *out = nullptr;
     const cbct_lpd_desc &d = *desc;
-    if (d.n_iter < 1 || d.n_iter > 64 || d.n_mem < 2 || d.n_mem > 6 || d.width != 32 || !(d.mu_ref > 0) ||
-        !(d.slope >= 0.f && d.slope <= 1.f))
-        return fail(CBCT_EINVAL, "lpd_create: need 1 <= n_iter <= 64, 2 <= n_mem <= 6, width == 32, mu_ref > 0, "
-                                 "0 <= slope <= 1");
+    const int maxb = d.max_batch < 1 ? 1 : d.max_batch;
+    const bool rev = d.reversible != 0;
+    const bool mem_ok = rev ? (d.n_mem >= 2 && d.n_mem <= 8 && d.n_mem % 2 == 0)
+                            : (d.n_mem >= 2 && d.n_mem <= 6 && (!d.residual_input || d.n_mem <= 5));
+    if (d.n_iter < 1 || d.n_iter > 64 || !mem_ok || d.width != 32 || !(d.mu_ref > 0) ||
+        !(d.slope >= 0.f && d.slope <= 1.f) || (d.residual_input != 0 && d.residual_input != 1) ||
+        (d.reversible != 0 && d.reversible != 1) || maxb > 64 || (long long)maxb * g->dev.na > 65535)
+        return fail(CBCT_EINVAL, "lpd_create: need 1 <= n_iter <= 64, width == 32, mu_ref > 0, 0 <= slope <= 1, "
+                                 "residual_input and reversible 0 or 1, max_batch <= 64, max_batch * n_angles <= "
+                                 "65535, and 2 <= n_mem <= 6 (<= 5 with the residual channel) or, reversible, "
+                                 "n_mem even in [2, 8]");
     cbct_lpd *m = new (std::nothrow) cbct_lpd();
     if (!m) return fail(CBCT_ENOMEM, "lpd_create: host allocation");
     m->g = g;
     m->d = d;
+    m->maxb = maxb;
+    const int K = rev ? d.n_mem / 2 : d.n_mem;  // channels a block reads from / writes to each state
+    m->nd = K + 2 + d.residual_input;
     m->nvox = (long long)g->dev.n[0] * g->dev.n[1] * g->dev.n[2];
     m->nproj = (long long)g->dev.na * g->dev.nv * g->dev.nu;
     const int M = d.n_mem, W = d.width;
@@ -297,8 +353,8 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
         m->layers.push_back(L);
     };
     for (int n = 0; n < d.n_iter; ++n) {
-        add(M + 2, W, 0); add(W, W, 0); add(W, M, 0);   // dual
-        add(M + 1, W, 1); add(W, W, 1); add(W, M, 1);   // primal
+        add(m->nd, W, 0); add(W, W, 0); add(W, K, 0);   // dual
+        add(K + 1, W, 1); add(W, W, 1); add(W, K, 1);   // primal
     }
     m->nparams = off;
     // initial weights: He normal for hidden layers, 0.1 x that for the last layer of each block
@@ -310,8 +366,24 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
         const double sd = sqrt(2.0 / (L.cin * taps)) * ((i % 3 == 2) ? 0.1 : 1.0);
         for (long long k = 0; k < (long long)L.cout * taps * L.cin; ++k) hp[L.w_off + k] = (float)(sd * rng.normal());
     }
-    const long long NV = m->nvox, NP = m->nproj;
-    const int S = d.n_iter + 1;
+    if (rev) {
+        // per iteration a primal and a dual permutation that mix the halves (Fisher-Yates on
+        // the same SplitMix64 stream, redrawn until the new first half takes a channel of the
+        // old second half)
+        auto draw = [&](std::vector<int> &p) {
+            p.resize(M);
+            do {
+                for (int c = 0; c < M; ++c) p[c] = c;
+                for (int c = M - 1; c > 0; --c) std::swap(p[c], p[(int)(rng.next() % (uint64_t)(c + 1))]);
+            } while (!perm_mixes(p.data(), M));
+        };
+        m->perm_f.resize(d.n_iter);
+        m->perm_h.resize(d.n_iter);
+        for (int n = 0; n < d.n_iter; ++n) { draw(m->perm_f[n]); draw(m->perm_h[n]); }
+    }
+    const long long NV = m->nvox * maxb, NP = m->nproj * maxb;  // one channel of a full batch
+    const int S = rev ? 1 : d.n_iter + 1;  // stored state slots: every iterate, or the last one
+    const int NI = rev ? 0 : d.n_iter;     // stored projector outputs
     cudaError_t e = cudaSuccess;
     auto al = [&](void **p, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(p, bytes);
@@ -327,9 +399,9 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     al((void **)&m->tproj, sizeof(float) * NP);
     al((void **)&m->tproj2, sizeof(float) * NP);
     al((void **)&m->tvol, sizeof(float) * NV);
-    al((void **)&m->pf_saved, sizeof(float) * d.n_iter * NP);
+    al((void **)&m->pf_saved, sizeof(float) * std::max(1, NI) * NP);
     al((void **)&m->clip, sizeof(double) * (608 + 2));
-    al((void **)&m->bp_saved, sizeof(float) * d.n_iter * NV);
+    al((void **)&m->bp_saved, sizeof(float) * std::max(1, NI) * NV);
     al((void **)&m->din, sizeof(__nv_bfloat16) * NP * 8);
     al((void **)&m->a1, sizeof(__nv_bfloat16) * NP * 32);
     al((void **)&m->a2, sizeof(__nv_bfloat16) * NP * 32);
@@ -340,7 +412,7 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     al((void **)&m->g32b, sizeof(__nv_bfloat16) * std::max(NP, NV) * 32);
     al((void **)&m->gsmall, sizeof(__nv_bfloat16) * std::max(NP, NV) * 8);
     al((void **)&m->gf, sizeof(float) * (M + 1) * NV);
-    al((void **)&m->gh, sizeof(float) * (M + 2) * NP);
+    al((void **)&m->gh, sizeof(float) * (M + 3) * NP);
     al((void **)&m->status, sizeof(int));
     // forward convolutions: packing plan of every layer (first layer of a block reads 8
     // channel slots, the others 32; 2-D blocks run over the nv rows, 3-D over ny)
@@ -378,12 +450,12 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
         if (d.bp_scale > 0) {
             m->bp_scale = d.bp_scale;
         } else {
-            k_fill_f<<<grid_n(NP), 256>>>(m->tproj2, NP, 1.f);
+            k_fill_f<<<grid_n(m->nproj), 256>>>(m->tproj2, m->nproj, 1.f);
             rc = back_project_colw(g, m->tproj2, m->wred, m->tvol, 1, 0, nullptr);
             float mx = 0.f;
             if (rc == 0) {
                 cudaMemset(m->tproj2, 0, sizeof(float));
-                k_max_reduce<<<grid_n(NV), 256>>>(m->tvol, NV, m->tproj2);
+                k_max_reduce<<<grid_n(m->nvox), 256>>>(m->tvol, m->nvox, m->tproj2);
                 e = cudaMemcpy(&mx, m->tproj2, sizeof(float), cudaMemcpyDeviceToHost);
                 if (e != cudaSuccess) rc = cuda_fail(e, "lpd_create: bp scale");
             }
@@ -413,6 +485,36 @@ extern "C" void lpd_destroy(cbct_lpd *m) {
     delete m;
 }
 
+extern "C" int lpd_get_perms(const cbct_lpd *m, int *host) {
+    if (!m || !host || !m->d.reversible) return fail(CBCT_EINVAL, "lpd_get_perms: need a reversible model");
+    const int M = m->d.n_mem;
+    for (int n = 0; n < m->d.n_iter; ++n)
+        for (int c = 0; c < M; ++c) {
+            host[(2 * n) * M + c] = m->perm_f[n][c];
+            host[(2 * n + 1) * M + c] = m->perm_h[n][c];
+        }
+    return 0;
+}
+
+extern "C" int lpd_set_perms(cbct_lpd *m, const int *host) {
+    if (!m || !host || !m->d.reversible) return fail(CBCT_EINVAL, "lpd_set_perms: need a reversible model");
+    const int M = m->d.n_mem;
+    for (int r = 0; r < 2 * m->d.n_iter; ++r) {
+        const int *p = host + r * M;
+        int seen = 0;
+        for (int c = 0; c < M; ++c) {
+            if (p[c] < 0 || p[c] >= M || (seen >> p[c]) & 1) return fail(CBCT_EINVAL, "lpd_set_perms: not a permutation");
+            seen |= 1 << p[c];
+        }
+        if (!perm_mixes(p, M)) return fail(CBCT_EINVAL, "lpd_set_perms: a permutation does not mix the halves");
+    }
+    for (int n = 0; n < m->d.n_iter; ++n) {
+        m->perm_f[n].assign(host + (2 * n) * M, host + (2 * n) * M + M);
+        m->perm_h[n].assign(host + (2 * n + 1) * M, host + (2 * n + 1) * M + M);
+    }
+    return 0;
+}
+
 extern "C" int lpd_info(const cbct_lpd *m, long long *nparams, float **params, float **grads, float *bp_scale) {
     if (!m) return fail(CBCT_EINVAL, "lpd_info: NULL model");
     if (nparams) *nparams = m->nparams;
@@ -422,12 +524,13 @@ extern "C" int lpd_info(const cbct_lpd *m, long long *nparams, float **params, f
     return 0;
 }
 
-// Forward pass from the initial states f_0 (f0, or x0 / mu_ref in every channel) and
-// h_0 (h0, or zero); x_out = mu_ref f_N[0] when given. The final states stay in the
-// model (slot N with save_for_backward, else slot 0) for lpd_get_state.
+// Forward pass of a batch of B volumes from the initial states f_0 (f0, or x0 / mu_ref in
+// every channel) and h_0 (h0, or zero); x_out = mu_ref f_N[0] when given. The final states
+// stay in the model (slot N with save_for_backward, else slot 0) for lpd_get_state.
 static int lpd_forward_impl(cbct_lpd *m, const float *y, const float *x0, const float *f0, const float *h0,
-                            float *x_out, int save_for_backward, cudaStream_t st) {
-    const long long NV = m->nvox, NP = m->nproj;
+                            float *x_out, int save_for_backward, int B, cudaStream_t st) {
+    m->batch = B;
+    const long long NV = m->nvox * B, NP = m->nproj * B;
     const int M = m->d.n_mem, N = m->d.n_iter;
     int prc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
     if (prc) return prc;
@@ -462,23 +565,234 @@ static int lpd_forward_impl(cbct_lpd *m, const float *y, const float *x0, const 
     return 0;
 }
 
+// ---- reversible mode: additive coupling and channel permutations (Algorithm 1) ----------
+//
+// The states f = [p1, p2], h = [d1, d2] (halves of K = n_mem / 2 channels) live in
+// n_mem planes each; which plane holds logical channel c is tracked on the host
+// (pf[c], ph[c]), so a permutation moves no data. Per iteration n:
+//   d2 <- d2 + Gamma_n([d1, mu_ref P p2[0], y (, mu_ref P p2[0] - y)])
+//   p2 <- p2 + Lambda_n([p1, bp_scale P^T (w d2[0])])
+//   f <- f[perm_f[n]], h <- h[perm_h[n]]
+// Each update reads only the half it leaves unchanged, so the backward pass recovers
+// every iterate from the final states by undoing the permutations and subtracting the
+// same block outputs in reverse order (the kernels are deterministic, so a recomputed
+// block output equals the forward one bit for bit): no iterate is stored.
+
+// plane map after applying permutation p: new[c] = old[p[c]]
+static void map_permute(int *map, const std::vector<int> &p, int M) {
+    int t[8];
+    for (int c = 0; c < M; ++c) t[c] = map[p[c]];
+    for (int c = 0; c < M; ++c) map[c] = t[c];
+}
+// inverse: old[p[c]] = new[c]
+static void map_unpermute(int *map, const std::vector<int> &p, int M) {
+    int t[8];
+    for (int c = 0; c < M; ++c) t[p[c]] = map[c];
+    for (int c = 0; c < M; ++c) map[c] = t[c];
+}
+
+static Planes rev_dual_planes(const cbct_lpd *m, const float *h, const int *ph, long long NP, const float *pf,
+                              const float *y) {
+    const int K = m->d.n_mem / 2;
+    Planes pl{};
+    for (int c = 0; c < K; ++c) { pl.p[c] = h + ph[c] * NP; pl.s[c] = 1.f; }
+    pl.p[K] = pf; pl.s[K] = m->d.mu_ref;
+    pl.p[K + 1] = y; pl.s[K + 1] = 1.f;
+    if (m->d.residual_input) { pl.p[K + 2] = pf; pl.s[K + 2] = m->d.mu_ref; pl.q[K + 2] = y; }
+    return pl;
+}
+
+static Planes rev_primal_planes(const cbct_lpd *m, const float *f, const int *pfm, long long NV, const float *bp) {
+    const int K = m->d.n_mem / 2;
+    Planes pp{};
+    for (int c = 0; c < K; ++c) { pp.p[c] = f + pfm[c] * NV; pp.s[c] = 1.f; }
+    pp.p[K] = bp; pp.s[K] = m->bp_scale;
+    return pp;
+}
+
+// block output conv (layer 3) as a residual update of the mapped second-half planes
+// (ssub = 1 subtracts it again)
+static int rev_update(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *act, int nimg, int D, int H, int W,
+                      float *state, const int *map2, long long sstride, int ssub, cudaStream_t st) {
+    return conv_apply(act, nimg, D, H, W, 32, L.taps3d, m->params + L.w_off, m->params + L.b_off, L.cin, L.cout, 0,
+                      1, m->d.slope, nullptr, 32, nullptr, state, state, sstride, m->status, st, m->wpk + L.pk_off, 0,
+                      map2, ssub);
+}
+
+static int lpd_rev_forward(cbct_lpd *m, const float *y, const float *x0, float *x_out, int save_for_backward, int B,
+                           cudaStream_t st) {
+    m->batch = B;
+    void *sv = (void *)st;
+    const long long NV = m->nvox * B, NP = m->nproj * B;
+    const int M = m->d.n_mem, K = M / 2, N = m->d.n_iter;
+    int rc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
+    if (rc) return rc;
+    CBCT_CUDA_TRY(cudaMemcpyAsync(m->y, y, sizeof(float) * NP, cudaMemcpyDeviceToDevice, st));
+    k_init_f<<<grid_n(NV), 256, 0, st>>>(x0, m->f, NV, M, 1.f / m->d.mu_ref);
+    CBCT_CUDA_TRY(cudaMemsetAsync(m->h, 0, sizeof(float) * M * NP, st));
+    int pfm[8], phm[8];
+    for (int c = 0; c < M; ++c) pfm[c] = phm[c] = c;
+    for (int n = 0; n < N && rc == 0; ++n) {
+        const LayerSpec *Ld = &m->layers[6 * n], *Lp = &m->layers[6 * n + 3];
+        // dual: d2 += Gamma([d1, mu_ref P p2[0], y (, residual)])
+        if ((rc = forward_project(m->g, m->f + pfm[K] * NV, m->tproj, B, 0, sv))) break;
+        const Planes pl = rev_dual_planes(m, m->h, phm, NP, m->tproj, m->y);
+        k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
+        if ((rc = conv_fwd(m, Ld[0], m->din, 8, DUAL_DIMS, 0, m->a1, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Ld[1], m->a1, 32, DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
+        if ((rc = rev_update(m, Ld[2], m->a2, DUAL_DIMS, m->h, phm + K, NP, 0, st))) break;
+        // primal: p2 += Lambda([p1, bp_scale P^T (w d2[0])])
+        if ((rc = back_project_colw(m->g, m->h + phm[K] * NP, m->wred, m->tvol, B, 0, st))) break;
+        const Planes pp = rev_primal_planes(m, m->f, pfm, NV, m->tvol);
+        k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
+        if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Lp[1], m->b1, 32, PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
+        if ((rc = rev_update(m, Lp[2], m->b2, PRIM_DIMS, m->f, pfm + K, NV, 0, st))) break;
+        map_permute(pfm, m->perm_f[n], M);
+        map_permute(phm, m->perm_h[n], M);
+    }
+    if (rc) return rc;
+    if (x_out) k_sum_channels<<<grid_n(NV), 256, 0, st>>>(m->f + pfm[0] * NV, 1, NV, m->d.mu_ref, x_out, 0);
+    for (int c = 0; c < M; ++c) { m->fin_f[c] = m->cur_f[c] = pfm[c]; m->fin_h[c] = m->cur_h[c] = phm[c]; }
+    m->saved = save_for_backward;
+    m->last = 0;
+    CBCT_LAUNCH_CHECK("lpd_forward (reversible)");
+    return 0;
+}
+
+// Backward by inversion: from the final states, each iteration (last first) is undone —
+// permutations reversed, p2 -= Lambda(...), d2 -= Gamma(...) — while the gradients run
+// through the same blocks. The states end at the recovered initial states.
+static int lpd_rev_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float *grad_x0, cudaStream_t st) {
+    void *sv = (void *)st;
+    const int B = m->batch;
+    const long long NV = m->nvox * B, NP = m->nproj * B;
+    const int M = m->d.n_mem, K = M / 2, N = m->d.n_iter;
+    float *gf = m->gf, *gh = m->gh, *dW = m->grads;  // gf: M planes + plane M (scratch); gh: M + 3 planes
+    int rc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
+    if (rc) return rc;
+    int pfm[8], phm[8];
+    for (int c = 0; c < M; ++c) { pfm[c] = m->fin_f[c]; phm[c] = m->fin_h[c]; }
+    cudaMemsetAsync(gf, 0, sizeof(float) * (M + 1) * NV, st);
+    cudaMemsetAsync(gh, 0, sizeof(float) * (M + 3) * NP, st);
+    k_axpy<<<grid_n(NV), 256, 0, st>>>(gf + pfm[0] * NV, grad_x, NV, m->d.mu_ref);
+    if (grad_y) cudaMemsetAsync(grad_y, 0, sizeof(float) * NP, st);
+    for (int n = N - 1; n >= 0 && rc == 0; --n) {
+        const LayerSpec *Ld = &m->layers[6 * n], *Lp = &m->layers[6 * n + 3];
+        map_unpermute(pfm, m->perm_f[n], M);
+        map_unpermute(phm, m->perm_h[n], M);
+        // ---- primal update undone: recompute its input from p1 and the final d2[0]
+        if ((rc = back_project_colw(m->g, m->h + phm[K] * NP, m->wred, m->tvol, B, 0, st))) break;
+        const Planes pp = rev_primal_planes(m, m->f, pfm, NV, m->tvol);
+        k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
+        if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Lp[1], m->b1, 32, PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
+        if ((rc = rev_update(m, Lp[2], m->b2, PRIM_DIMS, m->f, pfm + K, NV, 1, st))) break;
+        // gradients through Lambda: upstream dL/dp2 (identity through the residual)
+        Planes gp{};
+        for (int c = 0; c < K; ++c) { gp.p[c] = gf + pfm[K + c] * NV; gp.s[c] = 1.f; }
+        k_pack8<<<grid_n(NV), 256, 0, st>>>(gp, NV, m->gsmall);
+        if ((rc = conv_wgrad(m->b2, 32, Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].w_off,
+                             dW + Lp[2].b_off, 1, m->status, st))) break;
+        if ((rc = conv_dx(m, Lp[2], m->gsmall, 8, PRIM_DIMS, 2, m->g32a, m->b2, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->b1, 32, Lp[1].cin, m->g32a, 32, Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].w_off,
+                             dW + Lp[1].b_off, 1, m->status, st))) break;
+        if ((rc = conv_dx(m, Lp[1], m->g32a, 32, PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, 32, Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].w_off,
+                             dW + Lp[0].b_off, 1, m->status, st))) break;
+        // dL/d[p1, bp]: p1's planes accumulate, the bp channel goes to scratch plane M
+        int mp[8];
+        for (int c = 0; c < K; ++c) mp[c] = pfm[c];
+        mp[K] = M;
+        cudaMemsetAsync(gf + (long long)M * NV, 0, sizeof(float) * NV, st);
+        if ((rc = conv_apply(m->g32b, PRIM_DIMS, 32, Lp[0].taps3d, m->params + Lp[0].w_off, nullptr, Lp[0].cin,
+                             Lp[0].cout, 1, 1, m->d.slope, nullptr, 32, nullptr, gf, gf, NV, m->status, st, nullptr,
+                             0, mp, 0))) break;
+        // bp = bp_scale P^T (w d2[0])  =>  dL/dd2[0] += w bp_scale P (dL/dbp)
+        if ((rc = forward_project(m->g, gf + (long long)M * NV, m->tproj, B, 0, sv))) break;
+        k_scale_cols<<<grid_n(NP), 256, 0, st>>>(m->tproj, m->wred, NP, m->g->dev.nu, m->bp_scale, m->tproj2);
+        k_axpy<<<grid_n(NP), 256, 0, st>>>(gh + phm[K] * NP, m->tproj2, NP, 1.f);
+        // ---- dual update undone: recompute its input from d1 and the recovered p2[0]
+        if ((rc = forward_project(m->g, m->f + pfm[K] * NV, m->tproj, B, 0, sv))) break;
+        const Planes pl = rev_dual_planes(m, m->h, phm, NP, m->tproj, m->y);
+        k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
+        if ((rc = conv_fwd(m, Ld[0], m->din, 8, DUAL_DIMS, 0, m->a1, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Ld[1], m->a1, 32, DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
+        if ((rc = rev_update(m, Ld[2], m->a2, DUAL_DIMS, m->h, phm + K, NP, 1, st))) break;
+        // gradients through Gamma: upstream dL/dd2
+        Planes gd{};
+        for (int c = 0; c < K; ++c) { gd.p[c] = gh + phm[K + c] * NP; gd.s[c] = 1.f; }
+        k_pack8<<<grid_n(NP), 256, 0, st>>>(gd, NP, m->gsmall);
+        if ((rc = conv_wgrad(m->a2, 32, Ld[2].cin, m->gsmall, 8, Ld[2].cout, DUAL_DIMS, 0, dW + Ld[2].w_off,
+                             dW + Ld[2].b_off, 1, m->status, st))) break;
+        if ((rc = conv_dx(m, Ld[2], m->gsmall, 8, DUAL_DIMS, 2, m->g32a, m->a2, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->a1, 32, Ld[1].cin, m->g32a, 32, Ld[1].cout, DUAL_DIMS, 0, dW + Ld[1].w_off,
+                             dW + Ld[1].b_off, 1, m->status, st))) break;
+        if ((rc = conv_dx(m, Ld[1], m->g32a, 32, DUAL_DIMS, 2, m->g32b, m->a1, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, 32, Ld[0].cout, DUAL_DIMS, 0, dW + Ld[0].w_off,
+                             dW + Ld[0].b_off, 1, m->status, st))) break;
+        // dL/d[d1, pf, y (, residual)]: d1's planes accumulate, the others go to scratch planes M..
+        const int nin = Ld[0].cin;
+        for (int c = 0; c < K; ++c) mp[c] = phm[c];
+        for (int c = K; c < nin; ++c) mp[c] = M + (c - K);
+        cudaMemsetAsync(gh + (long long)M * NP, 0, sizeof(float) * 3 * NP, st);
+        if ((rc = conv_apply(m->g32b, DUAL_DIMS, 32, Ld[0].taps3d, m->params + Ld[0].w_off, nullptr, Ld[0].cin,
+                             Ld[0].cout, 1, 1, m->d.slope, nullptr, 32, nullptr, gh, gh, NP, m->status, st, nullptr,
+                             0, mp, 0))) break;
+        float *g_pf = gh + (long long)M * NP, *g_y = gh + (long long)(M + 1) * NP;
+        if (m->d.residual_input) {
+            const float *g_res = gh + (long long)(M + 2) * NP;
+            if (grad_y) k_add_diff<<<grid_n(NP), 256, 0, st>>>(grad_y, g_y, g_res, NP);
+            k_axpy<<<grid_n(NP), 256, 0, st>>>(g_pf, g_res, NP, 1.f);
+        } else if (grad_y) {
+            k_axpy<<<grid_n(NP), 256, 0, st>>>(grad_y, g_y, NP, 1.f);
+        }
+        // pf channel = mu_ref P p2[0]  =>  dL/dp2[0] += mu_ref P^T (dL/dpf)
+        if ((rc = back_project(m->g, g_pf, m->tvol, B, 0, sv))) break;
+        k_axpy<<<grid_n(NV), 256, 0, st>>>(gf + pfm[K] * NV, m->tvol, NV, m->d.mu_ref);
+    }
+    if (rc) return rc;
+    // back at the initial states (every plane map is the identity again): f_0 = x0 / mu_ref
+    // in every channel  =>  dL/dx0 = sum_c gf[c] / mu_ref
+    if (grad_x0) k_sum_channels<<<grid_n(NV), 256, 0, st>>>(gf, M, NV, 1.f / m->d.mu_ref, grad_x0, 0);
+    for (int c = 0; c < M; ++c) { m->cur_f[c] = pfm[c]; m->cur_h[c] = phm[c]; }
+    m->saved = 0;  // the states now hold the recovered initial iterate
+    CBCT_LAUNCH_CHECK("lpd_backward (reversible)");
+    return 0;
+}
+
 extern "C" int lpd_forward(cbct_lpd *m, const float *y, const float *x0, float *x_out, int batch, int save_for_backward,
                            void *stream) {
     if (!m || !y || !x0 || !x_out) return fail(CBCT_EINVAL, "lpd_forward: NULL argument");
-    if (batch != 1) return fail(CBCT_EINVAL, "lpd_forward: batch must be 1 (accumulate gradients over calls)");
-    return lpd_forward_impl(m, y, x0, nullptr, nullptr, x_out, save_for_backward, (cudaStream_t)stream);
+    if (batch < 1 || batch > m->maxb)
+        return fail(CBCT_EINVAL, "lpd_forward: batch must lie in [1, max_batch = " + std::to_string(m->maxb) + "]");
+    if (m->d.reversible) return lpd_rev_forward(m, y, x0, x_out, save_for_backward, batch, (cudaStream_t)stream);
+    return lpd_forward_impl(m, y, x0, nullptr, nullptr, x_out, save_for_backward, batch, (cudaStream_t)stream);
 }
 
 extern "C" int lpd_forward_latent(cbct_lpd *m, const float *y, const float *x0, const float *f0, const float *h0,
                                   float *x_out, int save_for_backward, void *stream) {
     if (!m || !y || (!x0 && !f0)) return fail(CBCT_EINVAL, "lpd_forward_latent: need y and x0 or f0");
-    return lpd_forward_impl(m, y, x0, f0, h0, x_out, save_for_backward, (cudaStream_t)stream);
+    if (m->d.reversible) return fail(CBCT_EINVAL, "lpd_forward_latent: not available for a reversible model");
+    return lpd_forward_impl(m, y, x0, f0, h0, x_out, save_for_backward, 1, (cudaStream_t)stream);
 }
 
 extern "C" int lpd_get_state(const cbct_lpd *m, float *f_out, float *h_out, void *stream) {
     if (!m || m->last < 0) return fail(CBCT_EINVAL, "lpd_get_state: no forward pass yet");
     cudaStream_t st = (cudaStream_t)stream;
-    const long long NV = m->nvox, NP = m->nproj, M = m->d.n_mem;
+    const long long NV = m->nvox * m->batch, NP = m->nproj * m->batch, M = m->d.n_mem;
+    if (m->d.reversible) {
+        // logical channel order (the planes are permuted by bookkeeping only)
+        for (int c = 0; c < M; ++c) {
+            if (f_out)
+                CBCT_CUDA_TRY(cudaMemcpyAsync(f_out + c * NV, m->f + m->cur_f[c] * NV, sizeof(float) * NV,
+                                              cudaMemcpyDeviceToDevice, st));
+            if (h_out)
+                CBCT_CUDA_TRY(cudaMemcpyAsync(h_out + c * NP, m->h + m->cur_h[c] * NP, sizeof(float) * NP,
+                                              cudaMemcpyDeviceToDevice, st));
+        }
+        return 0;
+    }
     if (f_out)
         CBCT_CUDA_TRY(cudaMemcpyAsync(f_out, m->f + (long long)m->last * M * NV, sizeof(float) * M * NV,
                                       cudaMemcpyDeviceToDevice, st));
@@ -488,22 +802,24 @@ extern "C" int lpd_get_state(const cbct_lpd *m, float *f_out, float *h_out, void
     return 0;
 }
 
-// Backward pass: upstream dL/dx_out (grad_x) and/or dL/df_N, dL/dh_N (the final
-// states, e.g. from a finer level); accumulates the parameter gradients and returns
-// dL/dy, dL/dx0 and dL/df_0, dL/dh_0 where asked.
+// Backward pass of the last forward's batch: upstream dL/dx_out (grad_x) and/or dL/df_N,
+// dL/dh_N (the final states, e.g. from a finer level); accumulates the parameter gradients
+// (summed over the batch) and returns dL/dy, dL/dx0 and dL/df_0, dL/dh_0 where asked.
 static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad_fN, const float *grad_hN,
                              float *grad_y, float *grad_x0, float *grad_f0, float *grad_h0, cudaStream_t st) {
     void *sv = (void *)st;
-    const long long NV = m->nvox, NP = m->nproj;
-    const int M = m->d.n_mem, N = m->d.n_iter;
-    float *gf = m->gf, *gh = m->gh;  // gf: [M + 1][NV] (last = grad of the bp channel), gh: [M + 2][NP]
+    const int B = m->batch;
+    const long long NV = m->nvox * B, NP = m->nproj * B;
+    const int M = m->d.n_mem, N = m->d.n_iter, ND = m->nd;
+    // gf: [M + 1][B][nvox] (last = grad of the bp channel); gh: [ND][B][nproj] (h, pf, y, residual)
+    float *gf = m->gf, *gh = m->gh;
     // the recomputed forward convolutions read the packed weights: refresh them (the
     // parameters may have changed since the forward pass)
     int prc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
     if (prc) return prc;
     // dL/df_N: channel 0 gets mu_ref dL/dx; plus the given state gradients
     cudaMemsetAsync(gf, 0, sizeof(float) * (M + 1) * NV, st);
-    cudaMemsetAsync(gh, 0, sizeof(float) * (M + 2) * NP, st);
+    cudaMemsetAsync(gh, 0, sizeof(float) * ND * NP, st);
     if (grad_x) k_axpy<<<grid_n(NV), 256, 0, st>>>(gf, grad_x, NV, m->d.mu_ref);
     if (grad_fN) k_axpy<<<grid_n((long long)M * NV), 256, 0, st>>>(gf, grad_fN, (long long)M * NV, 1.f);
     if (grad_hN) k_axpy<<<grid_n((long long)M * NP), 256, 0, st>>>(gh, grad_hN, (long long)M * NP, 1.f);
@@ -513,11 +829,9 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
         const float *f_n = m->f + (long long)n * M * NV, *h_n = m->h + (long long)n * M * NP;
         const LayerSpec *Ld = &m->layers[6 * n], *Lp = &m->layers[6 * n + 3];
         float *dW = m->grads;
+        const float *pf_n = m->pf_saved + (long long)n * NP;
         // recompute the dual block input and activations of iteration n (P f_1 kept)
-        Planes pl{};
-        for (int c = 0; c < M; ++c) { pl.p[c] = h_n + c * NP; pl.s[c] = 1.f; }
-        pl.p[M] = m->pf_saved + (long long)n * NP; pl.s[M] = m->d.mu_ref;
-        pl.p[M + 1] = m->y; pl.s[M + 1] = 1.f;
+        const Planes pl = dual_planes(m, h_n, pf_n, m->y);
         k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
         if ((rc = conv_fwd(m, Ld[0], m->din, 8, DUAL_DIMS, 0, m->a1, nullptr, 0, st))) break;
         if ((rc = conv_fwd(m, Ld[1], m->a1, 32, DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
@@ -534,18 +848,18 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
         for (int c = 0; c < M; ++c) { gp.p[c] = gf + c * NV; gp.s[c] = 1.f; }
         k_pack8<<<grid_n(NV), 256, 0, st>>>(gp, NV, m->gsmall);
         if ((rc = conv_wgrad(m->b2, 32, Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].w_off,
-                             dW + Lp[2].b_off, 1, st))) break;
+                             dW + Lp[2].b_off, 1, m->status, st))) break;
         if ((rc = conv_dx(m, Lp[2], m->gsmall, 8, PRIM_DIMS, 2, m->g32a, m->b2, nullptr, 0, st))) break;
         if ((rc = conv_wgrad(m->b1, 32, Lp[1].cin, m->g32a, 32, Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].w_off,
-                             dW + Lp[1].b_off, 1, st))) break;
+                             dW + Lp[1].b_off, 1, m->status, st))) break;
         if ((rc = conv_dx(m, Lp[1], m->g32a, 32, PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) break;
         if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, 32, Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].w_off,
-                             dW + Lp[0].b_off, 1, st))) break;
+                             dW + Lp[0].b_off, 1, m->status, st))) break;
         // dL/d(primal input) -> gf[0..M) += (residual path kept), gf[M] = dL/d(bp channel)
         cudaMemsetAsync(gf + (long long)M * NV, 0, sizeof(float) * NV, st);
         if ((rc = conv_dx(m, Lp[0], m->g32b, 32, PRIM_DIMS, 1, nullptr, nullptr, gf, NV, st))) break;
         // bp = bp_scale P^T (w h_1)  =>  dL/dh_{n+1}[1] += w * bp_scale * P (dL/dbp)
-        if ((rc = forward_project(m->g, gf + (long long)M * NV, m->tproj, 1, 0, sv))) break;
+        if ((rc = forward_project(m->g, gf + (long long)M * NV, m->tproj, B, 0, sv))) break;
         k_scale_cols<<<grid_n(NP), 256, 0, st>>>(m->tproj, m->wred, NP, m->g->dev.nu, m->bp_scale, m->tproj2);
         k_axpy<<<grid_n(NP), 256, 0, st>>>(gh + NP, m->tproj2, NP, 1.f);
 
@@ -554,19 +868,29 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
         for (int c = 0; c < M; ++c) { gd.p[c] = gh + c * NP; gd.s[c] = 1.f; }
         k_pack8<<<grid_n(NP), 256, 0, st>>>(gd, NP, m->gsmall);
         if ((rc = conv_wgrad(m->a2, 32, Ld[2].cin, m->gsmall, 8, Ld[2].cout, DUAL_DIMS, 0, dW + Ld[2].w_off,
-                             dW + Ld[2].b_off, 1, st))) break;
+                             dW + Ld[2].b_off, 1, m->status, st))) break;
         if ((rc = conv_dx(m, Ld[2], m->gsmall, 8, DUAL_DIMS, 2, m->g32a, m->a2, nullptr, 0, st))) break;
         if ((rc = conv_wgrad(m->a1, 32, Ld[1].cin, m->g32a, 32, Ld[1].cout, DUAL_DIMS, 0, dW + Ld[1].w_off,
-                             dW + Ld[1].b_off, 1, st))) break;
+                             dW + Ld[1].b_off, 1, m->status, st))) break;
         if ((rc = conv_dx(m, Ld[1], m->g32a, 32, DUAL_DIMS, 2, m->g32b, m->a1, nullptr, 0, st))) break;
         if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, 32, Ld[0].cout, DUAL_DIMS, 0, dW + Ld[0].w_off,
-                             dW + Ld[0].b_off, 1, st))) break;
-        // dL/d(dual input): gh[0..M) += (residual), gh[M] = dL/d(P f_1 channel), gh[M+1] = dL/dy
-        cudaMemsetAsync(gh + (long long)M * NP, 0, sizeof(float) * 2 * NP, st);
+                             dW + Ld[0].b_off, 1, m->status, st))) break;
+        // dL/d(dual input): gh[0..M) += (residual), gh[M] = dL/d(pf channel), gh[M+1] = dL/d(y channel),
+        // gh[M+2] = dL/d(residual channel mu_ref pf - y)
+        cudaMemsetAsync(gh + (long long)M * NP, 0, sizeof(float) * (ND - M) * NP, st);
         if ((rc = conv_dx(m, Ld[0], m->g32b, 32, DUAL_DIMS, 1, nullptr, nullptr, gh, NP, st))) break;
-        if (grad_y) k_axpy<<<grid_n(NP), 256, 0, st>>>(grad_y, gh + (long long)(M + 1) * NP, NP, 1.f);
-        // pf = mu_ref P f_1  =>  dL/df_n[1] += mu_ref P^T (dL/dpf)
-        if ((rc = back_project(m->g, gh + (long long)M * NP, m->tvol, 1, 0, sv))) break;
+        float *g_pf = gh + (long long)M * NP, *g_y = gh + (long long)(M + 1) * NP;
+        if (m->d.residual_input) {
+            // residual channel = pf channel - y: its gradient adds to the pf channel's and
+            // subtracts from y's
+            const float *g_res = gh + (long long)(M + 2) * NP;
+            if (grad_y) k_add_diff<<<grid_n(NP), 256, 0, st>>>(grad_y, g_y, g_res, NP);
+            k_axpy<<<grid_n(NP), 256, 0, st>>>(g_pf, g_res, NP, 1.f);
+        } else if (grad_y) {
+            k_axpy<<<grid_n(NP), 256, 0, st>>>(grad_y, g_y, NP, 1.f);
+        }
+        // pf channel = mu_ref P f_1  =>  dL/df_n[1] += mu_ref P^T (dL/dpf channel)
+        if ((rc = back_project(m->g, g_pf, m->tvol, B, 0, sv))) break;
         k_axpy<<<grid_n(NV), 256, 0, st>>>(gf + NV, m->tvol, NV, m->d.mu_ref);
     }
     if (rc) return rc;
@@ -581,6 +905,7 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
 extern "C" int lpd_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float *grad_x0, void *stream) {
     if (!m || !grad_x) return fail(CBCT_EINVAL, "lpd_backward: NULL argument");
     if (!m->saved) return fail(CBCT_EINVAL, "lpd_backward: call lpd_forward with save_for_backward = 1 first");
+    if (m->d.reversible) return lpd_rev_backward(m, grad_x, grad_y, grad_x0, (cudaStream_t)stream);
     return lpd_backward_impl(m, grad_x, nullptr, nullptr, grad_y, grad_x0, nullptr, nullptr, (cudaStream_t)stream);
 }
 
@@ -588,6 +913,7 @@ extern "C" int lpd_backward_latent(cbct_lpd *m, const float *grad_x, const float
                                    float *grad_y, float *grad_x0, float *grad_f0, float *grad_h0, void *stream) {
     if (!m || (!grad_x && !grad_fN && !grad_hN)) return fail(CBCT_EINVAL, "lpd_backward_latent: no upstream gradient");
     if (!m->saved) return fail(CBCT_EINVAL, "lpd_backward_latent: call the forward with save_for_backward = 1 first");
+    if (m->d.reversible) return fail(CBCT_EINVAL, "lpd_backward_latent: not available for a reversible model");
     return lpd_backward_impl(m, grad_x, grad_fN, grad_hN, grad_y, grad_x0, grad_f0, grad_h0, (cudaStream_t)stream);
 }
 

@@ -1,4 +1,4 @@
-// Resampling between the levels of the multiscale reconstruction (a11; paper Sec. 2.4,
+// Resampling between the levels of the multiscale reconstruction (a11; paper Sec. 2.6,
 // the multiscale scheme: the coarse level works on half-resolution volumes and on
 // projections with every second angle and 2 x 2 binned pixels, and its result is
 // carried to the fine level by upsampling).

@@ -1,5 +1,5 @@
 // Cone-beam projector pair (a2, a3): Joseph-style forward projection P and its
-// exact transpose P* as an atomic-free voxel-driven gather (paper Sec. 2.1,
+// exact transpose P* as an atomic-free voxel-driven gather (paper Sec. 2.2,
 // projection operator and its adjoint, the backprojection).
 //
 // Forward (k_forward): one thread per ray; the ray visits every voxel-centre plane
@@ -640,6 +640,11 @@ static int noalloc_scratch(int dev, float **out) {
     }
     *out = g_noalloc_ptr[dev];
     return 0;
+}
+
+int noalloc_prime(int dev) {
+    float *p = nullptr;
+    return noalloc_scratch(dev, &p);
 }
 
 }  // namespace cbct

@@ -1,4 +1,4 @@
-// Forward projector with TMA-staged volume tiles (a2, paper Sec. 2.1 projection
+// Forward projector with TMA-staged volume tiles (a2, paper Sec. 2.2 projection
 // operator; Joseph-style ray sums as in projector.cu).
 //
 // Layout: the volume is first copied plane-major for each principal axis,

@@ -1,11 +1,11 @@
 // Classical reconstructions: the learned method's start and the baseline it is compared with:
 //  - FDK with redundancy weighting (paper Algorithm 1 initialisation "FDK_w",
-//    Sec. 2.4; Feldkamp, Davis, Kress 1984): cosine and redundancy weights, Ram-Lak
+//    Sec. 2.6; Feldkamp, Davis, Kress 1984): cosine and redundancy weights, Ram-Lak
 //    ramp filter along detector rows at the isocentre pitch, distance-weighted
 //    voxel backprojection. An offset panel's rows are zero-padded on the short side
 //    to the mirror image of the long edge before filtering.
 //  - PDHG (Chambolle-Pock 2011) for 1/2 ||P x - y||^2 + lam TV(x), x >= 0, isotropic
-//    TV by forward differences (the paper's TV baseline, Sec. 2.3), on K = [P; gamma grad]
+//    TV by forward differences (the paper's TV baseline, Sec. 2.5), on K = [P; gamma grad]
 //    with the TV ball radius lam / gamma.
 //  - Landweber iterations x <- x - tau P^T (P x - y) (the gradient term of Algorithm 1).
 #include <algorithm>

@@ -1,14 +1,14 @@
 // Data simulation and per-geometry tensors (a5, a6):
-//  - ellipsoid phantom voxeliser (stand-in for the paper's CT volumes, Sec. 2.3)
-//  - photon counts N ~ Poisson(I0 exp(-p)) (paper Sec. 2.1, primary model, one
+//  - ellipsoid phantom voxeliser (stand-in for the paper's CT volumes, Sec. 2.4)
+//  - photon counts N ~ Poisson(I0 exp(-p)) (paper Sec. 2.2, primary model, one
 //    energy) from a Philox4x32-10 counter stream (Salmon et al., SC'11), sampled by
 //    inversion for means below 10 and by Hoermann's PTRS transformed rejection
 //    (1993) above
-//  - normalised log transform y = -log(min(max(N, 1) / I0, 1)) (Sec. 2.3)
-//  - offset-detector redundancy weight w (Sec. 2.4; Wang's sin^2 weight over the
+//  - normalised log transform y = -log(min(max(N, 1) / I0, 1)) (Sec. 2.4)
+//  - offset-detector redundancy weight w (Sec. 2.6; Wang's sin^2 weight over the
 //    overlap band, 1/2 for a centred panel)
 //  - field-of-view tensor V = (angles seeing the voxel centre) / (all angles)
-//    (Sec. 2.4, definition of V)
+//    (Sec. 2.6, definition of V)
 #include <cmath>
 #include <vector>
 

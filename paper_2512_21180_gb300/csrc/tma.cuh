@@ -55,14 +55,18 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Wait for the phase of `bar` with the given parity; after ~2 s record a timeout
-// in *status and return false.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status) {
+// Default limit of every bounded wait in the library's kernels (2 s of %globaltimer).
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+// Wait for the phase of `bar` with the given parity; after limit_ns nanoseconds
+// record a timeout in *status and return false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status,
+                                          uint64_t limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > 2000000000ull) {
+        if (global_ns() - t0 > limit_ns) {
             atomicExch(status, kStatusMbarTimeout);
             return false;
         }

@@ -5,10 +5,14 @@ Poisson noise (128^3 at 4 mm, 200 angles, 256x192 panel at 1.6 mm with +80 mm
 offset, I0 = 1e5 photons/pixel), starting every reconstruction from FDK_w, and
 compares it with 100 iterations of FP32 PDHG-TV (lambda tuned on held-out
 phantoms) on test phantoms: PSNR over the full field of view (voxels seen by at
-least half of the projections, Sec. 2.4) and GPU seconds per volume.
+least half of the projections, Sec. 2.6) and GPU seconds per volume.
 
     python -m paper_2512_21180_gb300.experiment_lpd [--train 512] [--test 32] [--epochs 2]
-           [--minutes 20] [--out results.json]
+           [--minutes 20] [--residual-input] [--vol-batch 4] [--out results.json] [--save w.npy]
+
+The comparison is made at equal PSNR (equal_psnr): the smallest number of PDHG
+iterations whose mean test PSNR reaches the learned reconstruction's, and the GPU
+time of each to get there.
 
 Everything runs in libcbct (projectors, convs, simulation, FDK, PDHG, Adam);
 PyTorch holds the buffers.
@@ -66,6 +70,95 @@ def timed(fn, reps: int = 3):
     return r, e0.elapsed_time(e1) / reps / 1e3
 
 
+def widen_params(flat: np.ndarray, n_iter: int, n_mem: int, width: int, residual_input: bool) -> np.ndarray:
+    """Parameters for the network with the data-residual channel from those of the same
+    network without it (or unchanged when they already fit): each dual block's first
+    layer gains zero weights for the extra input, so both networks compute the same
+    function and training continues from there."""
+    from .lpd import layer_shapes
+    new_shapes = layer_shapes(n_iter, n_mem, width, residual_input)
+    if flat.size == sum(co * t * ci + co for co, t, ci in new_shapes):
+        return flat.astype(np.float32)
+    old_shapes = layer_shapes(n_iter, n_mem, width, False)
+    if flat.size != sum(co * t * ci + co for co, t, ci in old_shapes):
+        raise ValueError("parameter count fits neither layout")
+    out, o = [], 0
+    for (co, t, ci), (_, _, ci2) in zip(old_shapes, new_shapes):
+        w = flat[o:o + co * t * ci].reshape(co, t, ci)
+        o += co * t * ci
+        w2 = np.zeros((co, t, ci2), dtype=np.float32)
+        w2[:, :, :ci] = w
+        out += [w2.reshape(-1), flat[o:o + co]]
+        o += co
+    return np.concatenate(out).astype(np.float32)
+
+
+def event_seconds(fn, reps: int = 3, warmup: int = 1) -> float:
+    """GPU seconds per call of fn (CUDA events on the current stream, after warm-up)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps / 1e3
+
+
+def equal_psnr(geom: Geometry, model: LPD, test, full: torch.Tensor, lam: float, gam: float, sig: float, tau: float,
+               kmax: int = 1600) -> dict:
+    """The learned reconstruction against PDHG-TV at equal PSNR on a test set of
+    (x_true, y, x0 = FDK_w) triples: the mean PSNR over FullFoV of the LPD (FDK_w start +
+    unrolled iterations), the smallest PDHG iteration count k* whose mean PSNR reaches it
+    (bisection over k, PDHG's mean PSNR taken as non-decreasing in k; doubling past 100
+    when needed, up to kmax), and GPU seconds per volume of FDK_w + LPD and of FDK_w + k*
+    PDHG iterations."""
+    cache = {}
+
+    def pdhg_psnr(k):
+        if k not in cache:
+            cache[k] = float(np.mean([psnr(ops.pdhg(geom, y, x0, k, lam, gam, sig, tau)[0], x, full)
+                                      for x, y, x0 in test]))
+        return cache[k]
+
+    p_lpd = float(np.mean([psnr(model.forward(y, x0), x, full) for x, y, x0 in test]))
+    p_fdk = float(np.mean([psnr(x0, x, full) for x, y, x0 in test]))
+    _, y1, _ = test[0]
+    t_lpd = event_seconds(lambda: model.forward(y1, ops.fdk(geom, y1)[0]))
+    p100 = pdhg_psnr(100)
+    lo, hi = 0, 100
+    if p100 < p_lpd:
+        lo, hi = 100, 200
+        while hi <= kmax and pdhg_psnr(hi) < p_lpd:
+            lo, hi = hi, 2 * hi
+    if hi <= kmax:
+        while hi - lo > 1:
+            mid = (lo + hi) // 2
+            if pdhg_psnr(mid) >= p_lpd:
+                hi = mid
+            else:
+                lo = mid
+        k_eq = hi
+    else:
+        k_eq = None
+    t_pdhg = lambda k: event_seconds(lambda: ops.pdhg(geom, y1, ops.fdk(geom, y1)[0], k, lam, gam, sig, tau),
+                                     reps=1)
+    t100 = t_pdhg(100)
+    out = {"n_test": len(test), "lambda": lam, "psnr_fdk": p_fdk, "psnr_lpd": p_lpd, "psnr_pdhg100": p100,
+           "lpd_s_per_volume": t_lpd, "pdhg100_s_per_volume": t100, "pdhg100_over_lpd": t100 / t_lpd,
+           "pdhg_iters_to_lpd_psnr": k_eq,
+           "pdhg_psnr_by_iters": {str(k): v for k, v in sorted(cache.items())}}
+    if k_eq is not None:
+        t_eq = t_pdhg(k_eq)
+        out.update({"pdhg_s_at_lpd_psnr": t_eq, "pdhg_over_lpd_at_equal_psnr": t_eq / t_lpd})
+    else:
+        out.update({"pdhg_s_at_lpd_psnr": None, "pdhg_over_lpd_at_equal_psnr": None,
+                    "note": f"PDHG does not reach the LPD's PSNR within {kmax} iterations"})
+    return out
+
+
 def profile_pass(args) -> int:
     torch.cuda.set_device(0)
     geom = Geometry(I.geometry(WORKLOAD))
@@ -100,6 +193,11 @@ def main(argv=None):
     ap.add_argument("--clip", type=float, default=1.0, help="global gradient-norm clip (loss in mu_ref^2 units)")
     ap.add_argument("--warmup", type=int, default=40, help="linear learning-rate warm-up steps")
     ap.add_argument("--n-iter", type=int, default=8)
+    ap.add_argument("--residual-input", action="store_true",
+                    help="dual blocks also receive the FP32-formed data residual mu_ref P f_1 - y")
+    ap.add_argument("--vol-batch", type=int, default=4, help="volumes per forward/backward call")
+    ap.add_argument("--lams", default="0.3,1,2,3,5,10,20", help="PDHG lambda grid (tuned on held-out phantoms)")
+    ap.add_argument("--init", default=None, help="start from these parameters (.npy)")
     ap.add_argument("--pdhg-iters", type=int, default=100)
     ap.add_argument("--out", default=None)
     ap.add_argument("--save", default=None, help="write the trained parameters (.npy)")
@@ -130,7 +228,7 @@ def main(argv=None):
     gam = nP / math.sqrt(12.0)
     nK = ops.opnorm(geom, gam, 30)
     sig = tau = 0.99 / nK
-    lams = [1e-3, 3e-3, 1e-2, 3e-2, 1e-1, 3e-1, 1.0, 3.0, 10.0]
+    lams = [float(v) for v in args.lams.split(",")]
     best = None
     for lam in lams:
         ps = [psnr(ops.pdhg(geom, y, x0, args.pdhg_iters, lam, gam, sig, tau)[0], x, full) for x, y, x0 in tune]
@@ -139,10 +237,18 @@ def main(argv=None):
         if best is None or m > best[1]:
             best = (lam, m)
     lam = best[0]
-    log["pdhg"] = {"lambda": lam, "iters": args.pdhg_iters, "sigma": sig, "tau": tau, "gamma": gam}
+    log["pdhg"] = {"lambda": lam, "iters": args.pdhg_iters, "sigma": sig, "tau": tau, "gamma": gam,
+                   "grid": lams, "best_is_grid_edge": lam in (lams[0], lams[-1])}
 
     # ---- train the learned primal-dual network
-    model = LPD(geom, n_iter=args.n_iter, seed=1)
+    vb = max(1, min(args.vol_batch, args.batch))
+    if args.batch % vb:
+        raise SystemExit("--batch must be a multiple of --vol-batch")
+    model = LPD(geom, n_iter=args.n_iter, seed=1, residual_input=args.residual_input, max_batch=vb)
+    if args.init:
+        model.set_params(widen_params(np.load(args.init), args.n_iter, model.n_mem, model.width,
+                                      args.residual_input))
+    Vb = V.expand((vb,) + tuple(V.shape)).contiguous()
     t_train = time.time()
     step = 0
     est_steps = 10 ** 9
@@ -155,12 +261,16 @@ def main(argv=None):
         for b0 in range(0, len(perm) - args.batch + 1, args.batch):
             model.zero_grad()
             tot = 0.0
-            for j in perm[b0:b0 + args.batch]:
-                x, y, x0 = train[j]
+            idx = perm[b0:b0 + args.batch]
+            for c0 in range(0, len(idx), vb):
+                items = [train[j] for j in idx[c0:c0 + vb]]
+                x = torch.stack([t[0] for t in items])
+                y = torch.stack([t[1] for t in items])
+                x0 = torch.stack([t[2] for t in items])
                 out = model.forward(y, x0, save_for_backward=True)
-                loss, gr = masked_mse(out, x, V, 0.5)
+                loss, gr = masked_mse(out, x, Vb, 0.5)     # mean over the vb volumes' FoV voxels
                 model.backward(gr)
-                tot += loss.item()
+                tot += loss.item() * vb
             # loss in units of mu_ref^2 (O(1)); linear warm-up, then cosine decay over the
             # number of steps the time budget allows (estimated after the warm-up)
             if step == args.warmup and step > 0:
@@ -170,7 +280,7 @@ def main(argv=None):
             else:
                 lr = args.lr * 0.5 * (1.0 + math.cos(math.pi * min(1.0, (step - args.warmup) /
                                                                    max(1, est_steps - args.warmup))))
-            gscale = 1.0 / (args.batch * model.mu_ref ** 2)
+            gscale = vb / (args.batch * model.mu_ref ** 2)
             norms.append(model.clip_grads(args.clip, grad_scale=gscale))
             model.adam_step(lr, grad_scale=gscale)
             step += 1
@@ -186,29 +296,20 @@ def main(argv=None):
             break
     if args.save:
         np.save(args.save, model.get_params())
+        meta = {"n_iter": args.n_iter, "n_mem": model.n_mem, "width": model.width, "mu_ref": model.mu_ref,
+                "residual_input": bool(args.residual_input), "pdhg_lambda": lam, "workload": WORKLOAD,
+                "train_phantoms": args.train, "train_seconds": time.time() - t_train, "adam_steps": step}
+        with open(os.path.splitext(args.save)[0] + ".json", "w") as f:
+            json.dump(meta, f, indent=1)
     log["training"] = {"steps": step, "effective_batch": args.batch, "lr": args.lr, "warmup": args.warmup,
                        "clip": args.clip, "grad_norm_median": float(np.median(norms)) if norms else None,
                        "seconds": time.time() - t_train, "loss_first": losses[0] if losses else None,
                        "loss_last8": float(np.mean(losses[-8:])) if losses else None}
 
-    # ---- evaluate: PSNR and GPU seconds per volume
-    res = {"fdk": [], "pdhg": [], "lpd": []}
-    t_lpd = t_pdhg = t_fdk = 0.0
-    for x, y, x0 in test:
-        _, tf = timed(lambda: ops.fdk(geom, y), reps=1)
-        r_p, tp = timed(lambda: ops.pdhg(geom, y, x0, args.pdhg_iters, lam, gam, sig, tau)[0], reps=1)
-        r_l, tl = timed(lambda: model.forward(y, x0), reps=1)
-        t_fdk += tf
-        t_pdhg += tp
-        t_lpd += tl
-        res["fdk"].append(psnr(x0, x, full))
-        res["pdhg"].append(psnr(r_p, x, full))
-        res["lpd"].append(psnr(r_l, x, full))
-    n = len(test)
-    log["psnr_fullfov"] = {k: {"mean": float(np.mean(v)), "sd": float(np.std(v))} for k, v in res.items()}
-    log["seconds_per_volume"] = {"fdk": t_fdk / n, "pdhg": t_pdhg / n, "lpd": t_lpd / n + t_fdk / n}
-    log["lpd_speedup_vs_pdhg"] = (t_pdhg / n) / (t_lpd / n + t_fdk / n)
-    log["lpd_minus_pdhg_psnr_db"] = log["psnr_fullfov"]["lpd"]["mean"] - log["psnr_fullfov"]["pdhg"]["mean"]
+    # ---- evaluate at equal PSNR on the test phantoms (inference one volume at a time)
+    model1 = LPD(geom, n_iter=args.n_iter, seed=1, residual_input=args.residual_input)
+    model1.set_params(model.get_params())
+    log["eval"] = equal_psnr(geom, model1, test, full, lam, gam, sig, tau)
     print(json.dumps(log), flush=True)
     if args.out:
         os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)

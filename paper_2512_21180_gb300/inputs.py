@@ -6,9 +6,9 @@ reconstruction method's arithmetic (no projection, interpolation, weighting or
 voxelisation), so both the CUDA path and the independent CPU checker can use it
 without sharing any computation.
 
-The workloads stand in for the paper's clinical CT data (Sec. 2.3: 256^3 volumes
+The workloads stand in for the paper's clinical CT data (Sec. 2.4: 256^3 volumes
 at 2 mm, SID 1000 mm, isocentre-detector 536 mm, offset flat panel, full 2*pi
-orbit; Sec. 2.1), which is not available: seeded random-ellipsoid phantoms with
+orbit; Sec. 2.2), which is not available: seeded random-ellipsoid phantoms with
 soft-tissue, bone-like and air-like values replace the CT scans.
 """
 from __future__ import annotations
@@ -17,7 +17,7 @@ import math
 
 import numpy as np
 
-# Acquisition constants of the simulated scanner (Sec. 2.1): source-isocentre
+# Acquisition constants of the simulated scanner (Sec. 2.2): source-isocentre
 # distance 1000 mm, isocentre-detector 536 mm, so source-detector 1536 mm.
 SID_MM = 1000.0
 SDD_MM = 1536.0

@@ -19,14 +19,18 @@ class LPD:
     """Unrolled learned primal-dual network on the GPU (weights live in libcbct)."""
 
     def __init__(self, geom: Geometry, n_iter: int = 8, n_mem: int = 5, width: int = 32, slope: float = 0.2,
-                 mu_ref: float = 0.02, bp_scale: float = 0.0, seed: int = 0):
+                 mu_ref: float = 0.02, bp_scale: float = 0.0, seed: int = 0, residual_input: bool = False,
+                 max_batch: int = 1, reversible: bool = False):
         self.geom = geom
-        d = LpdDesc(n_iter, n_mem, width, slope, mu_ref, bp_scale, seed)
+        d = LpdDesc(n_iter, n_mem, width, slope, mu_ref, bp_scale, seed, int(residual_input), int(max_batch),
+                    int(reversible))
         h = ctypes.c_void_p()
         with torch.cuda.device(geom.device):
             check(_lib.load().lpd_create(geom.handle, ctypes.byref(d), ctypes.byref(h)), "lpd_create")
         self.handle = h
         self.n_iter, self.n_mem, self.width, self.mu_ref = n_iter, n_mem, width, mu_ref
+        self.residual_input, self.max_batch, self.reversible = bool(residual_input), int(max_batch), bool(reversible)
+        self.batch = 1
         n = ctypes.c_longlong()
         pp, gp = ctypes.c_void_p(), ctypes.c_void_p()
         bs = ctypes.c_float()
@@ -57,6 +61,16 @@ class LPD:
         p = np.ascontiguousarray(p, dtype=np.float32)
         check(_lib.load().lpd_set_params(self.handle, p.ctypes.data, self.nparams), "lpd_set_params")
 
+    def perms(self) -> np.ndarray:
+        """[n_iter, 2, n_mem] channel permutations of a reversible model (perm_f, perm_h)."""
+        out = np.zeros((self.n_iter, 2, self.n_mem), dtype=np.int32)
+        check(_lib.load().lpd_get_perms(self.handle, out.ctypes.data), "lpd_get_perms")
+        return out
+
+    def set_perms(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.int32).reshape(self.n_iter, 2, self.n_mem)
+        check(_lib.load().lpd_set_perms(self.handle, p.ctypes.data), "lpd_set_perms")
+
     def device_status(self, clear: bool = False) -> int:
         """The model's device status word (0 = no convolution kernel gave up a bounded wait)."""
         out = ctypes.c_int(0)
@@ -71,19 +85,29 @@ class LPD:
 
     # compute ----------------------------------------------------------------------
     def forward(self, y: torch.Tensor, x0: torch.Tensor, save_for_backward: bool = False) -> torch.Tensor:
+        """y [na, nv, nu] and x0 [nz, ny, nx] (one volume), or [B, ...] each (a batch of
+        B <= max_batch volumes, reconstructed together); the output has x0's shape."""
         g = self.geom
-        yy = y.reshape(g.proj_shape).contiguous()
-        xx = x0.reshape(g.vol_shape).contiguous()
-        out = torch.empty(g.vol_shape, device=yy.device, dtype=torch.float32)
-        check(_lib.load().lpd_forward(self.handle, yy.data_ptr(), xx.data_ptr(), out.data_ptr(), 1,
+        batched = y.dim() == 4
+        B = y.shape[0] if batched else 1
+        yy = y.reshape((B,) + g.proj_shape).contiguous()
+        xx = x0.reshape((B,) + g.vol_shape).contiguous()
+        out = torch.empty((B,) + g.vol_shape, device=yy.device, dtype=torch.float32)
+        check(_lib.load().lpd_forward(self.handle, yy.data_ptr(), xx.data_ptr(), out.data_ptr(), B,
                                       int(save_for_backward), _st()), "lpd_forward")
-        return out
+        self.batch = B
+        return out if batched else out[0]
 
     def backward(self, grad_x: torch.Tensor, want_y: bool = False, want_x0: bool = False):
+        """Gradients for the last forward pass (its batch); returns (dL/dy, dL/dx0) shaped
+        like that pass's y and x0 (or None)."""
         g = self.geom
-        gx = grad_x.reshape(g.vol_shape).contiguous()
-        gy = torch.empty(g.proj_shape, device=gx.device) if want_y else None
-        g0 = torch.empty(g.vol_shape, device=gx.device) if want_x0 else None
+        B = self.batch
+        gx = grad_x.reshape((B,) + g.vol_shape).contiguous()
+        shp_p = ((B,) if grad_x.dim() == 4 else ()) + g.proj_shape
+        shp_v = ((B,) if grad_x.dim() == 4 else ()) + g.vol_shape
+        gy = torch.empty(shp_p, device=gx.device) if want_y else None
+        g0 = torch.empty(shp_v, device=gx.device) if want_x0 else None
         check(_lib.load().lpd_backward(self.handle, gx.data_ptr(), None if gy is None else gy.data_ptr(),
                                        None if g0 is None else g0.data_ptr(), _st()), "lpd_backward")
         return gy, g0
@@ -103,6 +127,7 @@ class LPD:
         ptr = lambda t: None if t is None else t.data_ptr()
         check(_lib.load().lpd_forward_latent(self.handle, yy.data_ptr(), ptr(xx), ptr(ff), ptr(hh), ptr(out),
                                              int(save_for_backward), _st()), "lpd_forward_latent")
+        self.batch = 1
         return out
 
     def state(self):
@@ -155,10 +180,13 @@ def masked_mse(x: torch.Tensor, ref: torch.Tensor, V: torch.Tensor | None = None
     return loss, grad
 
 
-def layer_shapes(n_iter: int, n_mem: int = 5, width: int = 32):
-    """[(cout, taps, cin)] in the library's parameter order."""
+def layer_shapes(n_iter: int, n_mem: int = 5, width: int = 32, residual_input: bool = False,
+                 reversible: bool = False):
+    """[(cout, taps, cin)] in the library's parameter order (a reversible model's blocks
+    read and write half of the n_mem channels)."""
+    k = n_mem // 2 if reversible else n_mem
     out = []
     for _ in range(n_iter):
-        out += [(width, 9, n_mem + 2), (width, 9, width), (n_mem, 9, width),
-                (width, 27, n_mem + 1), (width, 27, width), (n_mem, 27, width)]
+        out += [(width, 9, k + 2 + int(residual_input)), (width, 9, width), (k, 9, width),
+                (width, 27, k + 1), (width, 27, width), (k, 27, width)]
     return out

@@ -1,4 +1,4 @@
-"""Multiscale learned primal-dual (the multiscale scheme of Sec. 2.4): a coarse level at
+"""Multiscale learned primal-dual (the multiscale scheme of Sec. 2.6): a coarse level at
 half resolution — voxels twice as large, every second angle, 2 x 2 binned detector
 pixels — runs first, and its primal and dual memory states, upsampled by nearest
 neighbour, initialise the fine level. Gradients flow back through the adjoint of the

@@ -88,7 +88,7 @@ def test_two_level_lpd_matches_reference(O, M):
     split = lambda p: ([p[6 * n:6 * n + 3] for n in range(n_iter)], [p[6 * n + 3:6 * n + 6] for n in range(n_iter)])
     x, xc = S.lpd_multiscale(Gc, Gf, torch.tensor(y), torch.tensor(x0), torch.tensor(O.redundancy(Gc)),
                              torch.tensor(O.redundancy(Gf)), split(pc), split(pf), n_mem=5, mu_ref=mu,
-                             bp_c=bps, bp_f=bps)
+                             bp_c=bps, bp_f=bps, round_grads=True)
     assert rel_l2(to_np(xcg), xc.detach().numpy()) <= 1e-2
     assert rel_l2(to_np(xg), x.detach().numpy()) <= 1e-2
     assert rel_l2(x.detach().numpy(), S.up(xc.detach().numpy())) > 1e-3   # the fine level acted
@@ -96,5 +96,8 @@ def test_two_level_lpd_matches_reference(O, M):
     ((x * torch.tensor(r)).sum() + (xc * torch.tensor(rc)).sum()).backward()
     model.zero_grad()
     model.backward(to_gpu(r), to_gpu(rc))
-    assert rel_l2(model.fine.grads().astype(np.float64), flat_grads(pf)) <= 5e-2
-    assert rel_l2(model.coarse.grads().astype(np.float64), flat_grads(pc)) <= 5e-2
+    e_f = rel_l2(model.fine.grads().astype(np.float64), flat_grads(pf))
+    e_c = rel_l2(model.coarse.grads().astype(np.float64), flat_grads(pc))
+    print(f"two-level gradient parity: fine {e_f:.2e}, coarse {e_c:.2e}")
+    assert e_f <= 1e-2, e_f
+    assert e_c <= 1e-2, e_c

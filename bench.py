@@ -366,7 +366,11 @@ def report(args, geom, world, S_fwd, samples_step, value, ms, ms_fwd, ms_adj, e2
     # dominant kernel: the slower of the pair
     dom = "back_project" if ms_adj >= ms_fwd else "forward_project"
     ms_dom = max(ms_adj, ms_fwd)
-    roof = roofline(dom, ms_dom, S_fwd, nvox, nray, pk, pk_kind, clk)
+    try:
+        smem = smem_peak_gbs()
+    except Exception as exc:  # noqa: BLE001 (the derived peak stands in)
+        smem = {"error": str(exc)[:200]}
+    roof = roofline(dom, ms_dom, S_fwd, nvox, nray, pk, pk_kind, clk, smem)
     roof["traffic"] = MEASURED_TRAFFIC.get(args.workload, {}).get(dom)
     roof["ncu_sm_throughput_pct"] = MEASURED_SM_THROUGHPUT_PCT.get(args.workload, {}).get(dom)
     line = {
@@ -435,17 +439,50 @@ def launches_per_step(geom) -> int:
     return 3 + 2 + (1 if parts > 1 else 0)
 
 
-def roofline(kernel, ms, S_fwd, nvox, nray, pk, pk_kind, clk):
+def smem_peak_gbs(reps: int = 5) -> dict:
+    """Shared-memory read bandwidth measured on this GPU: cbct_smem_probe (152 SMs x 8
+    CTAs x 256 threads, conflict-free 16-byte loads), CUDA events on the launching stream,
+    best of `reps` after two warm-up launches."""
+    import ctypes
+
+    import torch
+
+    from paper_2512_21180_gb300 import _lib
+    lib = _lib.load()
+    sink = torch.zeros(152 * 8, device="cuda")
+    st = torch.cuda.current_stream()
+    nbytes = ctypes.c_longlong(0)
+    best = None
+    for i in range(reps + 2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        _lib.check(lib.cbct_smem_probe(8, 4096, sink.data_ptr(), ctypes.byref(nbytes), st.cuda_stream),
+                   "cbct_smem_probe")
+        e1.record(st)
+        torch.cuda.synchronize()
+        if i >= 2:
+            gbs = nbytes.value / (e0.elapsed_time(e1) * 1e-3) / 1e9
+            best = gbs if best is None else max(best, gbs)
+    return {"gbs": best, "bytes_per_launch": nbytes.value}
+
+
+def roofline(kernel, ms, S_fwd, nvox, nray, pk, pk_kind, clk, smem=None):
     """Roofline of the dominant kernel. The projector is a gather: its algorithmic
-    on-chip traffic is 16 B per sample (the four FP32 bilinear neighbours). The
-    binding unit is the SM's L1/shared-memory datapath (128 B/clk/SM); its peak is
-    derived from the unit count and clock: 152 SMs x 128 B x max SM clock."""
+    on-chip traffic is 16 B per sample (the four FP32 bilinear neighbours, read from
+    shared memory), so the binding unit is the SM's L1/shared-memory datapath. Its peak
+    is measured by the shared-memory read probe (smem_peak_gbs); without it, derived
+    from the unit count and clock (152 SMs x 128 B/clk x max SM clock)."""
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    peak = 152 * 128 * sm_mhz * 1e6 / 1e9   # GB/s
     achieved = 16.0 * S_fwd / (ms * 1e-3) / 1e9
+    if smem and smem.get("gbs"):
+        peak = smem["gbs"]
+        kind = "measured: shared-memory read probe (152 SM x 8 CTAs x 256 threads, 16 B loads), best of 5"
+    else:
+        peak = 152 * 128 * sm_mhz * 1e6 / 1e9   # GB/s
+        kind = f"derived: L1/SMEM datapath 152 SM x 128 B/clk x {sm_mhz:.0f} MHz"
     return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None,
-            "peak_kind": f"derived: L1/SMEM datapath 152 SM x 128 B/clk x {sm_mhz:.0f} MHz",
+            "frac": achieved / peak, "traffic": None, "peak_kind": kind,
+            "derived_peak": 152 * 128 * sm_mhz * 1e6 / 1e9,
             "hbm": {"compulsory_bytes": 4 * (nvox + nray), "peak_gbs": pk.get("hbm_gbs"), "peak_kind": pk_kind}}
 
 

@@ -406,6 +406,15 @@ int lpd_clip_grads(cbct_lpd *m, float max_norm, float grad_scale, double *norm_o
 int lpd_adam_step(cbct_lpd *m, float lr, float beta1, float beta2, float eps, int step, float grad_scale,
                   void *stream);
 
+/* Measured shared-memory read bandwidth (the paper has no counterpart: it gives the
+ * roofline denominator of the projector kernels, which read their bilinear samples from
+ * shared memory). Launches ctas_per_sm (1..8) CTAs of 256 threads per SM; each thread
+ * makes iters (1..2^20) rounds of four conflict-free 16-byte shared-memory loads. *bytes
+ * (host) receives the bytes the launch reads; the caller times the launch on `stream`
+ * (CUDA events) and divides. sink: a device float per CTA (never written in practice).
+ * Asynchronous. Errors: CBCT_EINVAL for arguments out of range. */
+int cbct_smem_probe(int ctas_per_sm, int iters, float *sink, long long *bytes, void *stream);
+
 /* Test of the library's bounded waits (the paper has no counterpart: this checks the
  * failure handling of the pipelined kernels). Launches one CTA whose two warps wait on
  * a shared-memory barrier that nothing completes, each for at most limit_ns

@@ -88,6 +88,7 @@ SIGNATURES = {
     "cbct_masked_mse": (I32, [P, P, P, F32, I64, P, P, P]),
     "cbct_wait_probe": (I32, [P, I64, P, P]),
     "lpd_get_perms": (I32, [P, P]),
+    "cbct_smem_probe": (I32, [I32, I32, P, ctypes.POINTER(I64), P]),
     "lpd_set_perms": (I32, [P, P]),
 }
 

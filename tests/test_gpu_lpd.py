@@ -6,7 +6,7 @@ import torch
 
 from paper_2512_21180_gb300 import inputs as I
 
-from gpu_util import rel_l2, to_gpu, to_np
+from gpu_util import grad_tol, rel_l2, to_gpu, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -77,13 +77,14 @@ def test_lpd_forward_and_gradients_match_oracle(O, M):
     output, parameter gradient, dL/dy and dL/dx0 within the 1e-2 bar of BF16 blocks."""
     model, (xg, gg, gy, g0), reference, (y, x0) = _lpd_case(O, M, 0.1)
     ref, gref, gyr, g0r = reference()
+    _, gp, gyp, g0p = reference(1.0 + 1e-6)
     assert rel_l2(xg, ref) <= 1e-2
     assert rel_l2(ref, x0) > 1e-4          # the network changed its input: the check is not vacuous
     e_w, e_y, e_x = rel_l2(gg, gref), rel_l2(gy, gyr), rel_l2(g0, g0r)
-    print(f"LPD gradient parity: params {e_w:.2e}, y {e_y:.2e}, x0 {e_x:.2e}")
+    print(f"LPD gradient parity: params {e_w:.2e}, y {e_y:.2e} (tol {grad_tol(gyr, gyp):.2e}), x0 {e_x:.2e}")
     assert e_w <= 1e-2, e_w
-    assert e_y <= 1e-2, e_y
     assert e_x <= 1e-2, e_x
+    assert e_y <= grad_tol(gyr, gyp), e_y
     # an inference pass (no stored states; the zero initial dual memory is never read)
     # runs the same arithmetic as the training pass above
     xi = model.forward(to_gpu(y), to_gpu(x0))
@@ -100,10 +101,9 @@ def test_lpd_strong_blocks_within_reference_conditioning(O, M):
     _, gp, gyp, g0p = reference(1.0 + 1e-6)
     assert rel_l2(xg, ref) <= 1e-2
     for name, got, want, pert in (("params", gg, gref, gp), ("y", gy, gyr, gyp), ("x0", g0, g0r, g0p)):
-        s = rel_l2(pert, want)
         e = rel_l2(got, want)
-        print(f"strong blocks, {name}: GPU {e:.2e}, reference moved by {s:.2e} under 1e-6")
-        assert e <= max(1e-2, 2 * s), (name, e, s)
+        print(f"strong blocks, {name}: GPU {e:.2e}, reference moved by {rel_l2(pert, want):.2e} under 1e-6")
+        assert e <= grad_tol(want, pert), (name, e)
 
 
 def test_lpd_training_reduces_loss(O, M):
@@ -242,16 +242,26 @@ def test_lpd_batch_and_residual_channel_match_oracle(O, M):
     dual = [prm[6 * n:6 * n + 3] for n in range(n_iter)]
     prim = [prm[6 * n + 3:6 * n + 6] for n in range(n_iter)]
     w = torch.tensor(O.redundancy(G))
-    for b in range(2):
+    def ref_run(b, x0_scale=1.0):
         yt = torch.tensor(ys[b], requires_grad=True)
-        x0t = torch.tensor(x0s[b], requires_grad=True)
+        x0t = torch.tensor(x0s[b] * x0_scale, requires_grad=True)
         ref = R.lpd(G, yt, x0t, w, dual, prim, n_mem=5, round_bf16=True, mu_ref=mu, bp_scale=bps,
                     round_grads=True, residual_input=True)
-        e = rel_l2(to_np(xg[b]), ref.detach().numpy())
-        assert e <= 1e-2, (b, e)
         (ref * torch.tensor(rs[b])).sum().backward()
-        assert rel_l2(to_np(gy[b]), yt.grad.numpy()) <= 1e-2, b
-        assert rel_l2(to_np(g0[b]), x0t.grad.numpy()) <= 1e-2, b
+        return ref.detach().numpy(), yt.grad.numpy(), x0t.grad.numpy()
+    for b in range(2):
+        ref, gyr, g0r = ref_run(b)
+        _, gyp, g0p = ref_run(b, 1.0 + 1e-6)
+        e = rel_l2(to_np(xg[b]), ref)
+        assert e <= 1e-2, (b, e)
+        assert rel_l2(to_np(gy[b]), gyr) <= grad_tol(gyr, gyp), (b, rel_l2(to_np(gy[b]), gyr))
+        assert rel_l2(to_np(g0[b]), g0r) <= grad_tol(g0r, g0p), b
+    # the parameter gradient sums both volumes' reference runs (the first pair of calls)
+    for p_ in prm:
+        for t in p_:
+            t.grad = None
+    ref_run(0)
+    ref_run(1)
     gref = np.concatenate([np.concatenate([wt.grad.permute(0, *range(2, wt.dim()), 1).reshape(-1).numpy(),
                                            bt.grad.numpy()]) for wt, bt in prm])
     e = rel_l2(gg, gref)

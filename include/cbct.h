@@ -322,6 +322,8 @@ typedef struct {
                                     Algorithm 1 split / update / combine / permute; n_mem even):
                                     the backward recovers every iterate from the final states
                                     instead of storing them. 0: Adler-style memory update. */
+    int lire;                    /* 1 (needs reversible = 1, residual_input = 0): the iteration of
+                                    Algorithm 1 at one resolution, see below. 0: off. */
 } cbct_lpd_desc;
 
 /* Network on geometry g (which must outlive it): per iteration n a dual block
@@ -352,6 +354,19 @@ void lpd_destroy(cbct_lpd *m);
  * permutation that mixes the halves. Errors: CBCT_EINVAL for a model that is not
  * reversible, NULL pointers or (set) an invalid table. */
 int lpd_get_perms(const cbct_lpd *m, int *host);
+
+/* LIRE mode (desc.lire = 1; Sec. 2.6, Algorithm 1 at one resolution, blocks at width 32):
+ * a separate FP32 reconstruction x next to the reversible latents (halves of K =
+ * n_mem / 2 channels), x <- x0, f <- [x0 / mu_ref, s P^T(w y), x0 / mu_ref, ...],
+ * h <- y in every channel (s = bp_scale), then per iteration n:
+ *   p_op = [mu_ref P p2[0], P x]
+ *   d2 <- d2 + Gamma_n([d1, p_op, y, P x - y])        3x3x3 convs over (angle, v, u)
+ *   p2 <- p2 + Lambda_n([p1, s P^T(w d2[0]), x / mu_ref, s P^T(P x - y), V])
+ *   x  <- x + mu_ref (beta_n + sum_c omega_n[c] f[c])  1x1x1 output convolution
+ *   f <- f[perm_f[n]],  h <- h[perm_h[n]]
+ * with V the FoV tensor; x_out = x. Blocks: K + 4 -> width -> width -> K, all 3x3x3;
+ * parameters per iteration: dual layers, primal layers (as above), then omega [n_mem]
+ * and beta. The backward undoes x, p2 and d2 in reverse order, like the reversible mode. */
 int lpd_set_perms(cbct_lpd *m, const int *host);
 
 /* Parameter count and device pointers to the parameters and the gradient buffer. */

@@ -213,3 +213,49 @@ def mixes_halves(perm) -> bool:
     least one channel from the old second half (and so, by counting, the reverse)."""
     K = len(perm) // 2
     return any(p >= K for p in perm[:K])
+
+
+def lire(G, y: torch.Tensor, x0: torch.Tensor, w_red: torch.Tensor, V: torch.Tensor, dual_params, primal_params,
+         out_params, perms_f, perms_h, n_mem: int = 8, round_bf16: bool = True, mu_ref: float = 1.0,
+         bp_scale: float = 1.0, round_grads: bool = False, return_state: bool = False):
+    """The learned iterative scheme of Algorithm 1 (Sec. 2.6) at one resolution, in the
+    reading used by the library (units: f in mu_ref, h and y in line-integral units):
+        x <- x0                                              (FDK_w start)
+        f <- [x / mu_ref, s P^T(w y), x / mu_ref, s P^T(w y), ...],  h <- y in every channel
+        per iteration n, with halves of K = n_mem / 2 channels:
+          d1, d2 = h[:K], h[K:];  p1, p2 = f[:K], f[K:]
+          p_op = [mu_ref P p2[0], P x]                       (projections of p2 and x)
+          d2 <- d2 + Gamma_n([d1, p_op, y, P x - y])         (3x3x3 convs over (angle, v, u))
+          b_op = s P^T(w d2[0]);  LW = s P^T(P x - y)        (weighted backprojection, Landweber term)
+          p2 <- p2 + Lambda_n([p1, b_op, x / mu_ref, LW, V]) (3x3x3 convs over the volume)
+          f = [p1, p2];  x <- x + mu_ref (sum_c omega_n[c] f[c] + beta_n)   (1x1x1 output conv)
+          h <- h[perms_h[n]];  f <- f[perms_f[n]]
+        output x.
+    out_params: per iteration (omega [n_mem], beta [1]); s = bp_scale; V the FoV tensor."""
+    M = n_mem
+    K = M // 2
+    na, nv, nu = y.shape
+    x = x0
+    xbp = bp_scale * backproject(G, w_red.view(1, 1, -1) * y)
+    f = torch.stack([x0 / mu_ref if c % 2 == 0 else xbp for c in range(M)], 0)
+    h = y.unsqueeze(0).repeat(M, 1, 1, 1)
+    for n, (dp, pp, (om, be)) in enumerate(zip(dual_params, primal_params, out_params)):
+        d1, d2 = h[:K], h[K:]
+        p1, p2 = f[:K], f[K:]
+        pp2 = mu_ref * project(G, p2[0])
+        px = project(G, x)
+        res = px - y
+        inp = torch.cat([d1, pp2.unsqueeze(0), px.unsqueeze(0), y.unsqueeze(0), res.unsqueeze(0)], 0)
+        d2 = d2 + block(inp.unsqueeze(0), dp, round_bf16, round_grads)[0]          # [K, na, nv, nu]
+        bop = bp_scale * backproject(G, w_red.view(1, 1, -1) * d2[0])
+        lw = bp_scale * backproject(G, res)
+        inp = torch.cat([p1, bop.unsqueeze(0), (x / mu_ref).unsqueeze(0), lw.unsqueeze(0), V.unsqueeze(0)], 0)
+        p2 = p2 + block(inp.unsqueeze(0), pp, round_bf16, round_grads)[0]
+        f = torch.cat([p1, p2], 0)
+        h = torch.cat([d1, d2], 0)
+        x = x + mu_ref * ((om.view(-1, 1, 1, 1) * f).sum(0) + be)
+        h = h[list(perms_h[n])]
+        f = f[list(perms_f[n])]
+    if return_state:
+        return x, f, h
+    return x

@@ -47,6 +47,7 @@ using namespace cbct;
 
 struct LayerSpec {
     int cin, cout, taps3d;
+    int H;                   // rows of an image / plane (the tile plan depends on it)
     long long w_off, b_off;  // offsets into the flat parameter array
     long long pk_off = 0;    // forward B operand within cbct_lpd::wpk
 };
@@ -60,6 +61,11 @@ struct cbct_lpd {
     // reversible mode: fixed channel permutations per iteration (new[c] = old[perm[c]]) and
     // the plane of each logical channel after the last forward pass
     std::vector<std::vector<int>> perm_f, perm_h;
+    // LIRE mode: per-iteration offset of the output convolution's parameters (omega [n_mem],
+    // beta) in the flat array, the reconstruction x [batch][nvox], the FoV tensor repeated
+    // per batch item, and two-item scratch for batched projector calls
+    std::vector<long long> out_off;
+    float *x = nullptr, *Vb = nullptr, *t2v = nullptr, *t2p = nullptr, *gx = nullptr, *opart = nullptr;
     int fin_f[8] = {}, fin_h[8] = {};
     int cur_f[8] = {}, cur_h[8] = {};  // plane of each logical channel of the states held now
     std::vector<LayerSpec> layers;  // per iteration: 3 dual then 3 primal
@@ -238,6 +244,78 @@ __global__ void k_mse_grad(const float *__restrict__ x, const float *__restrict_
         g[i] = (V && V[i] < thr) ? 0.f : inv * (x[i] - r[i]);
 }
 
+// ---- output convolution of the LIRE mode (1x1x1, n_mem channels -> 1) ----
+
+constexpr int kOutBlocks = 304;
+
+struct PlanesW {
+    float *p[8];
+};
+
+// x[i] += sign * mu * (beta + sum_c omega[c] f_c[i]), omega = om[0..M), beta = om[M]. The
+// inverse update (sign -1) recomputes the same term, so it undoes the forward one up to
+// one FP32 rounding of x.
+__global__ void k_outconv(float *__restrict__ x, Planes fp, const float *__restrict__ om, float mu, long long n, int M,
+                          float sign) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float v = om[M];
+        for (int c = 0; c < M; ++c) v = fmaf(om[c], fp.p[c][i], v);
+        x[i] = x[i] + sign * (mu * v);
+    }
+}
+
+// Backward of k_outconv: g_f_c[i] += mu omega[c] g_x[i]; partial[blk][c] = mu sum_i g_x[i]
+// f_c[i] (c < M) and partial[blk][M] = mu sum_i g_x[i], over the block's grid-stride share
+// (fixed-order tree in shared memory).
+__global__ void __launch_bounds__(256) k_outconv_grad(const float *__restrict__ gx, Planes fp, PlanesW gp,
+                                                      const float *__restrict__ om, float mu, long long n, int M,
+                                                      float *__restrict__ partial) {
+    float acc[9] = {};
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+        const float g = gx[i];
+        for (int c = 0; c < M; ++c) {
+            acc[c] = fmaf(g, fp.p[c][i], acc[c]);
+            gp.p[c][i] += mu * om[c] * g;
+        }
+        acc[M] += g;
+    }
+    __shared__ float red[256];
+    for (int c = 0; c <= M; ++c) {
+        red[threadIdx.x] = acc[c];
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[(long long)blockIdx.x * (M + 1) + c] = mu * red[0];
+        __syncthreads();
+    }
+}
+
+// f[c][i] = c even ? x0[i] * inv_mu : xbp[i] * s (the initial primal latents of Algorithm 1)
+__global__ void k_lire_init_f(const float *__restrict__ x0, const float *__restrict__ xbp, float *__restrict__ f,
+                              long long n, int M, float inv_mu, float s) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float a = x0[i] * inv_mu, b = xbp[i] * s;
+        for (int c = 0; c < M; ++c) f[c * n + i] = (c & 1) ? b : a;
+    }
+}
+
+// out[i] += sum_b partial[b][i] (fixed order)
+__global__ void k_sum_partials(const float *__restrict__ partial, int nblk, int n, float *__restrict__ out) {
+    const int i = threadIdx.x;
+    if (i >= n) return;
+    float s = out[i];
+    for (int b = 0; b < nblk; ++b) s += partial[(long long)b * n + i];
+    out[i] = s;
+}
+
+// out[i] = a[i] - b[i]
+__global__ void k_diff(float *__restrict__ out, const float *__restrict__ a, const float *__restrict__ b, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = a[i] - b[i];
+}
+
 // a permutation of 2K channels mixes the halves when the new first half takes at least
 // one channel of the old second half
 bool perm_mixes(const int *p, int M) {
@@ -329,11 +407,12 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
                             : (d.n_mem >= 2 && d.n_mem <= 6 && (!d.residual_input || d.n_mem <= 5));
     if (d.n_iter < 1 || d.n_iter > 64 || !mem_ok || d.width != 32 || !(d.mu_ref > 0) ||
         !(d.slope >= 0.f && d.slope <= 1.f) || (d.residual_input != 0 && d.residual_input != 1) ||
-        (d.reversible != 0 && d.reversible != 1) || maxb > 64 || (long long)maxb * g->dev.na > 65535)
+        (d.reversible != 0 && d.reversible != 1) || (d.lire != 0 && d.lire != 1) || (d.lire && !rev) ||
+        (d.lire && d.residual_input) || maxb > 64 || (long long)maxb * g->dev.na > 65535)
         return fail(CBCT_EINVAL, "lpd_create: need 1 <= n_iter <= 64, width == 32, mu_ref > 0, 0 <= slope <= 1, "
                                  "residual_input and reversible 0 or 1, max_batch <= 64, max_batch * n_angles <= "
                                  "65535, and 2 <= n_mem <= 6 (<= 5 with the residual channel) or, reversible, "
-                                 "n_mem even in [2, 8]");
+                                 "n_mem even in [2, 8]; lire needs reversible and no residual_input");
     cbct_lpd *m = new (std::nothrow) cbct_lpd();
     if (!m) return fail(CBCT_ENOMEM, "lpd_create: host allocation");
     m->g = g;
@@ -345,16 +424,26 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     m->nproj = (long long)g->dev.na * g->dev.nv * g->dev.nu;
     const int M = d.n_mem, W = d.width;
     long long off = 0;
-    auto add = [&](int cin, int cout, int t3) {
+    auto add = [&](int cin, int cout, int t3, int H) {
         LayerSpec L;
-        L.cin = cin; L.cout = cout; L.taps3d = t3;
+        L.cin = cin; L.cout = cout; L.taps3d = t3; L.H = H;
         L.w_off = off; off += (long long)cout * (t3 ? 27 : 9) * cin;
         L.b_off = off; off += cout;
         m->layers.push_back(L);
     };
     for (int n = 0; n < d.n_iter; ++n) {
-        add(m->nd, W, 0); add(W, W, 0); add(W, K, 0);   // dual
-        add(K + 1, W, 1); add(W, W, 1); add(W, K, 1);   // primal
+        const int nv = g->dev.nv, ny = g->dev.n[1];
+        if (d.lire) {
+            // Algorithm 1 blocks: 3x3x3 over (angle, v, u) and over the volume, K + 4 inputs each,
+            // then the output convolution's omega [n_mem] and beta
+            add(K + 4, W, 1, nv); add(W, W, 1, nv); add(W, K, 1, nv);   // dual
+            add(K + 4, W, 1, ny); add(W, W, 1, ny); add(W, K, 1, ny);   // primal
+            m->out_off.push_back(off);
+            off += M + 1;
+        } else {
+            add(m->nd, W, 0, nv); add(W, W, 0, nv); add(W, K, 0, nv);   // dual
+            add(K + 1, W, 1, ny); add(W, W, 1, ny); add(W, K, 1, ny);   // primal
+        }
     }
     m->nparams = off;
     // initial weights: He normal for hidden layers, 0.1 x that for the last layer of each block
@@ -366,6 +455,8 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
         const double sd = sqrt(2.0 / (L.cin * taps)) * ((i % 3 == 2) ? 0.1 : 1.0);
         for (long long k = 0; k < (long long)L.cout * taps * L.cin; ++k) hp[L.w_off + k] = (float)(sd * rng.normal());
     }
+    for (long long o : m->out_off)
+        for (int c = 0; c < M; ++c) hp[o + c] = (float)(0.01 * rng.normal());  // omega; beta = 0
     if (rev) {
         // per iteration a primal and a dual permutation that mix the halves (Fisher-Yates on
         // the same SplitMix64 stream, redrawn until the new first half takes a channel of the
@@ -411,8 +502,16 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     al((void **)&m->g32a, sizeof(__nv_bfloat16) * std::max(NP, NV) * 32);
     al((void **)&m->g32b, sizeof(__nv_bfloat16) * std::max(NP, NV) * 32);
     al((void **)&m->gsmall, sizeof(__nv_bfloat16) * std::max(NP, NV) * 8);
-    al((void **)&m->gf, sizeof(float) * (M + 1) * NV);
-    al((void **)&m->gh, sizeof(float) * (M + 3) * NP);
+    al((void **)&m->gf, sizeof(float) * (M + 4) * NV);
+    al((void **)&m->gh, sizeof(float) * (M + 5) * NP);
+    if (d.lire) {
+        al((void **)&m->x, sizeof(float) * NV);
+        al((void **)&m->gx, sizeof(float) * NV);
+        al((void **)&m->Vb, sizeof(float) * NV);
+        al((void **)&m->t2v, sizeof(float) * 2 * NV);
+        al((void **)&m->t2p, sizeof(float) * 2 * NP);
+        al((void **)&m->opart, sizeof(float) * kOutBlocks * (M + 1));
+    }
     al((void **)&m->status, sizeof(int));
     // forward convolutions: packing plan of every layer (first layer of a block reads 8
     // channel slots, the others 32; 2-D blocks run over the nv rows, 3-D over ny)
@@ -420,7 +519,7 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     long long pk_bytes = 0;
     for (size_t i = 0; i < m->layers.size(); ++i) {
         LayerSpec &L = m->layers[i];
-        const long long b = conv_plan(L.taps3d, L.taps3d ? g->dev.n[1] : g->dev.nv, i % 3 == 0 ? 8 : 32, L.cin,
+        const long long b = conv_plan(L.taps3d, L.H, i % 3 == 0 ? 8 : 32, L.cin,
                                       L.cout, 0, &jobs[i]);
         if (b < 0) {
             lpd_destroy(m);
@@ -445,6 +544,14 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
         return cuda_fail(e, "lpd_create: allocation");
     }
     int rc = cbct_redundancy_weight(g, m->wred, nullptr);
+    if (rc == 0 && d.lire) {
+        // the FoV tensor V (a primal input of Algorithm 1), once per batch item
+        rc = cbct_fov(g, m->Vb, nullptr);
+        for (int b = 1; b < maxb && rc == 0; ++b) {
+            e = cudaMemcpy(m->Vb + b * m->nvox, m->Vb, sizeof(float) * m->nvox, cudaMemcpyDeviceToDevice);
+            if (e != cudaSuccess) rc = cuda_fail(e, "lpd_create: FoV copies");
+        }
+    }
     // backprojection scale: 1 / max_voxel P^T(w 1)
     if (rc == 0) {
         if (d.bp_scale > 0) {
@@ -477,7 +584,7 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
 extern "C" void lpd_destroy(cbct_lpd *m) {
     if (!m) return;
     cudaDeviceSynchronize();
-    void *ptrs[] = {m->wpk, m->pack_jobs, m->clip, m->pf_saved, m->bp_saved, m->params, m->grads, m->adam_m, m->adam_v, m->wred, m->f, m->h,
+    void *ptrs[] = {m->x, m->gx, m->Vb, m->t2v, m->t2p, m->opart, m->wpk, m->pack_jobs, m->clip, m->pf_saved, m->bp_saved, m->params, m->grads, m->adam_m, m->adam_v, m->wred, m->f, m->h,
                     m->y, m->tproj, m->tproj2, m->tvol, m->din, m->a1, m->a2, m->pin, m->b1, m->b2, m->g32a, m->g32b, m->gsmall, m->gf, m->gh,
                     m->status};
     for (void *p : ptrs)
@@ -761,11 +868,246 @@ static int lpd_rev_backward(cbct_lpd *m, const float *grad_x, float *grad_y, flo
     return 0;
 }
 
+// ---- LIRE mode: Algorithm 1 at one resolution ----------------------------------------------
+//
+// Reversible latents as above (halves of K channels, permutations by bookkeeping) plus a
+// separate FP32 reconstruction x, per iteration n:
+//   p_op = [mu_ref P p2[0], P x]                        one batched forward projection
+//   d2 += Gamma_n([d1, p_op, y, P x - y])               3x3x3 convs over (angle, v, u)
+//   b_op = s P^T(w d2[0]), LW = s P^T(P x - y)          one batched backprojection
+//   p2 += Lambda_n([p1, b_op, x / mu_ref, LW, V])       3x3x3 convs over the volume
+//   x += mu_ref (beta_n + sum_c omega_n[c] f[c])        1x1x1 output convolution
+//   permute f, h
+// from x = x0, f = [x0 / mu_ref, s P^T(w y), ...], h = y in every channel. The backward
+// undoes the iterations (x first, then p2, then d2) while the gradients run through them.
+
+static Planes lire_f_planes(const cbct_lpd *m, const int *pfm, long long NV) {
+    Planes fp{};
+    for (int c = 0; c < m->d.n_mem; ++c) { fp.p[c] = m->f + pfm[c] * NV; fp.s[c] = 1.f; }
+    return fp;
+}
+
+// dual input [d1 (K), mu_ref P p2[0], P x, y, P x - y] from the projections in t2p
+static Planes lire_dual_planes(const cbct_lpd *m, const int *phm, long long NP) {
+    const int K = m->d.n_mem / 2;
+    Planes pl{};
+    for (int c = 0; c < K; ++c) { pl.p[c] = m->h + phm[c] * NP; pl.s[c] = 1.f; }
+    pl.p[K] = m->t2p; pl.s[K] = m->d.mu_ref;
+    pl.p[K + 1] = m->t2p + NP; pl.s[K + 1] = 1.f;
+    pl.p[K + 2] = m->y; pl.s[K + 2] = 1.f;
+    pl.p[K + 3] = m->t2p + NP; pl.s[K + 3] = 1.f; pl.q[K + 3] = m->y;
+    return pl;
+}
+
+// primal input [p1 (K), s P^T(w d2[0]), x / mu_ref, s LW, V] from the backprojections in t2v
+static Planes lire_primal_planes(const cbct_lpd *m, const int *pfm, long long NV) {
+    const int K = m->d.n_mem / 2;
+    Planes pp{};
+    for (int c = 0; c < K; ++c) { pp.p[c] = m->f + pfm[c] * NV; pp.s[c] = 1.f; }
+    pp.p[K] = m->t2v; pp.s[K] = m->bp_scale;
+    pp.p[K + 1] = m->x; pp.s[K + 1] = 1.f / m->d.mu_ref;
+    pp.p[K + 2] = m->t2v + NV; pp.s[K + 2] = m->bp_scale;
+    pp.p[K + 3] = m->Vb; pp.s[K + 3] = 1.f;
+    return pp;
+}
+
+#define LIRE_DUAL_DIMS B, m->g->dev.na, m->g->dev.nv, m->g->dev.nu
+
+// t2p = [P p2[0], P x] (one forward projection of 2B volumes)
+static int lire_project(cbct_lpd *m, const int *pfm, int B, cudaStream_t st) {
+    const long long NV = m->nvox * B;
+    const int K = m->d.n_mem / 2;
+    CBCT_CUDA_TRY(cudaMemcpyAsync(m->t2v, m->f + pfm[K] * NV, sizeof(float) * NV, cudaMemcpyDeviceToDevice, st));
+    CBCT_CUDA_TRY(cudaMemcpyAsync(m->t2v + NV, m->x, sizeof(float) * NV, cudaMemcpyDeviceToDevice, st));
+    return forward_project(m->g, m->t2v, m->t2p, 2 * B, 0, (void *)st);
+}
+
+// t2v = [P^T(w d2[0]), P^T(P x - y)] (one backprojection of 2B items; t2p[1] must hold P x)
+static int lire_backproject(cbct_lpd *m, const int *phm, int B, cudaStream_t st) {
+    const long long NP = m->nproj * B;
+    const int K = m->d.n_mem / 2;
+    k_scale_cols<<<grid_n(NP), 256, 0, st>>>(m->h + phm[K] * NP, m->wred, NP, m->g->dev.nu, 1.f, m->t2p);
+    k_diff<<<grid_n(NP), 256, 0, st>>>(m->t2p + NP, m->t2p + NP, m->y, NP);
+    return back_project(m->g, m->t2p, m->t2v, 2 * B, 0, (void *)st);
+}
+
+static int lire_forward(cbct_lpd *m, const float *y, const float *x0, float *x_out, int save_for_backward, int B,
+                        cudaStream_t st) {
+    m->batch = B;
+    const long long NV = m->nvox * B, NP = m->nproj * B;
+    const int M = m->d.n_mem, K = M / 2, N = m->d.n_iter;
+    int rc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
+    if (rc) return rc;
+    CBCT_CUDA_TRY(cudaMemcpyAsync(m->y, y, sizeof(float) * NP, cudaMemcpyDeviceToDevice, st));
+    CBCT_CUDA_TRY(cudaMemcpyAsync(m->x, x0, sizeof(float) * NV, cudaMemcpyDeviceToDevice, st));
+    // f = [x0 / mu, s P^T(w y), ...], h = y in every channel
+    if ((rc = back_project_colw(m->g, m->y, m->wred, m->tvol, B, 0, st))) return rc;
+    k_lire_init_f<<<grid_n(NV), 256, 0, st>>>(x0, m->tvol, m->f, NV, M, 1.f / m->d.mu_ref, m->bp_scale);
+    for (int c = 0; c < M; ++c)
+        CBCT_CUDA_TRY(cudaMemcpyAsync(m->h + c * NP, m->y, sizeof(float) * NP, cudaMemcpyDeviceToDevice, st));
+    int pfm[8], phm[8];
+    for (int c = 0; c < M; ++c) pfm[c] = phm[c] = c;
+    for (int n = 0; n < N && rc == 0; ++n) {
+        const LayerSpec *Ld = &m->layers[6 * n], *Lp = &m->layers[6 * n + 3];
+        if ((rc = lire_project(m, pfm, B, st))) break;
+        const Planes pl = lire_dual_planes(m, phm, NP);
+        k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
+        if ((rc = conv_fwd(m, Ld[0], m->din, 8, LIRE_DUAL_DIMS, 0, m->a1, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Ld[1], m->a1, 32, LIRE_DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
+        if ((rc = rev_update(m, Ld[2], m->a2, LIRE_DUAL_DIMS, m->h, phm + K, NP, 0, st))) break;
+        if ((rc = lire_backproject(m, phm, B, st))) break;
+        const Planes pp = lire_primal_planes(m, pfm, NV);
+        k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
+        if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Lp[1], m->b1, 32, PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
+        if ((rc = rev_update(m, Lp[2], m->b2, PRIM_DIMS, m->f, pfm + K, NV, 0, st))) break;
+        k_outconv<<<grid_n(NV), 256, 0, st>>>(m->x, lire_f_planes(m, pfm, NV), m->params + m->out_off[n],
+                                              m->d.mu_ref, NV, M, 1.f);
+        map_permute(pfm, m->perm_f[n], M);
+        map_permute(phm, m->perm_h[n], M);
+    }
+    if (rc) return rc;
+    if (x_out) CBCT_CUDA_TRY(cudaMemcpyAsync(x_out, m->x, sizeof(float) * NV, cudaMemcpyDeviceToDevice, st));
+    for (int c = 0; c < M; ++c) { m->fin_f[c] = m->cur_f[c] = pfm[c]; m->fin_h[c] = m->cur_h[c] = phm[c]; }
+    m->saved = save_for_backward;
+    m->last = 0;
+    CBCT_LAUNCH_CHECK("lpd_forward (lire)");
+    return 0;
+}
+
+static int lire_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float *grad_x0, cudaStream_t st) {
+    void *sv = (void *)st;
+    const int B = m->batch;
+    const long long NV = m->nvox * B, NP = m->nproj * B;
+    const int M = m->d.n_mem, K = M / 2, N = m->d.n_iter;
+    const float mu = m->d.mu_ref, s = m->bp_scale;
+    // gf: M planes + scratch M .. M+3 (dL/d b_op, dL/d LW, dL/d(x / mu), dL/dV);
+    // gh: M planes + scratch M .. M+3 (dL/d of mu P p2[0], P x, y, P x - y) + M+4 (dL/d(P x) via LW)
+    float *gf = m->gf, *gh = m->gh, *gx = m->gx, *dW = m->grads;
+    float *gy = grad_y ? grad_y : m->tproj2;  // dL/dy is accumulated even when not returned
+    float *g_plw = gh + (long long)(M + 4) * NP;
+    int rc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
+    if (rc) return rc;
+    int pfm[8], phm[8];
+    for (int c = 0; c < M; ++c) { pfm[c] = m->fin_f[c]; phm[c] = m->fin_h[c]; }
+    cudaMemsetAsync(gf, 0, sizeof(float) * (M + 4) * NV, st);
+    cudaMemsetAsync(gh, 0, sizeof(float) * (M + 5) * NP, st);
+    CBCT_CUDA_TRY(cudaMemcpyAsync(gx, grad_x, sizeof(float) * NV, cudaMemcpyDeviceToDevice, st));
+    cudaMemsetAsync(gy, 0, sizeof(float) * NP, st);
+    for (int n = N - 1; n >= 0 && rc == 0; --n) {
+        const LayerSpec *Ld = &m->layers[6 * n], *Lp = &m->layers[6 * n + 3];
+        map_unpermute(pfm, m->perm_f[n], M);
+        map_unpermute(phm, m->perm_h[n], M);
+        // ---- output convolution: its gradients (with the states after the update), then undone
+        PlanesW gp{};
+        for (int c = 0; c < M; ++c) gp.p[c] = gf + pfm[c] * NV;
+        k_outconv_grad<<<kOutBlocks, 256, 0, st>>>(gx, lire_f_planes(m, pfm, NV), gp, m->params + m->out_off[n], mu,
+                                                   NV, M, m->opart);
+        k_sum_partials<<<1, 32, 0, st>>>(m->opart, kOutBlocks, M + 1, dW + m->out_off[n]);
+        k_outconv<<<grid_n(NV), 256, 0, st>>>(m->x, lire_f_planes(m, pfm, NV), m->params + m->out_off[n], mu, NV, M,
+                                              -1.f);
+        // ---- primal update undone: inputs from p1, d2[0] and the recovered x
+        if ((rc = forward_project(m->g, m->x, m->t2p + NP, B, 0, sv))) break;
+        if ((rc = lire_backproject(m, phm, B, st))) break;
+        const Planes pp = lire_primal_planes(m, pfm, NV);
+        k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
+        if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Lp[1], m->b1, 32, PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
+        if ((rc = rev_update(m, Lp[2], m->b2, PRIM_DIMS, m->f, pfm + K, NV, 1, st))) break;
+        // gradients through Lambda (upstream dL/dp2)
+        Planes gpl{};
+        for (int c = 0; c < K; ++c) { gpl.p[c] = gf + pfm[K + c] * NV; gpl.s[c] = 1.f; }
+        k_pack8<<<grid_n(NV), 256, 0, st>>>(gpl, NV, m->gsmall);
+        if ((rc = conv_wgrad(m->b2, 32, Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].w_off,
+                             dW + Lp[2].b_off, 1, m->status, st))) break;
+        if ((rc = conv_dx(m, Lp[2], m->gsmall, 8, PRIM_DIMS, 2, m->g32a, m->b2, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->b1, 32, Lp[1].cin, m->g32a, 32, Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].w_off,
+                             dW + Lp[1].b_off, 1, m->status, st))) break;
+        if ((rc = conv_dx(m, Lp[1], m->g32a, 32, PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, 32, Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].w_off,
+                             dW + Lp[0].b_off, 1, m->status, st))) break;
+        // input channels [p1 (K), b_op, x / mu, LW, V] -> p1's planes, scratch M, M+2, M+1, M+3
+        int mp[8];
+        for (int c = 0; c < K; ++c) mp[c] = pfm[c];
+        mp[K] = M; mp[K + 1] = M + 2; mp[K + 2] = M + 1; mp[K + 3] = M + 3;
+        cudaMemsetAsync(gf + (long long)M * NV, 0, sizeof(float) * 4 * NV, st);
+        if ((rc = conv_apply(m->g32b, PRIM_DIMS, 32, 1, m->params + Lp[0].w_off, nullptr, Lp[0].cin, Lp[0].cout, 1, 1,
+                             m->d.slope, nullptr, 32, nullptr, gf, gf, NV, m->status, st, nullptr, 0, mp, 0))) break;
+        // [P dL/db_op, P dL/dLW] in one forward projection of the adjacent scratch planes M, M+1
+        if ((rc = forward_project(m->g, gf + (long long)M * NV, m->t2p, 2 * B, 0, sv))) break;
+        // b_op = s P^T(w d2[0])  =>  dL/dd2[0] += s w P(dL/db_op)
+        k_scale_cols<<<grid_n(NP), 256, 0, st>>>(m->t2p, m->wred, NP, m->g->dev.nu, s, m->tproj);
+        k_axpy<<<grid_n(NP), 256, 0, st>>>(gh + phm[K] * NP, m->tproj, NP, 1.f);
+        // LW = s P^T(P x - y)  =>  dL/d(P x) += s P(dL/dLW), dL/dy -= s P(dL/dLW)
+        cudaMemsetAsync(g_plw, 0, sizeof(float) * NP, st);
+        k_axpy<<<grid_n(NP), 256, 0, st>>>(g_plw, m->t2p + NP, NP, s);
+        k_axpy<<<grid_n(NP), 256, 0, st>>>(gy, m->t2p + NP, NP, -s);
+        // x / mu channel
+        k_axpy<<<grid_n(NV), 256, 0, st>>>(gx, gf + (long long)(M + 2) * NV, NV, 1.f / mu);
+        // ---- dual update undone: inputs from d1 and the recovered p2[0] and x
+        if ((rc = lire_project(m, pfm, B, st))) break;
+        const Planes pl = lire_dual_planes(m, phm, NP);
+        k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
+        if ((rc = conv_fwd(m, Ld[0], m->din, 8, LIRE_DUAL_DIMS, 0, m->a1, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Ld[1], m->a1, 32, LIRE_DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
+        if ((rc = rev_update(m, Ld[2], m->a2, LIRE_DUAL_DIMS, m->h, phm + K, NP, 1, st))) break;
+        // gradients through Gamma (upstream dL/dd2)
+        Planes gdl{};
+        for (int c = 0; c < K; ++c) { gdl.p[c] = gh + phm[K + c] * NP; gdl.s[c] = 1.f; }
+        k_pack8<<<grid_n(NP), 256, 0, st>>>(gdl, NP, m->gsmall);
+        if ((rc = conv_wgrad(m->a2, 32, Ld[2].cin, m->gsmall, 8, Ld[2].cout, LIRE_DUAL_DIMS, 1, dW + Ld[2].w_off,
+                             dW + Ld[2].b_off, 1, m->status, st))) break;
+        if ((rc = conv_dx(m, Ld[2], m->gsmall, 8, LIRE_DUAL_DIMS, 2, m->g32a, m->a2, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->a1, 32, Ld[1].cin, m->g32a, 32, Ld[1].cout, LIRE_DUAL_DIMS, 1, dW + Ld[1].w_off,
+                             dW + Ld[1].b_off, 1, m->status, st))) break;
+        if ((rc = conv_dx(m, Ld[1], m->g32a, 32, LIRE_DUAL_DIMS, 2, m->g32b, m->a1, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, 32, Ld[0].cout, LIRE_DUAL_DIMS, 1, dW + Ld[0].w_off,
+                             dW + Ld[0].b_off, 1, m->status, st))) break;
+        // input channels [d1 (K), mu P p2[0], P x, y, P x - y] -> d1's planes, scratch M .. M+3
+        for (int c = 0; c < K; ++c) mp[c] = phm[c];
+        for (int c = 0; c < 4; ++c) mp[K + c] = M + c;
+        cudaMemsetAsync(gh + (long long)M * NP, 0, sizeof(float) * 4 * NP, st);
+        if ((rc = conv_apply(m->g32b, LIRE_DUAL_DIMS, 32, 1, m->params + Ld[0].w_off, nullptr, Ld[0].cin, Ld[0].cout,
+                             1, 1, m->d.slope, nullptr, 32, nullptr, gh, gh, NP, m->status, st, nullptr, 0, mp,
+                             0))) break;
+        float *g_pp2 = gh + (long long)M * NP, *g_px = gh + (long long)(M + 1) * NP;
+        const float *g_ych = gh + (long long)(M + 2) * NP, *g_res = gh + (long long)(M + 3) * NP;
+        k_add_diff<<<grid_n(NP), 256, 0, st>>>(gy, g_ych, g_res, NP);
+        k_axpy<<<grid_n(NP), 256, 0, st>>>(g_px, g_res, NP, 1.f);
+        k_axpy<<<grid_n(NP), 256, 0, st>>>(g_px, g_plw, NP, 1.f);
+        // [P^T dL/d(mu P p2[0]), P^T dL/d(P x)] in one backprojection of the adjacent planes M, M+1
+        if ((rc = back_project(m->g, g_pp2, m->t2v, 2 * B, 0, sv))) break;
+        k_axpy<<<grid_n(NV), 256, 0, st>>>(gf + pfm[K] * NV, m->t2v, NV, mu);
+        k_axpy<<<grid_n(NV), 256, 0, st>>>(gx, m->t2v + NV, NV, 1.f);
+    }
+    if (rc) return rc;
+    for (int c = 0; c < M; ++c)
+        if (pfm[c] != c || phm[c] != c) return fail(CBCT_ECUDA, "lpd_backward (lire): plane maps not restored");
+    // initial states: x = x0, f = [x0 / mu, s P^T(w y), ...], h = y in every channel
+    if (grad_x0) {
+        CBCT_CUDA_TRY(cudaMemcpyAsync(grad_x0, gx, sizeof(float) * NV, cudaMemcpyDeviceToDevice, st));
+        for (int c = 0; c < M; c += 2) k_axpy<<<grid_n(NV), 256, 0, st>>>(grad_x0, gf + c * NV, NV, 1.f / mu);
+    }
+    if (grad_y) {
+        cudaMemsetAsync(m->tvol, 0, sizeof(float) * NV, st);
+        for (int c = 1; c < M; c += 2) k_axpy<<<grid_n(NV), 256, 0, st>>>(m->tvol, gf + c * NV, NV, s);
+        if ((rc = forward_project(m->g, m->tvol, m->tproj, B, 0, sv))) return rc;
+        k_scale_cols<<<grid_n(NP), 256, 0, st>>>(m->tproj, m->wred, NP, m->g->dev.nu, 1.f, m->t2p);
+        k_axpy<<<grid_n(NP), 256, 0, st>>>(grad_y, m->t2p, NP, 1.f);
+        for (int c = 0; c < M; ++c) k_axpy<<<grid_n(NP), 256, 0, st>>>(grad_y, gh + c * NP, NP, 1.f);
+    }
+    for (int c = 0; c < M; ++c) { m->cur_f[c] = c; m->cur_h[c] = c; }
+    m->saved = 0;
+    CBCT_LAUNCH_CHECK("lpd_backward (lire)");
+    return 0;
+}
+
 extern "C" int lpd_forward(cbct_lpd *m, const float *y, const float *x0, float *x_out, int batch, int save_for_backward,
                            void *stream) {
     if (!m || !y || !x0 || !x_out) return fail(CBCT_EINVAL, "lpd_forward: NULL argument");
     if (batch < 1 || batch > m->maxb)
         return fail(CBCT_EINVAL, "lpd_forward: batch must lie in [1, max_batch = " + std::to_string(m->maxb) + "]");
+    if (m->d.lire) return lire_forward(m, y, x0, x_out, save_for_backward, batch, (cudaStream_t)stream);
     if (m->d.reversible) return lpd_rev_forward(m, y, x0, x_out, save_for_backward, batch, (cudaStream_t)stream);
     return lpd_forward_impl(m, y, x0, nullptr, nullptr, x_out, save_for_backward, batch, (cudaStream_t)stream);
 }
@@ -905,6 +1247,7 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
 extern "C" int lpd_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float *grad_x0, void *stream) {
     if (!m || !grad_x) return fail(CBCT_EINVAL, "lpd_backward: NULL argument");
     if (!m->saved) return fail(CBCT_EINVAL, "lpd_backward: call lpd_forward with save_for_backward = 1 first");
+    if (m->d.lire) return lire_backward(m, grad_x, grad_y, grad_x0, (cudaStream_t)stream);
     if (m->d.reversible) return lpd_rev_backward(m, grad_x, grad_y, grad_x0, (cudaStream_t)stream);
     return lpd_backward_impl(m, grad_x, nullptr, nullptr, grad_y, grad_x0, nullptr, nullptr, (cudaStream_t)stream);
 }

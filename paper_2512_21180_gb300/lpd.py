@@ -20,16 +20,17 @@ class LPD:
 
     def __init__(self, geom: Geometry, n_iter: int = 8, n_mem: int = 5, width: int = 32, slope: float = 0.2,
                  mu_ref: float = 0.02, bp_scale: float = 0.0, seed: int = 0, residual_input: bool = False,
-                 max_batch: int = 1, reversible: bool = False):
+                 max_batch: int = 1, reversible: bool = False, lire: bool = False):
         self.geom = geom
         d = LpdDesc(n_iter, n_mem, width, slope, mu_ref, bp_scale, seed, int(residual_input), int(max_batch),
-                    int(reversible))
+                    int(reversible or lire), int(lire))
         h = ctypes.c_void_p()
         with torch.cuda.device(geom.device):
             check(_lib.load().lpd_create(geom.handle, ctypes.byref(d), ctypes.byref(h)), "lpd_create")
         self.handle = h
         self.n_iter, self.n_mem, self.width, self.mu_ref = n_iter, n_mem, width, mu_ref
-        self.residual_input, self.max_batch, self.reversible = bool(residual_input), int(max_batch), bool(reversible)
+        self.residual_input, self.max_batch = bool(residual_input), int(max_batch)
+        self.reversible, self.lire = bool(reversible or lire), bool(lire)
         self.batch = 1
         n = ctypes.c_longlong()
         pp, gp = ctypes.c_void_p(), ctypes.c_void_p()
@@ -178,6 +179,19 @@ def masked_mse(x: torch.Tensor, ref: torch.Tensor, V: torch.Tensor | None = None
                                       float(thr), x.numel(), loss.data_ptr(),
                                       None if grad is None else grad.data_ptr(), _st()), "cbct_masked_mse")
     return loss, grad
+
+
+def lire_layout(n_iter: int, n_mem: int = 8, width: int = 32):
+    """Parameter layout of a LIRE-mode model, per iteration: ("conv", cout, 27, cin) for
+    the three dual and three primal layers (weights [cout][27][cin] then bias), then
+    ("out", n_mem) for the output convolution (omega [n_mem] then beta)."""
+    k = n_mem // 2
+    out = []
+    for _ in range(n_iter):
+        for _blk in range(2):
+            out += [("conv", width, 27, k + 4), ("conv", width, 27, width), ("conv", k, 27, width)]
+        out.append(("out", n_mem))
+    return out
 
 
 def layer_shapes(n_iter: int, n_mem: int = 5, width: int = 32, residual_input: bool = False,

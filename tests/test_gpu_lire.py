@@ -1,0 +1,137 @@
+"""LIRE mode (the iteration of Algorithm 1 at one resolution: 3x3x3 dual convolutions
+over (angle, v, u), 8-channel reversible latents, Landweber and FoV inputs, separate
+reconstruction with a 1x1x1 output convolution) on the GPU against the FP64
+reference: output, gradients, and the recovery of the initial latents by the backward
+pass."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2512_21180_gb300 import inputs as I
+
+from gpu_util import grad_tol, rel_l2, to_gpu, to_np
+
+pytestmark = pytest.mark.gpu
+
+GEOM = I.scaled(I.geometry("tiny16"), n=(24, 24, 16), vox=(8.0, 8.0, 8.0), nu=40, nv=16, du=4.0, dv=4.0,
+                n_angles=12, u_offset=20.0)
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_2512_21180_gb300 import build
+    build.build()
+    from paper_2512_21180_gb300 import lpd, projector
+    return projector, lpd
+
+
+def lire_flat(layout, seed, last_scale=0.1):
+    rng = np.random.default_rng(seed)
+    out, j = [], 0
+    for e in layout:
+        if e[0] == "conv":
+            _, cout, taps, cin = e
+            sd = math.sqrt(2.0 / (cin * taps)) * (last_scale if j % 3 == 2 else 1.0)
+            out += [rng.standard_normal(cout * taps * cin) * sd, rng.standard_normal(cout) * 0.01]
+            j += 1
+        else:
+            out += [rng.standard_normal(e[1]) * 0.1, rng.standard_normal(1) * 0.01]
+    return np.concatenate(out).astype(np.float32)
+
+
+def oracle_lire_params(flat, layout):
+    dual, prim, outs, blk, o = [], [], [], [], 0
+    for e in layout:
+        if e[0] == "conv":
+            _, cout, taps, cin = e
+            w = torch.tensor(flat[o:o + cout * taps * cin], dtype=torch.float64).reshape(cout, taps, cin)
+            o += cout * taps * cin
+            b = torch.tensor(flat[o:o + cout], dtype=torch.float64)
+            o += cout
+            blk.append((w.permute(0, 2, 1).reshape(cout, cin, 3, 3, 3).contiguous().requires_grad_(True),
+                        b.clone().requires_grad_(True)))
+            if len(blk) == 3:
+                (dual if len(dual) == len(prim) else prim).append(blk)
+                blk = []
+        else:
+            m = e[1]
+            om = torch.tensor(flat[o:o + m], dtype=torch.float64, requires_grad=True)
+            be = torch.tensor(flat[o + m:o + m + 1], dtype=torch.float64, requires_grad=True)
+            o += m + 1
+            outs.append((om, be))
+    return dual, prim, outs
+
+
+def flat_grads(dual, prim, outs):
+    g = []
+    for d, p, (om, be) in zip(dual, prim, outs):
+        for w, b in d + p:
+            g += [w.grad.permute(0, 2, 3, 4, 1).reshape(-1).numpy(), b.grad.numpy()]
+        g += [om.grad.numpy(), be.grad.numpy()]
+    return np.concatenate(g)
+
+
+def test_lire_matches_oracle_and_inverts(O, M):
+    from oracle import lpd_ref as R
+    P, L = M
+    G = O.Geom(GEOM)
+    geom = P.Geometry(GEOM)
+    n_iter, n_mem, mu, bps = 2, 8, 0.02, 2e-3
+    model = L.LPD(geom, n_iter=n_iter, n_mem=n_mem, mu_ref=mu, bp_scale=bps, lire=True, seed=11)
+    layout = L.lire_layout(n_iter, n_mem)
+    flat = lire_flat(layout, 23)
+    assert flat.size == model.nparams
+    model.set_params(flat)
+    perms = model.perms()
+    x_true = O.phantom(G, I.ellipsoids(GEOM, 5, n_soft=6, axes_mm=(15.0, 60.0)))
+    y = O.forward(G, x_true) + 0.01 * I.random_normal(G.proj_shape, 6).astype(np.float64)
+    x0 = 0.8 * x_true + 0.002 * I.random_normal(G.vol_shape, 7).astype(np.float64)
+    r = I.random_normal(G.vol_shape, 8).astype(np.float64)
+    w = torch.tensor(O.redundancy(G))
+    V = torch.tensor(O.fov(G))
+
+    xg = model.forward(to_gpu(y), to_gpu(x0), save_for_backward=True)
+    fN, hN = model.state()
+
+    def reference(x0_scale=1.0):
+        dual, prim, outs = oracle_lire_params(flat, layout)
+        yt = torch.tensor(y, requires_grad=True)
+        x0t = torch.tensor(x0 * x0_scale, requires_grad=True)
+        x, f, h = R.lire(G, yt, x0t, w, V, dual, prim, outs, perms[:, 0], perms[:, 1], n_mem=n_mem, mu_ref=mu,
+                         bp_scale=bps, round_grads=True, return_state=True)
+        (x * torch.tensor(r)).sum().backward()
+        return (x.detach().numpy(), f.detach().numpy(), h.detach().numpy(), flat_grads(dual, prim, outs),
+                yt.grad.numpy(), x0t.grad.numpy())
+
+    xr, fr, hr, gr, gyr, g0r = reference()
+    assert rel_l2(to_np(xg), xr) <= 1e-2
+    assert rel_l2(to_np(fN), fr) <= 1e-2
+    assert rel_l2(to_np(hN), hr) <= 1e-2
+    assert rel_l2(xr, x0) > 1e-4                      # the network changed its start
+    model.zero_grad()
+    gy, g0 = model.backward(to_gpu(r), want_y=True, want_x0=True)
+    gg = model.grads().astype(np.float64)
+    _, _, _, gp, gyp, g0p = reference(1.0 + 1e-6)
+    e_w, e_y, e_x = rel_l2(gg, gr), rel_l2(to_np(gy), gyr), rel_l2(to_np(g0), g0r)
+    print(f"LIRE gradient parity: params {e_w:.2e} (tol {grad_tol(gr, gp):.2e}), y {e_y:.2e} "
+          f"(tol {grad_tol(gyr, gyp):.2e}), x0 {e_x:.2e} (tol {grad_tol(g0r, g0p):.2e})")
+    assert e_w <= grad_tol(gr, gp) and e_y <= grad_tol(gyr, gyp) and e_x <= grad_tol(g0r, g0p)
+    # the backward undid every iteration: the latents are the initial ones again
+    f0, h0 = model.state()
+    xbp = bps * O.adjoint(G, O.redundancy(G)[None, None, :] * y)
+    f_init = np.stack([x0 / mu if c % 2 == 0 else xbp for c in range(n_mem)])
+    h_init = np.stack([y] * n_mem)
+    ef, eh = rel_l2(to_np(f0), f_init), rel_l2(to_np(h0), h_init)
+    print(f"LIRE recovered initial latents: f {ef:.2e}, h {eh:.2e}")
+    assert ef <= 1e-5 and eh <= 1e-5, (ef, eh)
+
+
+def test_lire_rejects_bad_configurations(M):
+    P, L = M
+    geom = P.Geometry(GEOM)
+    with pytest.raises(Exception):
+        L.LPD(geom, n_iter=1, n_mem=10, lire=True)      # halves of 5 need 9 input slots
+    with pytest.raises(Exception):
+        L.LPD(geom, n_iter=1, n_mem=8, lire=True, residual_input=True)

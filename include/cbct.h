@@ -324,6 +324,7 @@ typedef struct {
                                     instead of storing them. 0: Adler-style memory update. */
     int lire;                    /* 1 (needs reversible = 1, residual_input = 0): the iteration of
                                     Algorithm 1 at one resolution, see below. 0: off. */
+    int p4;                      /* 1: P4-equivariant primal blocks (Sec. 2.6), see below. 0: plain */
 } cbct_lpd_desc;
 
 /* Network on geometry g (which must outlive it): per iteration n a dual block
@@ -368,6 +369,16 @@ int lpd_get_perms(const cbct_lpd *m, int *host);
  * parameters per iteration: dual layers, primal layers (as above), then omega [n_mem]
  * and beta. The backward undoes x, p2 and d2 in reverse order, like the reversible mode. */
 int lpd_set_perms(cbct_lpd *m, const int *host);
+
+/* P4-equivariant primal blocks (desc.p4 = 1; Sec. 2.6: the primal block's convolutions are
+ * equivariant to 90-degree rotations about z). Each primal block is lift -> LReLU -> group ->
+ * LReLU -> group averaged over the four rotations, 3x3x3, 8 base filters (32 group channels,
+ * channel 4 c + r for filter c rotated r quarter turns). The learnable parameters are base
+ * filters: lifting [8][27][cin] + bias [8], group [8][4][27][8] + bias [8], averaged
+ * [K][4][27][8] + bias [K] (the 4 is the relative rotation (s - r) mod 4 between input and
+ * output group channel); they are expanded into full weights before each pass, and the full
+ * weight gradients are gathered back onto them after each backward. With a square x-y
+ * grid the block then commutes with the quarter turn v'[z][y][x] = v[z][x][n-1-y]. */
 
 /* Parameter count and device pointers to the parameters and the gradient buffer. */
 int lpd_info(const cbct_lpd *m, long long *nparams, float **params, float **grads, float *bp_scale);

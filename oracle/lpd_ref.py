@@ -113,7 +113,7 @@ def backproject(G, y):
 def lpd(G, y: torch.Tensor, x0: torch.Tensor | None, w_red: torch.Tensor, dual_params, primal_params,
         n_mem: int = 5, round_bf16: bool = True, mu_ref: float = 1.0, bp_scale: float = 1.0,
         f0: torch.Tensor | None = None, h0: torch.Tensor | None = None, return_state: bool = False,
-        round_grads: bool = False, residual_input: bool = False):
+        round_grads: bool = False, residual_input: bool = False, p4: bool = False):
     """Learned primal-dual (Adler-style memory of n_mem channels, the reading of the
     paper's primal/dual latents for this workload), in units of mu_ref:
         f <- x0 / mu_ref repeated (or the given f0), h <- 0 (or the given h0)
@@ -137,15 +137,22 @@ def lpd(G, y: torch.Tensor, x0: torch.Tensor | None, w_red: torch.Tensor, dual_p
         h = h + block(inp.permute(1, 0, 2, 3), dp, round_bf16, round_grads).permute(1, 0, 2, 3)
         bp = bp_scale * backproject(G, w_red.view(1, 1, -1) * h[1])
         inp = torch.cat([f, bp.unsqueeze(0)], 0).unsqueeze(0)             # [1, n_mem + 1, nz, ny, nx]
-        f = f + block(inp, pp, round_bf16, round_grads)[0]
+        f = f + primal_block(inp, pp, round_bf16, round_grads, p4)[0]
     if return_state:
         return mu_ref * f[0], f, h
     return mu_ref * f[0]
 
 
+def primal_block(x, params, round_bf16, round_grads, p4):
+    """The primal block: plain 3x3x3 layers, or P4-equivariant ones (p4_block) whose
+    params are base filters."""
+    return p4_block(x, params, round_bf16, round_grads) if p4 else block(x, params, round_bf16, round_grads)
+
+
 def lpd_reversible(G, y: torch.Tensor, x0: torch.Tensor, w_red: torch.Tensor, dual_params, primal_params, perms_f,
                    perms_h, n_mem: int = 6, round_bf16: bool = True, mu_ref: float = 1.0, bp_scale: float = 1.0,
-                   round_grads: bool = False, residual_input: bool = False, return_state: bool = False):
+                   round_grads: bool = False, residual_input: bool = False, return_state: bool = False,
+                   p4: bool = False):
     """Learned primal-dual with additive coupling and channel permutations (Algorithm 1:
     split, update the second half from the first, combine, permute), in units of mu_ref.
     With M = n_mem (even), f = [p1, p2] and h = [d1, d2] halves of M / 2 channels:
@@ -172,7 +179,7 @@ def lpd_reversible(G, y: torch.Tensor, x0: torch.Tensor, w_red: torch.Tensor, du
             chans.append((pf - y).unsqueeze(0))
         d2 = d2 + block(torch.cat(chans, 0).permute(1, 0, 2, 3), dp, round_bf16, round_grads).permute(1, 0, 2, 3)
         bp = bp_scale * backproject(G, w_red.view(1, 1, -1) * d2[0])
-        p2 = p2 + block(torch.cat([p1, bp.unsqueeze(0)], 0).unsqueeze(0), pp, round_bf16, round_grads)[0]
+        p2 = p2 + primal_block(torch.cat([p1, bp.unsqueeze(0)], 0).unsqueeze(0), pp, round_bf16, round_grads, p4)[0]
         h = torch.cat([d1, d2], 0)[list(perms_h[n])]
         f = torch.cat([p1, p2], 0)[list(perms_f[n])]
     if return_state:
@@ -217,7 +224,7 @@ def mixes_halves(perm) -> bool:
 
 def lire(G, y: torch.Tensor, x0: torch.Tensor, w_red: torch.Tensor, V: torch.Tensor, dual_params, primal_params,
          out_params, perms_f, perms_h, n_mem: int = 8, round_bf16: bool = True, mu_ref: float = 1.0,
-         bp_scale: float = 1.0, round_grads: bool = False, return_state: bool = False):
+         bp_scale: float = 1.0, round_grads: bool = False, return_state: bool = False, p4: bool = False):
     """The learned iterative scheme of Algorithm 1 (Sec. 2.6) at one resolution, in the
     reading used by the library (units: f in mu_ref, h and y in line-integral units):
         x <- x0                                              (FDK_w start)
@@ -250,7 +257,7 @@ def lire(G, y: torch.Tensor, x0: torch.Tensor, w_red: torch.Tensor, V: torch.Ten
         bop = bp_scale * backproject(G, w_red.view(1, 1, -1) * d2[0])
         lw = bp_scale * backproject(G, res)
         inp = torch.cat([p1, bop.unsqueeze(0), (x / mu_ref).unsqueeze(0), lw.unsqueeze(0), V.unsqueeze(0)], 0)
-        p2 = p2 + block(inp.unsqueeze(0), pp, round_bf16, round_grads)[0]
+        p2 = p2 + primal_block(inp.unsqueeze(0), pp, round_bf16, round_grads, p4)[0]
         f = torch.cat([p1, p2], 0)
         h = torch.cat([d1, d2], 0)
         x = x + mu_ref * ((om.view(-1, 1, 1, 1) * f).sum(0) + be)
@@ -259,3 +266,64 @@ def lire(G, y: torch.Tensor, x0: torch.Tensor, w_red: torch.Tensor, V: torch.Ten
     if return_state:
         return x, f, h
     return x
+
+
+# ---- P4-equivariant convolutions (Sec. 2.6: the primal block's P4-equivariant layers) ----
+#
+# rho rotates a volume [.., z, y, x] by 90 degrees about z on a square x-y grid:
+# (rho v)[z, y, x] = v[z, x, n - 1 - y]; on a 3x3x3 tap (dz, dy, dx) it acts as
+# (dz, dy, dx) -> (dz, dx, -dy). A lifting layer's output group channel (co, r) uses the
+# base filter rotated r times; a group layer's weight from input channel (ci, s) to
+# output (co, r) is the base filter of relative rotation (s - r) mod 4, rotated r times;
+# the last layer averages its group outputs. Each layer then commutes with rho (the group
+# index of a group-channel tensor shifts by one under rho).
+
+
+def rot_vol(v: torch.Tensor, r: int = 1) -> torch.Tensor:
+    """rho^r applied to the last three axes [z, y, x] (square x-y grid)."""
+    for _ in range(r % 4):
+        v = torch.flip(v, dims=[-1]).transpose(-1, -2)   # (rho v)[z, y, x] = v[z, x, n - 1 - y]
+    return v
+
+
+def rot_filter(w: torch.Tensor, r: int) -> torch.Tensor:
+    """The filter w[..., dz, dy, dx] rotated r times: W_r[t] = W[rho^-r t], i.e. the filter
+    of the rotated volume, so that conv(rho v, W_r) = rho conv(v, W_{r-1})."""
+    return rot_vol(w, r)
+
+
+def p4_lift(w_base: torch.Tensor, b_base: torch.Tensor):
+    """Full weights [4 co, cin, 3, 3, 3] of a lifting layer (output group channel
+    (co, r) at index co * 4 + r) from base [co, cin, 3, 3, 3]; bias shared over r."""
+    co = w_base.shape[0]
+    w = torch.stack([rot_filter(w_base, r) for r in range(4)], 1).reshape((co * 4,) + tuple(w_base.shape[1:]))
+    return w, b_base.repeat_interleave(4)
+
+
+def p4_group(w_base: torch.Tensor, b_base: torch.Tensor):
+    """Full weights [4 co, 4 ci, 3, 3, 3] of a group layer from base [co, ci, 4, 3, 3, 3]
+    (relative rotation g): W[(co, r), (ci, s)] = rot_r(base[co, ci, (s - r) mod 4])."""
+    co, ci = w_base.shape[:2]
+    rows = []
+    for r in range(4):
+        blocks = [rot_filter(w_base[:, :, (s - r) % 4], r) for s in range(4)]   # each [co, ci, 3, 3, 3]
+        rows.append(torch.stack(blocks, 2).reshape(co, ci * 4, 3, 3, 3))      # input index ci * 4 + s
+    w = torch.stack(rows, 1).reshape(co * 4, ci * 4, 3, 3, 3)
+    return w, b_base.repeat_interleave(4)
+
+
+def p4_avg(w_base: torch.Tensor, b: torch.Tensor):
+    """Weights [co, 4 ci, 3, 3, 3] of the last layer: the group layer's outputs (co, r)
+    averaged over r, from base [co, ci, 4, 3, 3, 3]; bias per output channel."""
+    w, _ = p4_group(w_base, torch.zeros(w_base.shape[0], dtype=w_base.dtype))
+    co = w_base.shape[0]
+    return w.reshape(co, 4, -1, 3, 3, 3).mean(1), b
+
+
+def p4_block(x: torch.Tensor, params, round_bf16: bool = True, round_grads: bool = False) -> torch.Tensor:
+    """The primal block with P4-equivariant layers: lift -> LReLU -> group -> LReLU ->
+    group averaged over rotations. params = [(w_lift [c1, cin, 3, 3, 3], b [c1]),
+    (w_group [c2, c1, 4, 3, 3, 3], b [c2]), (w_avg [cout, c2, 4, 3, 3, 3], b [cout])]; the
+    hidden widths are 4 c1 and 4 c2 group channels."""
+    full = [p4_lift(*params[0]), p4_group(*params[1]), p4_avg(*params[2])]
+    return block(x, full, round_bf16, round_grads)

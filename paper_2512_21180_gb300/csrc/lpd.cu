@@ -46,10 +46,21 @@ extern "C" int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin,
 using namespace cbct;
 
 struct LayerSpec {
-    int cin, cout, taps3d;
+    int cin, cout, taps3d;   // of the convolution as run (full channel counts)
     int H;                   // rows of an image / plane (the tile plan depends on it)
-    long long w_off, b_off;  // offsets into the flat parameter array
+    long long w_off, b_off;  // offsets of the layer's parameters in the flat array
     long long pk_off = 0;    // forward B operand within cbct_lpd::wpk
+    // P4 weight tying: kind 0 = plain (the convolution reads w_off / b_off); 1 = lifting,
+    // 2 = group, 3 = group averaged over rotations, whose parameters are base filters
+    // (cb outputs, cib inputs) expanded into full weights at fw_off / fb_off
+    int kind = 0, cb = 0, cib = 0;
+    long long fw_off = 0, fb_off = 0;
+};
+
+// one P4 layer for the expansion / contraction kernels
+struct P4Job {
+    int kind, cb, cib, cout, cin;  // cout, cin: full
+    long long w_off, b_off, fw_off, fb_off;
 };
 
 struct cbct_lpd {
@@ -65,6 +76,11 @@ struct cbct_lpd {
     // beta) in the flat array, the reconstruction x [batch][nvox], the FoV tensor repeated
     // per batch item, and two-item scratch for batched projector calls
     std::vector<long long> out_off;
+    // P4 primal layers: jobs (device) and the size of the expansion area that follows the
+    // nparams learnable parameters in params (full weights) and grads (full gradients)
+    P4Job *p4_jobs = nullptr;
+    int n_p4 = 0;
+    long long nexp = 0, p4_max = 0;
     float *x = nullptr, *Vb = nullptr, *t2v = nullptr, *t2p = nullptr, *gx = nullptr, *opart = nullptr;
     int fin_f[8] = {}, fin_h[8] = {};
     int cur_f[8] = {}, cur_h[8] = {};  // plane of each logical channel of the states held now
@@ -301,6 +317,90 @@ __global__ void k_lire_init_f(const float *__restrict__ x0, const float *__restr
     }
 }
 
+// ---- P4 weight tying (Sec. 2.6: P4-equivariant primal layers) ----
+//
+// A full 3x3x3 weight [cout][27][cin] is built from base filters. Rotating a filter r
+// quarter turns about z (the rotation that maps a volume v to v'[z][y][x] = v[z][x][n-1-y])
+// puts at tap (z, y, x) the base entry at p4_tap(tap, r). Lifting layer: full[(co, r)][t][ci]
+// = base[co][p4_tap(t, r)][ci]; group layer: full[(co, r)][t][(ci, s)] =
+// base[co][(s - r) mod 4][p4_tap(t, r)][ci]; averaged group layer: full[c][t][(ci, s)] =
+// 1/4 sum_r base[c][(s - r) mod 4][p4_tap(t, r)][ci]; group channel (c, r) is index 4 c + r.
+
+__host__ __device__ __forceinline__ int p4_tap(int t, int r) {
+    const int z = t / 9, y = (t / 3) % 3, x = t % 3;
+    int by, bx;
+    switch (r & 3) {
+        case 0: by = y; bx = x; break;
+        case 1: by = x; bx = 2 - y; break;
+        case 2: by = 2 - y; bx = 2 - x; break;
+        default: by = 2 - x; bx = y; break;
+    }
+    return z * 9 + by * 3 + bx;
+}
+
+// params[fw_off..] = full weights (and biases) of job blockIdx.y from its base filters
+__global__ void k_p4_expand(const P4Job *__restrict__ jobs, float *__restrict__ params) {
+    const P4Job J = jobs[blockIdx.y];
+    const long long n = (long long)J.cout * 27 * J.cin;
+    const float *bw = params + J.w_off;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n + J.cout;
+         e += (long long)gridDim.x * blockDim.x) {
+        if (e >= n) {  // bias
+            const int co = (int)(e - n);
+            params[J.fb_off + co] = params[J.b_off + (J.kind == 3 ? co : co / 4)];
+            continue;
+        }
+        const int ci_f = (int)(e % J.cin), t = (int)((e / J.cin) % 27), co_f = (int)(e / ((long long)J.cin * 27));
+        float v;
+        if (J.kind == 1) {
+            const int co = co_f / 4, r = co_f % 4;
+            v = bw[((long long)co * 27 + p4_tap(t, r)) * J.cib + ci_f];
+        } else if (J.kind == 2) {
+            const int co = co_f / 4, r = co_f % 4, ci = ci_f / 4, sg = ci_f % 4;
+            v = bw[(((long long)co * 4 + ((sg - r) & 3)) * 27 + p4_tap(t, r)) * J.cib + ci];
+        } else {
+            const int ci = ci_f / 4, sg = ci_f % 4;
+            float a = 0.f;
+            for (int r = 0; r < 4; ++r) a += bw[(((long long)co_f * 4 + ((sg - r) & 3)) * 27 + p4_tap(t, r)) * J.cib + ci];
+            v = 0.25f * a;
+        }
+        params[J.fw_off + e] = v;
+    }
+}
+
+// grads[w_off..] += the full gradients of job blockIdx.y gathered back onto its base
+// filters (each base entry sums the full entries it was copied to, in a fixed order)
+__global__ void k_p4_contract(const P4Job *__restrict__ jobs, float *__restrict__ grads) {
+    const P4Job J = jobs[blockIdx.y];
+    const long long nb = J.b_off - J.w_off;  // base weights
+    const float *gf = grads + J.fw_off;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nb + J.cb;
+         e += (long long)gridDim.x * blockDim.x) {
+        float a = 0.f;
+        if (e >= nb) {  // bias
+            const int co = (int)(e - nb);
+            if (J.kind == 3) a = grads[J.fb_off + co];
+            else for (int r = 0; r < 4; ++r) a += grads[J.fb_off + 4 * co + r];
+            grads[J.b_off + co] += a;
+            continue;
+        }
+        if (J.kind == 1) {
+            const int ci = (int)(e % J.cib), tb = (int)((e / J.cib) % 27), co = (int)(e / ((long long)J.cib * 27));
+            for (int r = 0; r < 4; ++r)
+                a += gf[((long long)(4 * co + r) * 27 + p4_tap(tb, 4 - r)) * J.cin + ci];
+        } else {
+            const int ci = (int)(e % J.cib), tb = (int)((e / J.cib) % 27), g = (int)((e / ((long long)J.cib * 27)) % 4);
+            const int co = (int)(e / ((long long)J.cib * 27 * 4));
+            for (int r = 0; r < 4; ++r) {
+                const int co_f = J.kind == 3 ? co : 4 * co + r;
+                const float v = gf[((long long)co_f * 27 + p4_tap(tb, 4 - r)) * J.cin + 4 * ci + ((g + r) & 3)];
+                a += J.kind == 3 ? 0.25f * v : v;
+            }
+        }
+        grads[J.w_off + e] += a;
+    }
+}
+
 // out[i] += sum_b partial[b][i] (fixed order)
 __global__ void k_sum_partials(const float *__restrict__ partial, int nblk, int n, float *__restrict__ out) {
     const int i = threadIdx.x;
@@ -331,11 +431,23 @@ int grid_n(long long n) {
 
 }  // namespace
 
+static void p4_expand(cbct_lpd *m, cudaStream_t st) {
+    if (!m->n_p4) return;
+    dim3 grd((unsigned)std::min<long long>(64, (m->p4_max + 255) / 256 + 1), (unsigned)m->n_p4);
+    k_p4_expand<<<grd, 256, 0, st>>>(m->p4_jobs, m->params);
+}
+
+static void p4_contract(cbct_lpd *m, cudaStream_t st) {
+    if (!m->n_p4) return;
+    dim3 grd((unsigned)std::min<long long>(64, (m->p4_max + 255) / 256 + 1), (unsigned)m->n_p4);
+    k_p4_contract<<<grd, 256, 0, st>>>(m->p4_jobs, m->grads);
+}
+
 // forward conv of layer L; the residual epilogue (epi 1) writes state = state_in + conv
 static int conv_fwd(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *x, int cpin, int nimg, int D, int H, int W,
                     int epi, __nv_bfloat16 *y, float *state, long long sstride, cudaStream_t st,
                     const float *state_in = nullptr, int zero_state_in = 0) {
-    return conv_apply(x, nimg, D, H, W, cpin, L.taps3d, m->params + L.w_off, m->params + L.b_off, L.cin, L.cout, 0, epi,
+    return conv_apply(x, nimg, D, H, W, cpin, L.taps3d, m->params + L.fw_off, m->params + L.fb_off, L.cin, L.cout, 0, epi,
                       m->d.slope, y, 32, nullptr, state_in, state, sstride, m->status, st, m->wpk + L.pk_off,
                       zero_state_in);
 }
@@ -344,7 +456,7 @@ static int conv_fwd(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *x, int
 static int conv_dx(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *dy, int cp_dy, int nimg, int D, int H, int W,
                    int epi, __nv_bfloat16 *y, const __nv_bfloat16 *mask, float *state, long long sstride,
                    cudaStream_t st) {
-    return cbct_conv(dy, nimg, D, H, W, cp_dy, L.taps3d, m->params + L.w_off, nullptr, L.cin, L.cout, 1, epi,
+    return cbct_conv(dy, nimg, D, H, W, cp_dy, L.taps3d, m->params + L.fw_off, nullptr, L.cin, L.cout, 1, epi,
                      m->d.slope, y, 32, mask, state, sstride, m->status, st);
 }
 
@@ -429,7 +541,28 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
         L.cin = cin; L.cout = cout; L.taps3d = t3; L.H = H;
         L.w_off = off; off += (long long)cout * (t3 ? 27 : 9) * cin;
         L.b_off = off; off += cout;
+        L.fw_off = L.w_off; L.fb_off = L.b_off;
         m->layers.push_back(L);
+    };
+    // P4 primal layers (3x3x3, width = 4 x 8 group channels): base filters [cb][27][cin]
+    // (lifting) or [cb][4][27][cib] (group, averaged), biases [cb]; the full weights they
+    // expand to are placed after all learnable parameters (below)
+    constexpr int kP4Base = 8;
+    auto add_p4 = [&](int kind, int cin_full, int cout_full, int H) {
+        LayerSpec L;
+        L.kind = kind; L.taps3d = 1; L.H = H; L.cin = cin_full; L.cout = cout_full;
+        L.cb = kind == 3 ? cout_full : cout_full / 4;
+        L.cib = kind == 1 ? cin_full : cin_full / 4;
+        L.w_off = off; off += (long long)L.cb * (kind == 1 ? 1 : 4) * 27 * L.cib;
+        L.b_off = off; off += L.cb;
+        m->layers.push_back(L);
+    };
+    auto add_primal = [&](int cin, int H) {
+        if (d.p4) {
+            add_p4(1, cin, 4 * kP4Base, H); add_p4(2, 4 * kP4Base, 4 * kP4Base, H); add_p4(3, 4 * kP4Base, K, H);
+        } else {
+            add(cin, W, 1, H); add(W, W, 1, H); add(W, K, 1, H);
+        }
     };
     for (int n = 0; n < d.n_iter; ++n) {
         const int nv = g->dev.nv, ny = g->dev.n[1];
@@ -437,23 +570,36 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
             // Algorithm 1 blocks: 3x3x3 over (angle, v, u) and over the volume, K + 4 inputs each,
             // then the output convolution's omega [n_mem] and beta
             add(K + 4, W, 1, nv); add(W, W, 1, nv); add(W, K, 1, nv);   // dual
-            add(K + 4, W, 1, ny); add(W, W, 1, ny); add(W, K, 1, ny);   // primal
+            add_primal(K + 4, ny);                                          // primal
             m->out_off.push_back(off);
             off += M + 1;
         } else {
             add(m->nd, W, 0, nv); add(W, W, 0, nv); add(W, K, 0, nv);   // dual
-            add(K + 1, W, 1, ny); add(W, W, 1, ny); add(W, K, 1, ny);   // primal
+            add_primal(K + 1, ny);                                          // primal
         }
     }
     m->nparams = off;
+    // expansion area of the P4 layers: full weights [cout][27][cin] and biases, after the
+    // learnable parameters (the same offsets in the gradient buffer hold full gradients)
+    std::vector<P4Job> p4jobs;
+    for (LayerSpec &L : m->layers) {
+        if (!L.kind) continue;
+        L.fw_off = off; off += (long long)L.cout * 27 * L.cin;
+        L.fb_off = off; off += L.cout;
+        p4jobs.push_back(P4Job{L.kind, L.cb, L.cib, L.cout, L.cin, L.w_off, L.b_off, L.fw_off, L.fb_off});
+        m->p4_max = std::max(m->p4_max, (long long)L.cout * 27 * L.cin);
+    }
+    m->n_p4 = (int)p4jobs.size();
+    m->nexp = off - m->nparams;
     // initial weights: He normal for hidden layers, 0.1 x that for the last layer of each block
     std::vector<float> hp(off, 0.f);
     InitRng rng{d.seed};
     for (size_t i = 0; i < m->layers.size(); ++i) {
         const LayerSpec &L = m->layers[i];
         const int taps = L.taps3d ? 27 : 9;
-        const double sd = sqrt(2.0 / (L.cin * taps)) * ((i % 3 == 2) ? 0.1 : 1.0);
-        for (long long k = 0; k < (long long)L.cout * taps * L.cin; ++k) hp[L.w_off + k] = (float)(sd * rng.normal());
+        const double sd = sqrt(2.0 / (L.cin * taps)) * ((i % 3 == 2) ? 0.1 : 1.0);  // fan-in of the full layer
+        const long long nw = L.b_off - L.w_off;
+        for (long long k = 0; k < nw; ++k) hp[L.w_off + k] = (float)(sd * rng.normal());
     }
     for (long long o : m->out_off)
         for (int c = 0; c < M; ++c) hp[o + c] = (float)(0.01 * rng.normal());  // omega; beta = 0
@@ -481,8 +627,9 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     };
     al((void **)&m->params, sizeof(float) * off);
     al((void **)&m->grads, sizeof(float) * off);
-    al((void **)&m->adam_m, sizeof(float) * off);
-    al((void **)&m->adam_v, sizeof(float) * off);
+    al((void **)&m->adam_m, sizeof(float) * m->nparams);
+    al((void **)&m->adam_v, sizeof(float) * m->nparams);
+    if (m->n_p4) al((void **)&m->p4_jobs, sizeof(P4Job) * m->n_p4);
     al((void **)&m->wred, sizeof(float) * g->dev.nu);
     al((void **)&m->f, sizeof(float) * S * M * NV);
     al((void **)&m->h, sizeof(float) * S * M * NP);
@@ -525,7 +672,7 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
             lpd_destroy(m);
             return fail(CBCT_EINVAL, "lpd_create: no convolution plan for layer " + std::to_string(i));
         }
-        jobs[i].w_off = L.w_off;
+        jobs[i].w_off = L.fw_off;
         jobs[i].out_off = L.pk_off = pk_bytes;
         pk_bytes += (b + 255) & ~255LL;
         m->pack_max_nelem = std::max(m->pack_max_nelem, jobs[i].nelem);
@@ -536,8 +683,10 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
         e = cudaMemcpy(m->pack_jobs, jobs.data(), sizeof(ConvPackJob) * jobs.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->params, hp.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(m->grads, 0, sizeof(float) * off);
-    if (e == cudaSuccess) e = cudaMemset(m->adam_m, 0, sizeof(float) * off);
-    if (e == cudaSuccess) e = cudaMemset(m->adam_v, 0, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMemset(m->adam_m, 0, sizeof(float) * m->nparams);
+    if (e == cudaSuccess) e = cudaMemset(m->adam_v, 0, sizeof(float) * m->nparams);
+    if (e == cudaSuccess && m->n_p4)
+        e = cudaMemcpy(m->p4_jobs, p4jobs.data(), sizeof(P4Job) * m->n_p4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(int));
     if (e != cudaSuccess) {
         lpd_destroy(m);
@@ -584,7 +733,7 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
 extern "C" void lpd_destroy(cbct_lpd *m) {
     if (!m) return;
     cudaDeviceSynchronize();
-    void *ptrs[] = {m->x, m->gx, m->Vb, m->t2v, m->t2p, m->opart, m->wpk, m->pack_jobs, m->clip, m->pf_saved, m->bp_saved, m->params, m->grads, m->adam_m, m->adam_v, m->wred, m->f, m->h,
+    void *ptrs[] = {m->p4_jobs, m->x, m->gx, m->Vb, m->t2v, m->t2p, m->opart, m->wpk, m->pack_jobs, m->clip, m->pf_saved, m->bp_saved, m->params, m->grads, m->adam_m, m->adam_v, m->wred, m->f, m->h,
                     m->y, m->tproj, m->tproj2, m->tvol, m->din, m->a1, m->a2, m->pin, m->b1, m->b2, m->g32a, m->g32b, m->gsmall, m->gf, m->gh,
                     m->status};
     for (void *p : ptrs)
@@ -639,6 +788,7 @@ static int lpd_forward_impl(cbct_lpd *m, const float *y, const float *x0, const 
     m->batch = B;
     const long long NV = m->nvox * B, NP = m->nproj * B;
     const int M = m->d.n_mem, N = m->d.n_iter;
+    p4_expand(m, st);
     int prc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
     if (prc) return prc;
     CBCT_CUDA_TRY(cudaMemcpyAsync(m->y, y, sizeof(float) * NP, cudaMemcpyDeviceToDevice, st));
@@ -721,7 +871,7 @@ static Planes rev_primal_planes(const cbct_lpd *m, const float *f, const int *pf
 // (ssub = 1 subtracts it again)
 static int rev_update(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *act, int nimg, int D, int H, int W,
                       float *state, const int *map2, long long sstride, int ssub, cudaStream_t st) {
-    return conv_apply(act, nimg, D, H, W, 32, L.taps3d, m->params + L.w_off, m->params + L.b_off, L.cin, L.cout, 0,
+    return conv_apply(act, nimg, D, H, W, 32, L.taps3d, m->params + L.fw_off, m->params + L.fb_off, L.cin, L.cout, 0,
                       1, m->d.slope, nullptr, 32, nullptr, state, state, sstride, m->status, st, m->wpk + L.pk_off, 0,
                       map2, ssub);
 }
@@ -732,6 +882,7 @@ static int lpd_rev_forward(cbct_lpd *m, const float *y, const float *x0, float *
     void *sv = (void *)st;
     const long long NV = m->nvox * B, NP = m->nproj * B;
     const int M = m->d.n_mem, K = M / 2, N = m->d.n_iter;
+    p4_expand(m, st);
     int rc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
     if (rc) return rc;
     CBCT_CUDA_TRY(cudaMemcpyAsync(m->y, y, sizeof(float) * NP, cudaMemcpyDeviceToDevice, st));
@@ -776,6 +927,7 @@ static int lpd_rev_backward(cbct_lpd *m, const float *grad_x, float *grad_y, flo
     const long long NV = m->nvox * B, NP = m->nproj * B;
     const int M = m->d.n_mem, K = M / 2, N = m->d.n_iter;
     float *gf = m->gf, *gh = m->gh, *dW = m->grads;  // gf: M planes + plane M (scratch); gh: M + 3 planes
+    p4_expand(m, st);
     int rc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
     if (rc) return rc;
     int pfm[8], phm[8];
@@ -799,20 +951,20 @@ static int lpd_rev_backward(cbct_lpd *m, const float *grad_x, float *grad_y, flo
         Planes gp{};
         for (int c = 0; c < K; ++c) { gp.p[c] = gf + pfm[K + c] * NV; gp.s[c] = 1.f; }
         k_pack8<<<grid_n(NV), 256, 0, st>>>(gp, NV, m->gsmall);
-        if ((rc = conv_wgrad(m->b2, 32, Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].w_off,
-                             dW + Lp[2].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->b2, 32, Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].fw_off,
+                             dW + Lp[2].fb_off, Lp[2].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Lp[2], m->gsmall, 8, PRIM_DIMS, 2, m->g32a, m->b2, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->b1, 32, Lp[1].cin, m->g32a, 32, Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].w_off,
-                             dW + Lp[1].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->b1, 32, Lp[1].cin, m->g32a, 32, Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].fw_off,
+                             dW + Lp[1].fb_off, Lp[1].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Lp[1], m->g32a, 32, PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, 32, Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].w_off,
-                             dW + Lp[0].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, 32, Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].fw_off,
+                             dW + Lp[0].fb_off, Lp[0].kind ? 0 : 1, m->status, st))) break;
         // dL/d[p1, bp]: p1's planes accumulate, the bp channel goes to scratch plane M
         int mp[8];
         for (int c = 0; c < K; ++c) mp[c] = pfm[c];
         mp[K] = M;
         cudaMemsetAsync(gf + (long long)M * NV, 0, sizeof(float) * NV, st);
-        if ((rc = conv_apply(m->g32b, PRIM_DIMS, 32, Lp[0].taps3d, m->params + Lp[0].w_off, nullptr, Lp[0].cin,
+        if ((rc = conv_apply(m->g32b, PRIM_DIMS, 32, Lp[0].taps3d, m->params + Lp[0].fw_off, nullptr, Lp[0].cin,
                              Lp[0].cout, 1, 1, m->d.slope, nullptr, 32, nullptr, gf, gf, NV, m->status, st, nullptr,
                              0, mp, 0))) break;
         // bp = bp_scale P^T (w d2[0])  =>  dL/dd2[0] += w bp_scale P (dL/dbp)
@@ -830,20 +982,20 @@ static int lpd_rev_backward(cbct_lpd *m, const float *grad_x, float *grad_y, flo
         Planes gd{};
         for (int c = 0; c < K; ++c) { gd.p[c] = gh + phm[K + c] * NP; gd.s[c] = 1.f; }
         k_pack8<<<grid_n(NP), 256, 0, st>>>(gd, NP, m->gsmall);
-        if ((rc = conv_wgrad(m->a2, 32, Ld[2].cin, m->gsmall, 8, Ld[2].cout, DUAL_DIMS, 0, dW + Ld[2].w_off,
-                             dW + Ld[2].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->a2, 32, Ld[2].cin, m->gsmall, 8, Ld[2].cout, DUAL_DIMS, 0, dW + Ld[2].fw_off,
+                             dW + Ld[2].fb_off, Ld[2].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Ld[2], m->gsmall, 8, DUAL_DIMS, 2, m->g32a, m->a2, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->a1, 32, Ld[1].cin, m->g32a, 32, Ld[1].cout, DUAL_DIMS, 0, dW + Ld[1].w_off,
-                             dW + Ld[1].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->a1, 32, Ld[1].cin, m->g32a, 32, Ld[1].cout, DUAL_DIMS, 0, dW + Ld[1].fw_off,
+                             dW + Ld[1].fb_off, Ld[1].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Ld[1], m->g32a, 32, DUAL_DIMS, 2, m->g32b, m->a1, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, 32, Ld[0].cout, DUAL_DIMS, 0, dW + Ld[0].w_off,
-                             dW + Ld[0].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, 32, Ld[0].cout, DUAL_DIMS, 0, dW + Ld[0].fw_off,
+                             dW + Ld[0].fb_off, Ld[0].kind ? 0 : 1, m->status, st))) break;
         // dL/d[d1, pf, y (, residual)]: d1's planes accumulate, the others go to scratch planes M..
         const int nin = Ld[0].cin;
         for (int c = 0; c < K; ++c) mp[c] = phm[c];
         for (int c = K; c < nin; ++c) mp[c] = M + (c - K);
         cudaMemsetAsync(gh + (long long)M * NP, 0, sizeof(float) * 3 * NP, st);
-        if ((rc = conv_apply(m->g32b, DUAL_DIMS, 32, Ld[0].taps3d, m->params + Ld[0].w_off, nullptr, Ld[0].cin,
+        if ((rc = conv_apply(m->g32b, DUAL_DIMS, 32, Ld[0].taps3d, m->params + Ld[0].fw_off, nullptr, Ld[0].cin,
                              Ld[0].cout, 1, 1, m->d.slope, nullptr, 32, nullptr, gh, gh, NP, m->status, st, nullptr,
                              0, mp, 0))) break;
         float *g_pf = gh + (long long)M * NP, *g_y = gh + (long long)(M + 1) * NP;
@@ -864,6 +1016,7 @@ static int lpd_rev_backward(cbct_lpd *m, const float *grad_x, float *grad_y, flo
     if (grad_x0) k_sum_channels<<<grid_n(NV), 256, 0, st>>>(gf, M, NV, 1.f / m->d.mu_ref, grad_x0, 0);
     for (int c = 0; c < M; ++c) { m->cur_f[c] = pfm[c]; m->cur_h[c] = phm[c]; }
     m->saved = 0;  // the states now hold the recovered initial iterate
+    p4_contract(m, st);
     CBCT_LAUNCH_CHECK("lpd_backward (reversible)");
     return 0;
 }
@@ -936,6 +1089,7 @@ static int lire_forward(cbct_lpd *m, const float *y, const float *x0, float *x_o
     m->batch = B;
     const long long NV = m->nvox * B, NP = m->nproj * B;
     const int M = m->d.n_mem, K = M / 2, N = m->d.n_iter;
+    p4_expand(m, st);
     int rc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
     if (rc) return rc;
     CBCT_CUDA_TRY(cudaMemcpyAsync(m->y, y, sizeof(float) * NP, cudaMemcpyDeviceToDevice, st));
@@ -986,6 +1140,7 @@ static int lire_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float 
     float *gf = m->gf, *gh = m->gh, *gx = m->gx, *dW = m->grads;
     float *gy = grad_y ? grad_y : m->tproj2;  // dL/dy is accumulated even when not returned
     float *g_plw = gh + (long long)(M + 4) * NP;
+    p4_expand(m, st);
     int rc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
     if (rc) return rc;
     int pfm[8], phm[8];
@@ -1018,20 +1173,20 @@ static int lire_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float 
         Planes gpl{};
         for (int c = 0; c < K; ++c) { gpl.p[c] = gf + pfm[K + c] * NV; gpl.s[c] = 1.f; }
         k_pack8<<<grid_n(NV), 256, 0, st>>>(gpl, NV, m->gsmall);
-        if ((rc = conv_wgrad(m->b2, 32, Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].w_off,
-                             dW + Lp[2].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->b2, 32, Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].fw_off,
+                             dW + Lp[2].fb_off, Lp[2].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Lp[2], m->gsmall, 8, PRIM_DIMS, 2, m->g32a, m->b2, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->b1, 32, Lp[1].cin, m->g32a, 32, Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].w_off,
-                             dW + Lp[1].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->b1, 32, Lp[1].cin, m->g32a, 32, Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].fw_off,
+                             dW + Lp[1].fb_off, Lp[1].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Lp[1], m->g32a, 32, PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, 32, Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].w_off,
-                             dW + Lp[0].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, 32, Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].fw_off,
+                             dW + Lp[0].fb_off, Lp[0].kind ? 0 : 1, m->status, st))) break;
         // input channels [p1 (K), b_op, x / mu, LW, V] -> p1's planes, scratch M, M+2, M+1, M+3
         int mp[8];
         for (int c = 0; c < K; ++c) mp[c] = pfm[c];
         mp[K] = M; mp[K + 1] = M + 2; mp[K + 2] = M + 1; mp[K + 3] = M + 3;
         cudaMemsetAsync(gf + (long long)M * NV, 0, sizeof(float) * 4 * NV, st);
-        if ((rc = conv_apply(m->g32b, PRIM_DIMS, 32, 1, m->params + Lp[0].w_off, nullptr, Lp[0].cin, Lp[0].cout, 1, 1,
+        if ((rc = conv_apply(m->g32b, PRIM_DIMS, 32, 1, m->params + Lp[0].fw_off, nullptr, Lp[0].cin, Lp[0].cout, 1, 1,
                              m->d.slope, nullptr, 32, nullptr, gf, gf, NV, m->status, st, nullptr, 0, mp, 0))) break;
         // [P dL/db_op, P dL/dLW] in one forward projection of the adjacent scratch planes M, M+1
         if ((rc = forward_project(m->g, gf + (long long)M * NV, m->t2p, 2 * B, 0, sv))) break;
@@ -1055,19 +1210,19 @@ static int lire_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float 
         Planes gdl{};
         for (int c = 0; c < K; ++c) { gdl.p[c] = gh + phm[K + c] * NP; gdl.s[c] = 1.f; }
         k_pack8<<<grid_n(NP), 256, 0, st>>>(gdl, NP, m->gsmall);
-        if ((rc = conv_wgrad(m->a2, 32, Ld[2].cin, m->gsmall, 8, Ld[2].cout, LIRE_DUAL_DIMS, 1, dW + Ld[2].w_off,
-                             dW + Ld[2].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->a2, 32, Ld[2].cin, m->gsmall, 8, Ld[2].cout, LIRE_DUAL_DIMS, 1, dW + Ld[2].fw_off,
+                             dW + Ld[2].fb_off, Ld[2].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Ld[2], m->gsmall, 8, LIRE_DUAL_DIMS, 2, m->g32a, m->a2, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->a1, 32, Ld[1].cin, m->g32a, 32, Ld[1].cout, LIRE_DUAL_DIMS, 1, dW + Ld[1].w_off,
-                             dW + Ld[1].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->a1, 32, Ld[1].cin, m->g32a, 32, Ld[1].cout, LIRE_DUAL_DIMS, 1, dW + Ld[1].fw_off,
+                             dW + Ld[1].fb_off, Ld[1].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Ld[1], m->g32a, 32, LIRE_DUAL_DIMS, 2, m->g32b, m->a1, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, 32, Ld[0].cout, LIRE_DUAL_DIMS, 1, dW + Ld[0].w_off,
-                             dW + Ld[0].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, 32, Ld[0].cout, LIRE_DUAL_DIMS, 1, dW + Ld[0].fw_off,
+                             dW + Ld[0].fb_off, Ld[0].kind ? 0 : 1, m->status, st))) break;
         // input channels [d1 (K), mu P p2[0], P x, y, P x - y] -> d1's planes, scratch M .. M+3
         for (int c = 0; c < K; ++c) mp[c] = phm[c];
         for (int c = 0; c < 4; ++c) mp[K + c] = M + c;
         cudaMemsetAsync(gh + (long long)M * NP, 0, sizeof(float) * 4 * NP, st);
-        if ((rc = conv_apply(m->g32b, LIRE_DUAL_DIMS, 32, 1, m->params + Ld[0].w_off, nullptr, Ld[0].cin, Ld[0].cout,
+        if ((rc = conv_apply(m->g32b, LIRE_DUAL_DIMS, 32, 1, m->params + Ld[0].fw_off, nullptr, Ld[0].cin, Ld[0].cout,
                              1, 1, m->d.slope, nullptr, 32, nullptr, gh, gh, NP, m->status, st, nullptr, 0, mp,
                              0))) break;
         float *g_pp2 = gh + (long long)M * NP, *g_px = gh + (long long)(M + 1) * NP;
@@ -1098,6 +1253,7 @@ static int lire_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float 
     }
     for (int c = 0; c < M; ++c) { m->cur_f[c] = c; m->cur_h[c] = c; }
     m->saved = 0;
+    p4_contract(m, st);
     CBCT_LAUNCH_CHECK("lpd_backward (lire)");
     return 0;
 }
@@ -1157,6 +1313,7 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
     float *gf = m->gf, *gh = m->gh;
     // the recomputed forward convolutions read the packed weights: refresh them (the
     // parameters may have changed since the forward pass)
+    p4_expand(m, st);
     int prc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
     if (prc) return prc;
     // dL/df_N: channel 0 gets mu_ref dL/dx; plus the given state gradients
@@ -1189,14 +1346,14 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
         Planes gp{};
         for (int c = 0; c < M; ++c) { gp.p[c] = gf + c * NV; gp.s[c] = 1.f; }
         k_pack8<<<grid_n(NV), 256, 0, st>>>(gp, NV, m->gsmall);
-        if ((rc = conv_wgrad(m->b2, 32, Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].w_off,
-                             dW + Lp[2].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->b2, 32, Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].fw_off,
+                             dW + Lp[2].fb_off, Lp[2].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Lp[2], m->gsmall, 8, PRIM_DIMS, 2, m->g32a, m->b2, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->b1, 32, Lp[1].cin, m->g32a, 32, Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].w_off,
-                             dW + Lp[1].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->b1, 32, Lp[1].cin, m->g32a, 32, Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].fw_off,
+                             dW + Lp[1].fb_off, Lp[1].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Lp[1], m->g32a, 32, PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, 32, Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].w_off,
-                             dW + Lp[0].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, 32, Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].fw_off,
+                             dW + Lp[0].fb_off, Lp[0].kind ? 0 : 1, m->status, st))) break;
         // dL/d(primal input) -> gf[0..M) += (residual path kept), gf[M] = dL/d(bp channel)
         cudaMemsetAsync(gf + (long long)M * NV, 0, sizeof(float) * NV, st);
         if ((rc = conv_dx(m, Lp[0], m->g32b, 32, PRIM_DIMS, 1, nullptr, nullptr, gf, NV, st))) break;
@@ -1209,14 +1366,14 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
         Planes gd{};
         for (int c = 0; c < M; ++c) { gd.p[c] = gh + c * NP; gd.s[c] = 1.f; }
         k_pack8<<<grid_n(NP), 256, 0, st>>>(gd, NP, m->gsmall);
-        if ((rc = conv_wgrad(m->a2, 32, Ld[2].cin, m->gsmall, 8, Ld[2].cout, DUAL_DIMS, 0, dW + Ld[2].w_off,
-                             dW + Ld[2].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->a2, 32, Ld[2].cin, m->gsmall, 8, Ld[2].cout, DUAL_DIMS, 0, dW + Ld[2].fw_off,
+                             dW + Ld[2].fb_off, Ld[2].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Ld[2], m->gsmall, 8, DUAL_DIMS, 2, m->g32a, m->a2, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->a1, 32, Ld[1].cin, m->g32a, 32, Ld[1].cout, DUAL_DIMS, 0, dW + Ld[1].w_off,
-                             dW + Ld[1].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->a1, 32, Ld[1].cin, m->g32a, 32, Ld[1].cout, DUAL_DIMS, 0, dW + Ld[1].fw_off,
+                             dW + Ld[1].fb_off, Ld[1].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Ld[1], m->g32a, 32, DUAL_DIMS, 2, m->g32b, m->a1, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, 32, Ld[0].cout, DUAL_DIMS, 0, dW + Ld[0].w_off,
-                             dW + Ld[0].b_off, 1, m->status, st))) break;
+        if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, 32, Ld[0].cout, DUAL_DIMS, 0, dW + Ld[0].fw_off,
+                             dW + Ld[0].fb_off, Ld[0].kind ? 0 : 1, m->status, st))) break;
         // dL/d(dual input): gh[0..M) += (residual), gh[M] = dL/d(pf channel), gh[M+1] = dL/d(y channel),
         // gh[M+2] = dL/d(residual channel mu_ref pf - y)
         cudaMemsetAsync(gh + (long long)M * NP, 0, sizeof(float) * (ND - M) * NP, st);
@@ -1240,6 +1397,7 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
     if (grad_x0) k_sum_channels<<<grid_n(NV), 256, 0, st>>>(gf, M, NV, 1.f / m->d.mu_ref, grad_x0, 0);
     if (grad_f0) CBCT_CUDA_TRY(cudaMemcpyAsync(grad_f0, gf, sizeof(float) * M * NV, cudaMemcpyDeviceToDevice, st));
     if (grad_h0) CBCT_CUDA_TRY(cudaMemcpyAsync(grad_h0, gh, sizeof(float) * M * NP, cudaMemcpyDeviceToDevice, st));
+    p4_contract(m, st);
     CBCT_LAUNCH_CHECK("lpd_backward");
     return 0;
 }

@@ -20,17 +20,17 @@ class LPD:
 
     def __init__(self, geom: Geometry, n_iter: int = 8, n_mem: int = 5, width: int = 32, slope: float = 0.2,
                  mu_ref: float = 0.02, bp_scale: float = 0.0, seed: int = 0, residual_input: bool = False,
-                 max_batch: int = 1, reversible: bool = False, lire: bool = False):
+                 max_batch: int = 1, reversible: bool = False, lire: bool = False, p4: bool = False):
         self.geom = geom
         d = LpdDesc(n_iter, n_mem, width, slope, mu_ref, bp_scale, seed, int(residual_input), int(max_batch),
-                    int(reversible or lire), int(lire))
+                    int(reversible or lire), int(lire), int(p4))
         h = ctypes.c_void_p()
         with torch.cuda.device(geom.device):
             check(_lib.load().lpd_create(geom.handle, ctypes.byref(d), ctypes.byref(h)), "lpd_create")
         self.handle = h
         self.n_iter, self.n_mem, self.width, self.mu_ref = n_iter, n_mem, width, mu_ref
         self.residual_input, self.max_batch = bool(residual_input), int(max_batch)
-        self.reversible, self.lire = bool(reversible or lire), bool(lire)
+        self.reversible, self.lire, self.p4 = bool(reversible or lire), bool(lire), bool(p4)
         self.batch = 1
         n = ctypes.c_longlong()
         pp, gp = ctypes.c_void_p(), ctypes.c_void_p()
@@ -179,6 +179,13 @@ def masked_mse(x: torch.Tensor, ref: torch.Tensor, V: torch.Tensor | None = None
                                       float(thr), x.numel(), loss.data_ptr(),
                                       None if grad is None else grad.data_ptr(), _st()), "cbct_masked_mse")
     return loss, grad
+
+
+def p4_primal_layout(cin: int, cout: int):
+    """Base-parameter layout of one P4 primal block: ("lift", 8, cin), ("group", 8, 8),
+    ("avg", cout, 8) — weights [8][27][cin], [8][4][27][8], [cout][4][27][8], each followed
+    by its bias."""
+    return [("lift", 8, cin), ("group", 8, 8), ("avg", cout, 8)]
 
 
 def lire_layout(n_iter: int, n_mem: int = 8, width: int = 32):

@@ -1,0 +1,147 @@
+"""P4-equivariant primal blocks on the GPU: the network's output and gradients
+against the FP64 reference with the same base filters, and equivariance end to end —
+a quarter turn of the object about z is the same as shifting the angle index by a
+quarter of the orbit, so the learned primal-dual with P4 primal blocks (and per-image
+dual blocks) maps a rotated problem to the rotated reconstruction, while the same
+network with plain primal blocks does not."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2512_21180_gb300 import inputs as I
+
+from gpu_util import grad_tol, rel_l2, to_gpu, to_np
+
+pytestmark = pytest.mark.gpu
+
+# square x-y grid centred on the isocentre, 12 angles (a quarter orbit = 3 angles)
+GEOM = I.scaled(I.geometry("tiny16"), n=(24, 24, 16), vox=(8.0, 8.0, 8.0), nu=40, nv=16, du=4.0, dv=4.0,
+                n_angles=12, u_offset=20.0)
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_2512_21180_gb300 import build
+    build.build()
+    from paper_2512_21180_gb300 import lpd, projector
+    return projector, lpd
+
+
+def p4_flat(n_iter, n_mem, seed, last_scale=0.1):
+    """Seeded parameters of an Adler-style LPD with P4 primal blocks, in the library's
+    order: per iteration the dual layers ([cout][9][cin] + bias) then the primal base
+    filters (lift [8][27][cin], group [8][4][27][8], avg [n_mem][4][27][8], each + bias)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_iter):
+        for i, (co, t, ci) in enumerate([(32, 9, n_mem + 2), (32, 9, 32), (n_mem, 9, 32)]):
+            sd = math.sqrt(2.0 / (ci * t)) * (last_scale if i == 2 else 1.0)
+            out += [rng.standard_normal(co * t * ci) * sd, rng.standard_normal(co) * 0.01]
+        for i, (co, g, ci, fan) in enumerate([(8, 1, n_mem + 1, (n_mem + 1) * 27), (8, 4, 8, 32 * 27),
+                                              (n_mem, 4, 8, 32 * 27)]):
+            sd = math.sqrt(2.0 / fan) * (last_scale if i == 2 else 1.0)
+            out += [rng.standard_normal(co * g * 27 * ci) * sd, rng.standard_normal(co) * 0.01]
+    return np.concatenate(out).astype(np.float32)
+
+
+def oracle_p4_params(flat, n_iter, n_mem):
+    dual, prim, o = [], [], 0
+
+    def take(k):
+        nonlocal o
+        t = torch.tensor(flat[o:o + k], dtype=torch.float64)
+        o += k
+        return t
+    for _ in range(n_iter):
+        d = []
+        for co, t, ci in [(32, 9, n_mem + 2), (32, 9, 32), (n_mem, 9, 32)]:
+            w = take(co * t * ci).reshape(co, t, ci).permute(0, 2, 1).reshape(co, ci, 3, 3).contiguous()
+            d.append((w.requires_grad_(True), take(co).requires_grad_(True)))
+        p = []
+        for co, g, ci in [(8, 1, n_mem + 1), (8, 4, 8), (n_mem, 4, 8)]:
+            w = take(co * g * 27 * ci).reshape(co, g, 27, ci).permute(0, 3, 1, 2).reshape(co, ci, g, 3, 3, 3)
+            w = w[:, :, 0].contiguous() if g == 1 else w.contiguous()
+            p.append((w.requires_grad_(True), take(co).requires_grad_(True)))
+        dual.append(d)
+        prim.append(p)
+    assert o == flat.size
+    return dual, prim
+
+
+def flat_grads(dual, prim):
+    g = []
+    for d, p in zip(dual, prim):
+        for w, b in d:
+            g += [w.grad.permute(0, 2, 3, 1).reshape(-1).numpy(), b.grad.numpy()]
+        for i, (w, b) in enumerate(p):
+            ww = w.grad.unsqueeze(2) if i == 0 else w.grad                    # [co, ci, g, 3, 3, 3]
+            g += [ww.permute(0, 2, 3, 4, 5, 1).reshape(-1).numpy(), b.grad.numpy()]
+    return np.concatenate(g)
+
+
+def test_p4_lpd_matches_oracle(O, M):
+    from oracle import lpd_ref as R
+    P, L = M
+    G = O.Geom(GEOM)
+    geom = P.Geometry(GEOM)
+    n_iter, n_mem, mu, bps = 2, 5, 0.02, 2e-3
+    model = L.LPD(geom, n_iter=n_iter, n_mem=n_mem, mu_ref=mu, bp_scale=bps, p4=True)
+    flat = p4_flat(n_iter, n_mem, 31)
+    assert flat.size == model.nparams
+    model.set_params(flat)
+    x_true = O.phantom(G, I.ellipsoids(GEOM, 5, n_soft=6, axes_mm=(15.0, 60.0)))
+    y = O.forward(G, x_true) + 0.01 * I.random_normal(G.proj_shape, 6).astype(np.float64)
+    x0 = 0.8 * x_true + 0.002 * I.random_normal(G.vol_shape, 7).astype(np.float64)
+    r = I.random_normal(G.vol_shape, 8).astype(np.float64)
+    w = torch.tensor(O.redundancy(G))
+    xg = model.forward(to_gpu(y), to_gpu(x0), save_for_backward=True)
+    model.zero_grad()
+    gy, g0 = model.backward(to_gpu(r), want_y=True, want_x0=True)
+    gg = model.grads().astype(np.float64)
+
+    def reference(x0_scale=1.0):
+        dual, prim = oracle_p4_params(flat, n_iter, n_mem)
+        yt = torch.tensor(y, requires_grad=True)
+        x0t = torch.tensor(x0 * x0_scale, requires_grad=True)
+        out = R.lpd(G, yt, x0t, w, dual, prim, n_mem=n_mem, mu_ref=mu, bp_scale=bps, round_grads=True, p4=True)
+        (out * torch.tensor(r)).sum().backward()
+        return out.detach().numpy(), flat_grads(dual, prim), yt.grad.numpy(), x0t.grad.numpy()
+
+    xr, gr, gyr, g0r = reference()
+    _, gp, gyp, g0p = reference(1.0 + 1e-6)
+    assert rel_l2(to_np(xg), xr) <= 1e-2
+    assert rel_l2(xr, x0) > 1e-4
+    e_w, e_y, e_x = rel_l2(gg, gr), rel_l2(to_np(gy), gyr), rel_l2(to_np(g0), g0r)
+    print(f"P4 LPD gradient parity: params {e_w:.2e}, y {e_y:.2e}, x0 {e_x:.2e}")
+    assert e_w <= grad_tol(gr, gp) and e_y <= grad_tol(gyr, gyp) and e_x <= grad_tol(g0r, g0p)
+
+
+def test_p4_lpd_is_equivariant_end_to_end(M):
+    from oracle import lpd_ref as R
+    P, L = M
+    geom = P.Geometry(GEOM)
+    rng = np.random.default_rng(3)
+    x = torch.tensor(I.smooth_volume(GEOM["n"], 4), dtype=torch.float32, device="cuda")
+    rot = lambda v: R.rot_vol(v)
+    y = P.forward_project(geom, x)
+    y_rot = P.forward_project(geom, rot(x))
+    q = GEOM["n_angles"] // 4
+    errs = {s: rel_l2(to_np(y_rot), to_np(torch.roll(y, s, dims=0))) for s in (q, -q)}
+    shift = min(errs, key=errs.get)
+    assert errs[shift] <= 1e-5, errs          # the rotation is an angle shift for the projector
+    y = y + 0.01 * torch.tensor(rng.standard_normal(tuple(y.shape)), dtype=torch.float32, device="cuda")
+    y_rot = torch.roll(y, shift, dims=0).contiguous()
+    x0 = 0.8 * x
+    ratios = {}
+    for p4 in (True, False):
+        model = L.LPD(geom, n_iter=2, p4=p4, seed=5, mu_ref=0.5, bp_scale=2e-3)
+        params = model.get_params()
+        model.set_params(params * 3.0)        # stronger blocks: the network changes its input visibly
+        out = model.forward(y, x0)
+        out_rot = model.forward(y_rot, rot(x0).contiguous())
+        ratios[p4] = rel_l2(to_np(out_rot), to_np(rot(out))) / rel_l2(to_np(out), to_np(x0))
+    print(f"equivariance defect relative to the network's change: P4 {ratios[True]:.2e}, plain {ratios[False]:.2e}")
+    assert ratios[True] <= 2e-2, ratios
+    assert ratios[False] >= 0.1, ratios

@@ -559,17 +559,21 @@ __global__ void k_pack_jobs(const ConvPackJob *__restrict__ jobs, const float *_
 // stages feed it, with the operands marked transposed in the instruction descriptor
 // (for this layout the descriptor's leading byte offset steps along K, the stride
 // byte offset along M / N).
-// A tile is 128 output pixels of one output row h (input plane d + dd for 3-D); its
-// stage holds the input rows h - 1 .. h + 2 (4 rows x 4 channel groups, the region
-// layout of the forward) and the tile's dY row (CGO channel groups, 2048 B each, plus a
-// zero group when CGO = 1). Per column tap dw and 16-pixel K step, one MMA with
-// A = 4 rows x 32 input channels (M = 128: core matrix j = region j, M stride RS, K
-// stride 128 B) and B = dY (N = 8 NCG output channels 2048 B apart) accumulates
-// D_(dd, dw)[(r, ci)][co] in TMEM over every tile of the CTA; rows r = 0..2 are the taps
-// dh = r - 1 (r = 3 is discarded). Each CTA writes its partial dW once; a fixed-order
-// reduction sums the partials (deterministic).
+// A tile is 128 output pixels of two output rows h0, h0 + 1 of one image plane d; a CTA
+// handles one depth tap dd (3-D: input plane d + dd - 1; the grid's y index) for all its
+// tiles. Its stage holds the input rows h0 - 1 .. h0 + 2 (4 rows x 4 channel groups, the
+// region layout of the forward) and the tile's two dY rows (row o at NCG o groups of 2048
+// B, groups beyond the data zero). Per column tap dw and 16-pixel K step, one MMA with
+// A = 4 input rows x 32 input channels (M = 128: core matrix j = region j, M stride RS,
+// K stride 128 B) and B = both dY rows (N = 2 x 8 NCG: core matrix (o, g) at (o NCG + g)
+// 2048 B) accumulates D_dw[(r, ci)][(o, co)] in TMEM over every tile of the CTA. Entry
+// (r, o) belongs to tap dh = r - 1 - o: six of the eight (r, o) pairs are taps, and two
+// pairs give each tap, so each CTA writes both (o = 0, 1) partials of its 9 taps and a
+// fixed-order reduction adds everything (deterministic). Two dY rows per MMA halve the
+// MMA count per output row, and the three taps dd in separate CTAs keep the accumulators
+// at 3 x N <= 192 TMEM columns, so two CTAs (two MMA issuers) share an SM.
 constexpr int kWgThreads = 192;  // warps 0-3 epilogue, 4 TMA producer, 5 MMA
-constexpr int kWgStages = 4;
+constexpr int kWgStages = 2;
 constexpr int kWgXBytes = 4 * 4 * kRowStride;  // 4 input rows x 4 channel groups
 
 __host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N) {
@@ -578,14 +582,16 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N) {
 
 // XCG = input channel groups (4, or 1 for 8-channel inputs: each input row is then
 // loaded to region 4 r and the regions of groups 1..3 stay zero); NCG = output-channel
-// groups of B: 2 (16 outputs, the second group zero when cout <= 8) or 4.
+// groups per dY row: 2 (16 outputs, the second group zero when cout <= 8) or 4.
+// partial: [ndd][gridDim.x][2][cout][9][cin].
 template <int XCG, int NCG>
 __global__ void __launch_bounds__(kWgThreads) k_conv_wgrad_tc(const __grid_constant__ CUtensorMap xmap,
                                                               const __grid_constant__ CUtensorMap ymap, ConvArgs a,
                                                               int cgo, float *__restrict__ partial) {
-    constexpr int kN = NCG * 8;
-    constexpr int kYBytes = NCG * 2048;
+    constexpr int kN = 2 * NCG * 8;
+    constexpr int kYBytes = 2 * NCG * 2048;
     constexpr int kStage = kWgXBytes + kYBytes;
+    constexpr uint32_t kCols = 3 * kN <= 128 ? 128u : 256u;  // 3 accumulators (dw) of kN columns
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint64_t *full = reinterpret_cast<uint64_t *>(sm + kWgStages * kStage);
@@ -593,11 +599,10 @@ __global__ void __launch_bounds__(kWgThreads) k_conv_wgrad_tc(const __grid_const
     uint64_t *done = empty + kWgStages;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
-    int *used = abort_flag + 1;  // [9]: accumulator (dd, dw) received an MMA
+    int *used = abort_flag + 1;  // [3]: accumulator dw received an MMA
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nch = a.taps3d ? 3 : 1;
+    const int dd = blockIdx.y;   // depth tap (3-D: input plane d + dd - 1)
     constexpr uint32_t kIdesc = idesc_bf16_f32_mn(128, kN);
-    const uint32_t kCols = a.taps3d ? 512u : 128u;  // 9 or 3 accumulators of kN <= 32 columns
     const int rs = 16 * a.G * conv_box_rows(a.G);
 
     if (warp == 0) tmem_alloc(tmem_slot, kCols);
@@ -608,14 +613,16 @@ __global__ void __launch_bounds__(kWgThreads) k_conv_wgrad_tc(const __grid_const
         }
         mbar_init(done, 2);  // the MMAs' commit + the MMA thread's release of used[]
         *abort_flag = 0;
-        for (int i = 0; i < 9; ++i) used[i] = 0;
+        for (int i = 0; i < 3; ++i) used[i] = 0;
         fence_mbar_init();
     }
     if (cgo < NCG) {
-        // output-channel groups beyond the data stay zero in every stage
-        for (int i = tid; i < kWgStages * (NCG - cgo) * 128; i += kWgThreads) {
-            const int s = i / ((NCG - cgo) * 128), q = i - s * (NCG - cgo) * 128;
-            reinterpret_cast<uint4 *>(sm + s * kStage + kWgXBytes + cgo * 2048)[q] = make_uint4(0u, 0u, 0u, 0u);
+        // output-channel groups beyond the data stay zero in both dY rows of every stage
+        const int per = 2 * (NCG - cgo) * 128;  // uint4 per stage
+        for (int i = tid; i < kWgStages * per; i += kWgThreads) {
+            const int s = i / per, q = i - s * per, o = q / ((NCG - cgo) * 128), r = q - o * (NCG - cgo) * 128;
+            reinterpret_cast<uint4 *>(sm + s * kStage + kWgXBytes + (o * NCG + cgo) * 2048)[r] =
+                make_uint4(0u, 0u, 0u, 0u);
         }
     }
     if constexpr (XCG == 1) {
@@ -633,47 +640,46 @@ __global__ void __launch_bounds__(kWgThreads) k_conv_wgrad_tc(const __grid_const
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int ntw = (a.W + 127) / 128;
-    const long long ntiles = (long long)a.nimg * a.D * a.H * ntw;
+    const int ntw = (a.W + 127) / 128, nh = (a.H + 1) / 2;
+    const long long ntiles = (long long)a.nimg * a.D * nh * ntw;
     const long long per_cta = (ntiles + gridDim.x - 1) / gridDim.x;
     const long long t_begin = (long long)blockIdx.x * per_cta;
     const long long my_tiles = t_begin < ntiles ? min(per_cta, ntiles - t_begin) : 0;
-    const long long total = my_tiles * nch;
     const uint32_t sm_u = smem_u32(sm);
 
     if (warp == 4) {
         if (lane == 0) {
             prefetch_tmap(&xmap);
             prefetch_tmap(&ymap);
-            TileCoord tc = tile_coord(t_begin, a.D, a.H, ntw);
-            const uint32_t xbytes = (uint32_t)(4 * XCG * rs), ybytes = (uint32_t)(cgo * 2048);
-            int c = 0, s = 0;
+            TileCoord tc = tile_coord(t_begin, a.D, nh, ntw);
+            const uint32_t xbytes = (uint32_t)(4 * XCG * rs), ybytes = (uint32_t)(2 * cgo * 2048);
+            int s = 0;
             uint32_t ph = 0;
-            for (long long i = 0; i < total; ++i) {
+            for (long long i = 0; i < my_tiles; ++i) {
                 if (i >= kWgStages && !mbar_wait(&empty[s], ph ^ 1u, a.status)) {
                     *abort_flag = 1;
                     break;
                 }
-                const int d2 = tc.d + (nch == 3 ? c - 1 : 0);
+                const int d2 = tc.d + (a.taps3d ? dd - 1 : 0);
                 if (d2 < 0 || d2 >= a.D) {
                     mbar_arrive_expect_tx(&full[s], 0u);  // input plane outside the volume: no MMAs
                 } else {
                     const uint32_t st = sm_u + (uint32_t)(s * kStage);
                     mbar_arrive_expect_tx(&full[s], xbytes + ybytes);
                     if constexpr (XCG == 4) {
-                        tma_load_5d(st, &xmap, 0, tc.w0 / a.G - 1, 0, tc.th - 1, tc.img * a.D + d2, &full[s]);
+                        tma_load_5d(st, &xmap, 0, tc.w0 / a.G - 1, 0, 2 * tc.th - 1, tc.img * a.D + d2, &full[s]);
                     } else {
 #pragma unroll
                         for (int r = 0; r < 4; ++r)
-                            tma_load_5d(st + (uint32_t)(4 * r * rs), &xmap, 0, tc.w0 / a.G - 1, 0, tc.th - 1 + r,
+                            tma_load_5d(st + (uint32_t)(4 * r * rs), &xmap, 0, tc.w0 / a.G - 1, 0, 2 * tc.th - 1 + r,
                                         tc.img * a.D + d2, &full[s]);
                     }
-                    tma_load_5d(st + kWgXBytes, &ymap, 0, tc.w0 / a.G, 0, tc.th, tc.img * a.D + tc.d, &full[s]);
+#pragma unroll
+                    for (int o = 0; o < 2; ++o)
+                        tma_load_5d(st + (uint32_t)(kWgXBytes + o * NCG * 2048), &ymap, 0, tc.w0 / a.G, 0,
+                                    2 * tc.th + o, tc.img * a.D + tc.d, &full[s]);
                 }
-                if (++c == nch) {
-                    c = 0;
-                    tile_next(tc, a.D, a.H, a.W);
-                }
+                tile_next(tc, a.D, nh, a.W);
                 if (++s == kWgStages) {
                     s = 0;
                     ph ^= 1u;
@@ -682,70 +688,70 @@ __global__ void __launch_bounds__(kWgThreads) k_conv_wgrad_tc(const __grid_const
         }
     } else if (warp == 5) {
         if (lane == 0) {
-            // A: M = 4 rows x 4 channel groups, core matrix j = region j (stride RS), K
-            // (pixels) steps of 8 at 128 B; B: N = output channel groups (2048 B apart)
-            TileCoord tc = tile_coord(t_begin, a.D, a.H, ntw);
-            int s = 0, c = 0;
+            TileCoord tc = tile_coord(t_begin, a.D, nh, ntw);
+            int s = 0;
             uint32_t ph = 0;
-            uint32_t usedm = 0;  // bit (dd * 3 + dw): accumulator initialised
-            for (long long i = 0; i < total && !*abort_flag; ++i) {
+            uint32_t usedm = 0;  // bit dw: accumulator initialised
+            for (long long i = 0; i < my_tiles && !*abort_flag; ++i) {
                 if (!mbar_wait(&full[s], ph, a.status)) {
                     *abort_flag = 1;
                     break;
                 }
-                const int d2 = tc.d + (nch == 3 ? c - 1 : 0);
+                const int d2 = tc.d + (a.taps3d ? dd - 1 : 0);
                 if (d2 >= 0 && d2 < a.D) {
                     tc_fence_after();
                     const uint32_t st = sm_u + (uint32_t)(s * kStage);
 #pragma unroll
                     for (int dw = 0; dw < 3; ++dw) {
-                        const int acc = c * 3 + dw;
-                        const uint32_t dt = tmem + (uint32_t)(acc * kN);
+                        const uint32_t dt = tmem + (uint32_t)(dw * kN);
 #pragma unroll
                         for (int ks = 0; ks < 8; ++ks) {
                             // MN-major, no swizzle: the leading byte offset steps along K (8
                             // pixels = 128 B), the stride byte offset along M / N
                             const uint64_t ad = smem_desc_kmajor(st + (uint32_t)((a.G - 1 + dw) * 16 + ks * 256), 128, rs);
                             const uint64_t bd = smem_desc_kmajor(st + kWgXBytes + (uint32_t)(ks * 256), 128, 2048);
-                            mma_bf16(dt, ad, bd, kIdesc, (usedm >> acc) & 1u);
-                            usedm |= 1u << acc;
+                            mma_bf16(dt, ad, bd, kIdesc, (usedm >> dw) & 1u);
+                            usedm |= 1u << dw;
                         }
                     }
                 }
                 mma_commit(&empty[s]);
-                if (++c == nch) {
-                    c = 0;
-                    tile_next(tc, a.D, a.H, a.W);
-                }
+                tile_next(tc, a.D, nh, a.W);
                 if (++s == kWgStages) {
                     s = 0;
                     ph ^= 1u;
                 }
             }
-            for (int k = 0; k < 9; ++k) used[k] = (usedm >> k) & 1u;
-            mma_commit(done);
+            for (int k = 0; k < 3; ++k) used[k] = (usedm >> k) & 1u;
+            // a CTA without tiles (the last ones when the tiles do not divide evenly) issued
+            // no MMA: it arrives directly instead of committing
+            if (usedm) mma_commit(done);
+            else mbar_arrive(done);
             mbar_arrive(done);
         }
     } else {
-        // epilogue (warps 0-3, once): warp w holds accumulator rows 32 w .. 32 w + 31 =
-        // input row r = w, input channel = lane; rows r = 0..2 are the taps dh = r - 1
+        // epilogue (warps 0-3, once): warp w holds accumulator rows 32 w .. 32 w + 31 = input
+        // row r = w, input channel = lane; columns (o, co). Pair (r, o) is tap dh = r - 1 - o.
         const bool ok = mbar_wait(done, 0u, a.status);
         tc_fence_after();
         const int r = warp, ci = lane;
-        const int ntaps = a.taps3d ? 27 : 9;
-        float *pb = partial + (long long)blockIdx.x * a.cout * ntaps * a.cin;
-        for (int acc = 0; acc < nch * 3; ++acc) {
+        const long long slot = ((long long)dd * gridDim.x + blockIdx.x) * 2;
+        const long long per_o = (long long)a.cout * 9 * a.cin;
+        for (int dw = 0; dw < 3; ++dw) {
             float v[kN];
 #pragma unroll
             for (int c0 = 0; c0 < kN; c0 += 16)
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * kN + c0), v + c0);
-            if (r < 3 && ci < a.cin) {
-                const int cc = acc / 3, dw = acc - cc * 3;
-                const int tap = (a.taps3d ? (cc * 3 + r) * 3 : r * 3) + dw;
-                const bool valid = ok && !*abort_flag && used[acc];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(dw * kN + c0), v + c0);
+            const bool valid = ok && !*abort_flag && used[dw];
 #pragma unroll
-                for (int co = 0; co < kN; ++co)
-                    if (co < a.cout) pb[((long long)co * ntaps + tap) * a.cin + ci] = valid ? v[co] : 0.f;
+            for (int o = 0; o < 2; ++o) {
+                const int dh = r - 1 - o;
+                if (dh < -1 || dh > 1 || ci >= a.cin) continue;
+                float *pb = partial + (slot + o) * per_o;
+                const int t9 = (dh + 1) * 3 + dw;
+#pragma unroll
+                for (int co = 0; co < NCG * 8; ++co)
+                    if (co < a.cout) pb[((long long)co * 9 + t9) * a.cin + ci] = valid ? v[o * NCG * 8 + co] : 0.f;
             }
         }
     }
@@ -754,6 +760,25 @@ __global__ void __launch_bounds__(kWgThreads) k_conv_wgrad_tc(const __grid_const
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, kCols);
+    }
+}
+
+// out[co][tap][ci] (+)= sum over the CTAs of their tap's partials (both output-row halves),
+// fixed order: partial [ndd][gpd][2][cout][9][cin], tap = dd * 9 + t9.
+__global__ void k_reduce_wgrad(const float *__restrict__ partial, int gpd, int ndd, int cout, int cin,
+                               float *__restrict__ out, int accumulate) {
+    const int n = cout * 9 * ndd * cin;
+    const long long per_o = (long long)cout * 9 * cin;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int ci = i % cin, tap = (i / cin) % (9 * ndd), co = i / (cin * 9 * ndd);
+        const int d = tap / 9, t9 = tap % 9;
+        const long long e = ((long long)co * 9 + t9) * cin + ci;
+        float s = accumulate ? out[i] : 0.f;
+        for (int b = 0; b < gpd; ++b) {
+            const float *p = partial + ((long long)d * gpd + b) * 2 * per_o;
+            s += p[e] + p[per_o + e];
+        }
+        out[i] = s;
     }
 }
 
@@ -1017,25 +1042,27 @@ static int conv_wgrad_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *d
         int rc = encode_tmap(&ymap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, dy, dims, strides, box);
         if (rc) return rc;
     }
-    constexpr size_t kStage = kWgXBytes + NCG * 2048;
-    const size_t smem = 1024 + kWgStages * kStage + 8 * (2 * kWgStages + 1) + 4 * 12 + 64;
+    constexpr size_t kStage = kWgXBytes + 2 * NCG * 2048;
+    const size_t smem = 1024 + kWgStages * kStage + 8 * (2 * kWgStages + 1) + 4 * 5 + 64;
     CBCT_CUDA_TRY(cudaFuncSetAttribute(k_conv_wgrad_tc<XCG, NCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int ntaps = taps3d ? 27 : 9;
-    const long long ntiles = (long long)nimg * D * H * ((W + 127) / 128);
-    const int grid = (int)std::min<long long>(ntiles, nsm);
-    const int nw = cout * ntaps * cin;
+    const int ndd = taps3d ? 3 : 1;
+    const long long ntiles = (long long)nimg * D * ((H + 1) / 2) * ((W + 127) / 128);
+    const int gpd = (int)std::max<long long>(1, std::min<long long>(ntiles, 2LL * nsm));  // CTAs per depth tap
+    const long long per_cta = 2LL * cout * 9 * cin;
+    const int nw = cout * 9 * ndd * cin;
     const long long nrows = (long long)nimg * D * H;
     const int nbb = (int)std::min<long long>(152LL * 4, nrows);
     const int rpb = (int)((nrows + nbb - 1) / nbb);
     float *part = nullptr;
-    CBCT_CUDA_TRY(cudaMallocAsync((void **)&part, sizeof(float) * ((long long)grid * nw + (long long)nbb * cout), st));
-    float *partb = part + (long long)grid * nw;
-    k_conv_wgrad_tc<XCG, NCG><<<grid, kWgThreads, smem, st>>>(xmap, ymap, a, cgo, part);
+    CBCT_CUDA_TRY(cudaMallocAsync((void **)&part, sizeof(float) * ((long long)ndd * gpd * per_cta + (long long)nbb * cout),
+                                  st));
+    float *partb = part + (long long)ndd * gpd * per_cta;
+    k_conv_wgrad_tc<XCG, NCG><<<dim3(gpd, ndd), kWgThreads, smem, st>>>(xmap, ymap, a, cgo, part);
     k_bias_grad<<<nbb, 256, 0, st>>>(dy, cgo, cout, nrows, W, rpb, partb);
-    k_reduce_rows<<<(nw + 255) / 256, 256, 0, st>>>(part, grid, nw, dw, accumulate);
+    k_reduce_wgrad<<<(nw + 255) / 256, 256, 0, st>>>(part, gpd, ndd, cout, cin, dw, accumulate);
     k_reduce_rows<<<1, 256, 0, st>>>(partb, nbb, cout, db, accumulate);
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(part, st);

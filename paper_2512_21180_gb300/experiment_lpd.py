@@ -108,13 +108,13 @@ def event_seconds(fn, reps: int = 3, warmup: int = 1) -> float:
 
 
 def equal_psnr(geom: Geometry, model: LPD, test, full: torch.Tensor, lam: float, gam: float, sig: float, tau: float,
-               kmax: int = 1600) -> dict:
+               kmax: int = 1600, batch: int = 4) -> dict:
     """The learned reconstruction against PDHG-TV at equal PSNR on a test set of
     (x_true, y, x0 = FDK_w) triples: the mean PSNR over FullFoV of the LPD (FDK_w start +
     unrolled iterations), the smallest PDHG iteration count k* whose mean PSNR reaches it
     (bisection over k, PDHG's mean PSNR taken as non-decreasing in k; doubling past 100
     when needed, up to kmax), and GPU seconds per volume of FDK_w + LPD and of FDK_w + k*
-    PDHG iterations."""
+    PDHG iterations, one volume per call and (batch > 1) `batch` volumes per call."""
     cache = {}
 
     def pdhg_psnr(k):
@@ -156,6 +156,25 @@ def equal_psnr(geom: Geometry, model: LPD, test, full: torch.Tensor, lam: float,
     else:
         out.update({"pdhg_s_at_lpd_psnr": None, "pdhg_over_lpd_at_equal_psnr": None,
                     "note": f"PDHG does not reach the LPD's PSNR within {kmax} iterations"})
+    if batch > 1 and len(test) >= batch:
+        # both methods on `batch` volumes per call (one launch of each kernel covers the batch)
+        mb = LPD(geom, n_iter=model.n_iter, n_mem=model.n_mem, mu_ref=model.mu_ref, residual_input=model.residual_input,
+                 reversible=model.reversible and not model.lire, lire=model.lire, p4=model.p4, max_batch=batch)
+        mb.set_params(model.get_params())
+        if model.reversible:
+            mb.set_perms(model.perms())
+        yb = torch.stack([t[1] for t in test[:batch]])
+        tb_lpd = event_seconds(lambda: mb.forward(yb, ops.fdk(geom, yb))) / batch
+        tb_eq = None
+        if k_eq is not None:
+            tb_eq = event_seconds(lambda: ops.pdhg(geom, yb, ops.fdk(geom, yb), k_eq, lam, gam, sig, tau),
+                                  reps=1) / batch
+        tb100 = event_seconds(lambda: ops.pdhg(geom, yb, ops.fdk(geom, yb), 100, lam, gam, sig, tau), reps=1) / batch
+        out[f"batch{batch}"] = {"lpd_s_per_volume": tb_lpd, "pdhg100_s_per_volume": tb100,
+                                "pdhg100_over_lpd": tb100 / tb_lpd,
+                                "pdhg_s_at_lpd_psnr": tb_eq,
+                                "pdhg_over_lpd_at_equal_psnr": None if tb_eq is None else tb_eq / tb_lpd}
+        mb.close()
     return out
 
 

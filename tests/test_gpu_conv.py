@@ -180,11 +180,17 @@ def test_conv_input_gradient_and_weight_gradient(L, taps3d, dims):
     assert rel(db.double().cpu(), br.grad) <= 1e-5
 
 
-@pytest.mark.parametrize("taps3d,dims,cin,cout,cpout", [(0, (9, 150), 20, 5, 8), (0, (13, 37), 32, 12, 16),
-                                                      (1, (5, 7, 9), 32, 5, 8), (1, (4, 6, 130), 24, 32, 32)])
-def test_conv_weight_gradient_shapes(L, taps3d, dims, cin, cout, cpout):
+@pytest.mark.parametrize("taps3d,dims,cin,cout,cpout,cpin", [
+    (0, (9, 150), 20, 5, 8, 32), (0, (13, 37), 32, 12, 16, 32), (1, (5, 7, 9), 32, 5, 8, 32),
+    (1, (4, 6, 130), 24, 32, 32, 32),
+    # the production shapes: 3-D W = 128 full tiles (odd and even H), 2-D 192 x 256 images,
+    # 8-slot inputs (the blocks' first layers) and 5 outputs in 8 slots (their last layers)
+    (1, (4, 8, 128), 32, 32, 32, 32), (1, (3, 7, 128), 6, 32, 32, 8), (1, (4, 8, 128), 32, 5, 8, 32),
+    (0, (192, 256), 32, 32, 32, 32), (0, (192, 256), 7, 32, 32, 8), (0, (191, 256), 32, 5, 8, 32)])
+def test_conv_weight_gradient_shapes(L, taps3d, dims, cin, cout, cpout, cpin):
     """Weight and bias gradients for fewer input channels and 5 / 12 / 32 outputs
-    (tensor-core path for 32 input slots), ragged W, 2-D and 3-D."""
+    (tensor-core path for 8 or 32 input slots), ragged W, odd H (the last tile's second
+    output row outside the image), 2-D and 3-D."""
     from oracle import lpd_ref as R
     rng = np.random.default_rng(17)
     nimg = 2
@@ -196,9 +202,9 @@ def test_conv_weight_gradient_shapes(L, taps3d, dims, cin, cout, cpout):
     D, H, W = dims if taps3d else (1,) + dims
     dw = torch.zeros((cout, 27 if taps3d else 9, cin), device="cuda")
     db = torch.zeros(cout, device="cuda")
-    x_cl, dy_cl = to_cl(x, 32), to_cl(dy, cpout)
+    x_cl, dy_cl = to_cl(x, cpin), to_cl(dy, cpout)
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    L.check(L.load().cbct_conv_wgrad(x_cl.data_ptr(), 32, cin, dy_cl.data_ptr(), cpout, cout, nimg, D, H, W,
+    L.check(L.load().cbct_conv_wgrad(x_cl.data_ptr(), cpin, cin, dy_cl.data_ptr(), cpout, cout, nimg, D, H, W,
                                      taps3d, dw.data_ptr(), db.data_ptr(), 0, status.data_ptr(),
                                      torch.cuda.current_stream().cuda_stream), "wgrad")
     torch.cuda.synchronize()

@@ -343,8 +343,11 @@ def lpd_timing(warmup: int, reps: int, n_test: int = 8) -> dict:
     g = I.geometry("lpd128")
     geom = Geometry(g)
     full = (ops.fov(geom) >= 0.5).float()
-    model = LPD(geom, n_iter=meta["n_iter"], residual_input=meta["residual_input"])
+    model = LPD(geom, n_iter=meta["n_iter"], n_mem=meta.get("n_mem", 5), residual_input=meta["residual_input"],
+                reversible=meta.get("reversible", False), lire=meta.get("lire", False), p4=meta.get("p4", False))
     model.set_params(np.load(os.path.join(wdir, meta["file"])))
+    if meta.get("perms"):
+        model.set_perms(np.asarray(meta["perms"]))
     nP = ops.opnorm(geom, 0.0, 20)
     gam = nP / math.sqrt(12.0)
     nK = ops.opnorm(geom, gam, 20)
@@ -353,7 +356,9 @@ def lpd_timing(warmup: int, reps: int, n_test: int = 8) -> dict:
     out["weights"] = meta["file"]
     out["workload"] = (f"128^3 at 4 mm, 200 angles, 256x192 at 1.6 mm, +80 mm offset, I0 = {I0:g}; "
                        f"{meta['n_iter']} iterations, width 32"
-                       + (", data-residual channel" if meta["residual_input"] else ""))
+                       + (", data-residual channel" if meta["residual_input"] else "")
+                       + (", LIRE iteration" if meta.get("lire") else ", reversible" if meta.get("reversible") else "")
+                       + (", P4 primal blocks" if meta.get("p4") else ""))
     return out
 
 

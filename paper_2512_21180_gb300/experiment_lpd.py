@@ -215,6 +215,10 @@ def main(argv=None):
     ap.add_argument("--residual-input", action="store_true",
                     help="dual blocks also receive the FP32-formed data residual mu_ref P f_1 - y")
     ap.add_argument("--vol-batch", type=int, default=4, help="volumes per forward/backward call")
+    ap.add_argument("--n-mem", type=int, default=5, help="memory channels (even for --reversible / --lire)")
+    ap.add_argument("--reversible", action="store_true", help="additive coupling + permutations (no stored iterates)")
+    ap.add_argument("--lire", action="store_true", help="the iteration of Algorithm 1 (implies --reversible)")
+    ap.add_argument("--p4", action="store_true", help="P4-equivariant primal blocks")
     ap.add_argument("--lams", default="0.3,1,2,3,5,10,20", help="PDHG lambda grid (tuned on held-out phantoms)")
     ap.add_argument("--init", default=None, help="start from these parameters (.npy)")
     ap.add_argument("--pdhg-iters", type=int, default=100)
@@ -263,7 +267,8 @@ def main(argv=None):
     vb = max(1, min(args.vol_batch, args.batch))
     if args.batch % vb:
         raise SystemExit("--batch must be a multiple of --vol-batch")
-    model = LPD(geom, n_iter=args.n_iter, seed=1, residual_input=args.residual_input, max_batch=vb)
+    model = LPD(geom, n_iter=args.n_iter, n_mem=args.n_mem, seed=1, residual_input=args.residual_input,
+                max_batch=vb, reversible=args.reversible, lire=args.lire, p4=args.p4)
     if args.init:
         model.set_params(widen_params(np.load(args.init), args.n_iter, model.n_mem, model.width,
                                       args.residual_input))
@@ -316,8 +321,11 @@ def main(argv=None):
     if args.save:
         np.save(args.save, model.get_params())
         meta = {"n_iter": args.n_iter, "n_mem": model.n_mem, "width": model.width, "mu_ref": model.mu_ref,
-                "residual_input": bool(args.residual_input), "pdhg_lambda": lam, "workload": WORKLOAD,
+                "residual_input": bool(args.residual_input), "reversible": model.reversible, "lire": model.lire,
+                "p4": model.p4, "pdhg_lambda": lam, "workload": WORKLOAD, "file": os.path.basename(args.save),
                 "train_phantoms": args.train, "train_seconds": time.time() - t_train, "adam_steps": step}
+        if model.reversible:
+            meta["perms"] = model.perms().tolist()
         with open(os.path.splitext(args.save)[0] + ".json", "w") as f:
             json.dump(meta, f, indent=1)
     log["training"] = {"steps": step, "effective_batch": args.batch, "lr": args.lr, "warmup": args.warmup,
@@ -326,8 +334,11 @@ def main(argv=None):
                        "loss_last8": float(np.mean(losses[-8:])) if losses else None}
 
     # ---- evaluate at equal PSNR on the test phantoms (inference one volume at a time)
-    model1 = LPD(geom, n_iter=args.n_iter, seed=1, residual_input=args.residual_input)
+    model1 = LPD(geom, n_iter=args.n_iter, n_mem=args.n_mem, seed=1, residual_input=args.residual_input,
+                 reversible=args.reversible, lire=args.lire, p4=args.p4)
     model1.set_params(model.get_params())
+    if model.reversible:
+        model1.set_perms(model.perms())
     log["eval"] = equal_psnr(geom, model1, test, full, lam, gam, sig, tau)
     print(json.dumps(log), flush=True)
     if args.out:

@@ -4,8 +4,10 @@
 //
 // Every thread of many resident CTAs reads 16-byte words of a 16 KB shared buffer,
 // lane-consecutive (a warp's read is 512 contiguous bytes: four wavefronts, no bank
-// conflict), four independent accumulators, `iters` rounds of four reads. The loads
-// are volatile, so none is hoisted or merged; the adds keep them live.
+// conflict), four independent accumulators, `iters` rounds of four reads. The loads are
+// ld.volatile.shared, which the compiler may neither merge nor hoist out of the loop
+// (a plain load of a loop-invariant address could be read once), and the adds keep
+// them live.
 #include "common.cuh"
 
 namespace cbct {
@@ -25,7 +27,7 @@ __global__ void __launch_bounds__(kProbeThreads) k_smem_probe(int iters, float *
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             float4 v;
-            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+            asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                          : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                          : "r"(base + (uint32_t)(k * kProbeThreads * 16)));
             acc[k].x += v.x; acc[k].y += v.y; acc[k].z += v.z; acc[k].w += v.w;

@@ -143,5 +143,7 @@ def test_p4_lpd_is_equivariant_end_to_end(M):
         out_rot = model.forward(y_rot, rot(x0).contiguous())
         ratios[p4] = rel_l2(to_np(out_rot), to_np(rot(out))) / rel_l2(to_np(out), to_np(x0))
     print(f"equivariance defect relative to the network's change: P4 {ratios[True]:.2e}, plain {ratios[False]:.2e}")
-    assert ratios[True] <= 2e-2, ratios
-    assert ratios[False] >= 0.1, ratios
+    # the P4 network commutes with the rotation up to FP32 / BF16 rounding; the plain one
+    # does not (its defect is the part of its change that is not equivariant)
+    assert ratios[True] <= 1e-4, ratios
+    assert ratios[False] >= 1e-3 and ratios[True] <= 1e-2 * ratios[False], ratios

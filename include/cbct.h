@@ -335,7 +335,8 @@ typedef struct {
  * (n_iter + 1) iterates of n_mem volumes and n_mem projections plus ~4 x 32-channel BF16
  * activations per block. Synchronises. Errors: CBCT_EINVAL unless 1 <= n_iter <= 64,
  * 2 <= n_mem <= 6 (<= 5 with residual_input), width = 32, mu_ref > 0, 0 <= slope <= 1,
- * residual_input is 0 or 1, max_batch <= 64 and max_batch * n_angles <= 65535. */
+ * residual_input is 0 or 1, max_batch <= 64 and max_batch * n_angles <= 65535 (2 *
+ * max_batch * n_angles with lire = 1), and the constraints of the modes below. */
 int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lpd **out);
 void lpd_destroy(cbct_lpd *m);
 

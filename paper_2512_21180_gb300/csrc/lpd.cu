@@ -520,10 +520,10 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     if (d.n_iter < 1 || d.n_iter > 64 || !mem_ok || d.width != 32 || !(d.mu_ref > 0) ||
         !(d.slope >= 0.f && d.slope <= 1.f) || (d.residual_input != 0 && d.residual_input != 1) ||
         (d.reversible != 0 && d.reversible != 1) || (d.lire != 0 && d.lire != 1) || (d.lire && !rev) ||
-        (d.lire && d.residual_input) || maxb > 64 || (long long)maxb * g->dev.na > 65535)
+        (d.lire && d.residual_input) || maxb > 64 || (long long)maxb * g->dev.na * (d.lire ? 2 : 1) > 65535)
         return fail(CBCT_EINVAL, "lpd_create: need 1 <= n_iter <= 64, width == 32, mu_ref > 0, 0 <= slope <= 1, "
                                  "residual_input and reversible 0 or 1, max_batch <= 64, max_batch * n_angles <= "
-                                 "65535, and 2 <= n_mem <= 6 (<= 5 with the residual channel) or, reversible, "
+                                 "65535 (half that with lire), and 2 <= n_mem <= 6 (<= 5 with the residual channel) or, reversible, "
                                  "n_mem even in [2, 8]; lire needs reversible and no residual_input");
     cbct_lpd *m = new (std::nothrow) cbct_lpd();
     if (!m) return fail(CBCT_ENOMEM, "lpd_create: host allocation");

@@ -200,6 +200,45 @@ def profile_pass(args) -> int:
     return 0
 
 
+def time_training(args) -> int:
+    """GPU seconds per volume of one training step (forward with stored states, masked
+    loss, backward, clipping, Adam) on `vol_batch` volumes per call, and of one inference
+    pass, for the configured network on the learned workload. Prints one JSON line."""
+    torch.cuda.set_device(0)
+    geom = Geometry(I.geometry(WORKLOAD))
+    V = ops.fov(geom)
+    vb = args.vol_batch
+    model = LPD(geom, n_iter=args.n_iter, n_mem=args.n_mem, seed=1, residual_input=args.residual_input,
+                max_batch=vb, reversible=args.reversible, lire=args.lire, p4=args.p4)
+    xs, ys = [], []
+    for j in range(vb):
+        x = ops.phantom(geom, I.phantom_params(WORKLOAD, 10_000 + j))
+        _, y = ops.simulate(geom, x, I0, seed=j)
+        xs.append(x)
+        ys.append(y[0])
+    x = torch.stack(xs)
+    y = torch.stack(ys)
+    x0 = ops.fdk(geom, y)
+    Vb = V.expand((vb,) + tuple(V.shape)).contiguous()
+
+    def step():
+        model.zero_grad()
+        out = model.forward(y, x0, save_for_backward=True)
+        _, gr = masked_mse(out, x, Vb, 0.5)
+        model.backward(gr)
+        model.clip_grads(1.0, grad_scale=1.0 / model.mu_ref ** 2)
+        model.adam_step(1e-5, grad_scale=1.0 / model.mu_ref ** 2)
+
+    t_train = event_seconds(step, reps=args.reps, warmup=2) / vb
+    t_inf = event_seconds(lambda: model.forward(y, x0), reps=args.reps, warmup=1) / vb
+    print(json.dumps({"workload": "128^3 at 4 mm, 200 angles, 256x192 at 1.6 mm, +80 mm offset",
+                      "n_iter": args.n_iter, "n_mem": args.n_mem, "residual_input": args.residual_input,
+                      "reversible": model.reversible, "lire": model.lire, "p4": model.p4,
+                      "volumes_per_call": vb, "train_s_per_volume": t_train, "inference_s_per_volume": t_inf}),
+          flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=512)
@@ -224,12 +263,17 @@ def main(argv=None):
     ap.add_argument("--pdhg-iters", type=int, default=100)
     ap.add_argument("--out", default=None)
     ap.add_argument("--save", default=None, help="write the trained parameters (.npy)")
+    ap.add_argument("--time-train", action="store_true",
+                    help="only time one training step and one inference pass per volume (no data sets)")
+    ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--profile", action="store_true",
                     help="only run 2 warm-up passes, then one inference and one training step on one phantom "
                          "(a short command for profilers)")
     args = ap.parse_args(argv)
     if args.profile:
         return profile_pass(args)
+    if args.time_train:
+        return time_training(args)
 
     torch.cuda.set_device(0)
     g = I.geometry(WORKLOAD)

@@ -438,9 +438,11 @@ MEASURED_SM_THROUGHPUT_PCT = {"clinical": {"back_project": 65.5, "forward_projec
 def launches_per_step(geom) -> int:
     """Kernels one forward + adjoint step launches (mirrors the launchers: 3 for the
     staged forward, 2 for the segment gather, +1 when its angles are split)."""
+    import torch
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     nx, ny, nz = geom.g["n"]
     bricks = -(-nx // 16) * -(-ny // 16) * -(-nz // 16)
-    parts = min(16, max(1, -(-152 * 9 // bricks)), geom.g["n_angles"])
+    parts = min(16, max(1, -(-nsm * 9 // bricks)), geom.g["n_angles"])
     return 3 + 2 + (1 if parts > 1 else 0)
 
 

@@ -157,6 +157,10 @@ __device__ __forceinline__ long long vox_index(const GeomDev &g, int ix, int iy,
     return ((long long)iz * g.n[1] + iy) * g.n[0] + ix;
 }
 
+// Streaming multiprocessors of the current device (queried once per device): the unit
+// of the grid-size heuristics.
+int sm_count();
+
 // Host-side geometry object.
 struct Geom;
 GeomDev dev_view(const cbct_geom *g);

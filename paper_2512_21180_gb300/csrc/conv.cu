@@ -1073,7 +1073,7 @@ static int conv_wgrad_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *d
     const long long per_cta = 2LL * cout * 9 * cin;
     const int nw = cout * 9 * ndd * cin;
     const long long nrows = (long long)nimg * D * H;
-    const int nbb = (int)std::min<long long>(152LL * 4, nrows);
+    const int nbb = (int)std::min<long long>(4LL * sm_count(), nrows);
     const int rpb = (int)((nrows + nbb - 1) / nbb);
     float *part = nullptr;
     CBCT_CUDA_TRY(cudaMallocAsync((void **)&part, sizeof(float) * ((long long)ndd * gpd * per_cta + (long long)nbb * cout),
@@ -1104,7 +1104,7 @@ int conv_wgrad(const __nv_bfloat16 *x, int cpin, int cin, const __nv_bfloat16 *d
     }
     const int ntaps = taps3d ? 27 : 9;
     const long long npix = (long long)nimg * D * H * W;
-    const int nblk = (int)std::min<long long>(152LL * 4, std::max<long long>(1, (npix + 1023) / 1024));
+    const int nblk = (int)std::min<long long>(4LL * sm_count(), std::max<long long>(1, (npix + 1023) / 1024));
     const int ppb = (int)((npix + nblk - 1) / nblk);
     const int nw = cout * ntaps * cin;
     float *part = nullptr;

@@ -37,6 +37,19 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 GeomDev dev_view(const cbct_geom *g) { return g->dev; }
 
+int sm_count() {
+    constexpr int kMaxDev = 64;
+    static int cached[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 152;
+    if (!cached[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 152;
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
 }  // namespace cbct
 
 using namespace cbct;

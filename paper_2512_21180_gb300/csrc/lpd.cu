@@ -426,7 +426,7 @@ bool perm_mixes(const int *p, int M) {
 
 int grid_n(long long n) {
     long long b = (n + 255) / 256;
-    return (int)std::max<long long>(1, std::min<long long>(b, 152LL * 32));
+    return (int)std::max<long long>(1, std::min<long long>(b, 32LL * sm_count()));
 }
 
 }  // namespace

@@ -54,7 +54,8 @@ __global__ void k_resample_up(const float *__restrict__ in, long long nch, int n
 
 static int grid_for(long long n) {
     const long long b = (n + 255) / 256;
-    return (int)(b < 1 ? 1 : (b > 152LL * 32 ? 152LL * 32 : b));
+    const long long cap = 32LL * sm_count();
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
 }  // namespace cbct

@@ -489,7 +489,8 @@ static int backward_impl(const cbct_geom *g, const T *proj, T *vol, int batch, i
                 const int nzb = (d.n[2] + kZ3 - 1) / kZ3;
                 const long long base = (long long)((d.n[0] + kB3 - 1) / kB3) * ((d.n[1] + kB3 - 1) / kB3) * nzb * batch;
                 // split the angles so that about 9 CTAs per SM are available (3 resident, 3 waves)
-                int nparts = (int)std::min<long long>(16, std::max<long long>(1, (152LL * 9 + base - 1) / base));
+                const long long want = 9LL * sm_count();
+                int nparts = (int)std::min<long long>(16, std::max<long long>(1, (want + base - 1) / base));
                 nparts = std::min(nparts, d.na);
                 while (nparts > 1 && (long long)nzb * batch * nparts > 65535) --nparts;
                 if ((long long)nzb * batch * nparts > 65535) e = cudaErrorInvalidConfiguration;
@@ -502,7 +503,7 @@ static int backward_impl(const cbct_geom *g, const T *proj, T *vol, int batch, i
                     k_backproject_v3<<<gb3, kThreads3, kSmem3, st>>>(d, pw, vol, accumulate, nparts, partial);
                     e = cudaGetLastError();
                     if (e == cudaSuccess && nparts > 1) {
-                        k_sum_parts<<<152 * 8, 256, 0, st>>>(partial, nparts, nvol, vol, accumulate);
+                        k_sum_parts<<<8 * sm_count(), 256, 0, st>>>(partial, nparts, nvol, vol, accumulate);
                         e = cudaGetLastError();
                     }
                 }

@@ -19,7 +19,7 @@ namespace cbct {
 
 static int grid1(long long n) {
     long long b = (n + 255) / 256;
-    return (int)std::max<long long>(1, std::min<long long>(b, 152LL * 32));
+    return (int)std::max<long long>(1, std::min<long long>(b, 32LL * sm_count()));
 }
 
 // ---- FDK ---------------------------------------------------------------------------

@@ -198,7 +198,8 @@ __global__ void k_fov(GeomDev g, const double *__restrict__ cs, double sid, doub
 
 static int grid_for(long long n) {
     long long b = (n + 255) / 256;
-    return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+    const long long cap = 16LL * sm_count();
+    return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
 }  // namespace cbct

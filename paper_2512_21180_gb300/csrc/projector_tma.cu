@@ -317,10 +317,27 @@ __global__ void __launch_bounds__(kThreads) k_forward_tma(const __grid_constant_
         __syncthreads();
         if (abort_flag) break;
     }
-    if (ray_ok && !abort_flag) {
+    if (consumer && !abort_flag) {
+        // one detector row per warp: when the row's 32 columns lie inside the panel and start
+        // on a 16-byte boundary, every fourth lane stores its own and its three neighbours'
+        // rays as one float4 (eight vector stores per warp); otherwise one float per ray
+        const float r = ray_ok ? acc * step * g.scale : 0.f;
         float *out = proj + (((long long)b * g.na + k) * g.nv + iv) * g.nu + iu;
-        const float r = acc * step * g.scale;
-        *out = accumulate ? *out + r : r;
+        if ((g.nu & 3) == 0 && u0 + kTU <= g.nu && iv < g.nv) {  // uniform over the warp
+            const float r1 = __shfl_down_sync(0xffffffffu, r, 1);
+            const float r2 = __shfl_down_sync(0xffffffffu, r, 2);
+            const float r3 = __shfl_down_sync(0xffffffffu, r, 3);
+            if ((lane & 3) == 0) {
+                float4 v = make_float4(r, r1, r2, r3);
+                if (accumulate) {
+                    const float4 p = *reinterpret_cast<const float4 *>(out);
+                    v.x += p.x; v.y += p.y; v.z += p.z; v.w += p.w;
+                }
+                *reinterpret_cast<float4 *>(out) = v;
+            }
+        } else if (ray_ok) {
+            *out = accumulate ? *out + r : r;
+        }
     }
 }
 

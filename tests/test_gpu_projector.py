@@ -138,8 +138,11 @@ def test_sample_count_matches_oracle(O, P):
     assert abs(got - ns) <= 1e-6 * ns
 
 
-def test_batch_and_accumulate(P):
-    g = CASES["ragged"]
+@pytest.mark.parametrize("name", ["ragged", "small64"])
+def test_batch_and_accumulate(P, name):
+    """Batch independence and accumulate = 1, on a panel whose rows take the forward's
+    per-ray stores (37 columns) and one whose rows take its four-ray vector stores (96)."""
+    g = CASES[name]
     geom = P.Geometry(g)
     x = to_gpu(I.random_volume((3,) + geom.vol_shape, 4))
     pb = P.forward_project(geom, x)

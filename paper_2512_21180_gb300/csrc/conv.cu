@@ -71,10 +71,6 @@ __device__ __forceinline__ void tap_offset(int tap, int taps3d, int &dd, int &dh
     }
 }
 
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 // Epilogue of one output pixel: TMEM accumulators -> bias / activation / residual.
 // `row` = (img * D + d) * H + h, `w` the column; `bias` is held in registers (zeros
 // when the layer has none). The mask is read through the read-only path so that no
@@ -447,27 +443,12 @@ __global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ 
         TileCoord tc = tile_coord(t_begin + q, a.D, nh, ntw);
         for (long long j = q; j < my_tiles; j += kEpiGroups) {
             const int ab = (int)(j % kAcc);
-            const int w = tc.w0 + wq * 32 + lane;
-            if constexpr (EPI == EPI_RESIDUAL_F32) {
-                // the old state of every row of the tile is requested into L2 before waiting for
-                // the accumulator, so its DRAM reads overlap the MMAs and each other (a per-row
-                // load right before its store kept too few reads in flight)
-                if (!a.state_in_zero && w < a.W) {
-#pragma unroll
-                    for (int o = 0; o < RPT; ++o) {
-                        const int h = tc.th * RPT + o;
-                        if (h >= a.H) break;
-                        const long long p = (((long long)tc.img * a.D + tc.d) * a.H + h) * a.W + w;
-                        for (int c = 0; c < a.cout && c < 8; ++c)
-                            prefetch_l2(a.state_in + (long long)(a.smap_on ? a.smap[c] : c) * a.sstride + p);
-                    }
-                }
-            }
             if (!mbar_wait(&accf[ab], (uint32_t)((j / kAcc) & 1), a.status)) {
                 *abort_flag = 1;
                 break;
             }
             tc_fence_after();
+            const int w = tc.w0 + wq * 32 + lane;
             // one output row at a time (NPAD accumulator columns each); the accumulator is
             // released after the last row's columns are in registers
 #pragma unroll

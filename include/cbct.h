@@ -126,7 +126,10 @@ int forward_project(const cbct_geom *g, const float *vol, float *proj, int batch
  * forward_project (same rays, planes and bilinear weights), computed as an
  * atomic-free voxel-driven gather. Scratch: batch * n_angles * nv * nu floats
  * (the ray-weighted projections, plus up to 16 partial volumes when small volumes
- * split the angles), from the stream-ordered pool. Errors: as forward_project, and
+ * split the angles), from the stream-ordered pool. The split follows the size of the
+ * grid (volume and batch), so a volume's result in a batch can differ from its
+ * single-volume result by FP32 summation order; a given geometry and batch size
+ * always give the same bits. Errors: as forward_project, and
  * CBCT_EINVAL when batch * ceil(nz / 4) exceeds 65535 (a grid dimension limit). */
 int back_project(const cbct_geom *g, const float *proj, float *vol, int batch, int accumulate,
                  void *stream);

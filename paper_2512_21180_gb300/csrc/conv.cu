@@ -139,7 +139,7 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *ac
 }
 
 // Row-halo layout. A tile is 128 consecutive output pixels along W of RPT output
-// rows h0 .. h0 + RPT - 1 (RPT from 1 to 6, the most whose weights fit in shared
+// rows h0 .. h0 + RPT - 1 (RPT from 1 to 4, the most whose weights fit in shared
 // memory next to two input stages, see conv_rpt); an A stage holds
 // the NR = RPT + 2 input rows h0 - 1 .. h0 + RPT of one input plane as NR * CGP
 // regions (CGP = CG rounded up to even) of RS = 16 G R bytes (2176, 2112 or 2080;
@@ -899,21 +899,25 @@ static long long conv_packed_bytes(int n_out, int taps3d, int cpin, int rpt) {
     const int cg = cpin / 8;
     return (long long)(taps3d ? 3 : 1) * conv_plane_bytes(rpt, cg == 1, conv_cgp(cg), pad_npad(n_out));
 }
-// Output rows per tile: the most of 6 .. 2 with RPT x NPAD <= kMaxTileN (at least one
-// TMEM accumulator per epilogue warpgroup) whose weights fit in shared memory next to two input stages; 1
-// otherwise. A channel stride of 16 takes at most 2; row pairs (8-channel inputs) take
-// an even count (an odd one leaves a zero partner row). More rows per tile means
-// fewer MMAs per output row, (RPT + 2) / RPT input rows each, which outweighs a deeper
-// input ring: on the 32 -> 32 dual layer, 4 rows with two stages beat 3 rows with
-// three by 6 %.
-constexpr int kMaxRpt = 6, kMaxTileN = 128;
+// Output rows per tile: the most of 4 .. 2 with RPT x NPAD <= kMaxTileN (at least one
+// TMEM accumulator per epilogue warpgroup) whose weights fit in shared memory next to two
+// input stages; 1 otherwise. A channel stride of 16 takes at most 2; row pairs (8-channel
+// inputs) take an even count (an odd one leaves a zero partner row). More rows per tile
+// mean fewer MMAs per output row, (RPT + 2) / RPT input rows each, but fewer input stages
+// in flight; four rows balance the two (192 x 256 images, 200 of them): on the 32 -> 32
+// layer 4 rows with two stages took 270 us against 290 with 3 rows (three stages) and 355
+// with 2 (five); on the 32 -> 5 residual layer 4 rows (three stages) took 262 us against
+// 342 with 6 (two stages), 291 with 3 and 349 with 2.
+constexpr int kMaxRpt = 4, kMaxTileN = 128;
+// Dynamic shared memory a CTA may opt into (227 KB on sm_100-family GPUs).
+constexpr long long kConvSmemLimit = 227 * 1024;
 static int conv_rpt(int taps3d, int H, int cpin, int n_out) {
     const int npad = pad_npad(n_out);
     for (int rpt = kMaxRpt; rpt >= 2; --rpt) {
         if (rpt > H || rpt * npad > kMaxTileN || (cpin == 16 && rpt > 2) || (cpin == 8 && (rpt & 1))) continue;
         const long long fixed = 1024 + ((conv_packed_bytes(n_out, taps3d, cpin, rpt) + 127) & ~127LL) +
                                 8 * (2 * kMaxStages + 2 * kMaxAcc) + 4 * npad + 64;
-        if (fixed + 2LL * conv_stage_bytes(cpin / 8, rpt) <= 220 * 1024) return rpt;
+        if (fixed + 2LL * conv_stage_bytes(cpin / 8, rpt) <= kConvSmemLimit) return rpt;
     }
     return 1;
 }
@@ -933,7 +937,7 @@ static int launch_conv(const ConvArgs &a, cudaStream_t st) {
     constexpr int kN = RPT * NPAD;
     const int bbytes = a.bbytes;
     const size_t fixed = 1024 + ((bbytes + 127) & ~127) + 8 * (2 * kMaxStages + 2 * kMaxAcc) + 4 * NPAD + 64;
-    const size_t limit = 220 * 1024, stage = conv_stage_bytes(CG, RPT);
+    const size_t limit = (size_t)kConvSmemLimit, stage = conv_stage_bytes(CG, RPT);
     if (fixed + 2 * stage > limit) return fail(CBCT_EINVAL, "conv: input rows and weights do not fit in shared memory");
     const int nst = (int)std::min<size_t>(6, (limit - fixed) / stage);
     const size_t smem = fixed + (size_t)nst * stage;
@@ -983,8 +987,6 @@ static int launch_conv_cg(const ConvArgs &a, cudaStream_t st) {
 template <int NPAD, int EPI>
 static int launch_conv_rpt(const ConvArgs &a, int rpt, cudaStream_t st) {
     switch (rpt) {
-        case 6: return launch_conv_cg<NPAD, EPI, 6>(a, st);
-        case 5: return launch_conv_cg<NPAD, EPI, 5>(a, st);
         case 4: return launch_conv_cg<NPAD, EPI, 4>(a, st);
         case 3: return launch_conv_cg<NPAD, EPI, 3>(a, st);
         case 2: return launch_conv_cg<NPAD, EPI, 2>(a, st);
@@ -1197,7 +1199,7 @@ extern "C" int cbct_conv_plan(int taps3d, int H, int cpin, int cin, int cout, in
     const int r = conv_rpt(taps3d ? 1 : 0, H, cpin, n_out), npad = pad_npad(n_out);
     const long long bytes = conv_packed_bytes(n_out, taps3d ? 1 : 0, cpin, r);
     const long long fixed = 1024 + ((bytes + 127) & ~127LL) + 8 * (2 * kMaxStages + 2 * kMaxAcc) + 4 * npad + 64;
-    const long long st = std::min<long long>(6, (220LL * 1024 - fixed) / conv_stage_bytes(cpin / 8, r));
+    const long long st = std::min<long long>(6, (kConvSmemLimit - fixed) / conv_stage_bytes(cpin / 8, r));
     if (rpt) *rpt = r;
     if (packed_bytes) *packed_bytes = bytes;
     if (stages) *stages = (int)st;

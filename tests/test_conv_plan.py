@@ -6,7 +6,7 @@ import itertools
 
 import pytest
 
-SMEM_LIMIT = 220 * 1024
+SMEM_LIMIT = 227 * 1024
 
 
 @pytest.fixture(scope="module")
@@ -51,7 +51,7 @@ def test_plan_invariants(lib, taps3d, H, cpin, n_out):
     cin = min(cpin, 7 if cpin == 8 else cpin)
     rpt, nbytes, stages, acc = plan(lib, taps3d, H, cpin, cin, n_out)
     npad = 16 if n_out <= 16 else 32
-    assert 1 <= rpt <= 6
+    assert 1 <= rpt <= 4
     assert rpt == 1 or rpt <= H
     assert rpt * npad <= 128 or rpt == 1
     # one TMEM accumulator per epilogue warpgroup at least (4 warpgroups)
@@ -70,8 +70,8 @@ def test_plan_invariants(lib, taps3d, H, cpin, n_out):
 def test_plan_of_the_learned_blocks(lib):
     """The 128^3 workload's layers: dual (200 images of 192 x 256) and primal (128^3)."""
     assert plan(lib, 0, 192, 8, 7, 32)[0] == 4     # dual layer 1, row pairs
-    assert plan(lib, 0, 192, 32, 32, 32)[0] == 4   # dual layer 2
-    assert plan(lib, 0, 192, 32, 32, 5)[0] == 6    # dual layer 3 (residual, 16 slots)
+    assert plan(lib, 0, 192, 32, 32, 32)[:3:2] == (4, 3)   # dual layer 2: 4 rows, 3 input stages
+    assert plan(lib, 0, 192, 32, 32, 5)[:3:2] == (4, 3)    # dual layer 3 (residual, 16 slots)
     assert plan(lib, 1, 128, 8, 6, 32)[0] == 4     # primal layer 1
     assert plan(lib, 1, 128, 32, 32, 32)[0] == 2   # primal layer 2 (27-tap weights)
     assert plan(lib, 1, 128, 32, 32, 5)[0] == 4    # primal layer 3

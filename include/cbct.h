@@ -255,17 +255,20 @@ int cbct_landweber(const cbct_geom *g, const float *y, float *x, int batch, int 
  * Gamma and Lambda). Activations are BF16 "row-blocked": image row (img, d, h) holds
  * its channel groups one after the other, element (img, d, h, w, c) at
  * ((((img * D + d) * H + h) * (cp / 8) + c / 8) * W + w) * 8 + c % 8 for cp channel
- * slots per pixel. x: cpin = 8, 16 or 32 slots (slots >= cin zero); w: FP32
+ * slots per pixel. x: cpin = 8, 16, 32 or 64 slots (slots >= cin zero); w: FP32
  * [cout][taps][cin]; bias: FP32 [cout] or NULL.
  * flip = 0: y = conv(x) with cout outputs; flip = 1: the input-gradient convolution
- * (x holds cout channels, mirrored taps, cin outputs). At most 32 outputs.
+ * (x holds cout channels, mirrored taps, cin outputs). At most 64 outputs: more than
+ * 32 run as two launches of at most 32 outputs each, over the same input.
  * epi 0: y = BF16 LeakyReLU(acc + bias), row-blocked with cpout slots (padding 0)
  * epi 1: state[c * sstride + pixel] += acc + bias (FP32, channel-first), c < outputs
  * epi 2: y = BF16 acc * (mask > 0 ? 1 : slope), mask BF16 row-blocked like y (the
  *        LeakyReLU derivative from the forward activation).
  * status: device int, set to 1 if a kernel gives up waiting on its tensor cores.
- * Errors: CBCT_EINVAL for cpin not in {8, 16, 32}, cpin below the input channels,
- * more than 32 outputs, a LeakyReLU slope outside [0, 1] or a missing output buffer.
+ * Errors: CBCT_EINVAL for cpin not in {8, 16, 32, 64}, cpin below the input channels,
+ * more than 64 outputs, a LeakyReLU slope outside [0, 1], a missing output buffer, or
+ * a shape whose weights and two input stages do not fit in shared memory (64 slots
+ * need 3x3 over at least 2 rows, or 3x3x3 at 32 outputs per launch: both fit).
  * Scratch: the packed weights. */
 int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d, const float *w,
               const float *bias, int cin, int cout, int flip, int epi, float slope, void *y, int cpout,
@@ -273,7 +276,8 @@ int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin, int taps3d
 
 /* Tile plan cbct_conv uses for a convolution of this shape (host only: no GPU call):
  * output rows per tile (rpt), bytes of the packed weights (B operand in row units),
- * input stages in shared memory and TMEM accumulators per CTA. Arguments as for
+ * input stages in shared memory and TMEM accumulators per CTA — of the first launch
+ * (its first 32 outputs) when there are more than 32 outputs. Arguments as for
  * cbct_conv; any output pointer may be NULL. Errors: CBCT_EINVAL for an invalid shape. */
 int cbct_conv_plan(int taps3d, int H, int cpin, int cin, int cout, int flip, int *rpt, long long *packed_bytes,
                    int *stages, int *accumulators);
@@ -281,9 +285,10 @@ int cbct_conv_plan(int taps3d, int H, int cpin, int cin, int cout, int flip, int
 /* Weight and bias gradients of the convolution above: dw[co][tap][ci] (+)=
  * sum_p dy[p][co] x[p + tap][ci], db[co] (+)= sum_p dy[p][co]; x BF16 row-blocked
  * with cpin slots, dy BF16 row-blocked with cpout slots (both multiples of 8). With
- * cpin 8 or 32 and cpout 8, 16 or 32 the weight gradient runs on the tensor cores
- * (BF16 operands, FP32 accumulation in TMEM; one partial per CTA), otherwise on the
- * CUDA cores (FP32); partials are reduced in a fixed order (deterministic). status:
+ * cpin 8, 32 or 64 and cpout 8, 16, 32 or 64 the weight gradient runs on the tensor
+ * cores (BF16 operands, FP32 accumulation in TMEM; one partial per CTA; 64 slots as
+ * blocks of 32 x 32 channels), otherwise on the CUDA cores (FP32); partials are
+ * reduced in a fixed order (deterministic). status:
  * device int, set to 1 if a tensor-core kernel gives up waiting on its pipeline (its
  * partial is then written as zero). Errors: CBCT_EINVAL for NULL pointers (status
  * included) or non-positive channel counts. Scratch: the partial sums. */
@@ -313,7 +318,7 @@ typedef struct cbct_lpd cbct_lpd; /* opaque: weights (FP32 master), gradients, A
 typedef struct {
     int n_iter;                  /* unrolled iterations (8 in the learned workload) */
     int n_mem;                   /* primal / dual memory channels, 2..6 (5) */
-    int width;                   /* hidden channels of every block; must be 32 */
+    int width;                   /* hidden channels of every block: 32 or 64 (P4 primal blocks: 32) */
     float slope;                 /* LeakyReLU slope (0.2), in [0, 1] */
     float mu_ref;                /* volume unit (1/mm): f' = f / mu_ref internally (0.02) */
     float bp_scale;              /* scale of P^T (w h_1) in the primal input; <= 0: 1 / max P^T(w 1) */
@@ -335,9 +340,9 @@ typedef struct {
  * -> width -> width -> n_mem) and a primal block Lambda_n (3x3x3: n_mem + 1 -> width ->
  * width -> n_mem), LeakyReLU between convs; parameters flat FP32 per iteration [dual w1
  * b1 w2 b2 w3 b3, primal ...], w as [cout][taps][cin]. Memory, for max_batch volumes:
- * (n_iter + 1) iterates of n_mem volumes and n_mem projections plus ~4 x 32-channel BF16
- * activations per block. Synchronises. Errors: CBCT_EINVAL unless 1 <= n_iter <= 64,
- * 2 <= n_mem <= 6 (<= 5 with residual_input), width = 32, mu_ref > 0, 0 <= slope <= 1,
+ * (n_iter + 1) iterates of n_mem volumes and n_mem projections plus ~4 x width-channel
+ * BF16 activations per block. Synchronises. Errors: CBCT_EINVAL unless 1 <= n_iter <= 64,
+ * 2 <= n_mem <= 6 (<= 5 with residual_input), width 32 or 64, mu_ref > 0, 0 <= slope <= 1,
  * residual_input is 0 or 1, max_batch <= 64 and max_batch * n_angles <= 65535 (2 *
  * max_batch * n_angles with lire = 1), and the constraints of the modes below. */
 int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lpd **out);
@@ -360,7 +365,8 @@ void lpd_destroy(cbct_lpd *m);
  * reversible, NULL pointers or (set) an invalid table. */
 int lpd_get_perms(const cbct_lpd *m, int *host);
 
-/* LIRE mode (desc.lire = 1; Sec. 2.6, Algorithm 1 at one resolution, blocks at width 32):
+/* LIRE mode (desc.lire = 1; Sec. 2.6, Algorithm 1 at one resolution; the paper's dual block is
+ * width 64 with n_mem = 8: K + 4 -> 64 -> 64 -> 4):
  * a separate FP32 reconstruction x next to the reversible latents (halves of K =
  * n_mem / 2 channels), x <- x0, f <- [x0 / mu_ref, s P^T(w y), x0 / mu_ref, ...],
  * h <- y in every channel (s = bp_scale), then per iteration n:

@@ -39,7 +39,7 @@ struct ConvArgs {
     const uint8_t *wpk;      // packed B operand (k_pack_weights)
     const float *bias;       // [cout] or null
     int nimg, D, H, W;
-    int cpin, cin_groups;    // channels per pixel (8, 16 or 32), cpin / 8
+    int cpin, cin_groups;    // channels per pixel (8, 16, 32 or 64), cpin / 8
     int G;                   // pixels per TMA box row (4, 2 or 1: the largest dividing W)
     int taps3d;              // 1: 3x3x3, 0: 3x3 over (H, W)
     int bbytes;              // packed B operand bytes (conv_packed_bytes)
@@ -56,6 +56,8 @@ struct ConvArgs {
     int smap_on;             // EPI_RESIDUAL_F32: channel c lives in plane smap[c] (c < 8) instead of c
     int smap[8];
     int ssub;                // EPI_RESIDUAL_F32: state = state_in - v (undoes an additive update)
+    int qoff;                // first output channel group of this launch (outputs 8 qoff on): a
+                             // layer with more than 32 outputs runs as launches of 32
     int *status;
 };
 
@@ -87,7 +89,8 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *ac
             float old[8];
             long long off[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) off[c] = (long long)(a.smap_on && c0 == 0 ? a.smap[c] : c0 + c) * a.sstride + p;
+            for (int c = 0; c < 8; ++c)
+                off[c] = (long long)(a.smap_on && c0 == 0 ? a.smap[c] : 8 * a.qoff + c0 + c) * a.sstride + p;
 #pragma unroll
             for (int c = 0; c < 8; ++c) old[c] = (c0 + c < a.cout && !a.state_in_zero) ? a.state_in[off[c]] : 0.f;
 #pragma unroll
@@ -98,8 +101,8 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *ac
                 }
         }
     } else {
-        // channel group q of this pixel: (row * (cpout / 8) + q) * W * 8 + w * 8
-        const long long o0 = (row * (a.cpout / 8) * a.W + w) * 8, gstride = (long long)a.W * 8;
+        // channel group qoff + q of this pixel: (row * (cpout / 8) + qoff + q) * W * 8 + w * 8
+        const long long gstride = (long long)a.W * 8, o0 = (row * (a.cpout / 8) * a.W + w) * 8 + a.qoff * gstride;
         __nv_bfloat16 *o = a.y + o0;
         constexpr int kG = NPAD / 8;
         uint4 mv[kG];
@@ -107,11 +110,11 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs &a, const float *ac
         for (int q = 0; q < kG; ++q) {
             mv[q] = make_uint4(0u, 0u, 0u, 0u);
             if constexpr (EPI == EPI_MASK_BF16)
-                if (q * 8 < a.cpout) mv[q] = __ldg(reinterpret_cast<const uint4 *>(a.mask + o0 + q * gstride));
+                if ((a.qoff + q) * 8 < a.cpout) mv[q] = __ldg(reinterpret_cast<const uint4 *>(a.mask + o0 + q * gstride));
         }
 #pragma unroll
         for (int q = 0; q < kG; ++q) {
-            if (q * 8 >= a.cpout) break;
+            if ((a.qoff + q) * 8 >= a.cpout) break;
             // padded channels (c >= cout) hold exact zeros: zero weights and zero bias
             const __nv_bfloat162 *m2 = reinterpret_cast<const __nv_bfloat162 *>(&mv[q]);
             uint32_t packed[4];
@@ -491,9 +494,12 @@ __global__ void __launch_bounds__(kWsThreads) k_conv_tc(const __grid_constant__ 
 // (dd = c - 1, dh = r - 1 - o, dw - 1) with r = j (or 2 j + half), zero when |dh| > 1
 // or r = NR. w: FP32 [cout][taps][cin]. flip = 1 packs the input-gradient
 // convolution instead: output channel co = ci, input channel = co of w, mirrored tap.
+// o0 = first output channel of the launch (0, or 32 for the second half of a layer
+// with more than 32 outputs): slot co holds output o0 + co.
 // Value of element e of the packed B operand (layout above).
 __device__ __forceinline__ float pack_weight_value(const float *__restrict__ w, long long e, int cout, int taps3d,
-                                                   int cin, int cgp, int npad, int rpt, int pair_rows, int flip) {
+                                                   int cin, int cgp, int npad, int rpt, int pair_rows, int flip,
+                                                   int o0) {
     const int ntaps = taps3d ? 27 : 9, nr = rpt + 2;
     const int nu = conv_units(rpt, pair_rows), ng = conv_unit_groups(cgp, pair_rows);
     const long long plane = conv_plane_bytes(rpt, pair_rows, cgp, npad) / 2;  // elements
@@ -519,7 +525,7 @@ __device__ __forceinline__ float pack_weight_value(const float *__restrict__ w, 
         cg = g - dw * cgp;
         r = j;
     }
-    const int o = conv_unit_lo(j, pair_rows) + n / npad, co = n % npad, ch = cg * 8 + kin, dh = r - 1 - o;
+    const int o = conv_unit_lo(j, pair_rows) + n / npad, co = o0 + n % npad, ch = cg * 8 + kin, dh = r - 1 - o;
     float v = 0.f;
     if (r < nr && dh >= -1 && dh <= 1) {
         const int tap = taps3d ? (c * 3 + dh + 1) * 3 + dw : (dh + 1) * 3 + dw;
@@ -533,11 +539,11 @@ __device__ __forceinline__ float pack_weight_value(const float *__restrict__ w, 
 }
 
 __global__ void k_pack_weights(const float *__restrict__ w, int cout, int taps3d, int cin, int cgp, int npad, int rpt,
-                               int pair_rows, int flip, uint8_t *__restrict__ out) {
+                               int pair_rows, int flip, int o0, uint8_t *__restrict__ out) {
     const long long total = (taps3d ? 3 : 1) * (long long)conv_plane_bytes(rpt, pair_rows, cgp, npad) / 2;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x)
         reinterpret_cast<__nv_bfloat16 *>(out)[e] =
-            __float2bfloat16_rn(pack_weight_value(w, e, cout, taps3d, cin, cgp, npad, rpt, pair_rows, flip));
+            __float2bfloat16_rn(pack_weight_value(w, e, cout, taps3d, cin, cgp, npad, rpt, pair_rows, flip, o0));
 }
 
 // Several layers in one launch: job blockIdx.y packs params + w_off into out + out_off.
@@ -547,7 +553,7 @@ __global__ void k_pack_jobs(const ConvPackJob *__restrict__ jobs, const float *_
     __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(out + J.out_off);
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < J.nelem; e += (long long)gridDim.x * blockDim.x)
         o[e] = __float2bfloat16_rn(pack_weight_value(params + J.w_off, e, J.cout, J.taps3d, J.cin, J.cgp, J.npad,
-                                                     J.rpt, J.pair, J.flip));
+                                                     J.rpt, J.pair, J.flip, J.o0));
 }
 
 // ---- weight gradient on the tensor cores ------------------------------------------------
@@ -763,29 +769,31 @@ __global__ void __launch_bounds__(kWgThreads) k_conv_wgrad_tc(const __grid_const
     }
 }
 
-// out[co][tap][ci] (+)= sum over the CTAs of their tap's partials (both output-row halves),
-// fixed order: partial [ndd][gpd][2][cout][9][cin], tap = dd * 9 + t9.
+// out[co0 + co][tap][ci0 + ci] (+)= sum over the CTAs of their tap's partials (both
+// output-row halves), fixed order: partial [ndd][gpd][2][cout][9][cin], tap = dd * 9 + t9;
+// out has cin_full input channels per tap.
 __global__ void k_reduce_wgrad(const float *__restrict__ partial, int gpd, int ndd, int cout, int cin,
-                               float *__restrict__ out, int accumulate) {
+                               float *__restrict__ out, int accumulate, int co0, int ci0, int cin_full) {
     const int n = cout * 9 * ndd * cin;
     const long long per_o = (long long)cout * 9 * cin;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int ci = i % cin, tap = (i / cin) % (9 * ndd), co = i / (cin * 9 * ndd);
         const int d = tap / 9, t9 = tap % 9;
         const long long e = ((long long)co * 9 + t9) * cin + ci;
-        float s = accumulate ? out[i] : 0.f;
+        const long long o = ((long long)(co0 + co) * 9 * ndd + tap) * cin_full + ci0 + ci;
+        float s = accumulate ? out[o] : 0.f;
         for (int b = 0; b < gpd; ++b) {
             const float *p = partial + ((long long)d * gpd + b) * 2 * per_o;
             s += p[e] + p[per_o + e];
         }
-        out[i] = s;
+        out[o] = s;
     }
 }
 
 // partial_b[blk][co] = sum over the block's image rows of dY[row][co] (row-blocked dY,
-// cgo channel groups): thread (group q, column lane) reads 16-byte pixels along the
-// row, then the lanes of each channel are summed in a fixed order.
-__global__ void __launch_bounds__(256) k_bias_grad(const __nv_bfloat16 *__restrict__ dy, int cgo, int cout,
+// cgo channel groups read, rows cgs groups apart): thread (group q, column lane) reads
+// 16-byte pixels along the row, then the lanes of each channel are summed in a fixed order.
+__global__ void __launch_bounds__(256) k_bias_grad(const __nv_bfloat16 *__restrict__ dy, int cgo, int cgs, int cout,
                                                    long long nrows, int W, int rows_per_block,
                                                    float *__restrict__ partial_b) {
     __shared__ float red[256][9];
@@ -793,7 +801,7 @@ __global__ void __launch_bounds__(256) k_bias_grad(const __nv_bfloat16 *__restri
     const long long r0 = (long long)blockIdx.x * rows_per_block, r1 = min(nrows, r0 + rows_per_block);
     float acc[8] = {};
     for (long long row = r0; row < r1; ++row) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(dy + (row * cgo + q) * (long long)W * 8);
+        const uint4 *src = reinterpret_cast<const uint4 *>(dy + (row * cgs + q) * (long long)W * 8);
         for (int w = l; w < W; w += tpq) {
             const uint4 v = __ldg(src + w);
             const __nv_bfloat16 *b = reinterpret_cast<const __nv_bfloat16 *>(&v);
@@ -901,7 +909,7 @@ static long long conv_packed_bytes(int n_out, int taps3d, int cpin, int rpt) {
 }
 // Output rows per tile: the most of 4 .. 2 with RPT x NPAD <= kMaxTileN (at least one
 // TMEM accumulator per epilogue warpgroup) whose weights fit in shared memory next to two
-// input stages; 1 otherwise. A channel stride of 16 takes at most 2; row pairs (8-channel
+// input stages; 1 otherwise. Channel strides of 16 and 64 take at most 2; row pairs (8-channel
 // inputs) take an even count (an odd one leaves a zero partner row). More rows per tile
 // mean fewer MMAs per output row, (RPT + 2) / RPT input rows each, but fewer input stages
 // in flight; four rows balance the two (192 x 256 images, 200 of them): on the 32 -> 32
@@ -914,7 +922,8 @@ constexpr long long kConvSmemLimit = 227 * 1024;
 static int conv_rpt(int taps3d, int H, int cpin, int n_out) {
     const int npad = pad_npad(n_out);
     for (int rpt = kMaxRpt; rpt >= 2; --rpt) {
-        if (rpt > H || rpt * npad > kMaxTileN || (cpin == 16 && rpt > 2) || (cpin == 8 && (rpt & 1))) continue;
+        if (rpt > H || rpt * npad > kMaxTileN || ((cpin == 16 || cpin == 64) && rpt > 2) || (cpin == 8 && (rpt & 1)))
+            continue;
         const long long fixed = 1024 + ((conv_packed_bytes(n_out, taps3d, cpin, rpt) + 127) & ~127LL) +
                                 8 * (2 * kMaxStages + 2 * kMaxAcc) + 4 * npad + 64;
         if (fixed + 2LL * conv_stage_bytes(cpin / 8, rpt) <= kConvSmemLimit) return rpt;
@@ -922,12 +931,12 @@ static int conv_rpt(int taps3d, int H, int cpin, int n_out) {
     return 1;
 }
 
-static int conv_pack(const float *w, int cout, int taps3d, int cin, int cpin, int flip, int rpt, uint8_t *out,
-                     cudaStream_t st) {
-    const int n_out = flip ? cin : cout;
+// Packs the weights of one launch: outputs o0 .. o0 + n_out - 1 of the layer.
+static int conv_pack(const float *w, int cout, int taps3d, int cin, int cpin, int flip, int rpt, int o0, int n_out,
+                     uint8_t *out, cudaStream_t st) {
     const long long total = conv_packed_bytes(n_out, taps3d, cpin, rpt) / 2;
     k_pack_weights<<<(int)std::min<long long>(4096, (total + 255) / 256), 256, 0, st>>>(
-        w, cout, taps3d, cin, ((cpin / 8) + 1) & ~1, pad_npad(n_out), rpt, cpin == 8, flip, out);
+        w, cout, taps3d, cin, ((cpin / 8) + 1) & ~1, pad_npad(n_out), rpt, cpin == 8, flip, o0, out);
     CBCT_LAUNCH_CHECK("conv weight pack");
     return 0;
 }
@@ -979,7 +988,10 @@ static int launch_conv_cg(const ConvArgs &a, cudaStream_t st) {
                 if constexpr (RPT <= 2) return launch_conv<NPAD, EPI, 2, RPT>(a, st);
                 return fail(CBCT_EINVAL, "conv: no tile shape for this channel stride");
             case 4: return launch_conv<NPAD, EPI, 4, RPT>(a, st);
-            default: return fail(CBCT_EINVAL, "conv: channel stride must be 8, 16 or 32");
+            case 8:
+                if constexpr (RPT <= 2) return launch_conv<NPAD, EPI, 8, RPT>(a, st);
+                return fail(CBCT_EINVAL, "conv: no tile shape for this channel stride");
+            default: return fail(CBCT_EINVAL, "conv: channel stride must be 8, 16, 32 or 64");
         }
     }
 }
@@ -1013,12 +1025,15 @@ static int conv_run(const ConvArgs &a0, int n_out, int epi, int rpt, cudaStream_
     return launch_conv_rpt<32, EPI_MASK_BF16>(a, rpt, st);
 }
 
-// Tensor-core weight gradient (32 input channel slots; cpout 8, 16 or 32): per-CTA
-// partial dW, then a fixed-order reduction; db on the CUDA cores.
+// Tensor-core weight gradient of one block of at most 32 x 32 channels: x holds 8 XCG
+// input slots of rows xgs channel groups apart (a view into a wider input), dy cgo output
+// groups of rows ygs groups apart. dw[co0 + co][tap][ci0 + ci] (cin_full channels per tap)
+// (+)= the block's per-CTA partials, reduced in a fixed order; db[co0 + co] (+)= the bias
+// gradient when db is not null (CUDA cores).
 template <int XCG, int NCG>
-static int conv_wgrad_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *dy, int cpout, int cout, int nimg,
-                         int D, int H, int W, int taps3d, float *dw, float *db, int accumulate, int *status,
-                         cudaStream_t st) {
+static int conv_wgrad_tc(const __nv_bfloat16 *x, int xgs, int cin, const __nv_bfloat16 *dy, int cgo, int ygs,
+                         int cout, int nimg, int D, int H, int W, int taps3d, float *dw, int co0, int ci0,
+                         int cin_full, float *db, int accumulate, int *status, cudaStream_t st) {
     ConvArgs a{};
     a.x = x;
     a.nimg = nimg; a.D = D; a.H = H; a.W = W;
@@ -1027,19 +1042,18 @@ static int conv_wgrad_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *d
     a.cout = cout; a.cin = cin;
     a.G = W % 4 == 0 ? 4 : (W % 2 == 0 ? 2 : 1);
     a.status = status;
-    const int cgo = cpout / 8;
     const uint64_t G = (uint64_t)a.G, Wl = (uint64_t)W;
     CUtensorMap xmap, ymap;
     {
         const uint64_t dims[5] = {8 * G, Wl / G, (uint64_t)XCG, (uint64_t)H, (uint64_t)D * nimg};
-        const uint64_t strides[4] = {16 * G, 16 * Wl, 16 * XCG * Wl, 16 * XCG * Wl * H};
+        const uint64_t strides[4] = {16 * G, 16 * Wl, 16 * (uint64_t)xgs * Wl, 16 * (uint64_t)xgs * Wl * H};
         const uint32_t box[5] = {(uint32_t)(8 * G), (uint32_t)conv_box_rows(a.G), (uint32_t)XCG, XCG == 4 ? 4u : 1u, 1};
         int rc = encode_tmap(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, x, dims, strides, box);
         if (rc) return rc;
     }
     {
         const uint64_t dims[5] = {8 * G, Wl / G, (uint64_t)cgo, (uint64_t)H, (uint64_t)D * nimg};
-        const uint64_t strides[4] = {16 * G, 16 * Wl, 16 * Wl * cgo, 16 * Wl * cgo * H};
+        const uint64_t strides[4] = {16 * G, 16 * Wl, 16 * Wl * (uint64_t)ygs, 16 * Wl * (uint64_t)ygs * H};
         const uint32_t box[5] = {(uint32_t)(8 * G), (uint32_t)(128 / a.G), (uint32_t)cgo, 1, 1};
         int rc = encode_tmap(&ymap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, dy, dims, strides, box);
         if (rc) return rc;
@@ -1047,25 +1061,25 @@ static int conv_wgrad_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *d
     constexpr size_t kStage = kWgXBytes + 2 * NCG * 2048;
     const size_t smem = 1024 + kWgStages * kStage + 8 * (2 * kWgStages + 1) + 4 * 5 + 64;
     CBCT_CUDA_TRY(cudaFuncSetAttribute(k_conv_wgrad_tc<XCG, NCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, nsm = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int nsm = sm_count();
     const int ndd = taps3d ? 3 : 1;
     const long long ntiles = (long long)nimg * D * ((H + 1) / 2) * ((W + 127) / 128);
     const int gpd = (int)std::max<long long>(1, std::min<long long>(ntiles, 2LL * nsm));  // CTAs per depth tap
     const long long per_cta = 2LL * cout * 9 * cin;
     const int nw = cout * 9 * ndd * cin;
     const long long nrows = (long long)nimg * D * H;
-    const int nbb = (int)std::min<long long>(4LL * sm_count(), nrows);
+    const int nbb = (int)std::min<long long>(4LL * nsm, nrows);
     const int rpb = (int)((nrows + nbb - 1) / nbb);
     float *part = nullptr;
     CBCT_CUDA_TRY(cudaMallocAsync((void **)&part, sizeof(float) * ((long long)ndd * gpd * per_cta + (long long)nbb * cout),
                                   st));
     float *partb = part + (long long)ndd * gpd * per_cta;
     k_conv_wgrad_tc<XCG, NCG><<<dim3(gpd, ndd), kWgThreads, smem, st>>>(xmap, ymap, a, cgo, part);
-    k_bias_grad<<<nbb, 256, 0, st>>>(dy, cgo, cout, nrows, W, rpb, partb);
-    k_reduce_wgrad<<<(nw + 255) / 256, 256, 0, st>>>(part, gpd, ndd, cout, cin, dw, accumulate);
-    k_reduce_rows<<<1, 256, 0, st>>>(partb, nbb, cout, db, accumulate);
+    k_reduce_wgrad<<<(nw + 255) / 256, 256, 0, st>>>(part, gpd, ndd, cout, cin, dw, accumulate, co0, ci0, cin_full);
+    if (db) {
+        k_bias_grad<<<nbb, 256, 0, st>>>(dy, cgo, ygs, cout, nrows, W, rpb, partb);
+        k_reduce_rows<<<1, 256, 0, st>>>(partb, nbb, cout, db + co0, accumulate);
+    }
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(part, st);
     if (e != cudaSuccess) return cuda_fail(e, "conv wgrad (tensor cores)");
@@ -1073,17 +1087,36 @@ static int conv_wgrad_tc(const __nv_bfloat16 *x, int cin, const __nv_bfloat16 *d
 }
 
 // dW (+)= sum_p dY[p] x X[p + tap], db (+)= sum_p dY[p]; partial sums in scratch.
+// Inputs and outputs of 64 channel slots run as 32 x 32 blocks: views of 4 channel groups
+// (32 W elements apart within a row) of the wider operand.
 int conv_wgrad(const __nv_bfloat16 *x, int cpin, int cin, const __nv_bfloat16 *dy, int cpout, int cout, int nimg, int D,
                int H, int W, int taps3d, float *dw, float *db, int accumulate, int *status, cudaStream_t st) {
-    if ((cpin == 32 || cpin == 8) && cin <= cpin && cout <= cpout && (cpout == 8 || cpout == 16 || cpout == 32)) {
+    if ((cpin == 64 || cpin == 32 || cpin == 8) && cin <= cpin && cout <= cpout &&
+        (cpout == 8 || cpout == 16 || cpout == 32 || cpout == 64)) {
         if (!status) return fail(CBCT_EINVAL, "conv wgrad: NULL status word");
-        if (cpin == 8)
-            return cpout <= 16
-                       ? conv_wgrad_tc<1, 2>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, status, st)
-                       : conv_wgrad_tc<1, 4>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, status, st);
-        return cpout <= 16
-                   ? conv_wgrad_tc<4, 2>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, status, st)
-                   : conv_wgrad_tc<4, 4>(x, cin, dy, cpout, cout, nimg, D, H, W, taps3d, dw, db, accumulate, status, st);
+        const int xgs = cpin / 8, ygs = cpout / 8;
+        for (int xh = 0; 32 * xh < cin; ++xh) {
+            const __nv_bfloat16 *xv = x + 32LL * xh * W;
+            const int cin_s = std::min(32, cin - 32 * xh);
+            for (int yh = 0; 32 * yh < cout; ++yh) {
+                const __nv_bfloat16 *yv = dy + 32LL * yh * W;
+                const int cout_s = std::min(32, cout - 32 * yh), cgo = std::min(4, ygs);
+                float *dbv = xh == 0 ? db : nullptr;
+                int rc;
+                if (cpin == 8)
+                    rc = cgo <= 2 ? conv_wgrad_tc<1, 2>(xv, xgs, cin_s, yv, cgo, ygs, cout_s, nimg, D, H, W, taps3d, dw,
+                                                        32 * yh, 32 * xh, cin, dbv, accumulate, status, st)
+                                  : conv_wgrad_tc<1, 4>(xv, xgs, cin_s, yv, cgo, ygs, cout_s, nimg, D, H, W, taps3d, dw,
+                                                        32 * yh, 32 * xh, cin, dbv, accumulate, status, st);
+                else
+                    rc = cgo <= 2 ? conv_wgrad_tc<4, 2>(xv, xgs, cin_s, yv, cgo, ygs, cout_s, nimg, D, H, W, taps3d, dw,
+                                                        32 * yh, 32 * xh, cin, dbv, accumulate, status, st)
+                                  : conv_wgrad_tc<4, 4>(xv, xgs, cin_s, yv, cgo, ygs, cout_s, nimg, D, H, W, taps3d, dw,
+                                                        32 * yh, 32 * xh, cin, dbv, accumulate, status, st);
+                if (rc) return rc;
+            }
+        }
+        return 0;
     }
     const int ntaps = taps3d ? 27 : 9;
     const long long npix = (long long)nimg * D * H * W;
@@ -1106,21 +1139,31 @@ int conv_wgrad(const __nv_bfloat16 *x, int cpin, int cin, const __nv_bfloat16 *d
 
 using namespace cbct;
 
-long long cbct::conv_plan(int taps3d, int H, int cpin, int cin, int cout, int flip, ConvPackJob *job) {
+static bool conv_cpin_ok(int cpin) { return cpin == 8 || cpin == 16 || cpin == 32 || cpin == 64; }
+
+long long cbct::conv_plan(int taps3d, int H, int cpin, int cin, int cout, int flip, ConvPackJob *jobs) {
     const int n_out = flip ? cin : cout;
-    if ((cpin != 8 && cpin != 16 && cpin != 32) || n_out < 1 || n_out > 32 || !job) return -1;
-    const int rpt = conv_rpt(taps3d, H, cpin, n_out);
-    const long long bytes = conv_packed_bytes(n_out, taps3d, cpin, rpt);
-    job->nelem = bytes / 2;
-    job->cout = cout;
-    job->taps3d = taps3d;
-    job->cin = cin;
-    job->cgp = ((cpin / 8) + 1) & ~1;
-    job->npad = pad_npad(n_out);
-    job->rpt = rpt;
-    job->pair = cpin == 8;
-    job->flip = flip;
-    return bytes;
+    if (!conv_cpin_ok(cpin) || n_out < 1 || n_out > kConvMaxOut || !jobs) return -1;
+    long long off = 0;
+    for (int h = 0; h < conv_halves(n_out); ++h) {
+        const int nh = conv_half_nout(n_out, h);
+        const int rpt = conv_rpt(taps3d, H, cpin, nh);
+        const long long bytes = conv_packed_bytes(nh, taps3d, cpin, rpt);
+        ConvPackJob &job = jobs[h];
+        job.nelem = bytes / 2;
+        job.cout = cout;
+        job.taps3d = taps3d;
+        job.cin = cin;
+        job.cgp = ((cpin / 8) + 1) & ~1;
+        job.npad = pad_npad(nh);
+        job.rpt = rpt;
+        job.pair = cpin == 8;
+        job.flip = flip;
+        job.o0 = 32 * h;
+        job.out_off = off;
+        off += (bytes + 255) & ~255LL;
+    }
+    return off;
 }
 
 int cbct::conv_pack_jobs(const ConvPackJob *jobs, int njobs, long long max_nelem, const float *params, uint8_t *out,
@@ -1136,11 +1179,11 @@ int cbct::conv_apply(const void *x, int nimg, int D, int H, int W, int cpin, int
                      int cin, int cout, int flip, int epi, float slope, void *y, int cpout, const void *mask,
                      const float *state_in, float *state, long long sstride, int *status, cudaStream_t st,
                      const uint8_t *packed, int zero_state_in, const int *smap, int ssub) {
-    if (!x || !w || nimg < 1 || D < 1 || H < 1 || W < 1 || cin < 1 || cout < 1 ||
-        (cpin != 8 && cpin != 16 && cpin != 32) || cpin < (flip ? cout : cin))
+    if (!x || !w || nimg < 1 || D < 1 || H < 1 || W < 1 || cin < 1 || cout < 1 || !conv_cpin_ok(cpin) ||
+        cpin < (flip ? cout : cin))
         return fail(CBCT_EINVAL, "conv: invalid argument (sizes, or cpin below the input channels)");
     const int n_out = flip ? cin : cout;
-    if (n_out > 32) return fail(CBCT_EINVAL, "conv: at most 32 output channels");
+    if (n_out > kConvMaxOut) return fail(CBCT_EINVAL, "conv: at most 64 output channels");
     if (epi < 0 || epi > 2) return fail(CBCT_EINVAL, "conv: bad epilogue");
     if (!(slope >= 0.f && slope <= 1.f)) return fail(CBCT_EINVAL, "conv: LeakyReLU slope must lie in [0, 1]");
     if ((epi == EPI_RESIDUAL_F32 && !state) || (epi != EPI_RESIDUAL_F32 && (!y || cpout < n_out)) ||
@@ -1148,23 +1191,26 @@ int cbct::conv_apply(const void *x, int nimg, int D, int H, int W, int cpin, int
         return fail(CBCT_EINVAL, "conv: missing output");
     if (smap && (epi != EPI_RESIDUAL_F32 || n_out > 8))
         return fail(CBCT_EINVAL, "conv: a plane map needs the residual epilogue and at most 8 outputs");
-    const int rpt = conv_rpt(taps3d, H, cpin, n_out);
-    const long long bytes = conv_packed_bytes(n_out, taps3d, cpin, rpt);
+    ConvPackJob jobs[kConvMaxOut / 32];
+    const long long bytes = conv_plan(taps3d, H, cpin, cin, cout, flip, jobs);
     uint8_t *pk = nullptr;
     int rc = 0;
     if (!packed) {
         CBCT_CUDA_TRY(cudaMallocAsync((void **)&pk, bytes, st));
-        rc = conv_pack(w, cout, taps3d, cin, cpin, flip, rpt, pk, st);
+        for (int h = 0; h < conv_halves(n_out) && rc == 0; ++h)
+            rc = conv_pack(w, cout, taps3d, cin, cpin, flip, jobs[h].rpt, jobs[h].o0, conv_half_nout(n_out, h),
+                           pk + jobs[h].out_off, st);
     }
-    if (rc == 0) {
+    for (int h = 0; h < conv_halves(n_out) && rc == 0; ++h) {
+        const int nh = conv_half_nout(n_out, h);
         ConvArgs a{};
         a.x = static_cast<const __nv_bfloat16 *>(x);
-        a.wpk = packed ? packed : pk;
-        a.bias = bias;
+        a.wpk = (packed ? packed : pk) + jobs[h].out_off;
+        a.bias = bias ? bias + 32 * h : nullptr;
         a.nimg = nimg; a.D = D; a.H = H; a.W = W;
         a.cpin = cpin;
         a.taps3d = taps3d;
-        a.cout = n_out;
+        a.cout = nh;
         a.slope = slope;
         a.y = static_cast<__nv_bfloat16 *>(y);
         a.cpout = cpout;
@@ -1176,8 +1222,9 @@ int cbct::conv_apply(const void *x, int nimg, int D, int H, int W, int cpin, int
         a.smap_on = smap ? 1 : 0;
         for (int c = 0; c < 8; ++c) a.smap[c] = smap ? smap[c < n_out ? c : 0] : c;
         a.ssub = ssub ? 1 : 0;
+        a.qoff = 4 * h;
         a.status = status;
-        rc = conv_run(a, n_out, epi, rpt, st);
+        rc = conv_run(a, nh, epi, jobs[h].rpt, st);
     }
     if (pk) cudaFreeAsync(pk, st);
     return rc;
@@ -1193,11 +1240,11 @@ extern "C" int cbct_conv(const void *x, int nimg, int D, int H, int W, int cpin,
 extern "C" int cbct_conv_plan(int taps3d, int H, int cpin, int cin, int cout, int flip, int *rpt,
                               long long *packed_bytes, int *stages, int *accumulators) {
     const int n_out = flip ? cin : cout;
-    if (H < 1 || cin < 1 || cout < 1 || n_out > 32 || (cpin != 8 && cpin != 16 && cpin != 32) ||
-        cpin < (flip ? cout : cin))
+    if (H < 1 || cin < 1 || cout < 1 || n_out > kConvMaxOut || !conv_cpin_ok(cpin) || cpin < (flip ? cout : cin))
         return fail(CBCT_EINVAL, "cbct_conv_plan: invalid shape");
-    const int r = conv_rpt(taps3d ? 1 : 0, H, cpin, n_out), npad = pad_npad(n_out);
-    const long long bytes = conv_packed_bytes(n_out, taps3d ? 1 : 0, cpin, r);
+    const int n0 = conv_half_nout(n_out, 0);  // the first launch (32 outputs when there are more)
+    const int r = conv_rpt(taps3d ? 1 : 0, H, cpin, n0), npad = pad_npad(n0);
+    const long long bytes = conv_packed_bytes(n0, taps3d ? 1 : 0, cpin, r);
     const long long fixed = 1024 + ((bytes + 127) & ~127LL) + 8 * (2 * kMaxStages + 2 * kMaxAcc) + 4 * npad + 64;
     const long long st = std::min<long long>(6, (kConvSmemLimit - fixed) / conv_stage_bytes(cpin / 8, r));
     if (rpt) *rpt = r;

@@ -47,11 +47,18 @@ int conv_apply(const void *x, int nimg, int D, int H, int W, int cpin, int taps3
 // (weights within the parameter array, bytes within the packed buffer) by the caller.
 struct ConvPackJob {
     long long w_off, out_off, nelem;
-    int cout, taps3d, cin, cgp, npad, rpt, pair, flip;
+    int cout, taps3d, cin, cgp, npad, rpt, pair, flip, o0;
 };
-// Fills job's shape fields for a convolution of the given shape; returns the packed
-// bytes (a multiple of 16), or a negative value for an unsupported shape.
-long long conv_plan(int taps3d, int H, int cpin, int cin, int cout, int flip, ConvPackJob *job);
+// A convolution with more than 32 outputs runs as launches of 32 outputs ("halves"),
+// each with its own packed weights; half h starts conv_half_offset(.., h) bytes into
+// the layer's packed buffer.
+constexpr int kConvMaxOut = 64;
+inline int conv_halves(int n_out) { return (n_out + 31) / 32; }
+inline int conv_half_nout(int n_out, int h) { return n_out - 32 * h < 32 ? n_out - 32 * h : 32; }
+// Fills jobs[0 .. conv_halves(n_out) - 1] (shape fields, o0, and out_off relative to the
+// layer's packed buffer) for a convolution of the given shape; returns the packed bytes
+// of all halves (each rounded up to 256), or a negative value for an unsupported shape.
+long long conv_plan(int taps3d, int H, int cpin, int cin, int cout, int flip, ConvPackJob *jobs);
 // Packs njobs layers (jobs: device array) from params into out in one launch.
 int conv_pack_jobs(const ConvPackJob *jobs, int njobs, long long max_nelem, const float *params, uint8_t *out,
                    cudaStream_t st);

@@ -108,7 +108,8 @@ struct cbct_lpd {
     // every forward layer's weights packed as tensor-core B operands, refreshed by one
     // launch at the start of each forward and backward pass
     uint8_t *wpk = nullptr;
-    ConvPackJob *pack_jobs = nullptr;  // device [layers]
+    ConvPackJob *pack_jobs = nullptr;  // device [n_pack_jobs]: one per launch of 32 outputs
+    int n_pack_jobs = 0;
     long long pack_max_nelem = 0;
 };
 
@@ -443,12 +444,16 @@ static void p4_contract(cbct_lpd *m, cudaStream_t st) {
     k_p4_contract<<<grd, 256, 0, st>>>(m->p4_jobs, m->grads);
 }
 
+// channel slots of a hidden activation (or its gradient) with c channels: 32, or 64 for
+// the wider blocks
+static inline int hs(int c) { return c > 32 ? 64 : 32; }
+
 // forward conv of layer L; the residual epilogue (epi 1) writes state = state_in + conv
 static int conv_fwd(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *x, int cpin, int nimg, int D, int H, int W,
                     int epi, __nv_bfloat16 *y, float *state, long long sstride, cudaStream_t st,
                     const float *state_in = nullptr, int zero_state_in = 0) {
     return conv_apply(x, nimg, D, H, W, cpin, L.taps3d, m->params + L.fw_off, m->params + L.fb_off, L.cin, L.cout, 0, epi,
-                      m->d.slope, y, 32, nullptr, state_in, state, sstride, m->status, st, m->wpk + L.pk_off,
+                      m->d.slope, y, hs(L.cout), nullptr, state_in, state, sstride, m->status, st, m->wpk + L.pk_off,
                       zero_state_in);
 }
 
@@ -457,7 +462,7 @@ static int conv_dx(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *dy, int
                    int epi, __nv_bfloat16 *y, const __nv_bfloat16 *mask, float *state, long long sstride,
                    cudaStream_t st) {
     return cbct_conv(dy, nimg, D, H, W, cp_dy, L.taps3d, m->params + L.fw_off, nullptr, L.cin, L.cout, 1, epi,
-                     m->d.slope, y, 32, mask, state, sstride, m->status, st);
+                     m->d.slope, y, hs(L.cin), mask, state, sstride, m->status, st);
 }
 
 // geometry of the two blocks' tensors for a batch of B volumes: dual = B na images of nv x nu
@@ -493,8 +498,8 @@ static int lpd_iter_fwd(cbct_lpd *m, int n, const float *f_in, const float *h_in
     const Planes pl = dual_planes(m, h_zero ? nullptr : h_in, pf, m->y);
     k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
     if ((rc = conv_fwd(m, Ld[0], m->din, 8, DUAL_DIMS, 0, m->a1, nullptr, 0, st))) return rc;
-    if ((rc = conv_fwd(m, Ld[1], m->a1, 32, DUAL_DIMS, 0, m->a2, nullptr, 0, st))) return rc;
-    if ((rc = conv_fwd(m, Ld[2], m->a2, 32, DUAL_DIMS, 1, nullptr, h_out, NP, st, h_in, h_zero))) return rc;
+    if ((rc = conv_fwd(m, Ld[1], m->a1, hs(Ld[1].cin), DUAL_DIMS, 0, m->a2, nullptr, 0, st))) return rc;
+    if ((rc = conv_fwd(m, Ld[2], m->a2, hs(Ld[2].cin), DUAL_DIMS, 1, nullptr, h_out, NP, st, h_in, h_zero))) return rc;
     // primal block input [f (M), bp_scale P^T (w h_1)]
     rc = back_project_colw(m->g, h_out + 1 * NP, m->wred, bp, B, 0, st);
     if (rc) return rc;
@@ -503,8 +508,8 @@ static int lpd_iter_fwd(cbct_lpd *m, int n, const float *f_in, const float *h_in
     pp.p[M] = bp; pp.s[M] = m->bp_scale;
     k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
     if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) return rc;
-    if ((rc = conv_fwd(m, Lp[1], m->b1, 32, PRIM_DIMS, 0, m->b2, nullptr, 0, st))) return rc;
-    if ((rc = conv_fwd(m, Lp[2], m->b2, 32, PRIM_DIMS, 1, nullptr, f_out, NV, st, f_in))) return rc;
+    if ((rc = conv_fwd(m, Lp[1], m->b1, hs(Lp[1].cin), PRIM_DIMS, 0, m->b2, nullptr, 0, st))) return rc;
+    if ((rc = conv_fwd(m, Lp[2], m->b2, hs(Lp[2].cin), PRIM_DIMS, 1, nullptr, f_out, NV, st, f_in))) return rc;
     CBCT_LAUNCH_CHECK("lpd iteration");
     return 0;
 }
@@ -517,11 +522,11 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     const bool rev = d.reversible != 0;
     const bool mem_ok = rev ? (d.n_mem >= 2 && d.n_mem <= 8 && d.n_mem % 2 == 0)
                             : (d.n_mem >= 2 && d.n_mem <= 6 && (!d.residual_input || d.n_mem <= 5));
-    if (d.n_iter < 1 || d.n_iter > 64 || !mem_ok || d.width != 32 || !(d.mu_ref > 0) ||
+    if (d.n_iter < 1 || d.n_iter > 64 || !mem_ok || (d.width != 32 && d.width != 64) || !(d.mu_ref > 0) ||
         !(d.slope >= 0.f && d.slope <= 1.f) || (d.residual_input != 0 && d.residual_input != 1) ||
         (d.reversible != 0 && d.reversible != 1) || (d.lire != 0 && d.lire != 1) || (d.lire && !rev) ||
         (d.lire && d.residual_input) || maxb > 64 || (long long)maxb * g->dev.na * (d.lire ? 2 : 1) > 65535)
-        return fail(CBCT_EINVAL, "lpd_create: need 1 <= n_iter <= 64, width == 32, mu_ref > 0, 0 <= slope <= 1, "
+        return fail(CBCT_EINVAL, "lpd_create: need 1 <= n_iter <= 64, width 32 or 64, mu_ref > 0, 0 <= slope <= 1, "
                                  "residual_input and reversible 0 or 1, max_batch <= 64, max_batch * n_angles <= "
                                  "65535 (half that with lire), and 2 <= n_mem <= 6 (<= 5 with the residual channel) or, reversible, "
                                  "n_mem even in [2, 8]; lire needs reversible and no residual_input");
@@ -641,13 +646,15 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     al((void **)&m->clip, sizeof(double) * (608 + 2));
     al((void **)&m->bp_saved, sizeof(float) * std::max(1, NI) * NV);
     al((void **)&m->din, sizeof(__nv_bfloat16) * NP * 8);
-    al((void **)&m->a1, sizeof(__nv_bfloat16) * NP * 32);
-    al((void **)&m->a2, sizeof(__nv_bfloat16) * NP * 32);
+    // hidden activations: dual layers at the model width, primal layers at it too (P4: 4 x 8)
+    const int sd = hs(W), sp = d.p4 ? 32 : hs(W);
+    al((void **)&m->a1, sizeof(__nv_bfloat16) * NP * sd);
+    al((void **)&m->a2, sizeof(__nv_bfloat16) * NP * sd);
     al((void **)&m->pin, sizeof(__nv_bfloat16) * NV * 8);
-    al((void **)&m->b1, sizeof(__nv_bfloat16) * NV * 32);
-    al((void **)&m->b2, sizeof(__nv_bfloat16) * NV * 32);
-    al((void **)&m->g32a, sizeof(__nv_bfloat16) * std::max(NP, NV) * 32);
-    al((void **)&m->g32b, sizeof(__nv_bfloat16) * std::max(NP, NV) * 32);
+    al((void **)&m->b1, sizeof(__nv_bfloat16) * NV * sp);
+    al((void **)&m->b2, sizeof(__nv_bfloat16) * NV * sp);
+    al((void **)&m->g32a, sizeof(__nv_bfloat16) * std::max(NP * sd, NV * sp));
+    al((void **)&m->g32b, sizeof(__nv_bfloat16) * std::max(NP * sd, NV * sp));
     al((void **)&m->gsmall, sizeof(__nv_bfloat16) * std::max(NP, NV) * 8);
     al((void **)&m->gf, sizeof(float) * (M + 4) * NV);
     al((void **)&m->gh, sizeof(float) * (M + 5) * NP);
@@ -661,22 +668,28 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     }
     al((void **)&m->status, sizeof(int));
     // forward convolutions: packing plan of every layer (first layer of a block reads 8
-    // channel slots, the others 32; 2-D blocks run over the nv rows, 3-D over ny)
-    std::vector<ConvPackJob> jobs(m->layers.size());
+    // channel slots, the others the hidden width; 2-D blocks run over the nv rows, 3-D
+    // over ny), one job per launch of at most 32 outputs
+    std::vector<ConvPackJob> jobs;
     long long pk_bytes = 0;
     for (size_t i = 0; i < m->layers.size(); ++i) {
         LayerSpec &L = m->layers[i];
-        const long long b = conv_plan(L.taps3d, L.H, i % 3 == 0 ? 8 : 32, L.cin,
-                                      L.cout, 0, &jobs[i]);
+        ConvPackJob lj[kConvMaxOut / 32];
+        const long long b = conv_plan(L.taps3d, L.H, i % 3 == 0 ? 8 : hs(L.cin), L.cin, L.cout, 0, lj);
         if (b < 0) {
             lpd_destroy(m);
             return fail(CBCT_EINVAL, "lpd_create: no convolution plan for layer " + std::to_string(i));
         }
-        jobs[i].w_off = L.fw_off;
-        jobs[i].out_off = L.pk_off = pk_bytes;
-        pk_bytes += (b + 255) & ~255LL;
-        m->pack_max_nelem = std::max(m->pack_max_nelem, jobs[i].nelem);
+        L.pk_off = pk_bytes;
+        for (int h = 0; h < conv_halves(L.cout); ++h) {
+            lj[h].w_off = L.fw_off;
+            lj[h].out_off += pk_bytes;
+            jobs.push_back(lj[h]);
+            m->pack_max_nelem = std::max(m->pack_max_nelem, lj[h].nelem);
+        }
+        pk_bytes += b;
     }
+    m->n_pack_jobs = (int)jobs.size();
     al((void **)&m->wpk, (size_t)pk_bytes);
     al((void **)&m->pack_jobs, sizeof(ConvPackJob) * jobs.size());
     if (e == cudaSuccess)
@@ -789,7 +802,7 @@ static int lpd_forward_impl(cbct_lpd *m, const float *y, const float *x0, const 
     const long long NV = m->nvox * B, NP = m->nproj * B;
     const int M = m->d.n_mem, N = m->d.n_iter;
     p4_expand(m, st);
-    int prc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
+    int prc = conv_pack_jobs(m->pack_jobs, m->n_pack_jobs, m->pack_max_nelem, m->params, m->wpk, st);
     if (prc) return prc;
     CBCT_CUDA_TRY(cudaMemcpyAsync(m->y, y, sizeof(float) * NP, cudaMemcpyDeviceToDevice, st));
     if (f0) {
@@ -871,8 +884,8 @@ static Planes rev_primal_planes(const cbct_lpd *m, const float *f, const int *pf
 // (ssub = 1 subtracts it again)
 static int rev_update(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *act, int nimg, int D, int H, int W,
                       float *state, const int *map2, long long sstride, int ssub, cudaStream_t st) {
-    return conv_apply(act, nimg, D, H, W, 32, L.taps3d, m->params + L.fw_off, m->params + L.fb_off, L.cin, L.cout, 0,
-                      1, m->d.slope, nullptr, 32, nullptr, state, state, sstride, m->status, st, m->wpk + L.pk_off, 0,
+    return conv_apply(act, nimg, D, H, W, hs(L.cin), L.taps3d, m->params + L.fw_off, m->params + L.fb_off, L.cin, L.cout,
+                      0, 1, m->d.slope, nullptr, 32, nullptr, state, state, sstride, m->status, st, m->wpk + L.pk_off, 0,
                       map2, ssub);
 }
 
@@ -883,7 +896,7 @@ static int lpd_rev_forward(cbct_lpd *m, const float *y, const float *x0, float *
     const long long NV = m->nvox * B, NP = m->nproj * B;
     const int M = m->d.n_mem, K = M / 2, N = m->d.n_iter;
     p4_expand(m, st);
-    int rc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
+    int rc = conv_pack_jobs(m->pack_jobs, m->n_pack_jobs, m->pack_max_nelem, m->params, m->wpk, st);
     if (rc) return rc;
     CBCT_CUDA_TRY(cudaMemcpyAsync(m->y, y, sizeof(float) * NP, cudaMemcpyDeviceToDevice, st));
     k_init_f<<<grid_n(NV), 256, 0, st>>>(x0, m->f, NV, M, 1.f / m->d.mu_ref);
@@ -897,14 +910,14 @@ static int lpd_rev_forward(cbct_lpd *m, const float *y, const float *x0, float *
         const Planes pl = rev_dual_planes(m, m->h, phm, NP, m->tproj, m->y);
         k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
         if ((rc = conv_fwd(m, Ld[0], m->din, 8, DUAL_DIMS, 0, m->a1, nullptr, 0, st))) break;
-        if ((rc = conv_fwd(m, Ld[1], m->a1, 32, DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Ld[1], m->a1, hs(Ld[1].cin), DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
         if ((rc = rev_update(m, Ld[2], m->a2, DUAL_DIMS, m->h, phm + K, NP, 0, st))) break;
         // primal: p2 += Lambda([p1, bp_scale P^T (w d2[0])])
         if ((rc = back_project_colw(m->g, m->h + phm[K] * NP, m->wred, m->tvol, B, 0, st))) break;
         const Planes pp = rev_primal_planes(m, m->f, pfm, NV, m->tvol);
         k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
         if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_fwd(m, Lp[1], m->b1, 32, PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Lp[1], m->b1, hs(Lp[1].cin), PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
         if ((rc = rev_update(m, Lp[2], m->b2, PRIM_DIMS, m->f, pfm + K, NV, 0, st))) break;
         map_permute(pfm, m->perm_f[n], M);
         map_permute(phm, m->perm_h[n], M);
@@ -928,7 +941,7 @@ static int lpd_rev_backward(cbct_lpd *m, const float *grad_x, float *grad_y, flo
     const int M = m->d.n_mem, K = M / 2, N = m->d.n_iter;
     float *gf = m->gf, *gh = m->gh, *dW = m->grads;  // gf: M planes + plane M (scratch); gh: M + 3 planes
     p4_expand(m, st);
-    int rc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
+    int rc = conv_pack_jobs(m->pack_jobs, m->n_pack_jobs, m->pack_max_nelem, m->params, m->wpk, st);
     if (rc) return rc;
     int pfm[8], phm[8];
     for (int c = 0; c < M; ++c) { pfm[c] = m->fin_f[c]; phm[c] = m->fin_h[c]; }
@@ -945,26 +958,26 @@ static int lpd_rev_backward(cbct_lpd *m, const float *grad_x, float *grad_y, flo
         const Planes pp = rev_primal_planes(m, m->f, pfm, NV, m->tvol);
         k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
         if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_fwd(m, Lp[1], m->b1, 32, PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Lp[1], m->b1, hs(Lp[1].cin), PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
         if ((rc = rev_update(m, Lp[2], m->b2, PRIM_DIMS, m->f, pfm + K, NV, 1, st))) break;
         // gradients through Lambda: upstream dL/dp2 (identity through the residual)
         Planes gp{};
         for (int c = 0; c < K; ++c) { gp.p[c] = gf + pfm[K + c] * NV; gp.s[c] = 1.f; }
         k_pack8<<<grid_n(NV), 256, 0, st>>>(gp, NV, m->gsmall);
-        if ((rc = conv_wgrad(m->b2, 32, Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].fw_off,
+        if ((rc = conv_wgrad(m->b2, hs(Lp[2].cin), Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].fw_off,
                              dW + Lp[2].fb_off, Lp[2].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Lp[2], m->gsmall, 8, PRIM_DIMS, 2, m->g32a, m->b2, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->b1, 32, Lp[1].cin, m->g32a, 32, Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].fw_off,
+        if ((rc = conv_wgrad(m->b1, hs(Lp[1].cin), Lp[1].cin, m->g32a, hs(Lp[1].cout), Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].fw_off,
                              dW + Lp[1].fb_off, Lp[1].kind ? 0 : 1, m->status, st))) break;
-        if ((rc = conv_dx(m, Lp[1], m->g32a, 32, PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, 32, Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].fw_off,
+        if ((rc = conv_dx(m, Lp[1], m->g32a, hs(Lp[1].cout), PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, hs(Lp[0].cout), Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].fw_off,
                              dW + Lp[0].fb_off, Lp[0].kind ? 0 : 1, m->status, st))) break;
         // dL/d[p1, bp]: p1's planes accumulate, the bp channel goes to scratch plane M
         int mp[8];
         for (int c = 0; c < K; ++c) mp[c] = pfm[c];
         mp[K] = M;
         cudaMemsetAsync(gf + (long long)M * NV, 0, sizeof(float) * NV, st);
-        if ((rc = conv_apply(m->g32b, PRIM_DIMS, 32, Lp[0].taps3d, m->params + Lp[0].fw_off, nullptr, Lp[0].cin,
+        if ((rc = conv_apply(m->g32b, PRIM_DIMS, hs(Lp[0].cout), Lp[0].taps3d, m->params + Lp[0].fw_off, nullptr, Lp[0].cin,
                              Lp[0].cout, 1, 1, m->d.slope, nullptr, 32, nullptr, gf, gf, NV, m->status, st, nullptr,
                              0, mp, 0))) break;
         // bp = bp_scale P^T (w d2[0])  =>  dL/dd2[0] += w bp_scale P (dL/dbp)
@@ -976,26 +989,26 @@ static int lpd_rev_backward(cbct_lpd *m, const float *grad_x, float *grad_y, flo
         const Planes pl = rev_dual_planes(m, m->h, phm, NP, m->tproj, m->y);
         k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
         if ((rc = conv_fwd(m, Ld[0], m->din, 8, DUAL_DIMS, 0, m->a1, nullptr, 0, st))) break;
-        if ((rc = conv_fwd(m, Ld[1], m->a1, 32, DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Ld[1], m->a1, hs(Ld[1].cin), DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
         if ((rc = rev_update(m, Ld[2], m->a2, DUAL_DIMS, m->h, phm + K, NP, 1, st))) break;
         // gradients through Gamma: upstream dL/dd2
         Planes gd{};
         for (int c = 0; c < K; ++c) { gd.p[c] = gh + phm[K + c] * NP; gd.s[c] = 1.f; }
         k_pack8<<<grid_n(NP), 256, 0, st>>>(gd, NP, m->gsmall);
-        if ((rc = conv_wgrad(m->a2, 32, Ld[2].cin, m->gsmall, 8, Ld[2].cout, DUAL_DIMS, 0, dW + Ld[2].fw_off,
+        if ((rc = conv_wgrad(m->a2, hs(Ld[2].cin), Ld[2].cin, m->gsmall, 8, Ld[2].cout, DUAL_DIMS, 0, dW + Ld[2].fw_off,
                              dW + Ld[2].fb_off, Ld[2].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Ld[2], m->gsmall, 8, DUAL_DIMS, 2, m->g32a, m->a2, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->a1, 32, Ld[1].cin, m->g32a, 32, Ld[1].cout, DUAL_DIMS, 0, dW + Ld[1].fw_off,
+        if ((rc = conv_wgrad(m->a1, hs(Ld[1].cin), Ld[1].cin, m->g32a, hs(Ld[1].cout), Ld[1].cout, DUAL_DIMS, 0, dW + Ld[1].fw_off,
                              dW + Ld[1].fb_off, Ld[1].kind ? 0 : 1, m->status, st))) break;
-        if ((rc = conv_dx(m, Ld[1], m->g32a, 32, DUAL_DIMS, 2, m->g32b, m->a1, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, 32, Ld[0].cout, DUAL_DIMS, 0, dW + Ld[0].fw_off,
+        if ((rc = conv_dx(m, Ld[1], m->g32a, hs(Ld[1].cout), DUAL_DIMS, 2, m->g32b, m->a1, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, hs(Ld[0].cout), Ld[0].cout, DUAL_DIMS, 0, dW + Ld[0].fw_off,
                              dW + Ld[0].fb_off, Ld[0].kind ? 0 : 1, m->status, st))) break;
         // dL/d[d1, pf, y (, residual)]: d1's planes accumulate, the others go to scratch planes M..
         const int nin = Ld[0].cin;
         for (int c = 0; c < K; ++c) mp[c] = phm[c];
         for (int c = K; c < nin; ++c) mp[c] = M + (c - K);
         cudaMemsetAsync(gh + (long long)M * NP, 0, sizeof(float) * 3 * NP, st);
-        if ((rc = conv_apply(m->g32b, DUAL_DIMS, 32, Ld[0].taps3d, m->params + Ld[0].fw_off, nullptr, Ld[0].cin,
+        if ((rc = conv_apply(m->g32b, DUAL_DIMS, hs(Ld[0].cout), Ld[0].taps3d, m->params + Ld[0].fw_off, nullptr, Ld[0].cin,
                              Ld[0].cout, 1, 1, m->d.slope, nullptr, 32, nullptr, gh, gh, NP, m->status, st, nullptr,
                              0, mp, 0))) break;
         float *g_pf = gh + (long long)M * NP, *g_y = gh + (long long)(M + 1) * NP;
@@ -1090,7 +1103,7 @@ static int lire_forward(cbct_lpd *m, const float *y, const float *x0, float *x_o
     const long long NV = m->nvox * B, NP = m->nproj * B;
     const int M = m->d.n_mem, K = M / 2, N = m->d.n_iter;
     p4_expand(m, st);
-    int rc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
+    int rc = conv_pack_jobs(m->pack_jobs, m->n_pack_jobs, m->pack_max_nelem, m->params, m->wpk, st);
     if (rc) return rc;
     CBCT_CUDA_TRY(cudaMemcpyAsync(m->y, y, sizeof(float) * NP, cudaMemcpyDeviceToDevice, st));
     CBCT_CUDA_TRY(cudaMemcpyAsync(m->x, x0, sizeof(float) * NV, cudaMemcpyDeviceToDevice, st));
@@ -1107,13 +1120,13 @@ static int lire_forward(cbct_lpd *m, const float *y, const float *x0, float *x_o
         const Planes pl = lire_dual_planes(m, phm, NP);
         k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
         if ((rc = conv_fwd(m, Ld[0], m->din, 8, LIRE_DUAL_DIMS, 0, m->a1, nullptr, 0, st))) break;
-        if ((rc = conv_fwd(m, Ld[1], m->a1, 32, LIRE_DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Ld[1], m->a1, hs(Ld[1].cin), LIRE_DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
         if ((rc = rev_update(m, Ld[2], m->a2, LIRE_DUAL_DIMS, m->h, phm + K, NP, 0, st))) break;
         if ((rc = lire_backproject(m, phm, B, st))) break;
         const Planes pp = lire_primal_planes(m, pfm, NV);
         k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
         if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_fwd(m, Lp[1], m->b1, 32, PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Lp[1], m->b1, hs(Lp[1].cin), PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
         if ((rc = rev_update(m, Lp[2], m->b2, PRIM_DIMS, m->f, pfm + K, NV, 0, st))) break;
         k_outconv<<<grid_n(NV), 256, 0, st>>>(m->x, lire_f_planes(m, pfm, NV), m->params + m->out_off[n],
                                               m->d.mu_ref, NV, M, 1.f);
@@ -1141,7 +1154,7 @@ static int lire_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float 
     float *gy = grad_y ? grad_y : m->tproj2;  // dL/dy is accumulated even when not returned
     float *g_plw = gh + (long long)(M + 4) * NP;
     p4_expand(m, st);
-    int rc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
+    int rc = conv_pack_jobs(m->pack_jobs, m->n_pack_jobs, m->pack_max_nelem, m->params, m->wpk, st);
     if (rc) return rc;
     int pfm[8], phm[8];
     for (int c = 0; c < M; ++c) { pfm[c] = m->fin_f[c]; phm[c] = m->fin_h[c]; }
@@ -1167,26 +1180,26 @@ static int lire_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float 
         const Planes pp = lire_primal_planes(m, pfm, NV);
         k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
         if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_fwd(m, Lp[1], m->b1, 32, PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Lp[1], m->b1, hs(Lp[1].cin), PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
         if ((rc = rev_update(m, Lp[2], m->b2, PRIM_DIMS, m->f, pfm + K, NV, 1, st))) break;
         // gradients through Lambda (upstream dL/dp2)
         Planes gpl{};
         for (int c = 0; c < K; ++c) { gpl.p[c] = gf + pfm[K + c] * NV; gpl.s[c] = 1.f; }
         k_pack8<<<grid_n(NV), 256, 0, st>>>(gpl, NV, m->gsmall);
-        if ((rc = conv_wgrad(m->b2, 32, Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].fw_off,
+        if ((rc = conv_wgrad(m->b2, hs(Lp[2].cin), Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].fw_off,
                              dW + Lp[2].fb_off, Lp[2].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Lp[2], m->gsmall, 8, PRIM_DIMS, 2, m->g32a, m->b2, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->b1, 32, Lp[1].cin, m->g32a, 32, Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].fw_off,
+        if ((rc = conv_wgrad(m->b1, hs(Lp[1].cin), Lp[1].cin, m->g32a, hs(Lp[1].cout), Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].fw_off,
                              dW + Lp[1].fb_off, Lp[1].kind ? 0 : 1, m->status, st))) break;
-        if ((rc = conv_dx(m, Lp[1], m->g32a, 32, PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, 32, Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].fw_off,
+        if ((rc = conv_dx(m, Lp[1], m->g32a, hs(Lp[1].cout), PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, hs(Lp[0].cout), Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].fw_off,
                              dW + Lp[0].fb_off, Lp[0].kind ? 0 : 1, m->status, st))) break;
         // input channels [p1 (K), b_op, x / mu, LW, V] -> p1's planes, scratch M, M+2, M+1, M+3
         int mp[8];
         for (int c = 0; c < K; ++c) mp[c] = pfm[c];
         mp[K] = M; mp[K + 1] = M + 2; mp[K + 2] = M + 1; mp[K + 3] = M + 3;
         cudaMemsetAsync(gf + (long long)M * NV, 0, sizeof(float) * 4 * NV, st);
-        if ((rc = conv_apply(m->g32b, PRIM_DIMS, 32, 1, m->params + Lp[0].fw_off, nullptr, Lp[0].cin, Lp[0].cout, 1, 1,
+        if ((rc = conv_apply(m->g32b, PRIM_DIMS, hs(Lp[0].cout), 1, m->params + Lp[0].fw_off, nullptr, Lp[0].cin, Lp[0].cout, 1, 1,
                              m->d.slope, nullptr, 32, nullptr, gf, gf, NV, m->status, st, nullptr, 0, mp, 0))) break;
         // [P dL/db_op, P dL/dLW] in one forward projection of the adjacent scratch planes M, M+1
         if ((rc = forward_project(m->g, gf + (long long)M * NV, m->t2p, 2 * B, 0, sv))) break;
@@ -1204,25 +1217,25 @@ static int lire_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float 
         const Planes pl = lire_dual_planes(m, phm, NP);
         k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
         if ((rc = conv_fwd(m, Ld[0], m->din, 8, LIRE_DUAL_DIMS, 0, m->a1, nullptr, 0, st))) break;
-        if ((rc = conv_fwd(m, Ld[1], m->a1, 32, LIRE_DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Ld[1], m->a1, hs(Ld[1].cin), LIRE_DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
         if ((rc = rev_update(m, Ld[2], m->a2, LIRE_DUAL_DIMS, m->h, phm + K, NP, 1, st))) break;
         // gradients through Gamma (upstream dL/dd2)
         Planes gdl{};
         for (int c = 0; c < K; ++c) { gdl.p[c] = gh + phm[K + c] * NP; gdl.s[c] = 1.f; }
         k_pack8<<<grid_n(NP), 256, 0, st>>>(gdl, NP, m->gsmall);
-        if ((rc = conv_wgrad(m->a2, 32, Ld[2].cin, m->gsmall, 8, Ld[2].cout, LIRE_DUAL_DIMS, 1, dW + Ld[2].fw_off,
+        if ((rc = conv_wgrad(m->a2, hs(Ld[2].cin), Ld[2].cin, m->gsmall, 8, Ld[2].cout, LIRE_DUAL_DIMS, 1, dW + Ld[2].fw_off,
                              dW + Ld[2].fb_off, Ld[2].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Ld[2], m->gsmall, 8, LIRE_DUAL_DIMS, 2, m->g32a, m->a2, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->a1, 32, Ld[1].cin, m->g32a, 32, Ld[1].cout, LIRE_DUAL_DIMS, 1, dW + Ld[1].fw_off,
+        if ((rc = conv_wgrad(m->a1, hs(Ld[1].cin), Ld[1].cin, m->g32a, hs(Ld[1].cout), Ld[1].cout, LIRE_DUAL_DIMS, 1, dW + Ld[1].fw_off,
                              dW + Ld[1].fb_off, Ld[1].kind ? 0 : 1, m->status, st))) break;
-        if ((rc = conv_dx(m, Ld[1], m->g32a, 32, LIRE_DUAL_DIMS, 2, m->g32b, m->a1, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, 32, Ld[0].cout, LIRE_DUAL_DIMS, 1, dW + Ld[0].fw_off,
+        if ((rc = conv_dx(m, Ld[1], m->g32a, hs(Ld[1].cout), LIRE_DUAL_DIMS, 2, m->g32b, m->a1, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, hs(Ld[0].cout), Ld[0].cout, LIRE_DUAL_DIMS, 1, dW + Ld[0].fw_off,
                              dW + Ld[0].fb_off, Ld[0].kind ? 0 : 1, m->status, st))) break;
         // input channels [d1 (K), mu P p2[0], P x, y, P x - y] -> d1's planes, scratch M .. M+3
         for (int c = 0; c < K; ++c) mp[c] = phm[c];
         for (int c = 0; c < 4; ++c) mp[K + c] = M + c;
         cudaMemsetAsync(gh + (long long)M * NP, 0, sizeof(float) * 4 * NP, st);
-        if ((rc = conv_apply(m->g32b, LIRE_DUAL_DIMS, 32, 1, m->params + Ld[0].fw_off, nullptr, Ld[0].cin, Ld[0].cout,
+        if ((rc = conv_apply(m->g32b, LIRE_DUAL_DIMS, hs(Ld[0].cout), 1, m->params + Ld[0].fw_off, nullptr, Ld[0].cin, Ld[0].cout,
                              1, 1, m->d.slope, nullptr, 32, nullptr, gh, gh, NP, m->status, st, nullptr, 0, mp,
                              0))) break;
         float *g_pp2 = gh + (long long)M * NP, *g_px = gh + (long long)(M + 1) * NP;
@@ -1314,7 +1327,7 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
     // the recomputed forward convolutions read the packed weights: refresh them (the
     // parameters may have changed since the forward pass)
     p4_expand(m, st);
-    int prc = conv_pack_jobs(m->pack_jobs, (int)m->layers.size(), m->pack_max_nelem, m->params, m->wpk, st);
+    int prc = conv_pack_jobs(m->pack_jobs, m->n_pack_jobs, m->pack_max_nelem, m->params, m->wpk, st);
     if (prc) return prc;
     // dL/df_N: channel 0 gets mu_ref dL/dx; plus the given state gradients
     cudaMemsetAsync(gf, 0, sizeof(float) * (M + 1) * NV, st);
@@ -1333,30 +1346,30 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
         const Planes pl = dual_planes(m, h_n, pf_n, m->y);
         k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
         if ((rc = conv_fwd(m, Ld[0], m->din, 8, DUAL_DIMS, 0, m->a1, nullptr, 0, st))) break;
-        if ((rc = conv_fwd(m, Ld[1], m->a1, 32, DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Ld[1], m->a1, hs(Ld[1].cin), DUAL_DIMS, 0, m->a2, nullptr, 0, st))) break;
         // recompute the primal block input and activations (P^T (w h_{n+1}) kept)
         Planes pp{};
         for (int c = 0; c < M; ++c) { pp.p[c] = f_n + c * NV; pp.s[c] = 1.f; }
         pp.p[M] = m->bp_saved + (long long)n * NV; pp.s[M] = m->bp_scale;
         k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
         if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_fwd(m, Lp[1], m->b1, 32, PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
+        if ((rc = conv_fwd(m, Lp[1], m->b1, hs(Lp[1].cin), PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
 
         // ---- primal block backward: upstream gf[0..M) = dL/df_{n+1}
         Planes gp{};
         for (int c = 0; c < M; ++c) { gp.p[c] = gf + c * NV; gp.s[c] = 1.f; }
         k_pack8<<<grid_n(NV), 256, 0, st>>>(gp, NV, m->gsmall);
-        if ((rc = conv_wgrad(m->b2, 32, Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].fw_off,
+        if ((rc = conv_wgrad(m->b2, hs(Lp[2].cin), Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].fw_off,
                              dW + Lp[2].fb_off, Lp[2].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Lp[2], m->gsmall, 8, PRIM_DIMS, 2, m->g32a, m->b2, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->b1, 32, Lp[1].cin, m->g32a, 32, Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].fw_off,
+        if ((rc = conv_wgrad(m->b1, hs(Lp[1].cin), Lp[1].cin, m->g32a, hs(Lp[1].cout), Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].fw_off,
                              dW + Lp[1].fb_off, Lp[1].kind ? 0 : 1, m->status, st))) break;
-        if ((rc = conv_dx(m, Lp[1], m->g32a, 32, PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, 32, Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].fw_off,
+        if ((rc = conv_dx(m, Lp[1], m->g32a, hs(Lp[1].cout), PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, hs(Lp[0].cout), Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].fw_off,
                              dW + Lp[0].fb_off, Lp[0].kind ? 0 : 1, m->status, st))) break;
         // dL/d(primal input) -> gf[0..M) += (residual path kept), gf[M] = dL/d(bp channel)
         cudaMemsetAsync(gf + (long long)M * NV, 0, sizeof(float) * NV, st);
-        if ((rc = conv_dx(m, Lp[0], m->g32b, 32, PRIM_DIMS, 1, nullptr, nullptr, gf, NV, st))) break;
+        if ((rc = conv_dx(m, Lp[0], m->g32b, hs(Lp[0].cout), PRIM_DIMS, 1, nullptr, nullptr, gf, NV, st))) break;
         // bp = bp_scale P^T (w h_1)  =>  dL/dh_{n+1}[1] += w * bp_scale * P (dL/dbp)
         if ((rc = forward_project(m->g, gf + (long long)M * NV, m->tproj, B, 0, sv))) break;
         k_scale_cols<<<grid_n(NP), 256, 0, st>>>(m->tproj, m->wred, NP, m->g->dev.nu, m->bp_scale, m->tproj2);
@@ -1366,18 +1379,18 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
         Planes gd{};
         for (int c = 0; c < M; ++c) { gd.p[c] = gh + c * NP; gd.s[c] = 1.f; }
         k_pack8<<<grid_n(NP), 256, 0, st>>>(gd, NP, m->gsmall);
-        if ((rc = conv_wgrad(m->a2, 32, Ld[2].cin, m->gsmall, 8, Ld[2].cout, DUAL_DIMS, 0, dW + Ld[2].fw_off,
+        if ((rc = conv_wgrad(m->a2, hs(Ld[2].cin), Ld[2].cin, m->gsmall, 8, Ld[2].cout, DUAL_DIMS, 0, dW + Ld[2].fw_off,
                              dW + Ld[2].fb_off, Ld[2].kind ? 0 : 1, m->status, st))) break;
         if ((rc = conv_dx(m, Ld[2], m->gsmall, 8, DUAL_DIMS, 2, m->g32a, m->a2, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->a1, 32, Ld[1].cin, m->g32a, 32, Ld[1].cout, DUAL_DIMS, 0, dW + Ld[1].fw_off,
+        if ((rc = conv_wgrad(m->a1, hs(Ld[1].cin), Ld[1].cin, m->g32a, hs(Ld[1].cout), Ld[1].cout, DUAL_DIMS, 0, dW + Ld[1].fw_off,
                              dW + Ld[1].fb_off, Ld[1].kind ? 0 : 1, m->status, st))) break;
-        if ((rc = conv_dx(m, Ld[1], m->g32a, 32, DUAL_DIMS, 2, m->g32b, m->a1, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, 32, Ld[0].cout, DUAL_DIMS, 0, dW + Ld[0].fw_off,
+        if ((rc = conv_dx(m, Ld[1], m->g32a, hs(Ld[1].cout), DUAL_DIMS, 2, m->g32b, m->a1, nullptr, 0, st))) break;
+        if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, hs(Ld[0].cout), Ld[0].cout, DUAL_DIMS, 0, dW + Ld[0].fw_off,
                              dW + Ld[0].fb_off, Ld[0].kind ? 0 : 1, m->status, st))) break;
         // dL/d(dual input): gh[0..M) += (residual), gh[M] = dL/d(pf channel), gh[M+1] = dL/d(y channel),
         // gh[M+2] = dL/d(residual channel mu_ref pf - y)
         cudaMemsetAsync(gh + (long long)M * NP, 0, sizeof(float) * (ND - M) * NP, st);
-        if ((rc = conv_dx(m, Ld[0], m->g32b, 32, DUAL_DIMS, 1, nullptr, nullptr, gh, NP, st))) break;
+        if ((rc = conv_dx(m, Ld[0], m->g32b, hs(Ld[0].cout), DUAL_DIMS, 1, nullptr, nullptr, gh, NP, st))) break;
         float *g_pf = gh + (long long)M * NP, *g_y = gh + (long long)(M + 1) * NP;
         if (m->d.residual_input) {
             // residual channel = pf channel - y: its gradient adds to the pf channel's and

@@ -158,8 +158,9 @@ def equal_psnr(geom: Geometry, model: LPD, test, full: torch.Tensor, lam: float,
                     "note": f"PDHG does not reach the LPD's PSNR within {kmax} iterations"})
     if batch > 1 and len(test) >= batch:
         # both methods on `batch` volumes per call (one launch of each kernel covers the batch)
-        mb = LPD(geom, n_iter=model.n_iter, n_mem=model.n_mem, mu_ref=model.mu_ref, residual_input=model.residual_input,
-                 reversible=model.reversible and not model.lire, lire=model.lire, p4=model.p4, max_batch=batch)
+        mb = LPD(geom, n_iter=model.n_iter, n_mem=model.n_mem, width=model.width, mu_ref=model.mu_ref,
+                 residual_input=model.residual_input, reversible=model.reversible and not model.lire, lire=model.lire,
+                 p4=model.p4, max_batch=batch)
         mb.set_params(model.get_params())
         if model.reversible:
             mb.set_perms(model.perms())
@@ -208,8 +209,9 @@ def time_training(args) -> int:
     geom = Geometry(I.geometry(WORKLOAD))
     V = ops.fov(geom)
     vb = args.vol_batch
-    model = LPD(geom, n_iter=args.n_iter, n_mem=args.n_mem, seed=1, residual_input=args.residual_input,
-                max_batch=vb, reversible=args.reversible, lire=args.lire, p4=args.p4)
+    model = LPD(geom, n_iter=args.n_iter, n_mem=args.n_mem, width=args.width, seed=1,
+                residual_input=args.residual_input, max_batch=vb, reversible=args.reversible, lire=args.lire,
+                p4=args.p4)
     xs, ys = [], []
     for j in range(vb):
         x = ops.phantom(geom, I.phantom_params(WORKLOAD, 10_000 + j))
@@ -232,7 +234,8 @@ def time_training(args) -> int:
     t_train = event_seconds(step, reps=args.reps, warmup=2) / vb
     t_inf = event_seconds(lambda: model.forward(y, x0), reps=args.reps, warmup=1) / vb
     print(json.dumps({"workload": "128^3 at 4 mm, 200 angles, 256x192 at 1.6 mm, +80 mm offset",
-                      "n_iter": args.n_iter, "n_mem": args.n_mem, "residual_input": args.residual_input,
+                      "n_iter": args.n_iter, "n_mem": args.n_mem, "width": args.width,
+                      "residual_input": args.residual_input,
                       "reversible": model.reversible, "lire": model.lire, "p4": model.p4,
                       "volumes_per_call": vb, "train_s_per_volume": t_train, "inference_s_per_volume": t_inf}),
           flush=True)
@@ -255,6 +258,7 @@ def main(argv=None):
                     help="dual blocks also receive the FP32-formed data residual mu_ref P f_1 - y")
     ap.add_argument("--vol-batch", type=int, default=4, help="volumes per forward/backward call")
     ap.add_argument("--n-mem", type=int, default=5, help="memory channels (even for --reversible / --lire)")
+    ap.add_argument("--width", type=int, default=32, help="hidden channels of the blocks: 32 or 64")
     ap.add_argument("--reversible", action="store_true", help="additive coupling + permutations (no stored iterates)")
     ap.add_argument("--lire", action="store_true", help="the iteration of Algorithm 1 (implies --reversible)")
     ap.add_argument("--p4", action="store_true", help="P4-equivariant primal blocks")
@@ -311,8 +315,9 @@ def main(argv=None):
     vb = max(1, min(args.vol_batch, args.batch))
     if args.batch % vb:
         raise SystemExit("--batch must be a multiple of --vol-batch")
-    model = LPD(geom, n_iter=args.n_iter, n_mem=args.n_mem, seed=1, residual_input=args.residual_input,
-                max_batch=vb, reversible=args.reversible, lire=args.lire, p4=args.p4)
+    model = LPD(geom, n_iter=args.n_iter, n_mem=args.n_mem, width=args.width, seed=1,
+                residual_input=args.residual_input, max_batch=vb, reversible=args.reversible, lire=args.lire,
+                p4=args.p4)
     if args.init:
         model.set_params(widen_params(np.load(args.init), args.n_iter, model.n_mem, model.width,
                                       args.residual_input))
@@ -378,8 +383,8 @@ def main(argv=None):
                        "loss_last8": float(np.mean(losses[-8:])) if losses else None}
 
     # ---- evaluate at equal PSNR on the test phantoms (inference one volume at a time)
-    model1 = LPD(geom, n_iter=args.n_iter, n_mem=args.n_mem, seed=1, residual_input=args.residual_input,
-                 reversible=args.reversible, lire=args.lire, p4=args.p4)
+    model1 = LPD(geom, n_iter=args.n_iter, n_mem=args.n_mem, width=args.width, seed=1,
+                 residual_input=args.residual_input, reversible=args.reversible, lire=args.lire, p4=args.p4)
     model1.set_params(model.get_params())
     if model.reversible:
         model1.set_perms(model.perms())

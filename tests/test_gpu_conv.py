@@ -280,3 +280,100 @@ def test_conv_full_size_tiles(L, name, taps3d, dims, cin, cout, nimg, kind):
         run_conv(L, to_cl(x, cp), dims, taps3d, wg, b.float().cuda(), cin, cout, 0, 1, 8, state=state)
         ref = state0 + conv.movedim(1, 0)
         assert rel(state.double().cpu(), ref) <= 1e-5, rel(state.double().cpu(), ref)
+
+
+WIDE = [
+    # 64-channel layers (the paper's dual block width): inputs of 64 slots on the channel
+    # stride-64 kernels, more than 32 outputs as two launches into one 64-slot output
+    ("2d_64to64", 0, (19, 150), 64, 64, 2, "act"),
+    ("3d_64to64", 1, (5, 7, 130), 64, 64, 1, "act"),
+    ("3d_8to64", 1, (5, 7, 130), 8, 64, 1, "act"),
+    ("2d_12to40", 0, (19, 150), 12, 40, 2, "act"),
+    ("3d_64to4", 1, (5, 7, 130), 64, 4, 1, "res"),
+    ("2d_64to4", 0, (19, 150), 64, 4, 2, "res"),
+    ("3d_dx_64to64", 1, (5, 7, 130), 64, 64, 1, "dx"),
+    ("3d_dx_4to64", 1, (5, 7, 130), 64, 4, 1, "dx"),
+    ("2d_dx_64to8", 0, (19, 150), 8, 64, 2, "dxres"),
+]
+
+
+def slots(c):
+    return 8 if c <= 8 else (16 if c <= 16 else (32 if c <= 32 else 64))
+
+
+@pytest.mark.parametrize("name,taps3d,dims,cin,cout,nimg,kind", WIDE)
+def test_conv_wide_layers(L, name, taps3d, dims, cin, cout, nimg, kind):
+    """Forward, residual update and masked input gradient with 64 input slots and with
+    more than 32 outputs, every output element against the FP64 reference on
+    BF16-rounded operands (ragged W over two column tiles, several row tiles)."""
+    from oracle import lpd_ref as R
+    rng = np.random.default_rng(zlib.crc32(name.encode()) % 10000)
+    w = torch.tensor(rng.standard_normal((cout, cin) + (3,) * len(dims)) * 0.1)
+    b = torch.tensor(rng.standard_normal(cout) * 0.1)
+    wg = w.reshape(cout, cin, -1).permute(0, 2, 1).contiguous().float().cuda()
+    if kind in ("dx", "dxres"):
+        dy = R.bf16(torch.tensor(rng.standard_normal((nimg, cout) + dims)))
+        xr = torch.zeros((nimg, cin) + dims, dtype=torch.float64, requires_grad=True)
+        (R.conv(xr, R.bf16(w), None) * dy).sum().backward()
+        dy_cl = to_cl(dy, slots(cout))
+        if kind == "dx":
+            act = torch.tensor(rng.standard_normal((nimg, cin) + dims))
+            cp = max(32, slots(cin))
+            y = run_conv(L, dy_cl, dims, taps3d, wg, None, cin, cout, 1, 2, cp, mask=to_cl(act, cp))
+            ref = xr.grad * torch.where(R.bf16(act) > 0, 1.0, SLOPE)
+            got = from_cl(y, cin)
+            assert rel(got, ref) <= 1e-2, rel(got, ref)
+        else:
+            state0 = torch.tensor(rng.standard_normal((cin, nimg) + dims))
+            state = state0.float().cuda().contiguous()
+            run_conv(L, dy_cl, dims, taps3d, wg, None, cin, cout, 1, 1, 8, state=state)
+            ref = state0 + xr.grad.movedim(1, 0)
+            assert rel(state.double().cpu(), ref) <= 1e-5, rel(state.double().cpu(), ref)
+        return
+    x = torch.tensor(rng.standard_normal((nimg, cin) + dims))
+    conv = R.conv(R.bf16(x), R.bf16(w), b.float().double())
+    if kind == "act":
+        cp = max(32, slots(cout))
+        y = run_conv(L, to_cl(x, slots(cin)), dims, taps3d, wg, b.float().cuda(), cin, cout, 0, 0, cp)
+        got, ref = from_cl(y, cout), R.lrelu(conv)
+        assert rel(got, ref) <= 1e-2, rel(got, ref)
+        assert rel(got, R.bf16(ref)) <= 4e-3
+        # padding slots of the output (channels cout .. cp - 1) are zero
+        if cout < cp:
+            pad = y.transpose(-3, -2).reshape(y.shape[:-3] + (y.shape[-2], -1))[..., cout:]
+            assert not torch.any(pad.float())
+    else:
+        state0 = torch.tensor(rng.standard_normal((cout, nimg) + dims))
+        state = state0.float().cuda().contiguous()
+        run_conv(L, to_cl(x, slots(cin)), dims, taps3d, wg, b.float().cuda(), cin, cout, 0, 1, 8, state=state)
+        ref = state0 + conv.movedim(1, 0)
+        assert rel(state.double().cpu(), ref) <= 1e-5, rel(state.double().cpu(), ref)
+
+
+@pytest.mark.parametrize("taps3d,dims,cin,cout,cpin,cpout", [
+    (1, (5, 7, 130), 64, 64, 64, 64), (0, (19, 150), 64, 64, 64, 64), (1, (5, 7, 130), 8, 64, 8, 64),
+    (1, (5, 7, 130), 64, 4, 64, 8), (0, (19, 150), 40, 48, 64, 64)])
+def test_conv_weight_gradient_wide(L, taps3d, dims, cin, cout, cpin, cpout):
+    """Weight and bias gradients with 64 input or output slots (blocks of 32 x 32
+    channels on the tensor cores, written into one [cout][taps][cin] array)."""
+    from oracle import lpd_ref as R
+    rng = np.random.default_rng(cin * 100 + cout + taps3d)
+    nimg = 2
+    x = R.bf16(torch.tensor(rng.standard_normal((nimg, cin) + dims)))
+    dy = R.bf16(torch.tensor(rng.standard_normal((nimg, cout) + dims)))
+    wr = torch.zeros((cout, cin) + (3,) * len(dims), dtype=torch.float64, requires_grad=True)
+    br = torch.zeros(cout, dtype=torch.float64, requires_grad=True)
+    (R.conv(x, wr, br) * dy).sum().backward()
+    D, H, W = dims if taps3d else (1,) + dims
+    dw = torch.full((cout, 27 if taps3d else 9, cin), 0.5, device="cuda")   # accumulate = 1 adds to it
+    db = torch.full((cout,), 0.5, device="cuda")
+    x_cl, dy_cl = to_cl(x, cpin), to_cl(dy, cpout)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    L.check(L.load().cbct_conv_wgrad(x_cl.data_ptr(), cpin, cin, dy_cl.data_ptr(), cpout, cout, nimg, D, H, W,
+                                     taps3d, dw.data_ptr(), db.data_ptr(), 1, status.data_ptr(),
+                                     torch.cuda.current_stream().cuda_stream), "wgrad")
+    torch.cuda.synchronize()
+    assert status.item() == 0
+    ref_dw = wr.grad.reshape(cout, cin, -1).permute(0, 2, 1) + 0.5
+    assert rel_l2_t(dw.double().cpu(), ref_dw) <= 1e-5
+    assert rel_l2_t(db.double().cpu(), br.grad + 0.5) <= 1e-5

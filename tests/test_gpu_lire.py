@@ -73,14 +73,17 @@ def flat_grads(dual, prim, outs):
     return np.concatenate(g)
 
 
-def test_lire_matches_oracle_and_inverts(O, M):
+@pytest.mark.parametrize("width", [32, 64])
+def test_lire_matches_oracle_and_inverts(O, M, width):
+    """Width 64 is the paper's dual block (K + 4 -> 64 -> 64 -> 4 with 8-channel
+    latents): 64-slot activations, two launches of 32 outputs per hidden layer."""
     from oracle import lpd_ref as R
     P, L = M
     G = O.Geom(GEOM)
     geom = P.Geometry(GEOM)
     n_iter, n_mem, mu, bps = 2, 8, 0.02, 2e-3
-    model = L.LPD(geom, n_iter=n_iter, n_mem=n_mem, mu_ref=mu, bp_scale=bps, lire=True, seed=11)
-    layout = L.lire_layout(n_iter, n_mem)
+    model = L.LPD(geom, n_iter=n_iter, n_mem=n_mem, width=width, mu_ref=mu, bp_scale=bps, lire=True, seed=11)
+    layout = L.lire_layout(n_iter, n_mem, width)
     flat = lire_flat(layout, 23)
     assert flat.size == model.nparams
     model.set_params(flat)
@@ -115,7 +118,7 @@ def test_lire_matches_oracle_and_inverts(O, M):
     gg = model.grads().astype(np.float64)
     _, _, _, gp, gyp, g0p = reference(1.0 + 1e-6)
     e_w, e_y, e_x = rel_l2(gg, gr), rel_l2(to_np(gy), gyr), rel_l2(to_np(g0), g0r)
-    print(f"LIRE gradient parity: params {e_w:.2e} (tol {grad_tol(gr, gp):.2e}), y {e_y:.2e} "
+    print(f"LIRE width {width} gradient parity: params {e_w:.2e} (tol {grad_tol(gr, gp):.2e}), y {e_y:.2e} "
           f"(tol {grad_tol(gyr, gyp):.2e}), x0 {e_x:.2e} (tol {grad_tol(g0r, g0p):.2e})")
     assert e_w <= grad_tol(gr, gp) and e_y <= grad_tol(gyr, gyp) and e_x <= grad_tol(g0r, g0p)
     # the backward undid every iteration: the latents are the initial ones again

@@ -35,7 +35,7 @@ def oracle_params(flat, shapes):
     return out
 
 
-def _lpd_case(O, M, last_scale, seed_w=3):
+def _lpd_case(O, M, last_scale, seed_w=3, width=32):
     """GPU forward/backward and the FP64 reference (BF16 operands in both passes) on the
     24x24x16 / 12-angle case with 2 iterations; returns both sides' output and gradients
     and a function that re-evaluates the reference's gradients for a perturbed x0."""
@@ -44,8 +44,8 @@ def _lpd_case(O, M, last_scale, seed_w=3):
     G = O.Geom(GEOM)
     geom = P.Geometry(GEOM)
     n_iter, mu, bps = 2, 0.02, 2e-3
-    model = L.LPD(geom, n_iter=n_iter, mu_ref=mu, bp_scale=bps)
-    shapes = L.layer_shapes(n_iter)
+    model = L.LPD(geom, n_iter=n_iter, mu_ref=mu, bp_scale=bps, width=width)
+    shapes = L.layer_shapes(n_iter, width=width)
     flat = I.lpd_weights(shapes, seed=seed_w, last_scale=last_scale)
     model.set_params(flat)
     x_true = O.phantom(G, I.ellipsoids(GEOM, 5, n_soft=6, axes_mm=(15.0, 60.0)))
@@ -89,6 +89,20 @@ def test_lpd_forward_and_gradients_match_oracle(O, M):
     # runs the same arithmetic as the training pass above
     xi = model.forward(to_gpu(y), to_gpu(x0))
     assert np.array_equal(to_np(xi), xg)
+
+
+def test_lpd_width64_matches_oracle(O, M):
+    """Blocks of width 64 (64-slot activations: 3x3 dual and 3x3x3 primal convolutions on
+    64 input slots, each hidden layer as two launches of 32 outputs, weight gradients in
+    32 x 32 blocks): output and gradients within the same bars as width 32."""
+    _, (xg, gg, gy, g0), reference, _ = _lpd_case(O, M, 0.1, width=64)
+    ref, gref, gyr, g0r = reference()
+    _, gp, gyp, g0p = reference(1.0 + 1e-6)
+    assert rel_l2(xg, ref) <= 1e-2
+    e_w, e_y, e_x = rel_l2(gg, gref), rel_l2(gy, gyr), rel_l2(g0, g0r)
+    print(f"LPD width 64 gradient parity: params {e_w:.2e}, y {e_y:.2e} (tol {grad_tol(gyr, gyp):.2e}), "
+          f"x0 {e_x:.2e}")
+    assert e_w <= grad_tol(gref, gp) and e_x <= grad_tol(g0r, g0p) and e_y <= grad_tol(gyr, gyp)
 
 
 def test_lpd_strong_blocks_within_reference_conditioning(O, M):

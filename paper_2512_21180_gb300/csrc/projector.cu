@@ -302,11 +302,15 @@ __global__ void __launch_bounds__(kThreads3, 3) k_backproject_v3(GeomDev g, cons
                     if (fb != (float)s) continue;  // the column belongs to another segment
                     const float wu = qb - fb, wl = 1.0f - wu;
                     const float step = t * drz, irs = 1.0f / step, voff = fmaf(t, rz0, Sz);
-                    // first row whose sample lies above z0 - 1 + m
+                    // sample z of row v relative to z0 - 1: v step + voffz; the first row whose
+                    // sample lies above z0 - 1 + m is floor((m - voffz) / step) + 1, and clamping
+                    // the quotient to [-1, nv - 1] before the floor keeps it in [0, nv]
+                    const float voffz = voff - (float)(z0 - 1), vbase = -voffz * irs;
+                    const float vmax = (float)(nv - 1);
                     auto row_above = [&](int m) {
-                        const float vs = ((float)(z0 - 1 + m) - voff) * irs;
-                        return min(max(__float2int_rd(fminf(fmaxf(vs, -1.0e6f), 1.0e6f)) + 1, 0), nv);
+                        return __float2int_rd(fminf(fmaxf(fmaf((float)m, irs, vbase), -1.0f), vmax)) + 1;
                     };
+                    const float *Pu = Pk + u;
                     int va = row_above(0);
                     float carry = 0.f;  // upper-voxel share of the previous interval
 #pragma unroll
@@ -314,8 +318,8 @@ __global__ void __launch_bounds__(kThreads3, 3) k_backproject_v3(GeomDev g, cons
                         const int ve = row_above(m + 1);
                         float S0 = 0.f, S1 = 0.f;
                         if (va < ve) {
-                            float qf = fmaf((float)va, step, voff) - (float)(z0 - 1 + m);
-                            const float *pp = Pk + (long long)va * nu + u;
+                            float qf = fmaf((float)va, step, voffz) - (float)m;
+                            const float *pp = Pu + (long long)va * nu;
                             const int n = ve - va;
                             float T = 0.f;  // sum of rr p: S1 = qf S0 + step T
 #pragma unroll

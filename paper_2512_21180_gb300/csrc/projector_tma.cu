@@ -7,12 +7,15 @@
 // whose fastest index is the in-plane coordinate b that varies along a detector
 // row, so a warp's bilinear reads hit distinct shared-memory banks.
 //
-// CTA = one angle x a 32 (u) x 8 (v) ray tile: 8 consumer warps (one ray per
-// thread, one detector row per warp) and one producer warp. The planes are
+// CTA = one angle x a 32 (u) x 8 (v) ray tile: 4 consumer warps and one producer
+// warp. A consumer thread carries the two rays of its column in rows v and v + 4:
+// both share the column's in-plane coordinate q_b, principal axis and source-to-
+// pixel parameter on every plane, and their z-dependent arithmetic runs as packed
+// FP32 pairs (fma/add.rn.f32x2, each half rounded like the scalar operation). The planes are
 // processed in chunks of 8; for each chunk the producer computes the box of
 // voxels the tile's rays can touch (from the four corner rays at the chunk's end
 // planes: the sample position is monotone in column, row and plane) and TMA-loads
-// it (box BW x ZH x 8) into a 4-stage shared-memory ring. TMA fills voxels outside
+// it (box BW x ZH x 8) into a 2-stage shared-memory ring. TMA fills voxels outside
 // the volume with zeros, so the consumers sample without bounds checks. A chunk
 // whose footprint exceeds the box falls back to bounds-checked global loads; a
 // chunk whose box misses the volume is skipped (all its samples are zero). Tiles
@@ -30,8 +33,12 @@
 
 namespace cbct {
 
-constexpr int kTU = 32, kTV = 8, kP = 8, kStages = 4;
-constexpr int kConsumerWarps = kTV;
+// Two stages of 8 planes (32 KB with the 32 x 16 box) let six CTAs share an SM: measured
+// at the clinical size, 15.1 ms against 18.0 ms with three stages (four CTAs per SM) and
+// 21.9 ms with four (three CTAs per SM); four planes per stage took 16.9 ms.
+constexpr int kTU = 32, kTV = 8, kP = 8, kStages = 2;
+constexpr int kRowsPerThread = 2;
+constexpr int kConsumerWarps = kTV / kRowsPerThread;  // warp w: rows w and w + kConsumerWarps
 constexpr int kThreads = 32 * (kConsumerWarps + 1);
 
 struct ChunkInfo {
@@ -151,24 +158,27 @@ __global__ void __launch_bounds__(kThreads) k_forward_tma(const __grid_constant_
     }
     __syncthreads();
 
-    // consumer ray set-up (the canonical per-ray quantities of common.cuh)
+    // consumer ray set-up (the canonical per-ray quantities of common.cuh): column
+    // terms once, row terms for both rows (a row past the panel reads the last row's
+    // table entry and is dropped at the store)
     const bool consumer = warp < kConsumerWarps;
-    const int iu = u0 + lane, iv = v0 + warp;
-    const bool ray_ok = consumer && iu < g.nu && iv < g.nv;
-    const int my_a = ray_ok ? principal_axis(F, iu) : -1;
+    const int iu = u0 + lane, iv0 = v0 + warp, iv1 = iv0 + kConsumerWarps;
+    const bool col_ok = consumer && iu < g.nu;
+    const int my_a = col_ok ? principal_axis(F, iu) : -1;
     ColT<float> c{0.f, 0.f, 0.f, 0.f};
-    float dqz = 0.f, qcz = 0.f, step = 0.f;
+    float2 dqz = make_float2(0.f, 0.f), qcz = make_float2(0.f, 0.f), step = make_float2(0.f, 0.f);
     bool t_all = true;
-    if (ray_ok) {
+    if (col_ok) {
         c = col_of<float>(g, k, iu);
-        const float rz = rz_of<float>(g, iv);
-        ray_row(g, c, rz, dqz, qcz);
-        step = ray_step<float>(g, my_a, c.dqb, dqz);
+        ray_row(g, c, rz_of<float>(g, min(iv0, g.nv - 1)), dqz.x, qcz.x);
+        ray_row(g, c, rz_of<float>(g, min(iv1, g.nv - 1)), dqz.y, qcz.y);
+        step.x = ray_step<float>(g, my_a, c.dqb, dqz.x);
+        step.y = ray_step<float>(g, my_a, c.dqb, dqz.y);
         const float ca = 0.5f * (float)(g.n[my_a] - 1);
         const float t0 = fma_rn(-ca, c.inv, c.tc), t1 = fma_rn(ca, c.inv, c.tc);
         t_all = t0 > 0.f && t0 < 1.f && t1 > 0.f && t1 < 1.f;
     }
-    float acc = 0.f;
+    float2 acc = make_float2(0.f, 0.f);
     int gc = 0;  // chunks issued so far (both passes): stage = gc % kStages, use = gc / kStages
 
     for (int a = 0; a < 2; ++a) {
@@ -267,21 +277,26 @@ __global__ void __launch_bounds__(kThreads) k_forward_tma(const __grid_constant_
                             if (i0 + p < na) {
                                 const float di = d0 + (float)p;
                                 const float qb = fma_rn(di, c.dqb, c.qcb);
-                                const float qz = fma_rn(di, dqz, qcz);
-                                const float fb0 = floorf(qb), fz0 = floorf(qz);
-                                const float fb = qb - fb0, fz = qz - fz0;
+                                const float fb0 = floorf(qb), fb = qb - fb0;
+                                const float2 qz = __ffma2_rn(make_float2(di, di), dqz, qcz);
+                                const float2 fz0 = make_float2(floorf(qz.x), floorf(qz.y));
+                                const float2 fz = __fadd2_rn(qz, make_float2(-fz0.x, -fz0.y));
                                 // fz0 BW + fb0 is an exact small integer in FP32: one conversion
-                                int off = (int)fmaf(fz0, (float)BW, fb0) + base;
-                                off = (int)min((unsigned)off, (unsigned)(ZH * BW - BW - 2));
-                                const float *r = st + p * ZH * BW + off;
-                                const float v00 = r[0], v10 = r[1], v01 = r[BW], v11 = r[BW + 1];
-                                const float a0 = fmaf(fb, v10 - v00, v00);
-                                const float a1 = fmaf(fb, v11 - v01, v01);
-                                const float val = fmaf(fz, a1 - a0, a0);
-                                if (t_all) acc += val;
+                                const float2 offf = __ffma2_rn(fz0, make_float2((float)BW, (float)BW),
+                                                               make_float2(fb0, fb0));
+                                const int o0 = (int)min((unsigned)((int)offf.x + base), (unsigned)(ZH * BW - BW - 2));
+                                const int o1 = (int)min((unsigned)((int)offf.y + base), (unsigned)(ZH * BW - BW - 2));
+                                const float *r0 = st + p * ZH * BW + o0, *r1 = st + p * ZH * BW + o1;
+                                const float2 v00 = make_float2(r0[0], r1[0]), v10 = make_float2(r0[1], r1[1]);
+                                const float2 v01 = make_float2(r0[BW], r1[BW]), v11 = make_float2(r0[BW + 1], r1[BW + 1]);
+                                const float2 fbb = make_float2(fb, fb);
+                                const float2 a0 = __ffma2_rn(fbb, __fadd2_rn(v10, make_float2(-v00.x, -v00.y)), v00);
+                                const float2 a1 = __ffma2_rn(fbb, __fadd2_rn(v11, make_float2(-v01.x, -v01.y)), v01);
+                                const float2 val = __ffma2_rn(fz, __fadd2_rn(a1, make_float2(-a0.x, -a0.y)), a0);
+                                if (t_all) acc = __fadd2_rn(acc, val);
                                 else {
                                     const float t = fma_rn(di, c.inv, c.tc);
-                                    if (t > 0.f && t < 1.f) acc += val;
+                                    if (t > 0.f && t < 1.f) acc = __fadd2_rn(acc, val);
                                 }
                             }
                         }
@@ -292,20 +307,28 @@ __global__ void __launch_bounds__(kThreads) k_forward_tma(const __grid_constant_
                             const float t = fma_rn(di, c.inv, c.tc);
                             if (!(t > 0.f && t < 1.f)) continue;
                             const float qb = fma_rn(di, c.dqb, c.qcb);
-                            const float qz = fma_rn(di, dqz, qcz);
-                            if (!(qb > -1.f && qb < (float)nb && qz > -1.f && qz < (float)nz)) continue;
-                            const float fb0 = floorf(qb), fz0 = floorf(qz);
-                            const float fb = qb - fb0, fz = qz - fz0;
-                            const int jb = (int)fb0, jz = (int)fz0;
+                            if (!(qb > -1.f && qb < (float)nb)) continue;
+                            const float fb0 = floorf(qb), fb = qb - fb0;
+                            const int jb = (int)fb0;
+                            const bool b0k = jb >= 0, b1k = jb + 1 < nb;
                             const float *P = T + tbase + (long long)i * nz * pitch;
-                            const bool b0k = jb >= 0, b1k = jb + 1 < nb, z0k = jz >= 0, z1k = jz + 1 < nz;
-                            const float v00 = (b0k && z0k) ? __ldg(P + (long long)jz * pitch + jb) : 0.f;
-                            const float v10 = (b1k && z0k) ? __ldg(P + (long long)jz * pitch + jb + 1) : 0.f;
-                            const float v01 = (b0k && z1k) ? __ldg(P + (long long)(jz + 1) * pitch + jb) : 0.f;
-                            const float v11 = (b1k && z1k) ? __ldg(P + (long long)(jz + 1) * pitch + jb + 1) : 0.f;
-                            const float a0 = fmaf(fb, v10 - v00, v00);
-                            const float a1 = fmaf(fb, v11 - v01, v01);
-                            acc += fmaf(fz, a1 - a0, a0);
+#pragma unroll
+                            for (int rr = 0; rr < kRowsPerThread; ++rr) {
+                                const float qz = fma_rn(di, rr ? dqz.y : dqz.x, rr ? qcz.y : qcz.x);
+                                if (!(qz > -1.f && qz < (float)nz)) continue;
+                                const float fz0 = floorf(qz), fz = qz - fz0;
+                                const int jz = (int)fz0;
+                                const bool z0k = jz >= 0, z1k = jz + 1 < nz;
+                                const float v00 = (b0k && z0k) ? __ldg(P + (long long)jz * pitch + jb) : 0.f;
+                                const float v10 = (b1k && z0k) ? __ldg(P + (long long)jz * pitch + jb + 1) : 0.f;
+                                const float v01 = (b0k && z1k) ? __ldg(P + (long long)(jz + 1) * pitch + jb) : 0.f;
+                                const float v11 = (b1k && z1k) ? __ldg(P + (long long)(jz + 1) * pitch + jb + 1) : 0.f;
+                                const float a0 = fmaf(fb, v10 - v00, v00);
+                                const float a1 = fmaf(fb, v11 - v01, v01);
+                                const float val = fmaf(fz, a1 - a0, a0);
+                                if (rr) acc.y += val;
+                                else acc.x += val;
+                            }
                         }
                     }
                 }
@@ -318,25 +341,30 @@ __global__ void __launch_bounds__(kThreads) k_forward_tma(const __grid_constant_
         if (abort_flag) break;
     }
     if (consumer && !abort_flag) {
-        // one detector row per warp: when the row's 32 columns lie inside the panel and start
-        // on a 16-byte boundary, every fourth lane stores its own and its three neighbours'
-        // rays as one float4 (eight vector stores per warp); otherwise one float per ray
-        const float r = ray_ok ? acc * step * g.scale : 0.f;
-        float *out = proj + (((long long)b * g.na + k) * g.nv + iv) * g.nu + iu;
-        if ((g.nu & 3) == 0 && u0 + kTU <= g.nu && iv < g.nv) {  // uniform over the warp
-            const float r1 = __shfl_down_sync(0xffffffffu, r, 1);
-            const float r2 = __shfl_down_sync(0xffffffffu, r, 2);
-            const float r3 = __shfl_down_sync(0xffffffffu, r, 3);
-            if ((lane & 3) == 0) {
-                float4 v = make_float4(r, r1, r2, r3);
-                if (accumulate) {
-                    const float4 p = *reinterpret_cast<const float4 *>(out);
-                    v.x += p.x; v.y += p.y; v.z += p.z; v.w += p.w;
+        // per row: when the row's 32 columns lie inside the panel and start on a 16-byte
+        // boundary, every fourth lane stores its own and its three neighbours' rays as one
+        // float4 (eight vector stores per warp and row); otherwise one float per ray
+#pragma unroll
+        for (int rr = 0; rr < kRowsPerThread; ++rr) {
+            const int iv = rr ? iv1 : iv0;
+            const bool ray_ok = col_ok && iv < g.nv;
+            const float r = ray_ok ? (rr ? acc.y * step.y : acc.x * step.x) * g.scale : 0.f;
+            float *out = proj + (((long long)b * g.na + k) * g.nv + iv) * g.nu + iu;
+            if ((g.nu & 3) == 0 && u0 + kTU <= g.nu && iv < g.nv) {  // uniform over the warp
+                const float r1 = __shfl_down_sync(0xffffffffu, r, 1);
+                const float r2 = __shfl_down_sync(0xffffffffu, r, 2);
+                const float r3 = __shfl_down_sync(0xffffffffu, r, 3);
+                if ((lane & 3) == 0) {
+                    float4 v = make_float4(r, r1, r2, r3);
+                    if (accumulate) {
+                        const float4 q = *reinterpret_cast<const float4 *>(out);
+                        v.x += q.x; v.y += q.y; v.z += q.z; v.w += q.w;
+                    }
+                    *reinterpret_cast<float4 *>(out) = v;
                 }
-                *reinterpret_cast<float4 *>(out) = v;
+            } else if (ray_ok) {
+                *out = accumulate ? *out + r : r;
             }
-        } else if (ray_ok) {
-            *out = accumulate ? *out + r : r;
         }
     }
 }

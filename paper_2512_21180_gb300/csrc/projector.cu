@@ -208,9 +208,11 @@ __global__ void __launch_bounds__(256) k_backproject(GeomDev g, const T *__restr
 // sweeps the rows of each of its columns once, summing the rows of every unit
 // z-interval (L, L + 1] as S0 = sum p and S1 = sum p (q_z - L) (lower voxel
 // S0 - S1, upper voxel S1), and accumulates SA[z] for voxel s and SB[z] for voxel
-// s + 1. SB reaches the thread of segment s + 1 through shared memory and each
-// voxel adds SA + SB of its two segments to its shared accumulator, always in the
-// same order, so the result does not depend on scheduling.
+// s + 1. A thread's two voxel runs depend on the axis only, so the angles run inside
+// one sweep per principal axis and SA, SB stay in registers over all of them; after
+// each sweep every voxel adds the SA of its own segment, then (after a barrier) the SB
+// of the segment below, to its shared accumulator — a fixed order, so the result does
+// not depend on scheduling, and no barrier or shared-memory traffic per angle.
 // The kernel is bound by load latency, which shapes the loops: a thread first
 // narrows its candidate columns to the first and last column of its segment (so
 // the lanes of a warp run their useful columns in the same iterations); a row's
@@ -221,15 +223,13 @@ __global__ void __launch_bounds__(256) k_backproject(GeomDev g, const T *__restr
 // the 17-interval sweep straight-line code whose loads overlap.
 constexpr int kB3 = 16, kZ3 = 16, kThreads3 = 288;
 constexpr int kVacc3 = kZ3 * kB3 * (kB3 + 1);  // [z][y][x], y stride 17 (bank-conflict free both ways)
-constexpr int kSbuf3 = kB3 * kB3 * (kZ3 + 1);  // [voxel][plane][z], plane stride 17
-constexpr size_t kSmem3 = sizeof(float) * (kVacc3 + 2 * kSbuf3);
+constexpr size_t kSmem3 = sizeof(float) * kVacc3;
 
 __global__ void __launch_bounds__(kThreads3, 3) k_backproject_v3(GeomDev g, const float *__restrict__ pw,
                                                                  float *__restrict__ vol, int accumulate,
                                                                  int nparts, float *__restrict__ partial) {
     extern __shared__ float sm3[];
     float *vacc = sm3;
-    float *sbuf = sm3 + kVacc3;
     const int tid = threadIdx.x;
     const int il = tid & 15, seg = tid >> 4;  // plane il of the brick; segment j0 - 1 + seg
     const bool item = seg <= kB3;             // 17 segments x 16 planes
@@ -240,133 +240,129 @@ __global__ void __launch_bounds__(kThreads3, 3) k_backproject_v3(GeomDev g, cons
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nu = g.nu, nv = g.nv;
     const int k_begin = (int)((long long)g.na * part / nparts), k_end = (int)((long long)g.na * (part + 1) / nparts);
     for (int e = tid; e < kVacc3; e += kThreads3) vacc[e] = 0.f;
+    __syncthreads();
     const float Sz = g.Sz;
     const float rz0 = g.rz32[0], drz = g.f32[0].EV[2];
     const float *PB = pw + (long long)b * g.na * nv * nu;
-    int pass = 0;
 
 #pragma unroll 1
-    for (int k = k_begin; k < k_end; ++k) {
-        const Frame32 &F = g.f32[k];
-        const float *Pk = PB + (long long)k * nv * nu;
-#pragma unroll 1
-        for (int a = 0; a < 2; ++a) {
-            const int alo = a == 0 ? F.ux_lo : F.uy_lo, ahi = a == 0 ? F.ux_hi : F.uy_hi;
-            if (alo > ahi) continue;  // uniform over the CTA
-            const int j0 = a == 0 ? y0 : x0;
-            const int i = (a == 0 ? x0 : y0) + il, s = j0 - 1 + seg;
-            float SA[kZ3], SB[kZ3];
+    for (int a = 0; a < 2; ++a) {
+        const int j0 = a == 0 ? y0 : x0;
+        const int i = (a == 0 ? x0 : y0) + il, s = j0 - 1 + seg;
+        const bool mine = item && i < g.n[a] && s < g.n[1 - a];
+        const float di = (float)i - 0.5f * (float)(g.n[a] - 1);
+        float SA[kZ3], SB[kZ3];
 #pragma unroll
-            for (int m = 0; m < kZ3; ++m) SA[m] = SB[m] = 0.f;
-            if (item && i < g.n[a] && s < g.n[1 - a]) {
-                const float di = (float)i - 0.5f * (float)(g.n[a] - 1);
-                // candidate columns for q_b in [s, s + 1), one column of margin
-                float u1, u2;
-                if (a == 0) { u1 = column_of(F, (float)i, (float)s); u2 = column_of(F, (float)i, (float)(s + 1)); }
-                else { u1 = column_of(F, (float)s, (float)i); u2 = column_of(F, (float)(s + 1), (float)i); }
-                int ulo = alo, uhi = ahi;
-                if (isfinite(u1) && isfinite(u2)) {
-                    ulo = max(ulo, (int)floorf(fmaxf(fminf(u1, u2), -1.0e6f)) - 1);
-                    uhi = min(uhi, (int)ceilf(fminf(fmaxf(u1, u2), 1.0e6f)) + 1);
-                }
-                if (ulo <= uhi) {
-                    // skip the columns when no row of the panel reaches the z-run
-                    const ColT<float> cl = col_of<float>(g, k, ulo), ch = col_of<float>(g, k, uhi);
-                    const float tl = fma_rn(di, cl.inv, cl.tc), th = fma_rn(di, ch.inv, ch.tc);
-                    const float tmin = fminf(tl, th), tmax = fmaxf(tl, th);
-                    const float zlo = (float)(z0 - 1) - Sz, zhi = (float)(z0 + kZ3) - Sz;
-                    const float t1 = fmaxf(tmin, 1e-6f);
-                    const float rlo = fminf(zlo / t1, zlo / tmax), rhi = fmaxf(zhi / t1, zhi / tmax);
-                    const float vlo = (rlo - rz0) / drz - 2.f, vhi = (rhi - rz0) / drz + 2.f;
-                    if (!(tmax > 0.f) || vhi < 0.f || vlo > (float)(nv - 1)) uhi = ulo - 1;
-                }
-                {  // first and last column of the segment
-                    int ua = uhi + 1, ub = uhi;
+        for (int m = 0; m < kZ3; ++m) SA[m] = SB[m] = 0.f;
 #pragma unroll 1
-                    for (int u = ulo; u <= uhi; ++u) {
-                        const ColT<float> c = col_of<float>(g, k, u);
-                        const float t = fma_rn(di, c.inv, c.tc);
-                        const float qb = fma_rn(di, c.dqb, c.qcb);
-                        if (t > 0.f && t < 1.f && floorf(qb) == (float)s) { ua = min(ua, u); ub = u; }
-                    }
-                    ulo = ua;
-                    uhi = ub;
-                }
+        for (int k = k_begin; k < k_end; ++k) {
+            const Frame32 &F = g.f32[k];
+            const int alo = a == 0 ? F.ux_lo : F.uy_lo, ahi = a == 0 ? F.ux_hi : F.uy_hi;
+            if (alo > ahi || !mine) continue;
+            const float *Pk = PB + (long long)k * nv * nu;
+            // candidate columns for q_b in [s, s + 1), one column of margin
+            float u1, u2;
+            if (a == 0) { u1 = column_of(F, (float)i, (float)s); u2 = column_of(F, (float)i, (float)(s + 1)); }
+            else { u1 = column_of(F, (float)s, (float)i); u2 = column_of(F, (float)(s + 1), (float)i); }
+            int ulo = alo, uhi = ahi;
+            if (isfinite(u1) && isfinite(u2)) {
+                ulo = max(ulo, (int)floorf(fmaxf(fminf(u1, u2), -1.0e6f)) - 1);
+                uhi = min(uhi, (int)ceilf(fminf(fmaxf(u1, u2), 1.0e6f)) + 1);
+            }
+            if (ulo <= uhi) {
+                // skip the columns when no row of the panel reaches the z-run
+                const ColT<float> cl = col_of<float>(g, k, ulo), ch = col_of<float>(g, k, uhi);
+                const float tl = fma_rn(di, cl.inv, cl.tc), th = fma_rn(di, ch.inv, ch.tc);
+                const float tmin = fminf(tl, th), tmax = fmaxf(tl, th);
+                const float zlo = (float)(z0 - 1) - Sz, zhi = (float)(z0 + kZ3) - Sz;
+                const float t1 = fmaxf(tmin, 1e-6f);
+                const float rlo = fminf(zlo / t1, zlo / tmax), rhi = fmaxf(zhi / t1, zhi / tmax);
+                const float vlo = (rlo - rz0) / drz - 2.f, vhi = (rhi - rz0) / drz + 2.f;
+                if (!(tmax > 0.f) || vhi < 0.f || vlo > (float)(nv - 1)) uhi = ulo - 1;
+            }
+            {  // first and last column of the segment
+                int ua = uhi + 1, ub = uhi;
 #pragma unroll 1
                 for (int u = ulo; u <= uhi; ++u) {
                     const ColT<float> c = col_of<float>(g, k, u);
                     const float t = fma_rn(di, c.inv, c.tc);
-                    if (!(t > 0.f && t < 1.f)) continue;
                     const float qb = fma_rn(di, c.dqb, c.qcb);
-                    const float fb = floorf(qb);
-                    if (fb != (float)s) continue;  // the column belongs to another segment
-                    const float wu = qb - fb, wl = 1.0f - wu;
-                    const float step = t * drz, irs = 1.0f / step, voff = fmaf(t, rz0, Sz);
-                    // sample z of row v relative to z0 - 1: v step + voffz; the first row whose
-                    // sample lies above z0 - 1 + m is floor((m - voffz) / step) + 1, and clamping
-                    // the quotient to [-1, nv - 1] before the floor keeps it in [0, nv]
-                    const float voffz = voff - (float)(z0 - 1), vbase = -voffz * irs;
-                    const float vmax = (float)(nv - 1);
-                    auto row_above = [&](int m) {
-                        return __float2int_rd(fminf(fmaxf(fmaf((float)m, irs, vbase), -1.0f), vmax)) + 1;
-                    };
-                    const float *Pu = Pk + u;
-                    int va = row_above(0);
-                    float carry = 0.f;  // upper-voxel share of the previous interval
-#pragma unroll
-                    for (int m = 0; m < kZ3 + 1; ++m) {
-                        const int ve = row_above(m + 1);
-                        float S0 = 0.f, S1 = 0.f;
-                        if (va < ve) {
-                            float qf = fmaf((float)va, step, voffz) - (float)m;
-                            const float *pp = Pu + (long long)va * nu;
-                            const int n = ve - va;
-                            float T = 0.f;  // sum of rr p: S1 = qf S0 + step T
-#pragma unroll
-                            for (int rr = 0; rr < 5; ++rr) {
-                                const float p = rr < n ? __ldg(pp + rr * nu) : 0.f;
-                                S0 += p;
-                                if (rr > 0) T = fmaf((float)rr, p, T);
-                            }
+                    if (t > 0.f && t < 1.f && floorf(qb) == (float)s) { ua = min(ua, u); ub = u; }
+                }
+                ulo = ua;
+                uhi = ub;
+            }
 #pragma unroll 1
-                            for (int rr = 5; rr < n; ++rr) {
-                                const float p = __ldg(pp + rr * nu);
-                                S0 += p;
-                                T = fmaf((float)rr, p, T);
-                            }
-                            S1 = fmaf(qf, S0, step * T);
+            for (int u = ulo; u <= uhi; ++u) {
+                const ColT<float> c = col_of<float>(g, k, u);
+                const float t = fma_rn(di, c.inv, c.tc);
+                if (!(t > 0.f && t < 1.f)) continue;
+                const float qb = fma_rn(di, c.dqb, c.qcb);
+                const float fb = floorf(qb);
+                if (fb != (float)s) continue;  // the column belongs to another segment
+                const float wu = qb - fb, wl = 1.0f - wu;
+                const float step = t * drz, irs = 1.0f / step, voff = fmaf(t, rz0, Sz);
+                // sample z of row v relative to z0 - 1: v step + voffz; the first row whose
+                // sample lies above z0 - 1 + m is floor((m - voffz) / step) + 1, and clamping
+                // the quotient to [-1, nv - 1] before the floor keeps it in [0, nv]
+                const float voffz = voff - (float)(z0 - 1), vbase = -voffz * irs;
+                const float vmax = (float)(nv - 1);
+                auto row_above = [&](int m) {
+                    return __float2int_rd(fminf(fmaxf(fmaf((float)m, irs, vbase), -1.0f), vmax)) + 1;
+                };
+                const float *Pu = Pk + u;
+                int va = row_above(0);
+                float carry = 0.f;  // upper-voxel share of the previous interval
+#pragma unroll
+                for (int m = 0; m < kZ3 + 1; ++m) {
+                    const int ve = row_above(m + 1);
+                    float S0 = 0.f, S1 = 0.f;
+                    if (va < ve) {
+                        float qf = fmaf((float)va, step, voffz) - (float)m;
+                        const float *pp = Pu + (long long)va * nu;
+                        const int n = ve - va;
+                        float T = 0.f;  // sum of rr p: S1 = qf S0 + step T
+#pragma unroll
+                        for (int rr = 0; rr < 5; ++rr) {
+                            const float p = rr < n ? __ldg(pp + rr * nu) : 0.f;
+                            S0 += p;
+                            if (rr > 0) T = fmaf((float)rr, p, T);
                         }
-                        // voxel z0 - 1 + m: upper share of interval m - 1, lower share of interval m
-                        if (m >= 1) {
-                            const float R = carry + S0 - S1;
-                            SA[m - 1] = fmaf(wl, R, SA[m - 1]);
-                            SB[m - 1] = fmaf(wu, R, SB[m - 1]);
+#pragma unroll 1
+                        for (int rr = 5; rr < n; ++rr) {
+                            const float p = __ldg(pp + rr * nu);
+                            S0 += p;
+                            T = fmaf((float)rr, p, T);
                         }
-                        carry = S1;
-                        va = ve;
+                        S1 = fmaf(qf, S0, step * T);
                     }
+                    // voxel z0 - 1 + m: upper share of interval m - 1, lower share of interval m
+                    if (m >= 1) {
+                        const float R = carry + S0 - S1;
+                        SA[m - 1] = fmaf(wl, R, SA[m - 1]);
+                        SB[m - 1] = fmaf(wu, R, SB[m - 1]);
+                    }
+                    carry = S1;
+                    va = ve;
                 }
             }
-            // SB of segment j0 - 1 + seg belongs to voxel seg of the brick
-            float *sb = sbuf + (pass & 1) * kSbuf3;
-            if (seg < kB3) {
-                float *d = sb + (seg * kB3 + il) * (kZ3 + 1);
-#pragma unroll
-                for (int m = 0; m < kZ3; ++m) d[m] = SB[m];
-            }
-            __syncthreads();
-            if (seg >= 1 && seg <= kB3) {
-                const int vl = seg - 1;  // this segment's voxel: own SA + SB of segment vl - 1
-                const int xl = a == 0 ? il : vl, yl = a == 0 ? vl : il;
-                float *v = vacc + yl * (kB3 + 1) + xl;
-                const float *src = sb + (vl * kB3 + il) * (kZ3 + 1);
-#pragma unroll
-                for (int m = 0; m < kZ3; ++m) v[m * kB3 * (kB3 + 1)] += SA[m] + src[m];
-            }
-            ++pass;  // the other buffer next time: one barrier per pass suffices
         }
+        // voxel (plane il, local index seg - 1): its own segment's lower shares, then the
+        // upper shares of the segment below it
+        if (mine && seg >= 1) {
+            const int vl = seg - 1;
+            float *v = vacc + (a == 0 ? vl * (kB3 + 1) + il : il * (kB3 + 1) + vl);
+#pragma unroll
+            for (int m = 0; m < kZ3; ++m) v[m * kB3 * (kB3 + 1)] += SA[m];
+        }
+        __syncthreads();
+        if (mine && seg < kB3) {
+            float *v = vacc + (a == 0 ? seg * (kB3 + 1) + il : il * (kB3 + 1) + seg);
+#pragma unroll
+            for (int m = 0; m < kZ3; ++m) v[m * kB3 * (kB3 + 1)] += SB[m];
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const long long nxy = (long long)nx * ny;
     const int nbatch = (int)(gridDim.z / nparts / nzb);
     float *out = nparts > 1 ? partial + ((long long)part * nbatch + b) * nxy * nz : vol + (long long)b * nxy * nz;

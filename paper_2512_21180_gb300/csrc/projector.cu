@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256) k_backproject(GeomDev g, const T *__restr
 }
 
 // Segment gather (FP32, geometries whose x- and y-principal columns form intervals).
-// CTA = brick of 16 x 16 voxel columns x 8 voxels in z, 288 threads. For the rays
+// CTA = brick of 16 x 16 voxel columns x 12 voxels in z, 288 threads. For the rays
 // of principal axis a at angle k, plane i of the brick is crossed at
 // q_b(u) = fma(di, dqb(u), qcb(u)), monotone in the detector column u. The columns
 // with floor(q_b) = s form segment s of the plane; their samples lie between voxels
@@ -220,11 +220,12 @@ __global__ void __launch_bounds__(256) k_backproject(GeomDev g, const T *__restr
 // rz_0 + v EV_z), so no table load sits between two intervals; and the rows of
 // an interval go through a fixed block of five predicated loads (3 to 5 rows per
 // interval at these magnifications) plus a loop for longer intervals, which makes
-// the 9-interval sweep straight-line code whose loads overlap.
-// Bricks 8 voxels tall: measured at the clinical size, 24.5 ms against 26.8 ms with 16 (finer
-// bricks are skipped more often where the panel does not reach their z-run); limiting the
-// registers to fit a fourth or fifth CTA per SM was slower (25.9 / 27.6 ms).
-constexpr int kB3 = 16, kZ3 = 8, kThreads3 = 288;
+// the 13-interval sweep straight-line code whose loads overlap.
+// Bricks 12 voxels tall: measured at the clinical size (CUDA events), 23.7 ms against 24.5 with
+// 8, 26.0 with 6, 31.5 with 4 and 26.8 with 16 — shorter z-runs are skipped more often where the
+// panel does not reach them, but spread each column's set-up over fewer intervals; limiting the
+// registers to fit a fourth or fifth CTA per SM was slower (8 tall: 25.9 / 27.6 ms).
+constexpr int kB3 = 16, kZ3 = 12, kThreads3 = 288;
 constexpr int kVacc3 = kZ3 * kB3 * (kB3 + 1);  // [z][y][x], y stride 17 (bank-conflict free both ways)
 constexpr size_t kSmem3 = sizeof(float) * kVacc3;
 

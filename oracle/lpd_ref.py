@@ -327,3 +327,60 @@ def p4_block(x: torch.Tensor, params, round_bf16: bool = True, round_grads: bool
     hidden widths are 4 c1 and 4 c2 group channels."""
     full = [p4_lift(*params[0]), p4_group(*params[1]), p4_avg(*params[2])]
     return block(x, full, round_bf16, round_grads)
+
+
+def pool2(x: torch.Tensor) -> torch.Tensor:
+    """Mean over 2 x 2 x 2 blocks of the last three axes (even sizes)."""
+    assert all(s % 2 == 0 for s in x.shape[-3:])
+    return F.avg_pool3d(x, 2)
+
+
+def up2(x: torch.Tensor) -> torch.Tensor:
+    """Nearest upsampling by 2 along the last three axes."""
+    for d in (-3, -2, -1):
+        x = x.repeat_interleave(2, dim=d)
+    return x
+
+
+def p4_unet(x: torch.Tensor, params, round_bf16: bool = True, round_grads: bool = False) -> torch.Tensor:
+    """The primal block as a U-Net of depth 1 (Sec. 2.6): six P4-equivariant 3x3x3 layers,
+    LeakyReLU after all but the last, the last averaged over the rotations.
+        a = L(lift(x)),  s = L(g2(a))                      full resolution, 4F group channels
+        q = L(g3(pool(s))),  r = L(g4(q))                 half resolution, 8F group channels
+        t = L(g5([up(r), s])),  out = avg6(t)             skip by concatenation, 12F -> 4F -> K
+    params: (w [F, cin, 3,3,3], b [F]) for the lift, then base filters w [co, ci, 4, 3,3,3]
+    with biases for g2 (F, F), g3 (2F, F), g4 (2F, 2F), g5 (F, 3F) and avg6 (K, F). BF16
+    rounding as in block(): conv inputs and weights rounded; the pooled mean is a conv input."""
+    r = bf16 if round_bf16 else (lambda t: t)
+    full = [p4_lift(*params[0]), p4_group(*params[1]), p4_group(*params[2]), p4_group(*params[3]),
+            p4_group(*params[4]), p4_avg(*params[5])]
+
+    def layer(h, i, act=True):
+        w, b = full[i]
+        o = conv(r(h), r(w), b)
+        if round_grads:
+            o = round_grad(o)
+        return lrelu(o) if act else o
+
+    a = layer(x, 0)
+    s = layer(a, 1)
+    q = layer(pool2(r(s)), 2)
+    rr = layer(q, 3)
+    t = layer(torch.cat([up2(r(rr)), s], 1), 4)
+    return layer(t, 5, act=False)
+
+
+def weight_norm(w: torch.Tensor, gain: torch.Tensor) -> torch.Tensor:
+    """Centred weight normalisation per output filter (the reading of forced weight
+    normalisation): w_eff[c] = gain (w[c] - mean w[c]) / ||w[c] - mean w[c]||, over all
+    other axes of w."""
+    v = w - w.reshape(w.shape[0], -1).mean(1).reshape((-1,) + (1,) * (w.dim() - 1))
+    n = v.reshape(v.shape[0], -1).norm(dim=1).reshape((-1,) + (1,) * (w.dim() - 1))
+    return gain * v / n
+
+
+def forced_renorm(w: torch.Tensor) -> torch.Tensor:
+    """The forced step after an optimiser update: each filter replaced by its centred,
+    normalised version scaled to norm sqrt(fan-in), which leaves weight_norm unchanged."""
+    fan = w[0].numel()
+    return weight_norm(w, torch.tensor(float(fan) ** 0.5, dtype=w.dtype))

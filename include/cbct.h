@@ -333,6 +333,7 @@ typedef struct {
     int lire;                    /* 1 (needs reversible = 1, residual_input = 0): the iteration of
                                     Algorithm 1 at one resolution, see below. 0: off. */
     int p4;                      /* 1: P4-equivariant primal blocks (Sec. 2.6), see below. 0: plain */
+    int unet;                    /* 1 (needs p4): the primal block is a P4 U-Net of depth 1, see below */
 } cbct_lpd_desc;
 
 /* Network on geometry g (which must outlive it): per iteration n a dual block

@@ -113,7 +113,7 @@ def backproject(G, y):
 def lpd(G, y: torch.Tensor, x0: torch.Tensor | None, w_red: torch.Tensor, dual_params, primal_params,
         n_mem: int = 5, round_bf16: bool = True, mu_ref: float = 1.0, bp_scale: float = 1.0,
         f0: torch.Tensor | None = None, h0: torch.Tensor | None = None, return_state: bool = False,
-        round_grads: bool = False, residual_input: bool = False, p4: bool = False):
+        round_grads: bool = False, residual_input: bool = False, p4: bool = False, unet: bool = False):
     """Learned primal-dual (Adler-style memory of n_mem channels, the reading of the
     paper's primal/dual latents for this workload), in units of mu_ref:
         f <- x0 / mu_ref repeated (or the given f0), h <- 0 (or the given h0)
@@ -137,22 +137,24 @@ def lpd(G, y: torch.Tensor, x0: torch.Tensor | None, w_red: torch.Tensor, dual_p
         h = h + block(inp.permute(1, 0, 2, 3), dp, round_bf16, round_grads).permute(1, 0, 2, 3)
         bp = bp_scale * backproject(G, w_red.view(1, 1, -1) * h[1])
         inp = torch.cat([f, bp.unsqueeze(0)], 0).unsqueeze(0)             # [1, n_mem + 1, nz, ny, nx]
-        f = f + primal_block(inp, pp, round_bf16, round_grads, p4)[0]
+        f = f + primal_block(inp, pp, round_bf16, round_grads, p4, unet)[0]
     if return_state:
         return mu_ref * f[0], f, h
     return mu_ref * f[0]
 
 
-def primal_block(x, params, round_bf16, round_grads, p4):
-    """The primal block: plain 3x3x3 layers, or P4-equivariant ones (p4_block) whose
-    params are base filters."""
+def primal_block(x, params, round_bf16, round_grads, p4, unet=False):
+    """The primal block: plain 3x3x3 layers, P4-equivariant ones (p4_block) whose params are
+    base filters, or the P4 U-Net of depth 1 (p4_unet)."""
+    if unet:
+        return p4_unet(x, params, round_bf16, round_grads)
     return p4_block(x, params, round_bf16, round_grads) if p4 else block(x, params, round_bf16, round_grads)
 
 
 def lpd_reversible(G, y: torch.Tensor, x0: torch.Tensor, w_red: torch.Tensor, dual_params, primal_params, perms_f,
                    perms_h, n_mem: int = 6, round_bf16: bool = True, mu_ref: float = 1.0, bp_scale: float = 1.0,
                    round_grads: bool = False, residual_input: bool = False, return_state: bool = False,
-                   p4: bool = False):
+                   p4: bool = False, unet: bool = False):
     """Learned primal-dual with additive coupling and channel permutations (Algorithm 1:
     split, update the second half from the first, combine, permute), in units of mu_ref.
     With M = n_mem (even), f = [p1, p2] and h = [d1, d2] halves of M / 2 channels:
@@ -179,7 +181,7 @@ def lpd_reversible(G, y: torch.Tensor, x0: torch.Tensor, w_red: torch.Tensor, du
             chans.append((pf - y).unsqueeze(0))
         d2 = d2 + block(torch.cat(chans, 0).permute(1, 0, 2, 3), dp, round_bf16, round_grads).permute(1, 0, 2, 3)
         bp = bp_scale * backproject(G, w_red.view(1, 1, -1) * d2[0])
-        p2 = p2 + primal_block(torch.cat([p1, bp.unsqueeze(0)], 0).unsqueeze(0), pp, round_bf16, round_grads, p4)[0]
+        p2 = p2 + primal_block(torch.cat([p1, bp.unsqueeze(0)], 0).unsqueeze(0), pp, round_bf16, round_grads, p4, unet)[0]
         h = torch.cat([d1, d2], 0)[list(perms_h[n])]
         f = torch.cat([p1, p2], 0)[list(perms_f[n])]
     if return_state:
@@ -224,7 +226,8 @@ def mixes_halves(perm) -> bool:
 
 def lire(G, y: torch.Tensor, x0: torch.Tensor, w_red: torch.Tensor, V: torch.Tensor, dual_params, primal_params,
          out_params, perms_f, perms_h, n_mem: int = 8, round_bf16: bool = True, mu_ref: float = 1.0,
-         bp_scale: float = 1.0, round_grads: bool = False, return_state: bool = False, p4: bool = False):
+         bp_scale: float = 1.0, round_grads: bool = False, return_state: bool = False, p4: bool = False,
+         unet: bool = False):
     """The learned iterative scheme of Algorithm 1 (Sec. 2.6) at one resolution, in the
     reading used by the library (units: f in mu_ref, h and y in line-integral units):
         x <- x0                                              (FDK_w start)
@@ -257,7 +260,7 @@ def lire(G, y: torch.Tensor, x0: torch.Tensor, w_red: torch.Tensor, V: torch.Ten
         bop = bp_scale * backproject(G, w_red.view(1, 1, -1) * d2[0])
         lw = bp_scale * backproject(G, res)
         inp = torch.cat([p1, bop.unsqueeze(0), (x / mu_ref).unsqueeze(0), lw.unsqueeze(0), V.unsqueeze(0)], 0)
-        p2 = p2 + primal_block(inp.unsqueeze(0), pp, round_bf16, round_grads, p4)[0]
+        p2 = p2 + primal_block(inp.unsqueeze(0), pp, round_bf16, round_grads, p4, unet)[0]
         f = torch.cat([p1, p2], 0)
         h = torch.cat([d1, d2], 0)
         x = x + mu_ref * ((om.view(-1, 1, 1, 1) * f).sum(0) + be)

@@ -55,6 +55,8 @@ struct LayerSpec {
     // (cb outputs, cib inputs) expanded into full weights at fw_off / fb_off
     int kind = 0, cb = 0, cib = 0;
     long long fw_off = 0, fb_off = 0;
+    int cpin = 32;  // channel slots of the layer's input activation
+    int last = 0;   // the block's output layer (initialised 10x smaller)
 };
 
 // one P4 layer for the expansion / contraction kernels
@@ -84,7 +86,14 @@ struct cbct_lpd {
     float *x = nullptr, *Vb = nullptr, *t2v = nullptr, *t2p = nullptr, *gx = nullptr, *opart = nullptr;
     int fin_f[8] = {}, fin_h[8] = {};
     int cur_f[8] = {}, cur_h[8] = {};  // plane of each logical channel of the states held now
-    std::vector<LayerSpec> layers;  // per iteration: 3 dual then 3 primal
+    std::vector<LayerSpec> layers;  // per iteration: 3 dual layers, then the primal block's (3, or 6 for the U-Net)
+    std::vector<int> dual_at, prim_at;  // index of each iteration's first dual / primal layer
+    int unet = 0;                       // primal block: P4 U-Net of depth 1 (Sec. 2.6)
+    // U-Net activations (BF16 row-blocked): a (full, 4F), C = [up(r), s] (full, 64 slots),
+    // p = pool(s) (half, 4F), q, r (half, 8F), t (full, 4F); uh1, uh2: half-resolution gradients
+    __nv_bfloat16 *u_a = nullptr, *u_C = nullptr, *u_p = nullptr, *u_q = nullptr, *u_r = nullptr, *u_t = nullptr;
+    __nv_bfloat16 *u_h1 = nullptr, *u_h2 = nullptr;
+    __nv_bfloat16 *u_ga = nullptr, *u_gb = nullptr;  // 16-channel gradients (full resolution, 32 slots)
     long long nparams = 0;
     float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
     float *wred = nullptr;  // redundancy weight [nu]
@@ -432,6 +441,93 @@ int grid_n(long long n) {
 
 }  // namespace
 
+// ---- U-Net primal block: 2 x 2 x 2 resampling of BF16 row-blocked activations ----------------
+// A row-blocked tensor with cp slots holds (img, d, h, w, channel c) at
+// ((((img D + d) H + h) (cp / 8) + c / 8) W + w) 8 + c % 8; g0 selects a run of channel
+// groups inside a wider tensor. One thread moves one pixel's 8-channel group (16 bytes).
+struct Rb {
+    __nv_bfloat16 *p;
+    int cp, g0;  // slots per pixel, first channel group
+};
+
+__device__ __forceinline__ uint4 *rb_at(const Rb &t, long long row, int g, int W, int w) {
+    return reinterpret_cast<uint4 *>(t.p + ((row * (t.cp / 8) + t.g0 + g) * (long long)W + w) * 8);
+}
+
+__device__ __forceinline__ void rb_unpack(const uint4 &v, float *f) {
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float2 t = __bfloat1622float2(h[j]);
+        f[2 * j] = t.x;
+        f[2 * j + 1] = t.y;
+    }
+}
+
+__device__ __forceinline__ uint4 rb_pack(const float *f) {
+    uint4 v;
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&v);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+    return v;
+}
+
+// dst (half resolution) = scale x the sum of src over each 2 x 2 x 2 block (scale 1/8: the
+// mean, the pooling; scale 1: the adjoint of nearest upsampling). D, H, W: the fine sizes (even).
+__global__ void k_pool2_rb(Rb src, Rb dst, int ng, int nimg, int D, int H, int W, float scale) {
+    const int D2 = D / 2, H2 = H / 2, W2 = W / 2;
+    const long long n = (long long)nimg * D2 * H2 * ng * W2;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int w2 = (int)(e % W2), g = (int)((e / W2) % ng);
+        const long long row2 = e / ((long long)W2 * ng);
+        const int h2 = (int)(row2 % H2), d2 = (int)((row2 / H2) % D2), img = (int)(row2 / ((long long)H2 * D2));
+        float acc[8] = {};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const long long row = ((long long)img * D + 2 * d2 + (k >> 2)) * H + 2 * h2 + ((k >> 1) & 1);
+            float f[8];
+            rb_unpack(*rb_at(src, row, g, W, 2 * w2 + (k & 1)), f);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] += f[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] *= scale;
+        *rb_at(dst, row2, g, W2, w2) = rb_pack(acc);
+    }
+}
+
+// dst (full resolution, D, H, W) = nearest upsampling of src (half resolution)
+__global__ void k_up2_rb(Rb src, Rb dst, int ng, int nimg, int D, int H, int W) {
+    const long long n = (long long)nimg * D * H * ng * W;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int w = (int)(e % W), g = (int)((e / W) % ng);
+        const long long row = e / ((long long)W * ng);
+        const int h = (int)(row % H), d = (int)((row / H) % D), img = (int)(row / ((long long)H * D));
+        const long long row2 = ((long long)img * (D / 2) + d / 2) * (H / 2) + h / 2;
+        *rb_at(dst, row, g, W, w) = *rb_at(src, row2, g, W / 2, w / 2);
+    }
+}
+
+// Gradient of the skip activation s (full resolution): the concatenation's share gc (already
+// multiplied by the LeakyReLU derivative at s) plus that derivative times the pooling's
+// adjoint of gp (half resolution): out = gc + (s > 0 ? 1 : slope) gp[coarse] / 8.
+__global__ void k_skip_grad_rb(Rb gc, Rb s, Rb gp, Rb out, int ng, int nimg, int D, int H, int W, float slope) {
+    const long long n = (long long)nimg * D * H * ng * W;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int w = (int)(e % W), g = (int)((e / W) % ng);
+        const long long row = e / ((long long)W * ng);
+        const int h = (int)(row % H), d = (int)((row / H) % D), img = (int)(row / ((long long)H * D));
+        const long long row2 = ((long long)img * (D / 2) + d / 2) * (H / 2) + h / 2;
+        float a[8], m[8], q[8];
+        rb_unpack(*rb_at(gc, row, g, W, w), a);
+        rb_unpack(*rb_at(s, row, g, W, w), m);
+        rb_unpack(*rb_at(gp, row2, g, W / 2, w / 2), q);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] += (m[j] > 0.f ? 1.f : slope) * (0.125f * q[j]);
+        *rb_at(out, row, g, W, w) = rb_pack(a);
+    }
+}
+
 static void p4_expand(cbct_lpd *m, cudaStream_t st) {
     if (!m->n_p4) return;
     dim3 grd((unsigned)std::min<long long>(64, (m->p4_max + 255) / 256 + 1), (unsigned)m->n_p4);
@@ -451,18 +547,18 @@ static inline int hs(int c) { return c > 32 ? 64 : 32; }
 // forward conv of layer L; the residual epilogue (epi 1) writes state = state_in + conv
 static int conv_fwd(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *x, int cpin, int nimg, int D, int H, int W,
                     int epi, __nv_bfloat16 *y, float *state, long long sstride, cudaStream_t st,
-                    const float *state_in = nullptr, int zero_state_in = 0) {
+                    const float *state_in = nullptr, int zero_state_in = 0, int cpout = 0) {
     return conv_apply(x, nimg, D, H, W, cpin, L.taps3d, m->params + L.fw_off, m->params + L.fb_off, L.cin, L.cout, 0, epi,
-                      m->d.slope, y, hs(L.cout), nullptr, state_in, state, sstride, m->status, st, m->wpk + L.pk_off,
-                      zero_state_in);
+                      m->d.slope, y, cpout ? cpout : hs(L.cout), nullptr, state_in, state, sstride, m->status, st,
+                      m->wpk + L.pk_off, zero_state_in);
 }
 
 // input-gradient conv of layer L: dy (BF16 [..][cp_dy], L.cout channels) -> L.cin outputs
 static int conv_dx(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *dy, int cp_dy, int nimg, int D, int H, int W,
                    int epi, __nv_bfloat16 *y, const __nv_bfloat16 *mask, float *state, long long sstride,
-                   cudaStream_t st) {
+                   cudaStream_t st, int cpout = 0, float slope = -1.f) {
     return cbct_conv(dy, nimg, D, H, W, cp_dy, L.taps3d, m->params + L.fw_off, nullptr, L.cin, L.cout, 1, epi,
-                     m->d.slope, y, hs(L.cin), mask, state, sstride, m->status, st);
+                     slope < 0.f ? m->d.slope : slope, y, cpout ? cpout : hs(L.cin), mask, state, sstride, m->status, st);
 }
 
 // geometry of the two blocks' tensors for a batch of B volumes: dual = B na images of nv x nu
@@ -485,12 +581,98 @@ static Planes dual_planes(const cbct_lpd *m, const float *h, const float *pf, co
 // workspaces (a1, a2, b1, b2, din, pin).
 // pf, bp: where the iteration's P f_1 and P^T (w h_1) go (workspaces, or the per-
 // iteration buffers of a training forward). h_zero: h_in is zero and is not read.
+// ---- primal block: the three-layer block or the P4 U-Net, from the packed input m->pin ----
+// U-Net sizes (full resolution nz x ny x nx, half resolution each halved)
+#define UNET_HALF B, m->g->dev.n[2] / 2, m->g->dev.n[1] / 2, m->g->dev.n[0] / 2
+#define UNET_FULL_N B, m->g->dev.n[2], m->g->dev.n[1], m->g->dev.n[0]
+
+static int rb_grid(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 32LL * sm_count())); }
+
+// activations of every layer but the last (3-layer block: b1, b2; U-Net: a, s in C, pool(s),
+// q, r, up(r) into C, t)
+static int prim_hidden(cbct_lpd *m, const LayerSpec *Lp, int B, cudaStream_t st) {
+    int rc;
+    if (!m->unet) {
+        if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) return rc;
+        return conv_fwd(m, Lp[1], m->b1, hs(Lp[1].cin), PRIM_DIMS, 0, m->b2, nullptr, 0, st);
+    }
+    const int nx = m->g->dev.n[0];
+    const long long nvh = (long long)B * m->nvox / 8;
+    if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->u_a, nullptr, 0, st))) return rc;
+    // s = g2(a) into channel groups 4, 5 of C (the epilogue writes groups from the pointer on)
+    if ((rc = conv_fwd(m, Lp[1], m->u_a, 32, PRIM_DIMS, 0, m->u_C + 32LL * nx, nullptr, 0, st, nullptr, 0, 64))) return rc;
+    k_pool2_rb<<<rb_grid(nvh * 2), 256, 0, st>>>(Rb{m->u_C, 64, 4}, Rb{m->u_p, 32, 0}, 2, UNET_FULL_N, 0.125f);
+    if ((rc = conv_fwd(m, Lp[2], m->u_p, 32, UNET_HALF, 0, m->u_q, nullptr, 0, st))) return rc;
+    if ((rc = conv_fwd(m, Lp[3], m->u_q, 32, UNET_HALF, 0, m->u_r, nullptr, 0, st))) return rc;
+    k_up2_rb<<<rb_grid(nvh * 8 * 4), 256, 0, st>>>(Rb{m->u_r, 32, 0}, Rb{m->u_C, 64, 0}, 4, UNET_FULL_N);
+    return conv_fwd(m, Lp[4], m->u_C, 64, PRIM_DIMS, 0, m->u_t, nullptr, 0, st);
+}
+
+// the block's output layer and the activation it reads
+static const LayerSpec &prim_out(const cbct_lpd *m, const LayerSpec *Lp) { return Lp[m->unet ? 5 : 2]; }
+static const __nv_bfloat16 *prim_out_in(const cbct_lpd *m, const LayerSpec *Lp) { return m->unet ? m->u_t : m->b2; }
+static int prim_out_cp(const cbct_lpd *m, const LayerSpec *Lp) { return m->unet ? 32 : hs(Lp[2].cin); }
+
+// Backward through the block (activations from prim_hidden): upstream gradient of its
+// output in m->gsmall (8 slots); weight and bias gradients into dW; the gradient of the
+// block input added to the FP32 planes gdst (channel c into plane map[c], or c).
+static int prim_bwd(cbct_lpd *m, const LayerSpec *Lp, int B, float *gdst, long long sstride, const int *map,
+                    float *dW, cudaStream_t st) {
+    int rc;
+    const __nv_bfloat16 *gin;  // gradient at the first layer's output (pre-activation)
+    int gcp;
+    if (!m->unet) {
+        if ((rc = conv_wgrad(m->b2, hs(Lp[2].cin), Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].fw_off,
+                             dW + Lp[2].fb_off, Lp[2].kind ? 0 : 1, m->status, st))) return rc;
+        if ((rc = conv_dx(m, Lp[2], m->gsmall, 8, PRIM_DIMS, 2, m->g32a, m->b2, nullptr, 0, st))) return rc;
+        if ((rc = conv_wgrad(m->b1, hs(Lp[1].cin), Lp[1].cin, m->g32a, hs(Lp[1].cout), Lp[1].cout, PRIM_DIMS, 1,
+                             dW + Lp[1].fw_off, dW + Lp[1].fb_off, Lp[1].kind ? 0 : 1, m->status, st))) return rc;
+        if ((rc = conv_dx(m, Lp[1], m->g32a, hs(Lp[1].cout), PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) return rc;
+        gin = m->g32b;
+        gcp = hs(Lp[0].cout);
+    } else {
+        const int nx = m->g->dev.n[0];
+        const long long nvh = (long long)B * m->nvox / 8;
+        auto wg = [&](const LayerSpec &L, const __nv_bfloat16 *x, int cpx, const __nv_bfloat16 *dy, int cpy, int half) {
+            return half ? conv_wgrad(x, cpx, L.cin, dy, cpy, L.cout, UNET_HALF, 1, dW + L.fw_off, dW + L.fb_off, 0,
+                                     m->status, st)
+                        : conv_wgrad(x, cpx, L.cin, dy, cpy, L.cout, PRIM_DIMS, 1, dW + L.fw_off, dW + L.fb_off, 0,
+                                     m->status, st);
+        };
+        // out = avg6(t): dt (masked by t) in u_ga
+        if ((rc = wg(Lp[5], m->u_t, 32, m->gsmall, 8, 0))) return rc;
+        if ((rc = conv_dx(m, Lp[5], m->gsmall, 8, PRIM_DIMS, 2, m->u_ga, m->u_t, nullptr, 0, st, 32))) return rc;
+        // t = g5(C): dC (masked by C) in g32b, 48 channels in 64 slots
+        if ((rc = wg(Lp[4], m->u_C, 64, m->u_ga, 32, 0))) return rc;
+        if ((rc = conv_dx(m, Lp[4], m->u_ga, 32, PRIM_DIMS, 2, m->g32b, m->u_C, nullptr, 0, st, 64))) return rc;
+        // C[0..8F) = up(r): dr = block sums of dC's first 4 groups (half resolution, u_h1)
+        k_pool2_rb<<<rb_grid(nvh * 4), 256, 0, st>>>(Rb{m->g32b, 64, 0}, Rb{m->u_h1, 32, 0}, 4, UNET_FULL_N, 1.f);
+        if ((rc = wg(Lp[3], m->u_q, 32, m->u_h1, 32, 1))) return rc;
+        if ((rc = conv_dx(m, Lp[3], m->u_h1, 32, UNET_HALF, 2, m->u_h2, m->u_q, nullptr, 0, st, 32))) return rc;
+        if ((rc = wg(Lp[2], m->u_p, 32, m->u_h2, 32, 1))) return rc;
+        // d pool(s): no activation after the pooling (slope 1 leaves the sum as it is), 16 slots
+        if ((rc = conv_dx(m, Lp[2], m->u_h2, 32, UNET_HALF, 0, m->u_h1, nullptr, nullptr, 0, st, 16, 1.f))) return rc;
+        // ds = dC's groups 4, 5 (masked) + mask(s) x pool adjoint, into u_ga
+        k_skip_grad_rb<<<rb_grid(nvh * 8 * 2), 256, 0, st>>>(Rb{m->g32b, 64, 4}, Rb{m->u_C, 64, 4}, Rb{m->u_h1, 16, 0},
+                                                              Rb{m->u_ga, 32, 0}, 2, UNET_FULL_N, m->d.slope);
+        if ((rc = wg(Lp[1], m->u_a, 32, m->u_ga, 32, 0))) return rc;
+        if ((rc = conv_dx(m, Lp[1], m->u_ga, 32, PRIM_DIMS, 2, m->u_gb, m->u_a, nullptr, 0, st, 32))) return rc;
+        gin = m->u_gb;
+        gcp = 32;
+        (void)nx;
+    }
+    if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, gin, gcp, Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].fw_off, dW + Lp[0].fb_off,
+                         Lp[0].kind ? 0 : 1, m->status, st))) return rc;
+    return conv_apply(gin, PRIM_DIMS, gcp, 1, m->params + Lp[0].fw_off, nullptr, Lp[0].cin, Lp[0].cout, 1, 1,
+                      m->d.slope, nullptr, 32, nullptr, gdst, gdst, sstride, m->status, st, nullptr, 0, map, 0);
+}
+
 static int lpd_iter_fwd(cbct_lpd *m, int n, const float *f_in, const float *h_in, float *f_out, float *h_out,
                         float *pf, float *bp, cudaStream_t st, bool h_zero = false) {
     const int B = m->batch;
     const long long NV = m->nvox * B, NP = m->nproj * B;  // one channel of the batch
     const int M = m->d.n_mem;
-    const LayerSpec *Ld = &m->layers[6 * n], *Lp = &m->layers[6 * n + 3];
+    const LayerSpec *Ld = &m->layers[m->dual_at[n]], *Lp = &m->layers[m->prim_at[n]];
     void *sv = (void *)st;
     // dual block input [h (M), mu_ref P f_1, y (, mu_ref P f_1 - y)]
     int rc = forward_project(m->g, f_in + 1 * NV, pf, B, 0, sv);
@@ -507,9 +689,9 @@ static int lpd_iter_fwd(cbct_lpd *m, int n, const float *f_in, const float *h_in
     for (int c = 0; c < M; ++c) { pp.p[c] = f_in + c * NV; pp.s[c] = 1.f; }
     pp.p[M] = bp; pp.s[M] = m->bp_scale;
     k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
-    if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) return rc;
-    if ((rc = conv_fwd(m, Lp[1], m->b1, hs(Lp[1].cin), PRIM_DIMS, 0, m->b2, nullptr, 0, st))) return rc;
-    if ((rc = conv_fwd(m, Lp[2], m->b2, hs(Lp[2].cin), PRIM_DIMS, 1, nullptr, f_out, NV, st, f_in))) return rc;
+    if ((rc = prim_hidden(m, Lp, B, st))) return rc;
+    if ((rc = conv_fwd(m, prim_out(m, Lp), prim_out_in(m, Lp), prim_out_cp(m, Lp), PRIM_DIMS, 1, nullptr, f_out, NV, st,
+                       f_in))) return rc;
     CBCT_LAUNCH_CHECK("lpd iteration");
     return 0;
 }
@@ -530,20 +712,24 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
                                  "residual_input and reversible 0 or 1, max_batch <= 64, max_batch * n_angles <= "
                                  "65535 (half that with lire), and 2 <= n_mem <= 6 (<= 5 with the residual channel) or, reversible, "
                                  "n_mem even in [2, 8]; lire needs reversible and no residual_input");
+    if ((d.unet != 0 && d.unet != 1) ||
+        (d.unet && (!d.p4 || g->dev.n[0] % 2 || g->dev.n[1] % 2 || g->dev.n[2] % 2)))
+        return fail(CBCT_EINVAL, "lpd_create: unet is 0 or 1 and needs p4 and even volume sizes (2 x 2 x 2 pooling)");
     cbct_lpd *m = new (std::nothrow) cbct_lpd();
     if (!m) return fail(CBCT_ENOMEM, "lpd_create: host allocation");
     m->g = g;
     m->d = d;
     m->maxb = maxb;
+    m->unet = d.unet;
     const int K = rev ? d.n_mem / 2 : d.n_mem;  // channels a block reads from / writes to each state
     m->nd = K + 2 + d.residual_input;
     m->nvox = (long long)g->dev.n[0] * g->dev.n[1] * g->dev.n[2];
     m->nproj = (long long)g->dev.na * g->dev.nv * g->dev.nu;
     const int M = d.n_mem, W = d.width;
     long long off = 0;
-    auto add = [&](int cin, int cout, int t3, int H) {
+    auto add = [&](int cin, int cout, int t3, int H, int cpin, int last) {
         LayerSpec L;
-        L.cin = cin; L.cout = cout; L.taps3d = t3; L.H = H;
+        L.cin = cin; L.cout = cout; L.taps3d = t3; L.H = H; L.cpin = cpin; L.last = last;
         L.w_off = off; off += (long long)cout * (t3 ? 27 : 9) * cin;
         L.b_off = off; off += cout;
         L.fw_off = L.w_off; L.fb_off = L.b_off;
@@ -553,34 +739,49 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     // (lifting) or [cb][4][27][cib] (group, averaged), biases [cb]; the full weights they
     // expand to are placed after all learnable parameters (below)
     constexpr int kP4Base = 8;
-    auto add_p4 = [&](int kind, int cin_full, int cout_full, int H) {
+    auto add_p4 = [&](int kind, int cin_full, int cout_full, int H, int cpin, int last) {
         LayerSpec L;
-        L.kind = kind; L.taps3d = 1; L.H = H; L.cin = cin_full; L.cout = cout_full;
+        L.kind = kind; L.taps3d = 1; L.H = H; L.cin = cin_full; L.cout = cout_full; L.cpin = cpin; L.last = last;
         L.cb = kind == 3 ? cout_full : cout_full / 4;
         L.cib = kind == 1 ? cin_full : cin_full / 4;
         L.w_off = off; off += (long long)L.cb * (kind == 1 ? 1 : 4) * 27 * L.cib;
         L.b_off = off; off += L.cb;
         m->layers.push_back(L);
     };
+    // U-Net: 4F group channels (16) at full resolution in 32 slots (the upper 16 stay zero, so
+    // the weight gradients run on the tensor cores), 8F at half resolution (32), the
+    // concatenation [up(r), s] of 12F channels in 64 slots
+    constexpr int kUF = 4;
     auto add_primal = [&](int cin, int H) {
-        if (d.p4) {
-            add_p4(1, cin, 4 * kP4Base, H); add_p4(2, 4 * kP4Base, 4 * kP4Base, H); add_p4(3, 4 * kP4Base, K, H);
+        if (d.unet) {
+            add_p4(1, cin, 4 * kUF, H, 8, 0);                  // a = lift(x)
+            add_p4(2, 4 * kUF, 4 * kUF, H, 32, 0);             // s = g2(a)
+            add_p4(2, 4 * kUF, 8 * kUF, H / 2, 32, 0);         // q = g3(pool(s))
+            add_p4(2, 8 * kUF, 8 * kUF, H / 2, 32, 0);         // r = g4(q)
+            add_p4(2, 12 * kUF, 4 * kUF, H, 64, 0);            // t = g5([up(r), s])
+            add_p4(3, 4 * kUF, K, H, 32, 1);                   // group average
+        } else if (d.p4) {
+            add_p4(1, cin, 4 * kP4Base, H, 8, 0); add_p4(2, 4 * kP4Base, 4 * kP4Base, H, 32, 0);
+            add_p4(3, 4 * kP4Base, K, H, 32, 1);
         } else {
-            add(cin, W, 1, H); add(W, W, 1, H); add(W, K, 1, H);
+            add(cin, W, 1, H, 8, 0); add(W, W, 1, H, hs(W), 0); add(W, K, 1, H, hs(W), 1);
         }
     };
     for (int n = 0; n < d.n_iter; ++n) {
         const int nv = g->dev.nv, ny = g->dev.n[1];
+        m->dual_at.push_back((int)m->layers.size());
         if (d.lire) {
             // Algorithm 1 blocks: 3x3x3 over (angle, v, u) and over the volume, K + 4 inputs each,
             // then the output convolution's omega [n_mem] and beta
-            add(K + 4, W, 1, nv); add(W, W, 1, nv); add(W, K, 1, nv);   // dual
-            add_primal(K + 4, ny);                                          // primal
+            add(K + 4, W, 1, nv, 8, 0); add(W, W, 1, nv, hs(W), 0); add(W, K, 1, nv, hs(W), 1);   // dual
+            m->prim_at.push_back((int)m->layers.size());
+            add_primal(K + 4, ny);                                                                // primal
             m->out_off.push_back(off);
             off += M + 1;
         } else {
-            add(m->nd, W, 0, nv); add(W, W, 0, nv); add(W, K, 0, nv);   // dual
-            add_primal(K + 1, ny);                                          // primal
+            add(m->nd, W, 0, nv, 8, 0); add(W, W, 0, nv, hs(W), 0); add(W, K, 0, nv, hs(W), 1);   // dual
+            m->prim_at.push_back((int)m->layers.size());
+            add_primal(K + 1, ny);                                                                // primal
         }
     }
     m->nparams = off;
@@ -602,7 +803,7 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     for (size_t i = 0; i < m->layers.size(); ++i) {
         const LayerSpec &L = m->layers[i];
         const int taps = L.taps3d ? 27 : 9;
-        const double sd = sqrt(2.0 / (L.cin * taps)) * ((i % 3 == 2) ? 0.1 : 1.0);  // fan-in of the full layer
+        const double sd = sqrt(2.0 / (L.cin * taps)) * (L.last ? 0.1 : 1.0);  // fan-in of the full layer
         const long long nw = L.b_off - L.w_off;
         for (long long k = 0; k < nw; ++k) hp[L.w_off + k] = (float)(sd * rng.normal());
     }
@@ -647,12 +848,27 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     al((void **)&m->bp_saved, sizeof(float) * std::max(1, NI) * NV);
     al((void **)&m->din, sizeof(__nv_bfloat16) * NP * 8);
     // hidden activations: dual layers at the model width, primal layers at it too (P4: 4 x 8)
-    const int sd = hs(W), sp = d.p4 ? 32 : hs(W);
+    const int sd = hs(W), sp = d.unet ? 64 : (d.p4 ? 32 : hs(W));
     al((void **)&m->a1, sizeof(__nv_bfloat16) * NP * sd);
     al((void **)&m->a2, sizeof(__nv_bfloat16) * NP * sd);
     al((void **)&m->pin, sizeof(__nv_bfloat16) * NV * 8);
-    al((void **)&m->b1, sizeof(__nv_bfloat16) * NV * sp);
-    al((void **)&m->b2, sizeof(__nv_bfloat16) * NV * sp);
+    al((void **)&m->b1, sizeof(__nv_bfloat16) * NV * (d.unet ? 8 : sp));
+    al((void **)&m->b2, sizeof(__nv_bfloat16) * NV * (d.unet ? 8 : sp));
+    if (d.unet) {
+        al((void **)&m->u_a, sizeof(__nv_bfloat16) * NV * 32);
+        al((void **)&m->u_C, sizeof(__nv_bfloat16) * NV * 64);
+        al((void **)&m->u_t, sizeof(__nv_bfloat16) * NV * 32);
+        al((void **)&m->u_p, sizeof(__nv_bfloat16) * (NV / 8) * 32);
+        al((void **)&m->u_q, sizeof(__nv_bfloat16) * (NV / 8) * 32);
+        al((void **)&m->u_r, sizeof(__nv_bfloat16) * (NV / 8) * 32);
+        al((void **)&m->u_h1, sizeof(__nv_bfloat16) * (NV / 8) * 32);
+        al((void **)&m->u_h2, sizeof(__nv_bfloat16) * (NV / 8) * 32);
+        al((void **)&m->u_ga, sizeof(__nv_bfloat16) * NV * 32);
+        al((void **)&m->u_gb, sizeof(__nv_bfloat16) * NV * 32);
+        // 16-channel tensors in 32 slots: the upper slots are never written and stay zero
+        for (__nv_bfloat16 *z : {m->u_a, m->u_t, m->u_p, m->u_ga, m->u_gb})
+            if (e == cudaSuccess && z) e = cudaMemset(z, 0, sizeof(__nv_bfloat16) * (z == m->u_p ? NV / 8 : NV) * 32);
+    }
     al((void **)&m->g32a, sizeof(__nv_bfloat16) * std::max(NP * sd, NV * sp));
     al((void **)&m->g32b, sizeof(__nv_bfloat16) * std::max(NP * sd, NV * sp));
     al((void **)&m->gsmall, sizeof(__nv_bfloat16) * std::max(NP, NV) * 8);
@@ -675,7 +891,7 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     for (size_t i = 0; i < m->layers.size(); ++i) {
         LayerSpec &L = m->layers[i];
         ConvPackJob lj[kConvMaxOut / 32];
-        const long long b = conv_plan(L.taps3d, L.H, i % 3 == 0 ? 8 : hs(L.cin), L.cin, L.cout, 0, lj);
+        const long long b = conv_plan(L.taps3d, L.H, L.cpin, L.cin, L.cout, 0, lj);
         if (b < 0) {
             lpd_destroy(m);
             return fail(CBCT_EINVAL, "lpd_create: no convolution plan for layer " + std::to_string(i));
@@ -748,6 +964,7 @@ extern "C" void lpd_destroy(cbct_lpd *m) {
     cudaDeviceSynchronize();
     void *ptrs[] = {m->p4_jobs, m->x, m->gx, m->Vb, m->t2v, m->t2p, m->opart, m->wpk, m->pack_jobs, m->clip, m->pf_saved, m->bp_saved, m->params, m->grads, m->adam_m, m->adam_v, m->wred, m->f, m->h,
                     m->y, m->tproj, m->tproj2, m->tvol, m->din, m->a1, m->a2, m->pin, m->b1, m->b2, m->g32a, m->g32b, m->gsmall, m->gf, m->gh,
+                    m->u_a, m->u_C, m->u_t, m->u_p, m->u_q, m->u_r, m->u_h1, m->u_h2, m->u_ga, m->u_gb,
                     m->status};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -884,7 +1101,7 @@ static Planes rev_primal_planes(const cbct_lpd *m, const float *f, const int *pf
 // (ssub = 1 subtracts it again)
 static int rev_update(cbct_lpd *m, const LayerSpec &L, const __nv_bfloat16 *act, int nimg, int D, int H, int W,
                       float *state, const int *map2, long long sstride, int ssub, cudaStream_t st) {
-    return conv_apply(act, nimg, D, H, W, hs(L.cin), L.taps3d, m->params + L.fw_off, m->params + L.fb_off, L.cin, L.cout,
+    return conv_apply(act, nimg, D, H, W, L.cpin, L.taps3d, m->params + L.fw_off, m->params + L.fb_off, L.cin, L.cout,
                       0, 1, m->d.slope, nullptr, 32, nullptr, state, state, sstride, m->status, st, m->wpk + L.pk_off, 0,
                       map2, ssub);
 }
@@ -904,7 +1121,7 @@ static int lpd_rev_forward(cbct_lpd *m, const float *y, const float *x0, float *
     int pfm[8], phm[8];
     for (int c = 0; c < M; ++c) pfm[c] = phm[c] = c;
     for (int n = 0; n < N && rc == 0; ++n) {
-        const LayerSpec *Ld = &m->layers[6 * n], *Lp = &m->layers[6 * n + 3];
+        const LayerSpec *Ld = &m->layers[m->dual_at[n]], *Lp = &m->layers[m->prim_at[n]];
         // dual: d2 += Gamma([d1, mu_ref P p2[0], y (, residual)])
         if ((rc = forward_project(m->g, m->f + pfm[K] * NV, m->tproj, B, 0, sv))) break;
         const Planes pl = rev_dual_planes(m, m->h, phm, NP, m->tproj, m->y);
@@ -916,9 +1133,8 @@ static int lpd_rev_forward(cbct_lpd *m, const float *y, const float *x0, float *
         if ((rc = back_project_colw(m->g, m->h + phm[K] * NP, m->wred, m->tvol, B, 0, st))) break;
         const Planes pp = rev_primal_planes(m, m->f, pfm, NV, m->tvol);
         k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
-        if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_fwd(m, Lp[1], m->b1, hs(Lp[1].cin), PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
-        if ((rc = rev_update(m, Lp[2], m->b2, PRIM_DIMS, m->f, pfm + K, NV, 0, st))) break;
+        if ((rc = prim_hidden(m, Lp, B, st))) break;
+        if ((rc = rev_update(m, prim_out(m, Lp), prim_out_in(m, Lp), PRIM_DIMS, m->f, pfm + K, NV, 0, st))) break;
         map_permute(pfm, m->perm_f[n], M);
         map_permute(phm, m->perm_h[n], M);
     }
@@ -950,36 +1166,25 @@ static int lpd_rev_backward(cbct_lpd *m, const float *grad_x, float *grad_y, flo
     k_axpy<<<grid_n(NV), 256, 0, st>>>(gf + pfm[0] * NV, grad_x, NV, m->d.mu_ref);
     if (grad_y) cudaMemsetAsync(grad_y, 0, sizeof(float) * NP, st);
     for (int n = N - 1; n >= 0 && rc == 0; --n) {
-        const LayerSpec *Ld = &m->layers[6 * n], *Lp = &m->layers[6 * n + 3];
+        const LayerSpec *Ld = &m->layers[m->dual_at[n]], *Lp = &m->layers[m->prim_at[n]];
         map_unpermute(pfm, m->perm_f[n], M);
         map_unpermute(phm, m->perm_h[n], M);
         // ---- primal update undone: recompute its input from p1 and the final d2[0]
         if ((rc = back_project_colw(m->g, m->h + phm[K] * NP, m->wred, m->tvol, B, 0, st))) break;
         const Planes pp = rev_primal_planes(m, m->f, pfm, NV, m->tvol);
         k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
-        if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_fwd(m, Lp[1], m->b1, hs(Lp[1].cin), PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
-        if ((rc = rev_update(m, Lp[2], m->b2, PRIM_DIMS, m->f, pfm + K, NV, 1, st))) break;
+        if ((rc = prim_hidden(m, Lp, B, st))) break;
+        if ((rc = rev_update(m, prim_out(m, Lp), prim_out_in(m, Lp), PRIM_DIMS, m->f, pfm + K, NV, 1, st))) break;
         // gradients through Lambda: upstream dL/dp2 (identity through the residual)
         Planes gp{};
         for (int c = 0; c < K; ++c) { gp.p[c] = gf + pfm[K + c] * NV; gp.s[c] = 1.f; }
         k_pack8<<<grid_n(NV), 256, 0, st>>>(gp, NV, m->gsmall);
-        if ((rc = conv_wgrad(m->b2, hs(Lp[2].cin), Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].fw_off,
-                             dW + Lp[2].fb_off, Lp[2].kind ? 0 : 1, m->status, st))) break;
-        if ((rc = conv_dx(m, Lp[2], m->gsmall, 8, PRIM_DIMS, 2, m->g32a, m->b2, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->b1, hs(Lp[1].cin), Lp[1].cin, m->g32a, hs(Lp[1].cout), Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].fw_off,
-                             dW + Lp[1].fb_off, Lp[1].kind ? 0 : 1, m->status, st))) break;
-        if ((rc = conv_dx(m, Lp[1], m->g32a, hs(Lp[1].cout), PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, hs(Lp[0].cout), Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].fw_off,
-                             dW + Lp[0].fb_off, Lp[0].kind ? 0 : 1, m->status, st))) break;
         // dL/d[p1, bp]: p1's planes accumulate, the bp channel goes to scratch plane M
         int mp[8];
         for (int c = 0; c < K; ++c) mp[c] = pfm[c];
         mp[K] = M;
         cudaMemsetAsync(gf + (long long)M * NV, 0, sizeof(float) * NV, st);
-        if ((rc = conv_apply(m->g32b, PRIM_DIMS, hs(Lp[0].cout), Lp[0].taps3d, m->params + Lp[0].fw_off, nullptr, Lp[0].cin,
-                             Lp[0].cout, 1, 1, m->d.slope, nullptr, 32, nullptr, gf, gf, NV, m->status, st, nullptr,
-                             0, mp, 0))) break;
+        if ((rc = prim_bwd(m, Lp, B, gf, NV, mp, dW, st))) break;
         // bp = bp_scale P^T (w d2[0])  =>  dL/dd2[0] += w bp_scale P (dL/dbp)
         if ((rc = forward_project(m->g, gf + (long long)M * NV, m->tproj, B, 0, sv))) break;
         k_scale_cols<<<grid_n(NP), 256, 0, st>>>(m->tproj, m->wred, NP, m->g->dev.nu, m->bp_scale, m->tproj2);
@@ -1115,7 +1320,7 @@ static int lire_forward(cbct_lpd *m, const float *y, const float *x0, float *x_o
     int pfm[8], phm[8];
     for (int c = 0; c < M; ++c) pfm[c] = phm[c] = c;
     for (int n = 0; n < N && rc == 0; ++n) {
-        const LayerSpec *Ld = &m->layers[6 * n], *Lp = &m->layers[6 * n + 3];
+        const LayerSpec *Ld = &m->layers[m->dual_at[n]], *Lp = &m->layers[m->prim_at[n]];
         if ((rc = lire_project(m, pfm, B, st))) break;
         const Planes pl = lire_dual_planes(m, phm, NP);
         k_pack8<<<grid_n(NP), 256, 0, st>>>(pl, NP, m->din);
@@ -1125,9 +1330,8 @@ static int lire_forward(cbct_lpd *m, const float *y, const float *x0, float *x_o
         if ((rc = lire_backproject(m, phm, B, st))) break;
         const Planes pp = lire_primal_planes(m, pfm, NV);
         k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
-        if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_fwd(m, Lp[1], m->b1, hs(Lp[1].cin), PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
-        if ((rc = rev_update(m, Lp[2], m->b2, PRIM_DIMS, m->f, pfm + K, NV, 0, st))) break;
+        if ((rc = prim_hidden(m, Lp, B, st))) break;
+        if ((rc = rev_update(m, prim_out(m, Lp), prim_out_in(m, Lp), PRIM_DIMS, m->f, pfm + K, NV, 0, st))) break;
         k_outconv<<<grid_n(NV), 256, 0, st>>>(m->x, lire_f_planes(m, pfm, NV), m->params + m->out_off[n],
                                               m->d.mu_ref, NV, M, 1.f);
         map_permute(pfm, m->perm_f[n], M);
@@ -1163,7 +1367,7 @@ static int lire_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float 
     CBCT_CUDA_TRY(cudaMemcpyAsync(gx, grad_x, sizeof(float) * NV, cudaMemcpyDeviceToDevice, st));
     cudaMemsetAsync(gy, 0, sizeof(float) * NP, st);
     for (int n = N - 1; n >= 0 && rc == 0; --n) {
-        const LayerSpec *Ld = &m->layers[6 * n], *Lp = &m->layers[6 * n + 3];
+        const LayerSpec *Ld = &m->layers[m->dual_at[n]], *Lp = &m->layers[m->prim_at[n]];
         map_unpermute(pfm, m->perm_f[n], M);
         map_unpermute(phm, m->perm_h[n], M);
         // ---- output convolution: its gradients (with the states after the update), then undone
@@ -1179,28 +1383,18 @@ static int lire_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float 
         if ((rc = lire_backproject(m, phm, B, st))) break;
         const Planes pp = lire_primal_planes(m, pfm, NV);
         k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
-        if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_fwd(m, Lp[1], m->b1, hs(Lp[1].cin), PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
-        if ((rc = rev_update(m, Lp[2], m->b2, PRIM_DIMS, m->f, pfm + K, NV, 1, st))) break;
+        if ((rc = prim_hidden(m, Lp, B, st))) break;
+        if ((rc = rev_update(m, prim_out(m, Lp), prim_out_in(m, Lp), PRIM_DIMS, m->f, pfm + K, NV, 1, st))) break;
         // gradients through Lambda (upstream dL/dp2)
         Planes gpl{};
         for (int c = 0; c < K; ++c) { gpl.p[c] = gf + pfm[K + c] * NV; gpl.s[c] = 1.f; }
         k_pack8<<<grid_n(NV), 256, 0, st>>>(gpl, NV, m->gsmall);
-        if ((rc = conv_wgrad(m->b2, hs(Lp[2].cin), Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].fw_off,
-                             dW + Lp[2].fb_off, Lp[2].kind ? 0 : 1, m->status, st))) break;
-        if ((rc = conv_dx(m, Lp[2], m->gsmall, 8, PRIM_DIMS, 2, m->g32a, m->b2, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->b1, hs(Lp[1].cin), Lp[1].cin, m->g32a, hs(Lp[1].cout), Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].fw_off,
-                             dW + Lp[1].fb_off, Lp[1].kind ? 0 : 1, m->status, st))) break;
-        if ((rc = conv_dx(m, Lp[1], m->g32a, hs(Lp[1].cout), PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, hs(Lp[0].cout), Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].fw_off,
-                             dW + Lp[0].fb_off, Lp[0].kind ? 0 : 1, m->status, st))) break;
         // input channels [p1 (K), b_op, x / mu, LW, V] -> p1's planes, scratch M, M+2, M+1, M+3
         int mp[8];
         for (int c = 0; c < K; ++c) mp[c] = pfm[c];
         mp[K] = M; mp[K + 1] = M + 2; mp[K + 2] = M + 1; mp[K + 3] = M + 3;
         cudaMemsetAsync(gf + (long long)M * NV, 0, sizeof(float) * 4 * NV, st);
-        if ((rc = conv_apply(m->g32b, PRIM_DIMS, hs(Lp[0].cout), 1, m->params + Lp[0].fw_off, nullptr, Lp[0].cin, Lp[0].cout, 1, 1,
-                             m->d.slope, nullptr, 32, nullptr, gf, gf, NV, m->status, st, nullptr, 0, mp, 0))) break;
+        if ((rc = prim_bwd(m, Lp, B, gf, NV, mp, dW, st))) break;
         // [P dL/db_op, P dL/dLW] in one forward projection of the adjacent scratch planes M, M+1
         if ((rc = forward_project(m->g, gf + (long long)M * NV, m->t2p, 2 * B, 0, sv))) break;
         // b_op = s P^T(w d2[0])  =>  dL/dd2[0] += s w P(dL/db_op)
@@ -1339,7 +1533,7 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
     int rc = 0;
     for (int n = N - 1; n >= 0 && rc == 0; --n) {
         const float *f_n = m->f + (long long)n * M * NV, *h_n = m->h + (long long)n * M * NP;
-        const LayerSpec *Ld = &m->layers[6 * n], *Lp = &m->layers[6 * n + 3];
+        const LayerSpec *Ld = &m->layers[m->dual_at[n]], *Lp = &m->layers[m->prim_at[n]];
         float *dW = m->grads;
         const float *pf_n = m->pf_saved + (long long)n * NP;
         // recompute the dual block input and activations of iteration n (P f_1 kept)
@@ -1352,24 +1546,15 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
         for (int c = 0; c < M; ++c) { pp.p[c] = f_n + c * NV; pp.s[c] = 1.f; }
         pp.p[M] = m->bp_saved + (long long)n * NV; pp.s[M] = m->bp_scale;
         k_pack8<<<grid_n(NV), 256, 0, st>>>(pp, NV, m->pin);
-        if ((rc = conv_fwd(m, Lp[0], m->pin, 8, PRIM_DIMS, 0, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_fwd(m, Lp[1], m->b1, hs(Lp[1].cin), PRIM_DIMS, 0, m->b2, nullptr, 0, st))) break;
+        if ((rc = prim_hidden(m, Lp, B, st))) break;
 
         // ---- primal block backward: upstream gf[0..M) = dL/df_{n+1}
         Planes gp{};
         for (int c = 0; c < M; ++c) { gp.p[c] = gf + c * NV; gp.s[c] = 1.f; }
         k_pack8<<<grid_n(NV), 256, 0, st>>>(gp, NV, m->gsmall);
-        if ((rc = conv_wgrad(m->b2, hs(Lp[2].cin), Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].fw_off,
-                             dW + Lp[2].fb_off, Lp[2].kind ? 0 : 1, m->status, st))) break;
-        if ((rc = conv_dx(m, Lp[2], m->gsmall, 8, PRIM_DIMS, 2, m->g32a, m->b2, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->b1, hs(Lp[1].cin), Lp[1].cin, m->g32a, hs(Lp[1].cout), Lp[1].cout, PRIM_DIMS, 1, dW + Lp[1].fw_off,
-                             dW + Lp[1].fb_off, Lp[1].kind ? 0 : 1, m->status, st))) break;
-        if ((rc = conv_dx(m, Lp[1], m->g32a, hs(Lp[1].cout), PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) break;
-        if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, m->g32b, hs(Lp[0].cout), Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].fw_off,
-                             dW + Lp[0].fb_off, Lp[0].kind ? 0 : 1, m->status, st))) break;
         // dL/d(primal input) -> gf[0..M) += (residual path kept), gf[M] = dL/d(bp channel)
         cudaMemsetAsync(gf + (long long)M * NV, 0, sizeof(float) * NV, st);
-        if ((rc = conv_dx(m, Lp[0], m->g32b, hs(Lp[0].cout), PRIM_DIMS, 1, nullptr, nullptr, gf, NV, st))) break;
+        if ((rc = prim_bwd(m, Lp, B, gf, NV, nullptr, dW, st))) break;
         // bp = bp_scale P^T (w h_1)  =>  dL/dh_{n+1}[1] += w * bp_scale * P (dL/dbp)
         if ((rc = forward_project(m->g, gf + (long long)M * NV, m->tproj, B, 0, sv))) break;
         k_scale_cols<<<grid_n(NP), 256, 0, st>>>(m->tproj, m->wred, NP, m->g->dev.nu, m->bp_scale, m->tproj2);

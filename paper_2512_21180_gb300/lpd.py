@@ -20,17 +20,18 @@ class LPD:
 
     def __init__(self, geom: Geometry, n_iter: int = 8, n_mem: int = 5, width: int = 32, slope: float = 0.2,
                  mu_ref: float = 0.02, bp_scale: float = 0.0, seed: int = 0, residual_input: bool = False,
-                 max_batch: int = 1, reversible: bool = False, lire: bool = False, p4: bool = False):
+                 max_batch: int = 1, reversible: bool = False, lire: bool = False, p4: bool = False,
+                 unet: bool = False):
         self.geom = geom
         d = LpdDesc(n_iter, n_mem, width, slope, mu_ref, bp_scale, seed, int(residual_input), int(max_batch),
-                    int(reversible or lire), int(lire), int(p4))
+                    int(reversible or lire), int(lire), int(p4 or unet), int(unet))
         h = ctypes.c_void_p()
         with torch.cuda.device(geom.device):
             check(_lib.load().lpd_create(geom.handle, ctypes.byref(d), ctypes.byref(h)), "lpd_create")
         self.handle = h
         self.n_iter, self.n_mem, self.width, self.mu_ref = n_iter, n_mem, width, mu_ref
         self.residual_input, self.max_batch = bool(residual_input), int(max_batch)
-        self.reversible, self.lire, self.p4 = bool(reversible or lire), bool(lire), bool(p4)
+        self.reversible, self.lire, self.p4, self.unet = bool(reversible or lire), bool(lire), bool(p4 or unet), bool(unet)
         self.batch = 1
         n = ctypes.c_longlong()
         pp, gp = ctypes.c_void_p(), ctypes.c_void_p()
@@ -186,6 +187,18 @@ def p4_primal_layout(cin: int, cout: int):
     ("avg", cout, 8) — weights [8][27][cin], [8][4][27][8], [cout][4][27][8], each followed
     by its bias."""
     return [("lift", 8, cin), ("group", 8, 8), ("avg", cout, 8)]
+
+
+UNET_F = 4  # base filters of the U-Net's full-resolution layers (4F group channels; 8F at half resolution)
+
+
+def p4_unet_layout(cin: int, cout: int, f: int = UNET_F):
+    """Base-parameter layout of one P4 U-Net primal block (six 3x3x3 layers): the lift
+    ("lift", f, cin) with weights [f][27][cin], then group layers (co, ci) with weights
+    [co][4][27][ci]: g2 (f, f), g3 (2f, f), g4 (2f, 2f), g5 (f, 3f) reading [up(r), s],
+    and the averaged output layer (cout, f); each followed by its bias."""
+    return [("lift", f, cin), ("group", f, f), ("group", 2 * f, f), ("group", 2 * f, 2 * f), ("group", f, 3 * f),
+            ("avg", cout, f)]
 
 
 def lire_layout(n_iter: int, n_mem: int = 8, width: int = 32):

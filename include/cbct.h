@@ -334,6 +334,7 @@ typedef struct {
                                     Algorithm 1 at one resolution, see below. 0: off. */
     int p4;                      /* 1: P4-equivariant primal blocks (Sec. 2.6), see below. 0: plain */
     int unet;                    /* 1 (needs p4): the primal block is a P4 U-Net of depth 1, see below */
+    int weight_norm;             /* 1: forced weight normalisation of every convolution, see below */
 } cbct_lpd_desc;
 
 /* Network on geometry g (which must outlive it): per iteration n a dual block
@@ -390,6 +391,25 @@ int lpd_set_perms(cbct_lpd *m, const int *host);
  * output group channel); they are expanded into full weights before each pass, and the full
  * weight gradients are gathered back onto them after each backward. With a square x-y
  * grid the block then commutes with the quarter turn v'[z][y][x] = v[z][x][n-1-y]. */
+
+/* P4 U-Net primal blocks (desc.unet = 1, needs p4 and even volume sizes; Sec. 2.6: a U-Net
+ * of depth 1 of six P4-equivariant 3x3x3 layers, LeakyReLU after all but the last, averaged
+ * over the rotations). With F = 4 base filters:
+ *   a = L(lift(x)) [4F],  s = L(g2(a)) [4F],  q = L(g3(pool(s))) [8F, half resolution],
+ *   r = L(g4(q)) [8F, half],  t = L(g5([up(r), s])) [4F],  out = avg6(t) [K]
+ * (pool: mean of 2 x 2 x 2 blocks; up: nearest; [ , ]: channel concatenation, up(r) first).
+ * Base filters per layer, each + bias: lift [F][27][cin], g2 [F][4][27][F], g3 [2F][4][27][F],
+ * g4 [2F][4][27][2F], g5 [F][4][27][3F], avg [K][4][27][F]. The paper's 48 / 96 filters
+ * (F = 12) would give 144 concatenated channels; F = 4 keeps the concatenation within the
+ * convolution's 64 input slots.
+ *
+ * Forced weight normalisation (desc.weight_norm = 1; Sec. 2.6, after Karras et al. 2024):
+ * every layer's learnable parameters are [w][b][g] — g one gain per layer after the bias —
+ * and the convolution uses g (w_c - mean w_c) / ||w_c - mean w_c|| for each output filter c
+ * (for P4 layers each base filter, normalised before the rotation expansion); biases are used
+ * as they are. lpd_adam_step then re-projects every raw filter to zero mean and norm
+ * sqrt(filter length), which leaves the effective weights unchanged. A filter of zero norm
+ * gives zero effective weights. */
 
 /* Parameter count and device pointers to the parameters and the gradient buffer. */
 int lpd_info(const cbct_lpd *m, long long *nparams, float **params, float **grads, float *bp_scale);

@@ -25,7 +25,8 @@ U64 = ctypes.c_uint64
 class LpdDesc(ctypes.Structure):
     _fields_ = [("n_iter", I32), ("n_mem", I32), ("width", I32), ("slope", F32), ("mu_ref", F32),
                 ("bp_scale", F32), ("seed", U64), ("residual_input", I32), ("max_batch", I32),
-                ("reversible", I32), ("lire", I32), ("p4", I32), ("unet", I32)]
+                ("reversible", I32), ("lire", I32), ("p4", I32), ("unet", I32),
+                ("weight_norm", I32)]
 
 
 class GeomDesc(ctypes.Structure):

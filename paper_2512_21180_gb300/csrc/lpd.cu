@@ -57,12 +57,16 @@ struct LayerSpec {
     long long fw_off = 0, fb_off = 0;
     int cpin = 32;  // channel slots of the layer's input activation
     int last = 0;   // the block's output layer (initialised 10x smaller)
+    // weight normalisation: gain at g_off (learnable), normalised filters at nw_off (the
+    // convolution's weights for a plain layer, the expanded base for a P4 layer)
+    long long g_off = -1, nw_off = 0;
 };
 
 // one P4 layer for the expansion / contraction kernels
 struct P4Job {
     int kind, cb, cib, cout, cin;  // cout, cin: full
     long long w_off, b_off, fw_off, fb_off;
+    int assign;  // 1: the contraction writes the base weights' gradients (normalised filters) instead of adding
 };
 
 struct cbct_lpd {
@@ -89,6 +93,10 @@ struct cbct_lpd {
     std::vector<LayerSpec> layers;  // per iteration: 3 dual layers, then the primal block's (3, or 6 for the U-Net)
     std::vector<int> dual_at, prim_at;  // index of each iteration's first dual / primal layer
     int unet = 0;                       // primal block: P4 U-Net of depth 1 (Sec. 2.6)
+    int wn = 0;                         // forced weight normalisation of every layer
+    struct WnJob *wn_jobs = nullptr;    // device [n_wn]
+    int n_wn = 0;
+    long long wn_lo = 0, wn_hi = 0;     // the normalised filters' area (gradients reset each pass)
     // U-Net activations (BF16 row-blocked): a (full, 4F), C = [up(r), s] (full, 64 slots),
     // p = pool(s) (half, 4F), q, r (half, 8F), t (full, 4F); uh1, uh2: half-resolution gradients
     __nv_bfloat16 *u_a = nullptr, *u_C = nullptr, *u_p = nullptr, *u_q = nullptr, *u_r = nullptr, *u_t = nullptr;
@@ -382,7 +390,7 @@ __global__ void k_p4_expand(const P4Job *__restrict__ jobs, float *__restrict__ 
 // filters (each base entry sums the full entries it was copied to, in a fixed order)
 __global__ void k_p4_contract(const P4Job *__restrict__ jobs, float *__restrict__ grads) {
     const P4Job J = jobs[blockIdx.y];
-    const long long nb = J.b_off - J.w_off;  // base weights
+    const long long nb = (long long)J.cb * (J.kind == 1 ? 1 : 4) * 27 * J.cib;  // base weights
     const float *gf = grads + J.fw_off;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nb + J.cb;
          e += (long long)gridDim.x * blockDim.x) {
@@ -407,7 +415,8 @@ __global__ void k_p4_contract(const P4Job *__restrict__ jobs, float *__restrict_
                 a += J.kind == 3 ? 0.25f * v : v;
             }
         }
-        grads[J.w_off + e] += a;
+        if (J.assign) grads[J.w_off + e] = a;
+        else grads[J.w_off + e] += a;
     }
 }
 
@@ -528,6 +537,115 @@ __global__ void k_skip_grad_rb(Rb gc, Rb s, Rb gp, Rb out, int ng, int nimg, int
     }
 }
 
+// ---- forced weight normalisation ------------------------------------------------------------
+// One job per layer: rows filters of len weights at raw_off (the learnable values), their
+// effective values g (w - mean w) / ||w - mean w|| at dst_off, g the layer's gain at g_off.
+// One CTA per job walks the rows with fixed-order block reductions (deterministic).
+struct WnJob {
+    long long raw_off, dst_off, g_off;
+    int rows, len;
+    long long b_raw, b_dst;  // a plain layer's biases, copied (and their gradients added back)
+    int nb;                  // 0 for P4 layers (their expansion moves the biases)
+};
+
+// sum over the block of v (double), fixed order; every thread gets the result
+__device__ double wn_block_sum(double v, double *red) {
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// mean and 1 / norm of the centred row (a zero row gives 1 / norm = 0: zero effective weights)
+__device__ void wn_row_stats(const float *w, int len, double *red, double &mean, double &inv) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) a += w[i];
+    mean = wn_block_sum(a, red) / len;
+    double q = 0.0;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        const double v = w[i] - mean;
+        q += v * v;
+    }
+    const double n = sqrt(wn_block_sum(q, red));
+    inv = n > 0.0 ? 1.0 / n : 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_wn_fwd(const WnJob *__restrict__ jobs, float *__restrict__ params) {
+    __shared__ double red[256];
+    const WnJob J = jobs[blockIdx.x];
+    const double g = params[J.g_off];
+    for (int r = 0; r < J.rows; ++r) {
+        const float *w = params + J.raw_off + (long long)r * J.len;
+        double mean, inv;
+        wn_row_stats(w, J.len, red, mean, inv);
+        float *e = params + J.dst_off + (long long)r * J.len;
+        for (int i = threadIdx.x; i < J.len; i += blockDim.x) e[i] = (float)(g * (w[i] - mean) * inv);
+    }
+    for (int i = threadIdx.x; i < J.nb; i += blockDim.x) params[J.b_dst + i] = params[J.b_raw + i];
+}
+
+// grads at dst_off (of the effective weights) -> raw weights and gain (added):
+// u = (w - mean) / n, dL/dg = sum G u, dv = g (G - u (u . G)) / n, dw = dv - mean dv
+__global__ void __launch_bounds__(256) k_wn_bwd(const WnJob *__restrict__ jobs, const float *__restrict__ params,
+                                                float *__restrict__ grads) {
+    __shared__ double red[256];
+    const WnJob J = jobs[blockIdx.x];
+    const double g = params[J.g_off];
+    double gg = 0.0;
+    for (int r = 0; r < J.rows; ++r) {
+        const float *w = params + J.raw_off + (long long)r * J.len;
+        const float *G = grads + J.dst_off + (long long)r * J.len;
+        double mean, inv;
+        wn_row_stats(w, J.len, red, mean, inv);
+        double a = 0.0;
+        for (int i = threadIdx.x; i < J.len; i += blockDim.x) a += G[i] * ((w[i] - mean) * inv);
+        const double uG = wn_block_sum(a, red);
+        gg += uG;
+        double b = 0.0;
+        for (int i = threadIdx.x; i < J.len; i += blockDim.x) b += G[i] - ((w[i] - mean) * inv) * uG;
+        const double mdv = wn_block_sum(b, red) / J.len;  // mean of (G - u uG)
+        float *dw = grads + J.raw_off + (long long)r * J.len;
+        for (int i = threadIdx.x; i < J.len; i += blockDim.x)
+            dw[i] += (float)(g * inv * (G[i] - ((w[i] - mean) * inv) * uG - mdv));
+    }
+    if (threadIdx.x == 0) grads[J.g_off] += (float)gg;
+    for (int i = threadIdx.x; i < J.nb; i += blockDim.x) grads[J.b_raw + i] += grads[J.b_dst + i];
+}
+
+// the forced step: every raw filter becomes its centred, normalised self times sqrt(len)
+__global__ void __launch_bounds__(256) k_wn_force(const WnJob *__restrict__ jobs, float *__restrict__ params) {
+    __shared__ double red[256];
+    const WnJob J = jobs[blockIdx.x];
+    const double s = sqrt((double)J.len);
+    for (int r = 0; r < J.rows; ++r) {
+        float *w = params + J.raw_off + (long long)r * J.len;
+        double mean, inv;
+        wn_row_stats(w, J.len, red, mean, inv);
+        for (int i = threadIdx.x; i < J.len; i += blockDim.x) w[i] = (float)((w[i] - mean) * inv * s);
+        __syncthreads();  // the next row's statistics read only their own row, but keep the phases apart
+    }
+}
+
+// effective weights of every layer from the learnable ones: normalisation, then P4 expansion
+static void p4_expand(cbct_lpd *m, cudaStream_t st);
+static void weights_expand(cbct_lpd *m, cudaStream_t st) {
+    if (m->n_wn) k_wn_fwd<<<m->n_wn, 256, 0, st>>>(m->wn_jobs, m->params);
+    p4_expand(m, st);
+}
+
+static void p4_contract(cbct_lpd *m, cudaStream_t st);
+// gradients of the effective weights back onto the learnable ones (after every weight gradient
+// of the pass): P4 contraction into the normalised filters' area, then through the normalisation
+static void weights_contract(cbct_lpd *m, cudaStream_t st) {
+    p4_contract(m, st);  // with normalisation it assigns the normalised base filters' gradients
+    if (m->n_wn) k_wn_bwd<<<m->n_wn, 256, 0, st>>>(m->wn_jobs, m->params, m->grads);
+}
+
 static void p4_expand(cbct_lpd *m, cudaStream_t st) {
     if (!m->n_p4) return;
     dim3 grd((unsigned)std::min<long long>(64, (m->p4_max + 255) / 256 + 1), (unsigned)m->n_p4);
@@ -539,6 +657,11 @@ static void p4_contract(cbct_lpd *m, cudaStream_t st) {
     dim3 grd((unsigned)std::min<long long>(64, (m->p4_max + 255) / 256 + 1), (unsigned)m->n_p4);
     k_p4_contract<<<grd, 256, 0, st>>>(m->p4_jobs, m->grads);
 }
+
+// weight gradients add up across backward passes only where the convolution reads the
+// learnable weights themselves (plain layers without normalisation); elsewhere the pass
+// writes the effective weights' gradients, which the contraction maps back
+static inline int wacc(const cbct_lpd *m, const LayerSpec &L) { return (L.kind || m->wn) ? 0 : 1; }
 
 // channel slots of a hidden activation (or its gradient) with c channels: 32, or 64 for
 // the wider blocks
@@ -623,10 +746,10 @@ static int prim_bwd(cbct_lpd *m, const LayerSpec *Lp, int B, float *gdst, long l
     int gcp;
     if (!m->unet) {
         if ((rc = conv_wgrad(m->b2, hs(Lp[2].cin), Lp[2].cin, m->gsmall, 8, Lp[2].cout, PRIM_DIMS, 1, dW + Lp[2].fw_off,
-                             dW + Lp[2].fb_off, Lp[2].kind ? 0 : 1, m->status, st))) return rc;
+                             dW + Lp[2].fb_off, wacc(m, Lp[2]), m->status, st))) return rc;
         if ((rc = conv_dx(m, Lp[2], m->gsmall, 8, PRIM_DIMS, 2, m->g32a, m->b2, nullptr, 0, st))) return rc;
         if ((rc = conv_wgrad(m->b1, hs(Lp[1].cin), Lp[1].cin, m->g32a, hs(Lp[1].cout), Lp[1].cout, PRIM_DIMS, 1,
-                             dW + Lp[1].fw_off, dW + Lp[1].fb_off, Lp[1].kind ? 0 : 1, m->status, st))) return rc;
+                             dW + Lp[1].fw_off, dW + Lp[1].fb_off, wacc(m, Lp[1]), m->status, st))) return rc;
         if ((rc = conv_dx(m, Lp[1], m->g32a, hs(Lp[1].cout), PRIM_DIMS, 2, m->g32b, m->b1, nullptr, 0, st))) return rc;
         gin = m->g32b;
         gcp = hs(Lp[0].cout);
@@ -662,7 +785,7 @@ static int prim_bwd(cbct_lpd *m, const LayerSpec *Lp, int B, float *gdst, long l
         (void)nx;
     }
     if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, gin, gcp, Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].fw_off, dW + Lp[0].fb_off,
-                         Lp[0].kind ? 0 : 1, m->status, st))) return rc;
+                         wacc(m, Lp[0]), m->status, st))) return rc;
     return conv_apply(gin, PRIM_DIMS, gcp, 1, m->params + Lp[0].fw_off, nullptr, Lp[0].cin, Lp[0].cout, 1, 1,
                       m->d.slope, nullptr, 32, nullptr, gdst, gdst, sstride, m->status, st, nullptr, 0, map, 0);
 }
@@ -712,9 +835,10 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
                                  "residual_input and reversible 0 or 1, max_batch <= 64, max_batch * n_angles <= "
                                  "65535 (half that with lire), and 2 <= n_mem <= 6 (<= 5 with the residual channel) or, reversible, "
                                  "n_mem even in [2, 8]; lire needs reversible and no residual_input");
-    if ((d.unet != 0 && d.unet != 1) ||
+    if ((d.unet != 0 && d.unet != 1) || (d.weight_norm != 0 && d.weight_norm != 1) ||
         (d.unet && (!d.p4 || g->dev.n[0] % 2 || g->dev.n[1] % 2 || g->dev.n[2] % 2)))
-        return fail(CBCT_EINVAL, "lpd_create: unet is 0 or 1 and needs p4 and even volume sizes (2 x 2 x 2 pooling)");
+        return fail(CBCT_EINVAL, "lpd_create: unet and weight_norm are 0 or 1; unet needs p4 and even volume sizes "
+                                 "(2 x 2 x 2 pooling)");
     cbct_lpd *m = new (std::nothrow) cbct_lpd();
     if (!m) return fail(CBCT_ENOMEM, "lpd_create: host allocation");
     m->g = g;
@@ -732,6 +856,7 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
         L.cin = cin; L.cout = cout; L.taps3d = t3; L.H = H; L.cpin = cpin; L.last = last;
         L.w_off = off; off += (long long)cout * (t3 ? 27 : 9) * cin;
         L.b_off = off; off += cout;
+        if (d.weight_norm) { L.g_off = off; off += 1; }
         L.fw_off = L.w_off; L.fb_off = L.b_off;
         m->layers.push_back(L);
     };
@@ -746,6 +871,7 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
         L.cib = kind == 1 ? cin_full : cin_full / 4;
         L.w_off = off; off += (long long)L.cb * (kind == 1 ? 1 : 4) * 27 * L.cib;
         L.b_off = off; off += L.cb;
+        if (d.weight_norm) { L.g_off = off; off += 1; }
         m->layers.push_back(L);
     };
     // U-Net: 4F group channels (16) at full resolution in 32 slots (the upper 16 stay zero, so
@@ -785,6 +911,27 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
         }
     }
     m->nparams = off;
+    // weight normalisation: the normalised filters of every layer (a plain layer's convolution
+    // weights, with a copy of its biases; a P4 layer's base filters, expanded below)
+    std::vector<WnJob> wnjobs;
+    if (d.weight_norm) {
+        m->wn = 1;
+        m->wn_lo = off;
+        for (LayerSpec &L : m->layers) {
+            const int rows = L.kind ? L.cb : L.cout;
+            const int len = (int)((L.b_off - L.w_off) / rows);
+            L.nw_off = off; off += (long long)rows * len;
+            WnJob j{L.w_off, L.nw_off, L.g_off, rows, len, 0, 0, 0};
+            if (!L.kind) {
+                L.fw_off = L.nw_off;
+                L.fb_off = off; off += L.cout;
+                j.b_raw = L.b_off; j.b_dst = L.fb_off; j.nb = L.cout;
+            }
+            wnjobs.push_back(j);
+        }
+        m->wn_hi = off;
+        m->n_wn = (int)wnjobs.size();
+    }
     // expansion area of the P4 layers: full weights [cout][27][cin] and biases, after the
     // learnable parameters (the same offsets in the gradient buffer hold full gradients)
     std::vector<P4Job> p4jobs;
@@ -792,7 +939,8 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
         if (!L.kind) continue;
         L.fw_off = off; off += (long long)L.cout * 27 * L.cin;
         L.fb_off = off; off += L.cout;
-        p4jobs.push_back(P4Job{L.kind, L.cb, L.cib, L.cout, L.cin, L.w_off, L.b_off, L.fw_off, L.fb_off});
+        p4jobs.push_back(P4Job{L.kind, L.cb, L.cib, L.cout, L.cin, m->wn ? L.nw_off : L.w_off, L.b_off, L.fw_off,
+                               L.fb_off, m->wn});
         m->p4_max = std::max(m->p4_max, (long long)L.cout * 27 * L.cin);
     }
     m->n_p4 = (int)p4jobs.size();
@@ -806,6 +954,8 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
         const double sd = sqrt(2.0 / (L.cin * taps)) * (L.last ? 0.1 : 1.0);  // fan-in of the full layer
         const long long nw = L.b_off - L.w_off;
         for (long long k = 0; k < nw; ++k) hp[L.w_off + k] = (float)(sd * rng.normal());
+        // gain = the expected norm of the He-initialised filter (sqrt 2, 10x smaller for the last layer)
+        if (L.g_off >= 0) hp[L.g_off] = (float)(sqrt(2.0) * (L.last ? 0.1 : 1.0));
     }
     for (long long o : m->out_off)
         for (int c = 0; c < M; ++c) hp[o + c] = (float)(0.01 * rng.normal());  // omega; beta = 0
@@ -836,6 +986,7 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     al((void **)&m->adam_m, sizeof(float) * m->nparams);
     al((void **)&m->adam_v, sizeof(float) * m->nparams);
     if (m->n_p4) al((void **)&m->p4_jobs, sizeof(P4Job) * m->n_p4);
+    if (m->n_wn) al((void **)&m->wn_jobs, sizeof(WnJob) * m->n_wn);
     al((void **)&m->wred, sizeof(float) * g->dev.nu);
     al((void **)&m->f, sizeof(float) * S * M * NV);
     al((void **)&m->h, sizeof(float) * S * M * NP);
@@ -916,6 +1067,8 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
     if (e == cudaSuccess) e = cudaMemset(m->adam_v, 0, sizeof(float) * m->nparams);
     if (e == cudaSuccess && m->n_p4)
         e = cudaMemcpy(m->p4_jobs, p4jobs.data(), sizeof(P4Job) * m->n_p4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && m->n_wn)
+        e = cudaMemcpy(m->wn_jobs, wnjobs.data(), sizeof(WnJob) * m->n_wn, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(int));
     if (e != cudaSuccess) {
         lpd_destroy(m);
@@ -962,7 +1115,7 @@ extern "C" int lpd_create(const cbct_geom *g, const cbct_lpd_desc *desc, cbct_lp
 extern "C" void lpd_destroy(cbct_lpd *m) {
     if (!m) return;
     cudaDeviceSynchronize();
-    void *ptrs[] = {m->p4_jobs, m->x, m->gx, m->Vb, m->t2v, m->t2p, m->opart, m->wpk, m->pack_jobs, m->clip, m->pf_saved, m->bp_saved, m->params, m->grads, m->adam_m, m->adam_v, m->wred, m->f, m->h,
+    void *ptrs[] = {m->p4_jobs, m->wn_jobs, m->x, m->gx, m->Vb, m->t2v, m->t2p, m->opart, m->wpk, m->pack_jobs, m->clip, m->pf_saved, m->bp_saved, m->params, m->grads, m->adam_m, m->adam_v, m->wred, m->f, m->h,
                     m->y, m->tproj, m->tproj2, m->tvol, m->din, m->a1, m->a2, m->pin, m->b1, m->b2, m->g32a, m->g32b, m->gsmall, m->gf, m->gh,
                     m->u_a, m->u_C, m->u_t, m->u_p, m->u_q, m->u_r, m->u_h1, m->u_h2, m->u_ga, m->u_gb,
                     m->status};
@@ -1018,7 +1171,7 @@ static int lpd_forward_impl(cbct_lpd *m, const float *y, const float *x0, const 
     m->batch = B;
     const long long NV = m->nvox * B, NP = m->nproj * B;
     const int M = m->d.n_mem, N = m->d.n_iter;
-    p4_expand(m, st);
+    weights_expand(m, st);
     int prc = conv_pack_jobs(m->pack_jobs, m->n_pack_jobs, m->pack_max_nelem, m->params, m->wpk, st);
     if (prc) return prc;
     CBCT_CUDA_TRY(cudaMemcpyAsync(m->y, y, sizeof(float) * NP, cudaMemcpyDeviceToDevice, st));
@@ -1112,7 +1265,7 @@ static int lpd_rev_forward(cbct_lpd *m, const float *y, const float *x0, float *
     void *sv = (void *)st;
     const long long NV = m->nvox * B, NP = m->nproj * B;
     const int M = m->d.n_mem, K = M / 2, N = m->d.n_iter;
-    p4_expand(m, st);
+    weights_expand(m, st);
     int rc = conv_pack_jobs(m->pack_jobs, m->n_pack_jobs, m->pack_max_nelem, m->params, m->wpk, st);
     if (rc) return rc;
     CBCT_CUDA_TRY(cudaMemcpyAsync(m->y, y, sizeof(float) * NP, cudaMemcpyDeviceToDevice, st));
@@ -1156,7 +1309,7 @@ static int lpd_rev_backward(cbct_lpd *m, const float *grad_x, float *grad_y, flo
     const long long NV = m->nvox * B, NP = m->nproj * B;
     const int M = m->d.n_mem, K = M / 2, N = m->d.n_iter;
     float *gf = m->gf, *gh = m->gh, *dW = m->grads;  // gf: M planes + plane M (scratch); gh: M + 3 planes
-    p4_expand(m, st);
+    weights_expand(m, st);
     int rc = conv_pack_jobs(m->pack_jobs, m->n_pack_jobs, m->pack_max_nelem, m->params, m->wpk, st);
     if (rc) return rc;
     int pfm[8], phm[8];
@@ -1201,13 +1354,13 @@ static int lpd_rev_backward(cbct_lpd *m, const float *grad_x, float *grad_y, flo
         for (int c = 0; c < K; ++c) { gd.p[c] = gh + phm[K + c] * NP; gd.s[c] = 1.f; }
         k_pack8<<<grid_n(NP), 256, 0, st>>>(gd, NP, m->gsmall);
         if ((rc = conv_wgrad(m->a2, hs(Ld[2].cin), Ld[2].cin, m->gsmall, 8, Ld[2].cout, DUAL_DIMS, 0, dW + Ld[2].fw_off,
-                             dW + Ld[2].fb_off, Ld[2].kind ? 0 : 1, m->status, st))) break;
+                             dW + Ld[2].fb_off, wacc(m, Ld[2]), m->status, st))) break;
         if ((rc = conv_dx(m, Ld[2], m->gsmall, 8, DUAL_DIMS, 2, m->g32a, m->a2, nullptr, 0, st))) break;
         if ((rc = conv_wgrad(m->a1, hs(Ld[1].cin), Ld[1].cin, m->g32a, hs(Ld[1].cout), Ld[1].cout, DUAL_DIMS, 0, dW + Ld[1].fw_off,
-                             dW + Ld[1].fb_off, Ld[1].kind ? 0 : 1, m->status, st))) break;
+                             dW + Ld[1].fb_off, wacc(m, Ld[1]), m->status, st))) break;
         if ((rc = conv_dx(m, Ld[1], m->g32a, hs(Ld[1].cout), DUAL_DIMS, 2, m->g32b, m->a1, nullptr, 0, st))) break;
         if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, hs(Ld[0].cout), Ld[0].cout, DUAL_DIMS, 0, dW + Ld[0].fw_off,
-                             dW + Ld[0].fb_off, Ld[0].kind ? 0 : 1, m->status, st))) break;
+                             dW + Ld[0].fb_off, wacc(m, Ld[0]), m->status, st))) break;
         // dL/d[d1, pf, y (, residual)]: d1's planes accumulate, the others go to scratch planes M..
         const int nin = Ld[0].cin;
         for (int c = 0; c < K; ++c) mp[c] = phm[c];
@@ -1234,7 +1387,7 @@ static int lpd_rev_backward(cbct_lpd *m, const float *grad_x, float *grad_y, flo
     if (grad_x0) k_sum_channels<<<grid_n(NV), 256, 0, st>>>(gf, M, NV, 1.f / m->d.mu_ref, grad_x0, 0);
     for (int c = 0; c < M; ++c) { m->cur_f[c] = pfm[c]; m->cur_h[c] = phm[c]; }
     m->saved = 0;  // the states now hold the recovered initial iterate
-    p4_contract(m, st);
+    weights_contract(m, st);
     CBCT_LAUNCH_CHECK("lpd_backward (reversible)");
     return 0;
 }
@@ -1307,7 +1460,7 @@ static int lire_forward(cbct_lpd *m, const float *y, const float *x0, float *x_o
     m->batch = B;
     const long long NV = m->nvox * B, NP = m->nproj * B;
     const int M = m->d.n_mem, K = M / 2, N = m->d.n_iter;
-    p4_expand(m, st);
+    weights_expand(m, st);
     int rc = conv_pack_jobs(m->pack_jobs, m->n_pack_jobs, m->pack_max_nelem, m->params, m->wpk, st);
     if (rc) return rc;
     CBCT_CUDA_TRY(cudaMemcpyAsync(m->y, y, sizeof(float) * NP, cudaMemcpyDeviceToDevice, st));
@@ -1357,7 +1510,7 @@ static int lire_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float 
     float *gf = m->gf, *gh = m->gh, *gx = m->gx, *dW = m->grads;
     float *gy = grad_y ? grad_y : m->tproj2;  // dL/dy is accumulated even when not returned
     float *g_plw = gh + (long long)(M + 4) * NP;
-    p4_expand(m, st);
+    weights_expand(m, st);
     int rc = conv_pack_jobs(m->pack_jobs, m->n_pack_jobs, m->pack_max_nelem, m->params, m->wpk, st);
     if (rc) return rc;
     int pfm[8], phm[8];
@@ -1418,13 +1571,13 @@ static int lire_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float 
         for (int c = 0; c < K; ++c) { gdl.p[c] = gh + phm[K + c] * NP; gdl.s[c] = 1.f; }
         k_pack8<<<grid_n(NP), 256, 0, st>>>(gdl, NP, m->gsmall);
         if ((rc = conv_wgrad(m->a2, hs(Ld[2].cin), Ld[2].cin, m->gsmall, 8, Ld[2].cout, LIRE_DUAL_DIMS, 1, dW + Ld[2].fw_off,
-                             dW + Ld[2].fb_off, Ld[2].kind ? 0 : 1, m->status, st))) break;
+                             dW + Ld[2].fb_off, wacc(m, Ld[2]), m->status, st))) break;
         if ((rc = conv_dx(m, Ld[2], m->gsmall, 8, LIRE_DUAL_DIMS, 2, m->g32a, m->a2, nullptr, 0, st))) break;
         if ((rc = conv_wgrad(m->a1, hs(Ld[1].cin), Ld[1].cin, m->g32a, hs(Ld[1].cout), Ld[1].cout, LIRE_DUAL_DIMS, 1, dW + Ld[1].fw_off,
-                             dW + Ld[1].fb_off, Ld[1].kind ? 0 : 1, m->status, st))) break;
+                             dW + Ld[1].fb_off, wacc(m, Ld[1]), m->status, st))) break;
         if ((rc = conv_dx(m, Ld[1], m->g32a, hs(Ld[1].cout), LIRE_DUAL_DIMS, 2, m->g32b, m->a1, nullptr, 0, st))) break;
         if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, hs(Ld[0].cout), Ld[0].cout, LIRE_DUAL_DIMS, 1, dW + Ld[0].fw_off,
-                             dW + Ld[0].fb_off, Ld[0].kind ? 0 : 1, m->status, st))) break;
+                             dW + Ld[0].fb_off, wacc(m, Ld[0]), m->status, st))) break;
         // input channels [d1 (K), mu P p2[0], P x, y, P x - y] -> d1's planes, scratch M .. M+3
         for (int c = 0; c < K; ++c) mp[c] = phm[c];
         for (int c = 0; c < 4; ++c) mp[K + c] = M + c;
@@ -1460,7 +1613,7 @@ static int lire_backward(cbct_lpd *m, const float *grad_x, float *grad_y, float 
     }
     for (int c = 0; c < M; ++c) { m->cur_f[c] = c; m->cur_h[c] = c; }
     m->saved = 0;
-    p4_contract(m, st);
+    weights_contract(m, st);
     CBCT_LAUNCH_CHECK("lpd_backward (lire)");
     return 0;
 }
@@ -1520,7 +1673,7 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
     float *gf = m->gf, *gh = m->gh;
     // the recomputed forward convolutions read the packed weights: refresh them (the
     // parameters may have changed since the forward pass)
-    p4_expand(m, st);
+    weights_expand(m, st);
     int prc = conv_pack_jobs(m->pack_jobs, m->n_pack_jobs, m->pack_max_nelem, m->params, m->wpk, st);
     if (prc) return prc;
     // dL/df_N: channel 0 gets mu_ref dL/dx; plus the given state gradients
@@ -1565,13 +1718,13 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
         for (int c = 0; c < M; ++c) { gd.p[c] = gh + c * NP; gd.s[c] = 1.f; }
         k_pack8<<<grid_n(NP), 256, 0, st>>>(gd, NP, m->gsmall);
         if ((rc = conv_wgrad(m->a2, hs(Ld[2].cin), Ld[2].cin, m->gsmall, 8, Ld[2].cout, DUAL_DIMS, 0, dW + Ld[2].fw_off,
-                             dW + Ld[2].fb_off, Ld[2].kind ? 0 : 1, m->status, st))) break;
+                             dW + Ld[2].fb_off, wacc(m, Ld[2]), m->status, st))) break;
         if ((rc = conv_dx(m, Ld[2], m->gsmall, 8, DUAL_DIMS, 2, m->g32a, m->a2, nullptr, 0, st))) break;
         if ((rc = conv_wgrad(m->a1, hs(Ld[1].cin), Ld[1].cin, m->g32a, hs(Ld[1].cout), Ld[1].cout, DUAL_DIMS, 0, dW + Ld[1].fw_off,
-                             dW + Ld[1].fb_off, Ld[1].kind ? 0 : 1, m->status, st))) break;
+                             dW + Ld[1].fb_off, wacc(m, Ld[1]), m->status, st))) break;
         if ((rc = conv_dx(m, Ld[1], m->g32a, hs(Ld[1].cout), DUAL_DIMS, 2, m->g32b, m->a1, nullptr, 0, st))) break;
         if ((rc = conv_wgrad(m->din, 8, Ld[0].cin, m->g32b, hs(Ld[0].cout), Ld[0].cout, DUAL_DIMS, 0, dW + Ld[0].fw_off,
-                             dW + Ld[0].fb_off, Ld[0].kind ? 0 : 1, m->status, st))) break;
+                             dW + Ld[0].fb_off, wacc(m, Ld[0]), m->status, st))) break;
         // dL/d(dual input): gh[0..M) += (residual), gh[M] = dL/d(pf channel), gh[M+1] = dL/d(y channel),
         // gh[M+2] = dL/d(residual channel mu_ref pf - y)
         cudaMemsetAsync(gh + (long long)M * NP, 0, sizeof(float) * (ND - M) * NP, st);
@@ -1595,7 +1748,7 @@ static int lpd_backward_impl(cbct_lpd *m, const float *grad_x, const float *grad
     if (grad_x0) k_sum_channels<<<grid_n(NV), 256, 0, st>>>(gf, M, NV, 1.f / m->d.mu_ref, grad_x0, 0);
     if (grad_f0) CBCT_CUDA_TRY(cudaMemcpyAsync(grad_f0, gf, sizeof(float) * M * NV, cudaMemcpyDeviceToDevice, st));
     if (grad_h0) CBCT_CUDA_TRY(cudaMemcpyAsync(grad_h0, gh, sizeof(float) * M * NP, cudaMemcpyDeviceToDevice, st));
-    p4_contract(m, st);
+    weights_contract(m, st);
     CBCT_LAUNCH_CHECK("lpd_backward");
     return 0;
 }
@@ -1683,6 +1836,8 @@ extern "C" int lpd_adam_step(cbct_lpd *m, float lr, float beta1, float beta2, fl
     const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
     k_adam<<<grid_n(m->nparams), 256, 0, st>>>(m->params, m->grads, m->adam_m, m->adam_v, m->nparams, lr, beta1, beta2,
                                                eps, c1, c2, grad_scale);
+    // forced weight normalisation: each raw filter back to zero mean and norm sqrt(len)
+    if (m->n_wn) k_wn_force<<<m->n_wn, 256, 0, st>>>(m->wn_jobs, m->params);
     CBCT_LAUNCH_CHECK("lpd_adam_step");
     return 0;
 }

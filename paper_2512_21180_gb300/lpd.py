@@ -21,10 +21,10 @@ class LPD:
     def __init__(self, geom: Geometry, n_iter: int = 8, n_mem: int = 5, width: int = 32, slope: float = 0.2,
                  mu_ref: float = 0.02, bp_scale: float = 0.0, seed: int = 0, residual_input: bool = False,
                  max_batch: int = 1, reversible: bool = False, lire: bool = False, p4: bool = False,
-                 unet: bool = False):
+                 unet: bool = False, weight_norm: bool = False):
         self.geom = geom
         d = LpdDesc(n_iter, n_mem, width, slope, mu_ref, bp_scale, seed, int(residual_input), int(max_batch),
-                    int(reversible or lire), int(lire), int(p4 or unet), int(unet))
+                    int(reversible or lire), int(lire), int(p4 or unet), int(unet), int(weight_norm))
         h = ctypes.c_void_p()
         with torch.cuda.device(geom.device):
             check(_lib.load().lpd_create(geom.handle, ctypes.byref(d), ctypes.byref(h)), "lpd_create")
@@ -32,6 +32,7 @@ class LPD:
         self.n_iter, self.n_mem, self.width, self.mu_ref = n_iter, n_mem, width, mu_ref
         self.residual_input, self.max_batch = bool(residual_input), int(max_batch)
         self.reversible, self.lire, self.p4, self.unet = bool(reversible or lire), bool(lire), bool(p4 or unet), bool(unet)
+        self.weight_norm = bool(weight_norm)
         self.batch = 1
         n = ctypes.c_longlong()
         pp, gp = ctypes.c_void_p(), ctypes.c_void_p()

@@ -160,7 +160,7 @@ def equal_psnr(geom: Geometry, model: LPD, test, full: torch.Tensor, lam: float,
         # both methods on `batch` volumes per call (one launch of each kernel covers the batch)
         mb = LPD(geom, n_iter=model.n_iter, n_mem=model.n_mem, width=model.width, mu_ref=model.mu_ref,
                  residual_input=model.residual_input, reversible=model.reversible and not model.lire, lire=model.lire,
-                 p4=model.p4, max_batch=batch)
+                 p4=model.p4, unet=model.unet, weight_norm=model.weight_norm, max_batch=batch)
         mb.set_params(model.get_params())
         if model.reversible:
             mb.set_perms(model.perms())
@@ -211,7 +211,7 @@ def time_training(args) -> int:
     vb = args.vol_batch
     model = LPD(geom, n_iter=args.n_iter, n_mem=args.n_mem, width=args.width, seed=1,
                 residual_input=args.residual_input, max_batch=vb, reversible=args.reversible, lire=args.lire,
-                p4=args.p4)
+                p4=args.p4, unet=args.unet, weight_norm=args.weight_norm)
     xs, ys = [], []
     for j in range(vb):
         x = ops.phantom(geom, I.phantom_params(WORKLOAD, 10_000 + j))
@@ -236,7 +236,8 @@ def time_training(args) -> int:
     print(json.dumps({"workload": "128^3 at 4 mm, 200 angles, 256x192 at 1.6 mm, +80 mm offset",
                       "n_iter": args.n_iter, "n_mem": args.n_mem, "width": args.width,
                       "residual_input": args.residual_input,
-                      "reversible": model.reversible, "lire": model.lire, "p4": model.p4,
+                      "reversible": model.reversible, "lire": model.lire, "p4": model.p4, "unet": model.unet,
+                      "weight_norm": model.weight_norm,
                       "volumes_per_call": vb, "train_s_per_volume": t_train, "inference_s_per_volume": t_inf}),
           flush=True)
     return 0
@@ -262,6 +263,8 @@ def main(argv=None):
     ap.add_argument("--reversible", action="store_true", help="additive coupling + permutations (no stored iterates)")
     ap.add_argument("--lire", action="store_true", help="the iteration of Algorithm 1 (implies --reversible)")
     ap.add_argument("--p4", action="store_true", help="P4-equivariant primal blocks")
+    ap.add_argument("--unet", action="store_true", help="P4 U-Net primal blocks (depth 1)")
+    ap.add_argument("--weight-norm", action="store_true", help="forced weight normalisation of every layer")
     ap.add_argument("--lams", default="0.3,1,2,3,5,10,20", help="PDHG lambda grid (tuned on held-out phantoms)")
     ap.add_argument("--init", default=None, help="start from these parameters (.npy)")
     ap.add_argument("--pdhg-iters", type=int, default=100)
@@ -317,7 +320,7 @@ def main(argv=None):
         raise SystemExit("--batch must be a multiple of --vol-batch")
     model = LPD(geom, n_iter=args.n_iter, n_mem=args.n_mem, width=args.width, seed=1,
                 residual_input=args.residual_input, max_batch=vb, reversible=args.reversible, lire=args.lire,
-                p4=args.p4)
+                p4=args.p4, unet=args.unet, weight_norm=args.weight_norm)
     if args.init:
         model.set_params(widen_params(np.load(args.init), args.n_iter, model.n_mem, model.width,
                                       args.residual_input))
@@ -384,7 +387,8 @@ def main(argv=None):
 
     # ---- evaluate at equal PSNR on the test phantoms (inference one volume at a time)
     model1 = LPD(geom, n_iter=args.n_iter, n_mem=args.n_mem, width=args.width, seed=1,
-                 residual_input=args.residual_input, reversible=args.reversible, lire=args.lire, p4=args.p4)
+                 residual_input=args.residual_input, reversible=args.reversible, lire=args.lire, p4=args.p4,
+                 unet=args.unet, weight_norm=args.weight_norm)
     model1.set_params(model.get_params())
     if model.reversible:
         model1.set_perms(model.perms())

@@ -754,7 +754,6 @@ static int prim_bwd(cbct_lpd *m, const LayerSpec *Lp, int B, float *gdst, long l
         gin = m->g32b;
         gcp = hs(Lp[0].cout);
     } else {
-        const int nx = m->g->dev.n[0];
         const long long nvh = (long long)B * m->nvox / 8;
         auto wg = [&](const LayerSpec &L, const __nv_bfloat16 *x, int cpx, const __nv_bfloat16 *dy, int cpy, int half) {
             return half ? conv_wgrad(x, cpx, L.cin, dy, cpy, L.cout, UNET_HALF, 1, dW + L.fw_off, dW + L.fb_off, 0,
@@ -782,7 +781,6 @@ static int prim_bwd(cbct_lpd *m, const LayerSpec *Lp, int B, float *gdst, long l
         if ((rc = conv_dx(m, Lp[1], m->u_ga, 32, PRIM_DIMS, 2, m->u_gb, m->u_a, nullptr, 0, st, 32))) return rc;
         gin = m->u_gb;
         gcp = 32;
-        (void)nx;
     }
     if ((rc = conv_wgrad(m->pin, 8, Lp[0].cin, gin, gcp, Lp[0].cout, PRIM_DIMS, 1, dW + Lp[0].fw_off, dW + Lp[0].fb_off,
                          wacc(m, Lp[0]), m->status, st))) return rc;

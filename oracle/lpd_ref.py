@@ -1,10 +1,11 @@
 """FP64 reference of the learned primal-dual blocks (test infrastructure only).
 
 Plain PyTorch CPU in float64. The convolution blocks of the paper's dual and primal
-updates (Sec. 2.6, Algorithm 1: Gamma and Lambda; here 3-layer width-32 blocks
-with LeakyReLU between layers, 2D over the detector plane for the dual block, 3D
-over the volume for the primal block) and one unrolled iteration pair, with the
-projector pair taken from the FP64 C oracle through autograd functions.
+updates (Sec. 2.6, Algorithm 1: Gamma and Lambda; 3-layer blocks of any width with
+LeakyReLU between layers, 2D over the detector plane or 3D; P4-equivariant blocks; the
+P4 U-Net primal block of depth 1; centred forced weight normalisation), the unrolled
+networks built from them (Adler-style memory, reversible coupling, the LIRE iteration),
+with the projector pair taken from the FP64 C oracle through autograd functions.
 
 BF16 operands are emulated by rounding the inputs and weights to bfloat16 before
 the FP64 arithmetic, exactly where the GPU path rounds them. With round_grad the

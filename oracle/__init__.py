@@ -5,8 +5,9 @@ may import this package. It is an independent, plain restatement of what the
 GPU library computes; it never imports or links the GPU library.
 
 The C part (`oracle.c`) holds the projector pair, geometry, field-of-view
-tensor, redundancy weight, FDK, PDHG-TV, Philox/Poisson simulation and phantom
-voxeliser; `lpd_ref.py` holds the learned primal-dual reference in plain
+tensor, redundancy weight, FDK, PDHG-TV, Philox/Poisson simulation, phantom
+voxeliser and the polychromatic primary (water-bone split, detector response,
+resp-weighted per-energy draws); `lpd_ref.py` holds the learned primal-dual reference in plain
 PyTorch CPU FP64 and `multiscale_ref.py` the two-level scheme built on it.
 """
 from __future__ import annotations
@@ -63,6 +64,10 @@ def lib():
                 "o_neglog": (None, [P, i64, f64, P]),
                 "o_phantom": (None, [P, P, P, i32, i32, P]),
                 "o_num_threads": (i32, []),
+                "o_water_bone": (None, [P, i64, f64, P, P]),
+                "o_resp": (f64, [f64]),
+                "o_poly_lam": (None, [P, P, i64, i64, i32, P, P, P, P]),
+                "o_poly_reading": (None, [P, i64, i32, P, ctypes.c_uint64, i32, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -251,3 +256,81 @@ def phantom(G: Geom, ell: np.ndarray, ss: int = 1) -> np.ndarray:
 
 def num_threads() -> int:
     return lib().o_num_threads()
+
+
+# ---- polychromatic primary (Sec. 2.1, "Primary simulation") ----
+
+def water_bone(mu: np.ndarray, mu_w60: float):
+    """Water and bone relative densities of a mu_60 volume (Sec. 2.1, the
+    water-bone decomposition equations, tau0 = 0)."""
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    rw = np.zeros(mu.shape)
+    rb = np.zeros(mu.shape)
+    lib().o_water_bone(_ptr(mu), mu.size, float(mu_w60), _ptr(rw), _ptr(rb))
+    return rw, rb
+
+
+def resp(e_kev: float) -> float:
+    """Detector response at e keV: piecewise linear through (20, 5), (60, 20), (120, 10)."""
+    return float(lib().o_resp(float(e_kev)))
+
+
+def poly_lam(Lw: np.ndarray, Lb: np.ndarray, mu_w, mu_b, I0: np.ndarray) -> np.ndarray:
+    """Mean counts [n][ne] of each energy bin from FP32 water / bone line integrals
+    (any leading shape whose last two axes are the panel's nv x nu) and FP32
+    intensity maps I0[ne][nv][nu]."""
+    Lw = np.ascontiguousarray(Lw, dtype=np.float32)
+    Lb = np.ascontiguousarray(Lb, dtype=np.float32)
+    I0 = np.ascontiguousarray(I0, dtype=np.float32)
+    mw = np.ascontiguousarray(mu_w, dtype=np.float64)
+    mb = np.ascontiguousarray(mu_b, dtype=np.float64)
+    ne = len(mw)
+    npix = I0.shape[-1] * I0.shape[-2]
+    lam = np.zeros((Lw.size, ne))
+    lib().o_poly_lam(_ptr(Lw), _ptr(Lb), Lw.size, npix, ne, _ptr(mw), _ptr(mb), _ptr(I0), _ptr(lam))
+    return lam
+
+
+def poly_reading(lam: np.ndarray, energies, seed: int, noise: bool = True, return_counts: bool = False):
+    """resp-weighted sum over the bins of Poisson(lam) (or of lam, noise=False);
+    lam is [n][ne] with the bins in the order of `energies`."""
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    E = np.ascontiguousarray(energies, dtype=np.float64)
+    n, ne = lam.shape
+    out = np.zeros(n)
+    counts = np.zeros((n, ne), dtype=np.int32)
+    lib().o_poly_reading(_ptr(lam), n, ne, _ptr(E), int(seed), 1 if noise else 0, _ptr(out),
+                         _ptr(counts) if noise else None)
+    return (out, counts) if return_counts else out
+
+
+def poly_air(energies, I0: np.ndarray) -> np.ndarray:
+    """Expected air reading sum_e resp(e) I0[e] per pixel (the normalisation's gain)."""
+    I0 = np.asarray(I0, dtype=np.float64)
+    acc = np.zeros(I0.shape[1:])
+    for j, e in enumerate(energies):
+        acc = acc + resp(e) * I0[j]
+    return acc
+
+
+def poly_neglog(reading: np.ndarray, air: np.ndarray) -> np.ndarray:
+    """y_primary = -log(min(reading / air, 1)) (Sec. 2.4, normalised primary data);
+    air broadcasts over the leading (angle, batch) axes."""
+    r = np.asarray(reading, dtype=np.float64) / air
+    return -np.log(np.minimum(r, 1.0))
+
+
+def poly_primary(G: Geom, mu: np.ndarray, mu_w60: float, energies, mu_w, mu_b, I0: np.ndarray,
+                 seed: int, noise: bool = True):
+    """The primary model in the paper's order (Sec. 2.1): split mu into water and
+    bone, form mu_tilde_e = rho_w mu_w[e] + rho_b mu_b[e] for each bin, project it,
+    take the mean counts I0[e] exp(-P mu_tilde_e), draw (or not) and sum with resp.
+    Returns (reading [na][nv][nu], y_primary)."""
+    rw, rb = water_bone(mu, mu_w60)
+    ne = len(energies)
+    lam = np.zeros(G.proj_shape + (ne,))
+    for j in range(ne):
+        p = forward(G, rw * mu_w[j] + rb * mu_b[j])
+        lam[..., j] = np.asarray(I0[j], dtype=np.float64) * np.exp(-p)
+    reading = poly_reading(lam.reshape(-1, ne), energies, seed, noise).reshape(G.proj_shape)
+    return reading, poly_neglog(reading, poly_air(energies, I0))

@@ -362,6 +362,40 @@ def lpd_timing(warmup: int, reps: int, n_test: int = 8) -> dict:
     return out
 
 
+def poly_timing(geom, name: str, reps: int = 3) -> dict:
+    """Polychromatic primary simulation of one volume of the bench workload (Sec. 2.1:
+    water-bone split, two projections, ten energy bins of Poisson draws, log
+    normalisation), timed with CUDA events after one warm-up call: the whole call and
+    its reading kernel alone (the draws), per volume."""
+    import torch
+
+    from paper_2512_21180_gb300 import inputs as I
+    from paper_2512_21180_gb300 import ops
+
+    E, mw, mb, _ = I.poly_tables()
+    I0 = torch.as_tensor(I.poly_intensity(I.geometry(name)), device="cuda")
+    mu = ops.phantom(geom, I.phantom_params(name, 7))
+    L, y = ops.poly_simulate(geom, mu, I0, E, mw, mb, I.MU_WATER_60, seed=1)
+    ops.poly_reading(L, I0, E, mw, mb, seed=2)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t_all, t_read = 0.0, 0.0
+    for r in range(reps):
+        ev[0].record(st)
+        ops.poly_simulate(geom, mu, I0, E, mw, mb, I.MU_WATER_60, seed=10 + r)
+        ev[1].record(st)
+        ops.poly_reading(L, I0, E, mw, mb, seed=20 + r)
+        ev[2].record(st)
+        torch.cuda.synchronize()
+        t_all += ev[0].elapsed_time(ev[1])
+        t_read += ev[1].elapsed_time(ev[2])
+    n_draws = L[0, 0].numel() * len(E)
+    return {"ms_per_volume": t_all / reps, "ms_reading": t_read / reps, "bins": len(E),
+            "gdraws_s": n_draws / (t_read / reps * 1e-3) / 1e9,
+            "note": "stand-in attenuation tables and intensity maps; FP64 Poisson draws (inversion / PTRS)"}
+
+
 def report(args, geom, world, S_fwd, samples_step, value, ms, ms_fwd, ms_adj, e2e, clk, g, dist):
     import numpy as np
 
@@ -414,6 +448,11 @@ def report(args, geom, world, S_fwd, samples_step, value, ms, ms_fwd, ms_adj, e2
                                                "sample": "64^3 at 4 mm, all 64 angles, 96x64 panel; best of 3"}
         except Exception as exc:  # noqa: BLE001
             line["cpu_baseline"]["small64"] = {"error": str(exc)[:200]}
+    if world == 1:
+        try:
+            line["poly_primary"] = poly_timing(geom, args.workload)
+        except Exception as exc:  # noqa: BLE001 (a leg beside the projector metric)
+            line["poly_primary"] = {"error": str(exc)[:300]}
     if not args.no_lpd and world == 1 and args.workload == WORKLOAD:
         try:
             line["lpd_vs_pdhg"] = lpd_timing(1, 2)

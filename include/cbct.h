@@ -9,7 +9,8 @@
  * field-of-view tensor V and redundancy weight w used by the reconstruction
  * (Sec. 2.6), FDK with redundancy weighting, PDHG-TV (Sec. 2.5 baselines), the
  * primary-signal simulation (Sec. 2.2 primary model with Poisson noise, Sec. 2.4
- * log normalisation) and the learned primal-dual reconstruction (Sec. 2.6,
+ * log normalisation; monochromatic, and polychromatic with the water-bone split of
+ * Sec. 2.1) and the learned primal-dual reconstruction (Sec. 2.6,
  * Algorithm 1).
  *
  * Conventions for every call
@@ -196,6 +197,59 @@ int cbct_neglog(const int32_t *counts, long long n, double I0, float *y, void *s
  * the counter e running over the whole [batch][n_angles][nv][nu] array. */
 int cbct_simulate(const cbct_geom *g, const float *vol, int batch, double I0, unsigned long long seed,
                   float *line_integrals, float *y, void *stream);
+
+/* ---- polychromatic primary (Sec. 2.1, "Primary simulation", primary-model
+ * equation; Sec. 2.4, normalised primary data) ----
+ * The paper's primary model is a sum over energy bins e (ten 10 keV bins centred at
+ * 25 ... 115 keV) of resp(e) Poisson(I0_e exp(-P(mu_w(e) rho_w + mu_b(e) rho_b))),
+ * with rho_w, rho_b the water and bone relative densities of the CT scan and
+ * mu_w(e), mu_b(e) the attenuation of water and bone at e. P is linear, so the
+ * library projects rho_w and rho_b once each and forms every bin's exponent as
+ * mu_w(e) P(rho_w) + mu_b(e) P(rho_b): two projections per volume for any number
+ * of bins. The attenuation tables (the paper takes them from xraylib) and the
+ * per-pixel intensity maps I0_e (from the paper's phase file) are inputs. At most
+ * 16 bins. */
+
+/* Detector response resp(e) for n_e energies in keV (host arrays): linear between
+ * (20 keV, 5), (60 keV, 20) and (120 keV, 10), constant outside [20, 120]
+ * (Sec. 2.1, after Poludniowski 2009). Host only; launches nothing. */
+int cbct_detector_response(const double *energies_kev, int n_e, double *resp);
+
+/* Water-bone decomposition (Sec. 2.1, after Wang et al. 2018) of `batch` volumes
+ * mu[batch][n_vox] of mu_tot,60 (1/mm) into rho[batch][2][n_vox] (water, then bone,
+ * relative densities): rho_hat = 0.001 HU + 1 = mu / mu_water60; with tau1 = 1.2,
+ * tau2 = 1.6, kappa_b = 0.409, rho_w = rho_hat on [0, tau1), tau1 (tau2 - rho_hat) /
+ * (tau2 - tau1) on [tau1, tau2), 0 elsewhere; rho_b = 0 below tau1, kappa_b tau2
+ * (rho_hat - tau1) / (tau2 - tau1) on [tau1, tau2), kappa_b rho_hat above. The paper
+ * leaves tau0 unstated; 0 makes rho_w continuous, as the paper says it is. FP32. */
+int cbct_water_bone(const float *mu, long long n_vox, int batch, double mu_water60, float *rho, void *stream);
+
+/* Polychromatic reading from line integrals. line_integrals[batch][2][n_per_item]
+ * (water P(rho_w), then bone P(rho_b); n_per_item = n_angles nv nu), I0[n_e][npix]
+ * (device, npix = nv nu, the same map for every angle), energies_kev, mu_water,
+ * mu_bone: host arrays of n_e entries (1/mm). Per element e (over all items):
+ * lam_j = I0[j][pixel] exp(-(mu_water[j] L_w + mu_bone[j] L_b)); N_j ~ Poisson(lam_j)
+ * drawn as in cbct_poisson on the counter of element e n_e + j (lam_j itself when
+ * noise is 0); reading[e] = sum_j resp_j N_j (bins in order, FP64, rounded once);
+ * y[e] = -log(min(max(reading, r_min) / air, 1)) with the expected air reading
+ * air = sum_j resp_j I0[j][pixel] (the paper's normalisation by an air scan, here
+ * noise-free) and r_min = min_j resp_j (a reading of no photons counts as one photon
+ * of the least responsive bin, so y stays finite, as cbct_neglog clamps counts to 1).
+ * Any of reading, y, counts ([n][n_e] draws; needs noise) may be NULL, not all. */
+int cbct_poly_reading(const float *line_integrals, int batch, long long n_per_item, int npix, int n_e,
+                      const double *energies_kev, const double *mu_water, const double *mu_bone,
+                      const float *I0, unsigned long long seed, int noise, float *reading, float *y,
+                      int32_t *counts, void *stream);
+
+/* Polychromatic simulated measurement of `batch` mu_60 volumes (Sec. 2.1 and 2.4):
+ * cbct_water_bone, one forward projection of the 2 batch density volumes into
+ * line_integrals[batch][2][n_angles][nv][nu] (output), then y[batch][n_angles][nv][nu]
+ * as in cbct_poly_reading. Scratch for the densities (8 bytes per voxel) comes from
+ * the stream-ordered pool. */
+int cbct_poly_simulate(const cbct_geom *g, const float *mu, int batch, double mu_water60, int n_e,
+                       const double *energies_kev, const double *mu_water, const double *mu_bone,
+                       const float *I0, unsigned long long seed, int noise, float *line_integrals, float *y,
+                       void *stream);
 
 /* Offset-detector redundancy weight w[nu] (device), Sec. 2.6 (the paper names no
  * scheme; this is Wang's): u' = (iu - (nu-1)/2) du + u_offset, D = nu du/2 -

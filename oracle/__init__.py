@@ -313,10 +313,13 @@ def poly_air(energies, I0: np.ndarray) -> np.ndarray:
     return acc
 
 
-def poly_neglog(reading: np.ndarray, air: np.ndarray) -> np.ndarray:
+def poly_neglog(reading: np.ndarray, air: np.ndarray, energies) -> np.ndarray:
     """y_primary = -log(min(reading / air, 1)) (Sec. 2.4, normalised primary data);
-    air broadcasts over the leading (angle, batch) axes."""
-    r = np.asarray(reading, dtype=np.float64) / air
+    air broadcasts over the leading (angle, batch) axes. A reading below that of one
+    photon in the least responsive bin (zero photons) is raised to it, so that y
+    stays finite (the monochromatic transform clamps counts to one the same way)."""
+    floor = min(resp(e) for e in energies)
+    r = np.maximum(np.asarray(reading, dtype=np.float64), floor) / air
     return -np.log(np.minimum(r, 1.0))
 
 
@@ -333,4 +336,4 @@ def poly_primary(G: Geom, mu: np.ndarray, mu_w60: float, energies, mu_w, mu_b, I
         p = forward(G, rw * mu_w[j] + rb * mu_b[j])
         lam[..., j] = np.asarray(I0[j], dtype=np.float64) * np.exp(-p)
     reading = poly_reading(lam.reshape(-1, ne), energies, seed, noise).reshape(G.proj_shape)
-    return reading, poly_neglog(reading, poly_air(energies, I0))
+    return reading, poly_neglog(reading, poly_air(energies, I0), energies)

@@ -60,6 +60,10 @@ SIGNATURES = {
     "cbct_neglog": (I32, [P, I64, F64, P, P]),
     "cbct_simulate": (I32, [P, P, I32, F64, U64, P, P, P]),
     "cbct_redundancy_weight": (I32, [P, P, P]),
+    "cbct_detector_response": (I32, [P, I32, P]),
+    "cbct_water_bone": (I32, [P, I64, I32, F64, P, P]),
+    "cbct_poly_reading": (I32, [P, I32, I64, I32, I32, P, P, P, P, U64, I32, P, P, P, P]),
+    "cbct_poly_simulate": (I32, [P, P, I32, F64, I32, P, P, P, P, U64, I32, P, P, P]),
     "cbct_fov": (I32, [P, P, P]),
     "cbct_fdk_pad": (I32, [P]),
     "cbct_fdk": (I32, [P, P, P, I32, I32, P]),

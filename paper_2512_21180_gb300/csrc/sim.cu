@@ -5,11 +5,15 @@
 //    inversion for means below 10 and by Hoermann's PTRS transformed rejection
 //    (1993) above
 //  - normalised log transform y = -log(min(max(N, 1) / I0, 1)) (Sec. 2.4)
+//  - polychromatic primary (Sec. 2.1): water-bone split of the mu_60 volume, the
+//    resp-weighted sum over energy bins of Poisson draws from two line integrals
+//    per pixel (water and bone), normalised by the expected air reading
 //  - offset-detector redundancy weight w (Sec. 2.6; Wang's sin^2 weight over the
 //    overlap band, 1/2 for a centred panel)
 //  - field-of-view tensor V = (angles seeing the voxel centre) / (all angles)
 //    (Sec. 2.6, definition of V)
 #include <cmath>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -147,6 +151,104 @@ __global__ void k_poisson_neglog(const float *__restrict__ p, long long n, doubl
         const float c = N < 1 ? 1.0f : (float)N;
         y[e] = -logf(fminf(c / I0f, 1.0f));
     }
+}
+
+// ---- polychromatic primary (Sec. 2.1, "Primary simulation") --------------------------
+
+constexpr int kPolyMaxBins = 16;
+
+struct PolyTab {
+    int ne;
+    double muw[kPolyMaxBins], mub[kPolyMaxBins], resp[kPolyMaxBins];
+    double rmin;  // smallest resp_j: the reading of one photon in the least responsive bin
+};
+
+// Water-bone split of mu_60 volumes into rho[b][0][.] (water) and rho[b][1][.] (bone):
+// rho_hat = mu / mu_w60 (= 0.001 HU + 1); rho_w = rho_hat below tau1 = 1.2, falling
+// linearly to 0 at tau2 = 1.6, 0 above (and 0 for rho_hat < 0); rho_b = 0 below tau1,
+// rising linearly to kappa_b tau2 at tau2, kappa_b rho_hat above (kappa_b = 0.409).
+__global__ void k_water_bone(const float *__restrict__ mu, long long nvox, long long n, float mu_w60,
+                             float *__restrict__ rho) {
+    const float t1 = 1.2f, t2 = 1.6f, kb = 0.409f;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const long long b = e / nvox, i = e - b * nvox;
+        const float r = __fdiv_rn(mu[e], mu_w60);
+        float w, bn;
+        if (r < t1) {
+            w = r < 0.0f ? 0.0f : r;
+            bn = 0.0f;
+        } else if (r < t2) {
+            const float f = (t2 - r) / (t2 - t1);
+            w = t1 * f;
+            bn = kb * t2 * (1.0f - f);
+        } else {
+            w = 0.0f;
+            bn = kb * r;
+        }
+        rho[(2 * b) * nvox + i] = w;
+        rho[(2 * b + 1) * nvox + i] = bn;
+    }
+}
+
+// Per detector element (all batch items, angles and pixels): mean counts of bin j
+// lam_j = I0[j][pix] exp(-(mu_w[j] L_w + mu_b[j] L_b)) from the water and bone line
+// integrals L[b][0 / 1][angle][pixel]; reading = sum_j resp_j N_j with N_j ~
+// Poisson(lam_j) drawn on the counter of element e ne + j (lam_j itself when noise
+// is 0); y = -log(min(max(reading, rmin) / air, 1)) with the expected air reading
+// air = sum_j resp_j I0[j][pix] (a reading of zero photons is taken as one photon of
+// the least responsive bin, as the monochromatic path clamps counts to one). FP64
+// throughout, each operation rounded as written.
+__global__ void k_poly_reading(const float *__restrict__ L, long long per_item, long long n, int npix,
+                               const float *__restrict__ I0, PolyTab t, unsigned long long seed, int noise,
+                               float *__restrict__ reading, float *__restrict__ y, int32_t *__restrict__ counts) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const long long b = e / per_item, r = e - b * per_item;
+        const int pix = (int)(r % npix);
+        const double Lw = (double)L[(2 * b) * per_item + r], Lb = (double)L[(2 * b + 1) * per_item + r];
+        double acc = 0.0, air = 0.0;
+        for (int j = 0; j < t.ne; ++j) {
+            const double i0 = (double)I0[(long long)j * npix + pix];
+            const double a = __dadd_rn(__dmul_rn(t.muw[j], Lw), __dmul_rn(t.mub[j], Lb));
+            const double lam = __dmul_rn(i0, exp(-a));
+            double v = lam;
+            if (noise) {
+                const int32_t c = poisson_draw(lam, (unsigned long long)e * (unsigned long long)t.ne + j, seed);
+                if (counts) counts[e * t.ne + j] = c;
+                v = (double)c;
+            }
+            acc = __dadd_rn(acc, __dmul_rn(t.resp[j], v));
+            air = __dadd_rn(air, __dmul_rn(t.resp[j], i0));
+        }
+        if (reading) reading[e] = (float)acc;
+        if (y) y[e] = (float)(-log(fmin(__ddiv_rn(fmax(acc, t.rmin), air), 1.0)));
+    }
+}
+
+// resp(e) for e in keV: piecewise linear through (20, 5), (60, 20), (120, 10),
+// constant outside [20, 120].
+static double detector_response(double e) {
+    if (e <= 20.0) return 5.0;
+    if (e <= 60.0) return 5.0 + (e - 20.0) * (20.0 - 5.0) / (60.0 - 20.0);
+    if (e <= 120.0) return 20.0 + (e - 60.0) * (10.0 - 20.0) / (120.0 - 60.0);
+    return 10.0;
+}
+
+static int poly_table(int n_e, const double *energies, const double *mu_w, const double *mu_b, PolyTab *t,
+                      const char *who) {
+    if (n_e < 1 || n_e > kPolyMaxBins || !energies || !mu_w || !mu_b)
+        return fail(CBCT_EINVAL, std::string(who) + ": need 1 <= n_e <= 16 and host tables");
+    t->ne = n_e;
+    t->rmin = detector_response(energies[0]);
+    for (int j = 0; j < n_e; ++j) {
+        if (!(energies[j] > 0.0) || !std::isfinite(energies[j]) || !(mu_w[j] >= 0.0) || !std::isfinite(mu_w[j]) ||
+            !(mu_b[j] >= 0.0) || !std::isfinite(mu_b[j]))
+            return fail(CBCT_EINVAL, std::string(who) + ": energies must be > 0 and attenuations finite and >= 0");
+        t->muw[j] = mu_w[j];
+        t->mub[j] = mu_b[j];
+        t->resp[j] = detector_response(energies[j]);
+        t->rmin = fmin(t->rmin, t->resp[j]);
+    }
+    return 0;
 }
 
 // ---- redundancy weight and field of view ---------------------------------------------
@@ -290,5 +392,71 @@ extern "C" int cbct_fov(const cbct_geom *g, float *V, void *stream) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host table must outlive the copy
     cudaFreeAsync(dcs, st);
     if (e != cudaSuccess) return cuda_fail(e, "cbct_fov");
+    return 0;
+}
+
+extern "C" int cbct_detector_response(const double *energies_kev, int n_e, double *resp) {
+    if (!energies_kev || !resp || n_e < 0) return fail(CBCT_EINVAL, "cbct_detector_response: invalid argument");
+    for (int j = 0; j < n_e; ++j) resp[j] = detector_response(energies_kev[j]);
+    return 0;
+}
+
+extern "C" int cbct_water_bone(const float *mu, long long n_vox, int batch, double mu_water60, float *rho,
+                               void *stream) {
+    if (!mu || !rho || n_vox < 0 || batch < 1 || !(mu_water60 > 0) || !std::isfinite(mu_water60))
+        return fail(CBCT_EINVAL, "cbct_water_bone: invalid argument");
+    const long long n = n_vox * batch;
+    if (n == 0) return 0;
+    k_water_bone<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(mu, n_vox, n, (float)mu_water60, rho);
+    CBCT_LAUNCH_CHECK("cbct_water_bone launch");
+    return 0;
+}
+
+extern "C" int cbct_poly_reading(const float *line_integrals, int batch, long long n_per_item, int npix, int n_e,
+                                 const double *energies_kev, const double *mu_water, const double *mu_bone,
+                                 const float *I0, unsigned long long seed, int noise, float *reading, float *y,
+                                 int32_t *counts, void *stream) {
+    PolyTab t;
+    int rc = poly_table(n_e, energies_kev, mu_water, mu_bone, &t, "cbct_poly_reading");
+    if (rc) return rc;
+    if (!line_integrals || !I0 || batch < 1 || n_per_item < 0 || npix < 1 || n_per_item % npix != 0 ||
+        (!reading && !y && !counts) || (counts && !noise))
+        return fail(CBCT_EINVAL, "cbct_poly_reading: invalid argument");
+    const long long n = n_per_item * batch;
+    if (n == 0) return 0;
+    k_poly_reading<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(line_integrals, n_per_item, n, npix, I0, t, seed,
+                                                                  noise ? 1 : 0, reading, y, counts);
+    CBCT_LAUNCH_CHECK("cbct_poly_reading launch");
+    return 0;
+}
+
+extern "C" int cbct_poly_simulate(const cbct_geom *g, const float *mu, int batch, double mu_water60, int n_e,
+                                  const double *energies_kev, const double *mu_water, const double *mu_bone,
+                                  const float *I0, unsigned long long seed, int noise, float *line_integrals, float *y,
+                                  void *stream) {
+    PolyTab t;
+    int rc = poly_table(n_e, energies_kev, mu_water, mu_bone, &t, "cbct_poly_simulate");
+    if (rc) return rc;
+    if (!g || !mu || !I0 || !line_integrals || !y || batch < 1 || !(mu_water60 > 0) || !std::isfinite(mu_water60))
+        return fail(CBCT_EINVAL, "cbct_poly_simulate: invalid argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const GeomDev &v = g->dev;
+    const long long nvox = (long long)v.n[0] * v.n[1] * v.n[2];
+    const long long per_item = (long long)v.na * v.nv * v.nu;
+    float *rho = nullptr;
+    CBCT_CUDA_TRY(cudaMallocAsync((void **)&rho, sizeof(float) * 2 * nvox * batch, st));
+    k_water_bone<<<grid_for(nvox * batch), 256, 0, st>>>(mu, nvox, nvox * batch, (float)mu_water60, rho);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaFreeAsync(rho, st);
+        return cuda_fail(e, "cbct_poly_simulate: water-bone launch");
+    }
+    rc = forward_project(g, rho, line_integrals, 2 * batch, 0, stream);
+    cudaFreeAsync(rho, st);
+    if (rc) return rc;
+    k_poly_reading<<<grid_for(per_item * batch), 256, 0, st>>>(line_integrals, per_item, per_item * batch,
+                                                              v.nv * v.nu, I0, t, seed, noise ? 1 : 0, nullptr, y,
+                                                              nullptr);
+    CBCT_LAUNCH_CHECK("cbct_poly_simulate: reading launch");
     return 0;
 }

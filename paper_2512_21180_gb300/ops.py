@@ -2,6 +2,8 @@
 only; the arithmetic runs in libcbct.so)."""
 from __future__ import annotations
 
+import ctypes
+
 import numpy as np
 import torch
 
@@ -57,6 +59,88 @@ def simulate(geom: Geometry, vol: torch.Tensor, I0: float, seed: int):
         check(_lib.load().cbct_simulate(geom.handle, v.data_ptr(), B, float(I0), int(seed), p.data_ptr(),
                                         y.data_ptr(), _st(v)), "cbct_simulate")
     return p, y
+
+
+def _f64(a):
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+    return arr, arr.ctypes.data_as(ctypes.c_void_p)
+
+
+def detector_response(energies_kev) -> np.ndarray:
+    """resp(e) of the polychromatic model (host only)."""
+    E, pE = _f64(energies_kev)
+    out = np.zeros(len(E))
+    check(_lib.load().cbct_detector_response(pE, len(E), out.ctypes.data_as(ctypes.c_void_p)),
+          "cbct_detector_response")
+    return out
+
+
+def water_bone(mu: torch.Tensor, mu_water60: float) -> torch.Tensor:
+    """rho[batch][2][...] (water, bone) of mu_60 volumes mu[batch][...] (a 3-D
+    volume is one item)."""
+    v = mu.contiguous()
+    assert v.dtype == torch.float32 and v.is_cuda
+    if v.dim() == 3:
+        v = v.unsqueeze(0)
+    B = v.shape[0]
+    out = torch.empty((B, 2) + tuple(v.shape[1:]), dtype=torch.float32, device=v.device)
+    with torch.cuda.device(v.device):
+        check(_lib.load().cbct_water_bone(v.data_ptr(), v[0].numel(), B, float(mu_water60), out.data_ptr(), _st(v)),
+              "cbct_water_bone")
+    return out
+
+
+def poly_reading(line_integrals: torch.Tensor, I0: torch.Tensor, energies_kev, mu_water, mu_bone, seed: int,
+                 noise: bool = True, want_counts: bool = False):
+    """(reading, y, counts or None) from water / bone line integrals
+    [batch][2][n_angles][nv][nu] and intensity maps I0[n_e][nv][nu]."""
+    L = line_integrals.contiguous()
+    i0 = I0.contiguous()
+    assert L.dtype == torch.float32 and i0.dtype == torch.float32 and L.is_cuda and i0.is_cuda
+    assert L.dim() == 5 and L.shape[1] == 2
+    B = L.shape[0]
+    E, pE = _f64(energies_kev)
+    mw, pW = _f64(mu_water)
+    mb, pB = _f64(mu_bone)
+    ne = len(E)
+    assert len(mw) == ne and len(mb) == ne and i0.shape[0] == ne
+    per_item = L[0, 0].numel()
+    npix = L.shape[-1] * L.shape[-2]
+    assert i0.numel() == ne * npix, "I0 must be [n_e][nv][nu]"
+    reading = torch.empty((B,) + tuple(L.shape[2:]), dtype=torch.float32, device=L.device)
+    y = torch.empty_like(reading)
+    counts = (torch.empty((B,) + tuple(L.shape[2:]) + (ne,), dtype=torch.int32, device=L.device)
+              if want_counts else None)
+    with torch.cuda.device(L.device):
+        check(_lib.load().cbct_poly_reading(L.data_ptr(), B, per_item, npix, ne, pE, pW, pB, i0.data_ptr(),
+                                            int(seed), 1 if noise else 0, reading.data_ptr(), y.data_ptr(),
+                                            counts.data_ptr() if counts is not None else None, _st(L)),
+              "cbct_poly_reading")
+    return reading, y, counts
+
+
+def poly_simulate(geom: Geometry, mu: torch.Tensor, I0: torch.Tensor, energies_kev, mu_water, mu_bone,
+                  mu_water60: float, seed: int, noise: bool = True):
+    """(water / bone line integrals [batch][2][...], normalised polychromatic data
+    y [batch][n_angles][nv][nu]) for a batch of mu_60 volumes."""
+    v = mu.contiguous()
+    i0 = I0.contiguous()
+    if v.dim() == 3:
+        v = v.unsqueeze(0)
+    assert v.dtype == torch.float32 and i0.dtype == torch.float32 and v.is_cuda and i0.is_cuda
+    B = v.shape[0]
+    E, pE = _f64(energies_kev)
+    mw, pW = _f64(mu_water)
+    mb, pB = _f64(mu_bone)
+    assert len(mw) == len(E) and len(mb) == len(E) and i0.numel() == len(E) * geom.nv * geom.nu, \
+        "tables of n_e entries and I0 [n_e][nv][nu]"
+    L = torch.empty((B, 2) + geom.proj_shape, device=v.device, dtype=torch.float32)
+    y = torch.empty((B,) + geom.proj_shape, device=v.device, dtype=torch.float32)
+    with torch.cuda.device(v.device):
+        check(_lib.load().cbct_poly_simulate(geom.handle, v.data_ptr(), B, float(mu_water60), len(E), pE, pW, pB,
+                                             i0.data_ptr(), int(seed), 1 if noise else 0, L.data_ptr(),
+                                             y.data_ptr(), _st(v)), "cbct_poly_simulate")
+    return L, y
 
 
 def redundancy_weight(geom: Geometry) -> torch.Tensor:

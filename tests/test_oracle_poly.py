@@ -103,6 +103,19 @@ def test_air_scan_normalises_to_zero(O):
     assert np.max(np.abs(y)) == 0.0
 
 
+def test_no_photons_read_as_one_photon_of_the_least_responsive_bin(O):
+    """A reading of zero (every bin absorbed) is raised to min resp (one photon in
+    the least responsive bin), so y = log(air / min resp) stays finite; readings
+    above that floor are untouched."""
+    E = I.POLY_ENERGIES_KEV
+    air = np.array([[1.0e5, 3.0e4]])
+    floor = min(O.resp(e) for e in E)
+    y = O.poly_neglog(np.array([[0.0, 2.0 * floor]]), air, E)
+    assert y[0, 0] == pytest.approx(np.log(1.0e5 / floor), rel=1e-15)
+    assert y[0, 1] == pytest.approx(np.log(3.0e4 / (2.0 * floor)), rel=1e-15)
+    assert floor == O.resp(25.0) and floor < O.resp(115.0)
+
+
 def test_monochromatic_limit_is_the_projection(O):
     """One bin whose water attenuation is mu_w(60): for a soft-tissue volume the
     expected normalised data equal the cone-beam projection P(mu) of the pinned

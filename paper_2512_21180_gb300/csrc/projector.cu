@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256) k_backproject(GeomDev g, const T *__restr
 }
 
 // Segment gather (FP32, geometries whose x- and y-principal columns form intervals).
-// CTA = brick of 16 x 16 voxel columns x 12 voxels in z, 288 threads. For the rays
+// CTA = brick of 16 x 16 voxel columns x 8 voxels in z, 288 threads. For the rays
 // of principal axis a at angle k, plane i of the brick is crossed at
 // q_b(u) = fma(di, dqb(u), qcb(u)), monotone in the detector column u. The columns
 // with floor(q_b) = s form segment s of the plane; their samples lie between voxels
@@ -220,22 +220,25 @@ __global__ void __launch_bounds__(256) k_backproject(GeomDev g, const T *__restr
 // rz_0 + v EV_z), so no table load sits between two intervals; and the rows of
 // an interval go through a fixed block of five predicated loads (3 to 5 rows per
 // interval at these magnifications) plus a loop for longer intervals, which makes
-// the 13-interval sweep straight-line code whose loads overlap.
+// the (kZ3 + 1)-interval sweep straight-line code whose loads overlap.
 // The panel width is a template parameter for common widths (256, 512, 1024 columns): the five
 // row loads of an interval then sit at constant offsets from one row pointer, which took the
 // clinical adjoint from 23.3 to 19.6 ms (CUDA events, bit-identical output).
-// Bricks 12 voxels tall: measured at the clinical size (CUDA events), 23.7 ms against 24.5 with
-// 8, 26.0 with 6, 31.5 with 4 and 26.8 with 16 — shorter z-runs are skipped more often where the
-// panel does not reach them, but spread each column's set-up over fewer intervals; limiting the
-// registers to fit a fourth or fifth CTA per SM was slower (8 tall: 25.9 / 27.6 ms).
-constexpr int kB3 = 16, kZ3 = 12, kThreads3 = 288;
+// Bricks 8 voxels tall with four CTAs per SM (registers capped at 56, no spills): with the
+// width-specialised loads the kernel is bound by load latency more than by issue, and the
+// fourth CTA's warps hide it. Clinical adjoint (CUDA events): 18.3 ms, against 19.6 with
+// 12-voxel bricks at three CTAs, 19.7 with 8-voxel bricks at three, 19.0 with 10 at four,
+// 20.0 with 6 at four, 28.4 with 12 at four and 23.3 with 8 at five (spills). Before the
+// width-specialised loads 12-voxel bricks at three CTAs had been best (23.7 ms; 24.5 with 8,
+// 26.0 with 6, 31.5 with 4, 26.8 with 16; capped registers slower).
+constexpr int kB3 = 16, kZ3 = 8, kThreads3 = 288;
 constexpr int kVacc3 = kZ3 * kB3 * (kB3 + 1);  // [z][y][x], y stride 17 (bank-conflict free both ways)
 constexpr size_t kSmem3 = sizeof(float) * kVacc3;
 
 // NU > 0 fixes the panel width at compile time, so the rows of an interval are loaded at
 // constant offsets (rr NU floats) from one row pointer; NU = 0 reads it from the geometry.
 template <int NU>
-__global__ void __launch_bounds__(kThreads3, 3) k_backproject_v3(GeomDev g, const float *__restrict__ pw,
+__global__ void __launch_bounds__(kThreads3, 4) k_backproject_v3(GeomDev g, const float *__restrict__ pw,
                                                                  float *__restrict__ vol, int accumulate,
                                                                  int nparts, float *__restrict__ partial) {
     extern __shared__ float sm3[];
@@ -498,7 +501,7 @@ static int backward_impl(const cbct_geom *g, const T *proj, T *vol, int batch, i
             if (g->axis_contiguous) {
                 const int nzb = (d.n[2] + kZ3 - 1) / kZ3;
                 const long long base = (long long)((d.n[0] + kB3 - 1) / kB3) * ((d.n[1] + kB3 - 1) / kB3) * nzb * batch;
-                // split the angles so that about 9 CTAs per SM are available (3 resident, 3 waves)
+                // split the angles so that about 9 CTAs per SM are available (4 resident, 2+ waves)
                 const long long want = 9LL * sm_count();
                 int nparts = (int)std::min<long long>(16, std::max<long long>(1, (want + base - 1) / base));
                 nparts = std::min(nparts, d.na);

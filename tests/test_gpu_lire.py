@@ -128,7 +128,14 @@ def test_lire_matches_oracle_and_inverts(O, M, width):
     h_init = np.stack([y] * n_mem)
     ef, eh = rel_l2(to_np(f0), f_init), rel_l2(to_np(h0), h_init)
     print(f"LIRE recovered initial latents: f {ef:.2e}, h {eh:.2e}")
-    assert ef <= 1e-5 and eh <= 1e-5, (ef, eh)
+    # Each update is added and later subtracted in FP32 (one rounding each way), and a
+    # recovered half re-enters the blocks and projections of the earlier iterations, which
+    # carry that rounding on; the LIRE iteration has three coupled updates (x, p2, d2) per
+    # iteration. Measured 0.8e-5 / 1.4e-5 (f / h) with the 8-voxel-brick adjoint, below 1e-5
+    # with the 12-voxel one (same algorithm, different FP32 summation order): the bound
+    # leaves room for that spread, far below any error of the inversion itself (a missing
+    # or misordered update moves the states by O(1)).
+    assert ef <= 5e-5 and eh <= 5e-5, (ef, eh)
 
 
 def test_lire_rejects_bad_configurations(M):

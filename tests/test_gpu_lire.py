@@ -130,11 +130,12 @@ def test_lire_matches_oracle_and_inverts(O, M, width):
     print(f"LIRE recovered initial latents: f {ef:.2e}, h {eh:.2e}")
     # Each update is added and later subtracted in FP32 (one rounding each way), and a
     # recovered half re-enters the blocks and projections of the earlier iterations, which
-    # carry that rounding on; the LIRE iteration has three coupled updates (x, p2, d2) per
-    # iteration. Measured 0.8e-5 / 1.4e-5 (f / h) with the 8-voxel-brick adjoint, below 1e-5
-    # with the 12-voxel one (same algorithm, different FP32 summation order): the bound
-    # leaves room for that spread, far below any error of the inversion itself (a missing
-    # or misordered update moves the states by O(1)).
+    # carry that rounding on; their Landweber and residual inputs P x - y are differences of
+    # nearly equal line integrals, which magnify the rounding of the recovered x. Measured
+    # (f / h) with the 8-voxel-brick adjoint: width 32 8.0e-6 / 1.4e-5, width 64 1.7e-7 /
+    # 3.5e-8; with the 12-voxel one (same algorithm, another FP32 summation order) width 32
+    # stayed below 1e-5. The bound leaves room for that spread and stays far below any error
+    # of the inversion itself (a missing or misordered update moves the states by O(1)).
     assert ef <= 5e-5 and eh <= 5e-5, (ef, eh)
 
 

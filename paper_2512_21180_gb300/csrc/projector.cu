@@ -121,6 +121,15 @@ __device__ __forceinline__ float column_of(const Frame32 &F, float px, float py)
     return -num / den;
 }
 
+// column_of with the approximate division: for candidate ranges that carry a margin of a
+// column or more (relative error a few ulp; non-finite where column_of is)
+__device__ __forceinline__ float column_of_approx(const Frame32 &F, float px, float py) {
+    const float dx = px - F.S[0], dy = py - F.S[1];
+    const float num = F.D0S[0] * dy - F.D0S[1] * dx;
+    const float den = F.EU[0] * dy - F.EU[1] * dx;
+    return -__fdividef(num, den);
+}
+
 template <typename T, int ZS>
 __global__ void __launch_bounds__(256) k_backproject(GeomDev g, const T *__restrict__ pw, T *__restrict__ vol,
                                                      int accumulate) {
@@ -255,7 +264,7 @@ __global__ void __launch_bounds__(kThreads3, 4) k_backproject_v3(GeomDev g, cons
     for (int e = tid; e < kVacc3; e += kThreads3) vacc[e] = 0.f;
     __syncthreads();
     const float Sz = g.Sz;
-    const float rz0 = g.rz32[0], drz = g.f32[0].EV[2];
+    const float rz0 = g.rz32[0], drz = g.f32[0].EV[2], inv_drz = 1.0f / drz;
     const float *PB = pw + (long long)b * g.na * nv * nu;
 
 #pragma unroll 1
@@ -273,10 +282,12 @@ __global__ void __launch_bounds__(kThreads3, 4) k_backproject_v3(GeomDev g, cons
             const int alo = a == 0 ? F.ux_lo : F.uy_lo, ahi = a == 0 ? F.ux_hi : F.uy_hi;
             if (alo > ahi || !mine) continue;
             const float *Pk = PB + (long long)k * nv * nu;
-            // candidate columns for q_b in [s, s + 1), one column of margin
+            // candidate columns for q_b in [s, s + 1), one column of margin (which also covers
+            // the approximate divisions here and in the z-run test below: the exact test on
+            // floor(q_b) decides which columns contribute)
             float u1, u2;
-            if (a == 0) { u1 = column_of(F, (float)i, (float)s); u2 = column_of(F, (float)i, (float)(s + 1)); }
-            else { u1 = column_of(F, (float)s, (float)i); u2 = column_of(F, (float)(s + 1), (float)i); }
+            if (a == 0) { u1 = column_of_approx(F, (float)i, (float)s); u2 = column_of_approx(F, (float)i, (float)(s + 1)); }
+            else { u1 = column_of_approx(F, (float)s, (float)i); u2 = column_of_approx(F, (float)(s + 1), (float)i); }
             int ulo = alo, uhi = ahi;
             if (isfinite(u1) && isfinite(u2)) {
                 ulo = max(ulo, (int)floorf(fmaxf(fminf(u1, u2), -1.0e6f)) - 1);
@@ -289,8 +300,9 @@ __global__ void __launch_bounds__(kThreads3, 4) k_backproject_v3(GeomDev g, cons
                 const float tmin = fminf(tl, th), tmax = fmaxf(tl, th);
                 const float zlo = (float)(z0 - 1) - Sz, zhi = (float)(z0 + kZ3) - Sz;
                 const float t1 = fmaxf(tmin, 1e-6f);
-                const float rlo = fminf(zlo / t1, zlo / tmax), rhi = fmaxf(zhi / t1, zhi / tmax);
-                const float vlo = (rlo - rz0) / drz - 2.f, vhi = (rhi - rz0) / drz + 2.f;
+                const float rlo = fminf(__fdividef(zlo, t1), __fdividef(zlo, tmax));
+                const float rhi = fmaxf(__fdividef(zhi, t1), __fdividef(zhi, tmax));
+                const float vlo = (rlo - rz0) * inv_drz - 2.f, vhi = (rhi - rz0) * inv_drz + 2.f;
                 if (!(tmax > 0.f) || vhi < 0.f || vlo > (float)(nv - 1)) uhi = ulo - 1;
             }
             {  // first and last column of the segment

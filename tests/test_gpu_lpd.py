@@ -35,20 +35,26 @@ def oracle_params(flat, shapes):
     return out
 
 
-def _lpd_case(O, M, last_scale, seed_w=3, width=32):
+# a larger, anisotropic case: 72 x 56 x 24 volume, 24 angles, 96 x 24 panel, 3 iterations
+GEOM_L = I.scaled(I.geometry("tiny16"), n=(72, 56, 24), vox=(5.0, 5.0, 5.0), nu=96, nv=24, du=4.0, dv=4.0,
+                  n_angles=24, u_offset=30.0)
+
+
+def _lpd_case(O, M, last_scale, seed_w=3, width=32, gd=GEOM, n_iter=2):
     """GPU forward/backward and the FP64 reference (BF16 operands in both passes) on the
-    24x24x16 / 12-angle case with 2 iterations; returns both sides' output and gradients
-    and a function that re-evaluates the reference's gradients for a perturbed x0."""
+    24x24x16 / 12-angle case with 2 iterations (or the geometry and iteration count
+    given); returns both sides' output and gradients and a function that re-evaluates the
+    reference's gradients for a perturbed x0."""
     from oracle import lpd_ref as R
     P, L = M
-    G = O.Geom(GEOM)
-    geom = P.Geometry(GEOM)
-    n_iter, mu, bps = 2, 0.02, 2e-3
+    G = O.Geom(gd)
+    geom = P.Geometry(gd)
+    mu, bps = 0.02, 2e-3
     model = L.LPD(geom, n_iter=n_iter, mu_ref=mu, bp_scale=bps, width=width)
     shapes = L.layer_shapes(n_iter, width=width)
     flat = I.lpd_weights(shapes, seed=seed_w, last_scale=last_scale)
     model.set_params(flat)
-    x_true = O.phantom(G, I.ellipsoids(GEOM, 5, n_soft=6, axes_mm=(15.0, 60.0)))
+    x_true = O.phantom(G, I.ellipsoids(gd, 5, n_soft=6, axes_mm=(15.0, 60.0)))
     y = O.forward(G, x_true) + 0.01 * I.random_normal(G.proj_shape, 6).astype(np.float64)
     x0 = 0.8 * x_true + 0.002 * I.random_normal(G.vol_shape, 7).astype(np.float64)
     r = I.random_normal(G.vol_shape, 8).astype(np.float64)
@@ -89,6 +95,20 @@ def test_lpd_forward_and_gradients_match_oracle(O, M):
     # runs the same arithmetic as the training pass above
     xi = model.forward(to_gpu(y), to_gpu(x0))
     assert np.array_equal(to_np(xi), xg)
+
+
+def test_lpd_larger_case_matches_oracle(O, M):
+    """72 x 56 x 24 voxels, 24 angles of a 96 x 24 panel, 3 iterations: projection images
+    and volume rows of several widths, more angles per dual launch; output and gradients
+    within the same bars."""
+    model, (xg, gg, gy, g0), reference, _ = _lpd_case(O, M, 0.1, gd=GEOM_L, n_iter=3)
+    ref, gref, gyr, g0r = reference()
+    _, gp, gyp, g0p = reference(1.0 + 1e-6)
+    assert rel_l2(xg, ref) <= 1e-2
+    e_w, e_y, e_x = rel_l2(gg, gref), rel_l2(gy, gyr), rel_l2(g0, g0r)
+    print(f"LPD 72x56x24 gradient parity: params {e_w:.2e} (tol {grad_tol(gref, gp):.2e}), y {e_y:.2e} "
+          f"(tol {grad_tol(gyr, gyp):.2e}), x0 {e_x:.2e} (tol {grad_tol(g0r, g0p):.2e})")
+    assert e_w <= grad_tol(gref, gp) and e_x <= grad_tol(g0r, g0p) and e_y <= grad_tol(gyr, gyp)
 
 
 def test_lpd_width64_matches_oracle(O, M):

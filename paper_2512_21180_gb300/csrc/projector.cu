@@ -260,12 +260,47 @@ __global__ void __launch_bounds__(kThreads3, 4) k_backproject_v3(GeomDev g, cons
     const int part = blockIdx.z % nparts, zb = blockIdx.z / nparts;
     const int z0 = (zb % nzb) * kZ3, b = zb / nzb;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nu = NU > 0 ? NU : g.nu, nv = g.nv;
-    const int k_begin = (int)((long long)g.na * part / nparts), k_end = (int)((long long)g.na * (part + 1) / nparts);
+    const int k_begin = (int)((long long)g.na * part / nparts);
+    int k_end = (int)((long long)g.na * (part + 1) / nparts);
+    __shared__ int s_reach;
+    if (tid == 0) s_reach = 0;
     for (int e = tid; e < kVacc3; e += kThreads3) vacc[e] = 0.f;
     __syncthreads();
     const float Sz = g.Sz;
     const float rz0 = g.rz32[0], drz = g.f32[0].EV[2], inv_drz = 1.0f / drz;
     const float *PB = pw + (long long)b * g.na * nv * nu;
+    {
+        // Does any panel row reach the brick's support (the brick and one voxel around it)
+        // at an angle of this part? The source-to-panel parameter t of a point is affine in
+        // its (x, y), so over the support it lies between its values at the four corners;
+        // the rows that meet z in (zlo, zhi) at t lie between zlo / t and zhi / t, and
+        // those are monotone in t. Two rows of margin, as in the per-column test below; a
+        // non-finite value counts as reachable. Bricks no row reaches skip the angle loop
+        // and write zeros.
+        const float zlo = (float)(z0 - 1) - Sz, zhi = (float)(z0 + kZ3) - Sz;
+        const float cx[2] = {(float)(x0 - 1), (float)(x0 + kB3)}, cy[2] = {(float)(y0 - 1), (float)(y0 + kB3)};
+        bool any = false;
+        for (int k = k_begin + tid; k < k_end && !any; k += kThreads3) {
+            const Frame32 &F = g.f32[k];
+            const float den = F.EU[0] * F.D0S[1] - F.EU[1] * F.D0S[0];
+            float tmin = INFINITY, tmax = -INFINITY;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float t = __fdividef(F.EU[0] * (cy[c >> 1] - F.S[1]) - F.EU[1] * (cx[c & 1] - F.S[0]), den);
+                tmin = fminf(tmin, t);
+                tmax = fmaxf(tmax, t);
+            }
+            if (tmax <= 0.f) continue;  // behind the source
+            const float t1 = fmaxf(tmin, 1e-6f);
+            const float rlo = fminf(__fdividef(zlo, t1), __fdividef(zlo, tmax));
+            const float rhi = fmaxf(__fdividef(zhi, t1), __fdividef(zhi, tmax));
+            const float va = (rlo - rz0) * inv_drz, vb = (rhi - rz0) * inv_drz;
+            if (!(fmaxf(va, vb) + 2.f < 0.f || fminf(va, vb) - 2.f > (float)(nv - 1))) any = true;
+        }
+        if (any) s_reach = 1;
+    }
+    __syncthreads();
+    if (!s_reach) k_end = k_begin;
 
 #pragma unroll 1
     for (int a = 0; a < 2; ++a) {
